@@ -1,0 +1,215 @@
+"""Pins for the CPU oracle: facts fixed by the paper and by mathematics.
+
+Each ``pin_*`` takes a bound oracle library (the real one, or a copy with a
+planted mistake) and raises ``AssertionError`` if the oracle disagrees with:
+
+* the worked example of Section 3.1 (Figure 1: AAC, AGT, GTA) -- printed facts
+  plus the states and supply links worked by hand from Algorithms 1-2;
+* the Wu-Manber tables of Algorithm 4 worked by hand (Section 3.2 hash);
+* closed forms: a single run of one letter, de Bruijn texts, m = 1, n < m;
+* Python's ``re`` engine (overlapping lookahead search), a library routine
+  that enumerates occurrences independently of every route here.
+
+``tests/test_oracle_pins.py`` runs them on the oracle; ``tests/test_oracle_mutants.py``
+plants mistakes in a copy of the oracle and checks that some pin fails.
+"""
+from __future__ import annotations
+
+import json
+import os
+import re
+
+import numpy as np
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _pairs(occ):
+    i, r = oracle.unpack(occ)
+    return list(zip(i.tolist(), r.tolist()))
+
+
+def _all_routes(T, P, lib, B=None):
+    """(name, occ, counts) from every oracle route on the same input."""
+    P = oracle._as_patterns(P)
+    m = P.shape[1]
+    out = [("brute",) + oracle.brute(T, P, lib=lib),
+           ("dict1",) + oracle.dictionary(T, P, threads=1, lib=lib),
+           ("dict3",) + oracle.dictionary(T, P, threads=3, lib=lib),
+           ("ac",) + oracle.ac_search(T, P, lib=lib)]
+    for b in ([B] if B else sorted({1, min(2, m), min(3, m)})):
+        out.append((f"wm{b}",) + oracle.wm_search(T, P, b, min(2, m), lib=lib))
+    return out
+
+
+def _regex_matches(T: bytes, P):
+    """Occurrences enumerated by Python's regex engine (zero-width lookahead)."""
+    res = []
+    for r, p in enumerate(P):
+        for mo in re.finditer(b"(?=" + re.escape(bytes(p)) + b")", T):
+            res.append((mo.start(), r))
+    return sorted(res)
+
+
+def _check_against(expected_pairs, T, P, lib, B=None):
+    d = len(P)
+    exp_counts = np.zeros(d, dtype=np.int64)
+    for _, r in expected_pairs:
+        exp_counts[r] += 1
+    for name, occ, counts in _all_routes(T, P, lib, B):
+        got = _pairs(occ)
+        assert got == expected_pairs, f"{name}: occurrences differ ({len(got)} vs {len(expected_pairs)})"
+        assert np.array_equal(counts, exp_counts), f"{name}: per-pattern counts differ"
+
+
+# ---------------------------------------------------------------------------
+def pin_ac_worked_example(lib):
+    g = _golden("ac_worked_example.json")
+    ac = oracle.ACAutomaton(g["patterns"], lib=lib)
+    for q, c, v in g["printed_facts"]["goto"]:
+        assert ac.goto(q, c) == v, f"printed fact g({q},{c})={v}"
+    for q, v in g["printed_facts"]["supply"]:
+        assert ac.supply(q) == v, f"printed fact Supply({q})={v}"
+    h = g["derived_by_hand"]
+    assert ac.nstates == len(h["labels"])
+    for q, c, v in h["trie_edges"]:
+        assert ac.goto(q, c) == v, f"trie edge g({q},{c})={v}"
+    for q, label in h["labels"].items():
+        assert ac.depth(int(q)) == len(label)
+    for q, v in h["supply"].items():
+        assert ac.supply(int(q)) == v, f"Supply({q})={v}"
+    for q in range(ac.nstates):
+        assert ac.output(q) == h["output"].get(str(q), []), f"Output({q})"
+    # after Algorithm 2 the root loops on every other byte; deeper misses stay fail
+    assert ac.goto(0, "T") == 0 and ac.goto(0, "C") == 0 and ac.goto(0, "N") == 0
+    assert ac.goto(1, "T") == -1 and ac.goto(3, "A") == -1
+    occ, _ = ac.search(h["text"])
+    assert _pairs(occ) == [tuple(x) for x in h["matches_i_r"]]
+    _check_against([tuple(x) for x in h["matches_i_r"]], h["text"].encode(),
+                   [p.encode() for p in g["patterns"]], lib)
+
+
+def pin_wm_tables_example(lib):
+    g = _golden("wm_tables_example.json")
+    w = oracle.WMTables(g["patterns"], g["B"], g["Bp"], lib=lib)
+    assert w.tsize == g["table_size"]
+    for h in range(w.tsize):
+        want = g["shift"].get(str(h), g["shift_default"])
+        assert w.shift(h) == want, f"SHIFT[{h}] = {w.shift(h)}, hand value {want}"
+        assert w.hash_list(h) == g["hash_lists"].get(str(h), []), f"HASH[{h}]"
+    for r, v in enumerate(g["prefix"]):
+        assert w.prefix(r) == v, f"PREFIX[{r}]"
+    w3 = oracle.WMTables(["ACGT"], 3, 2, lib=lib)
+    assert w3.shift(g["three_char_hash"]["ACG"]) == 1  # block ACG ends one before the end
+    assert w3.shift(g["three_char_hash"]["ACG"] + 1) == 2  # never-seen value keeps m-B+1
+    occ, _ = w.search(g["text"])
+    assert _pairs(occ) == [tuple(x) for x in g["matches_i_r"]]
+    _check_against([tuple(x) for x in g["matches_i_r"]], g["text"].encode(),
+                   [p.encode() for p in g["patterns"]], lib)
+
+
+def pin_single_letter_run(lib):
+    # a^m occurs at every start of a^n: n - m + 1 times (two copies -> each r)
+    for n, m in [(1, 1), (5, 5), (17, 3), (64, 8), (40, 12)]:
+        T = b"A" * n
+        P = [b"A" * m, b"C" * m, b"A" * m]
+        exp = sorted([(i, 0) for i in range(n - m + 1)] + [(i, 2) for i in range(n - m + 1)])
+        _check_against(exp, T, P, lib)
+
+
+def _de_bruijn(k: int, m: int) -> list[int]:
+    """Textbook de Bruijn sequence B(k, m) by concatenating Lyndon words (FKM)."""
+    a = [0] * (k * m)
+    seq: list[int] = []
+
+    def db(t, p):
+        if t > m:
+            if m % p == 0:
+                seq.extend(a[1:p + 1])
+        else:
+            a[t] = a[t - p]
+            db(t + 1, p)
+            for j in range(a[t - p] + 1, k):
+                a[t] = j
+                db(t + 1, t)
+
+    db(1, 1)
+    return seq
+
+
+def pin_de_bruijn(lib):
+    # a linearised de Bruijn text holds every m-mer exactly once
+    for m in (2, 3, 4):
+        s = _de_bruijn(4, m)
+        s = s + s[: m - 1]
+        T = bytes(b"ACGT"[c] for c in s)
+        assert len(T) == 4 ** m + m - 1
+        P = [bytes(b"ACGT"[(x >> (2 * (m - 1 - j))) & 3] for j in range(m)) for x in range(4 ** m)]
+        for name, occ, counts in _all_routes(T, P, lib):
+            assert np.all(counts == 1), f"{name}: every m-mer exactly once"
+            i, r = oracle.unpack(occ)
+            assert sorted(i.tolist()) == list(range(4 ** m)), f"{name}: one m-mer per start"
+            for ii, rr in zip(i.tolist(), r.tolist()):
+                assert T[ii:ii + m] == P[rr], f"{name}: wrong pattern at {ii}"
+
+
+def pin_degenerate_sizes(lib):
+    _check_against([], b"ACG", [b"ACGT"], lib)          # n < m
+    _check_against([(0, 0)], b"ACGT", [b"ACGT"], lib)   # n == m
+    _check_against([], b"ACGTACGT", [b"TTTT"], lib)     # absent pattern
+    T = b"GATTACA"                                      # m = 1
+    exp = sorted([(i, 0) for i, c in enumerate(T) if c == ord("A")] +
+                 [(i, 1) for i, c in enumerate(T) if c == ord("T")])
+    _check_against(exp, T, [b"A", b"T"], lib)
+
+
+def pin_regex_random(lib, cases: int = 60, seed: int = 7):
+    rng = np.random.default_rng(seed)
+    for case in range(cases):
+        k = int(rng.integers(1, 5))
+        alphabet = b"ACGTN\n"[: k + 1]
+        n = int(rng.integers(0, 400))
+        m = int(rng.integers(1, 9))
+        d = int(rng.integers(1, 12))
+        T = bytes(alphabet[j] for j in rng.integers(0, len(alphabet), n))
+        P = []
+        for _ in range(d):
+            if n >= m and rng.random() < 0.5:
+                s = int(rng.integers(0, n - m + 1))
+                P.append(T[s:s + m])
+            else:
+                P.append(bytes(alphabet[j] for j in rng.integers(0, len(alphabet), m)))
+        if rng.random() < 0.3:
+            P.append(P[0])  # duplicate pattern
+        exp = _regex_matches(T, P)
+        _check_against(exp, T, P, lib)
+
+
+def pin_periodic(lib):
+    T = b"AC" * 50
+    _check_against([(i, 0) for i in range(0, 97, 2)], T, [b"ACAC"], lib)
+    T = b"AAC" * 20
+    P = [b"AACA", b"ACAA", b"CAAC", b"AAAA"]
+    _check_against(_regex_matches(T, P), T, P, lib)
+
+
+ALL_PINS = [pin_ac_worked_example, pin_wm_tables_example, pin_single_letter_run,
+            pin_de_bruijn, pin_degenerate_sizes, pin_regex_random, pin_periodic]
+
+
+def run_all(lib) -> list[str]:
+    """Names of the pins that fail for ``lib`` (empty list: all hold)."""
+    failed = []
+    for pin in ALL_PINS:
+        try:
+            pin(lib)
+        except AssertionError as e:
+            failed.append(f"{pin.__name__}: {e}")
+    return failed

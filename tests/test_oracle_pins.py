@@ -1,0 +1,44 @@
+"""The oracle against facts fixed by the paper and by mathematics (no GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from tests import oracle_pins
+
+
+@pytest.mark.parametrize("pin", oracle_pins.ALL_PINS, ids=lambda p: p.__name__)
+def test_pin(pin):
+    pin(oracle._load())
+
+
+def test_routes_agree_on_small_uniform_workload():
+    """1 MiB uniform text, d=100, m=8 (50 sampled, 50 random): four routes agree,
+    and the invariants that hold at any size hold."""
+    from paper_1407_2889_gb300 import synth
+    T, P = synth.small_uniform_case()
+    T = T[: 1 << 17]  # brute force over 128 KiB keeps this test short
+    P = synth.mixed_patterns(T, 100, 8, 0)
+    occ_b, cnt_b = oracle.brute(T, P)
+    occ_d, cnt_d = oracle.dictionary(T, P, threads=4)
+    occ_a, cnt_a = oracle.ac_search(T, P)
+    occ_w, cnt_w = oracle.wm_search(T, P, 2)
+    for occ, cnt in [(occ_d, cnt_d), (occ_a, cnt_a), (occ_w, cnt_w)]:
+        assert np.array_equal(occ, occ_b)
+        assert np.array_equal(cnt, cnt_b)
+    assert cnt_b.sum() == occ_b.size
+    assert np.all(np.diff(occ_b.astype(np.uint64)) > 0)  # strictly sorted by (i, r)
+    i, r = oracle.unpack(occ_b)
+    win = T[i[:, None] + np.arange(8)[None, :]]
+    assert np.array_equal(win, P[r])  # every reported pair is an occurrence
+    assert np.all(cnt_b[:50] >= 1)  # each pattern copied from the text occurs
+
+
+def test_duplicate_patterns_have_equal_counts():
+    from paper_1407_2889_gb300 import synth
+    T = synth.uniform_dna(1 << 14, 3)
+    P = synth.mixed_patterns(T, 40, 5, 3)
+    P = np.concatenate([P, P[:10]])
+    occ, cnt = oracle.dictionary(T, P, threads=2)
+    assert np.array_equal(cnt[:10], cnt[40:50])
+    occ_a, cnt_a = oracle.ac_search(T, P)
+    assert np.array_equal(occ_a, occ) and np.array_equal(cnt_a, cnt)
