@@ -1,0 +1,385 @@
+"""Benchmark: text GB/s of the multi-pattern scan on one GB300.
+
+Workload (default): the EST-shaped 1 GiB text (seed 1) scanned by the
+Aho-Corasick DFA kernel for the d=8000, m=8 pattern set (4000 copied from the
+text, 4000 random) -- the pattern-set size of the paper's optimisation study
+(Section 6, Figure 4) -- in list mode: per-pattern counts plus the sorted
+(i, r) list. One step = one pm_scan_device call over the whole text, with the
+text already resident in HBM (1 GiB > L2, so no flush is needed). Secondary
+measurements in the same run (outside the timed steps): WM with B=3, AC
+counts-only, and the other (d, m) sets.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank scans its own copy of the text (replicas,
+weak scaling); the reported value is the sum over ranks divided by the
+slowest rank's time. ``--impl reference`` times the CPU oracle (dictionary
+route, all host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "text GB/s scanned on 1 GB300 (AC & WM), batched vs plain; % of HBM roofline"
+KERNEL_SOURCES = ["paper_1407_2889_gb300/csrc/scan_ac.cu", "paper_1407_2889_gb300/csrc/scan_common.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel_name: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source and the same workload; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    e = rec.get(kernel_name)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(T: np.ndarray, P: np.ndarray, target_s: float = 12.0):
+    """Time the oracle's dictionary route (all host cores) on a prefix sized
+    for about target_s seconds of work. Returns (GB/s, cores, sample text)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    probe = min(T.size, 4 << 20)
+    t0 = time.perf_counter()
+    oracle.dictionary(T[:probe], P, threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    size = int(min(T.size, max(probe, probe * target_s / dt)))
+    t0 = time.perf_counter()
+    occ, _ = oracle.dictionary(T[:size], P, threads=cores)
+    dt = time.perf_counter() - t0
+    return size / dt / 1e9, cores, f"first {size} bytes of the text ({size / 2**20:.0f} MiB), d={P.shape[0]}, m={P.shape[1]}, {occ.size} occurrences, {dt:.1f} s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--d", type=int, default=8000)
+    ap.add_argument("--m", type=int, default=8)
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--text-mib", type=int, default=0,
+                    help="scan only this many MiB of the text (profiling captures); 0 = all 1 GiB")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, rank):
+    """The oracle as it stands, on the host cores, as the reference arm."""
+    if rank != 0:
+        return
+    from paper_1407_2889_gb300 import synth
+    import oracle
+    T = synth.est_text(synth.EST_N, 1)
+    _, P = synth.est_case(args.d, args.m, text=T)
+    cores = os.cpu_count() or 1
+    sample = 8 << 20
+    for _ in range(max(args.warmup, 0) and 1):
+        oracle.dictionary(T[:sample], P, threads=cores)
+    times = []
+    for k in range(args.steps if args.steps <= 20 else 20):
+        off = (k * 7919 * 4096) % (T.size - sample)
+        t0 = time.perf_counter()
+        oracle.dictionary(T[off:off + sample], P, threads=cores)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = sample * len(times) / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"EST-shaped text, AC list mode, d={args.d}, m={args.m}; oracle dictionary route on {sample >> 20} MiB samples",
+                   "text_bytes": sample, "d": args.d, "m": args.m},
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{len(times)} samples of {sample >> 20} MiB of the 1 GiB EST text"},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    from paper_1407_2889_gb300 import pmscan as pm
+    from paper_1407_2889_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    T = synth.est_text(synth.EST_N, 1)
+    _, P = synth.est_case(args.d, args.m, text=T)
+    if args.text_mib:
+        T = T[: args.text_mib << 20]
+    n = T.size
+    d = P.shape[0]
+    s = pm.PatternSet.ac(P)
+    info = s.info()
+    stream = torch.cuda.Stream()
+    d_text = torch.from_numpy(T).cuda()
+    ws = torch.zeros(s.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    counts = torch.zeros(d, dtype=torch.int64, device="cuda")
+    nocc = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def launch(h, occ_buf, cap, flags=0, wsb=ws):
+        pm.pm_scan_device(h, d_text, n, flags, counts, occ_buf, cap, nocc, wsb, wsb.numel(), stream)
+
+    # size the occurrence buffer from a first run
+    with torch.cuda.stream(stream):
+        probe = torch.zeros(1, dtype=torch.int64, device="cuda")
+        launch(s.h, probe, 0)
+        stream.synchronize()
+        total = int(nocc.item())
+        occ = torch.empty(max(total, 1), dtype=torch.int64, device="cuda")
+        for _ in range(max(args.warmup, 3)):
+            launch(s.h, occ, occ.numel())
+        stream.synchronize()
+        assert pm.pm_scan_status(ws, stream) == pm.PM_OK
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t_all0.record(stream)
+        for k in range(args.steps):
+            starts[k].record(stream)
+            launch(s.h, occ, occ.numel())
+            ends[k].record(stream)
+        t_all1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    elapsed_ms = t_all0.elapsed_time(t_all1)
+    per_launch = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    if dist:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    assert pm.pm_scan_status(ws, stream) == pm.PM_OK
+    assert int(nocc.item()) == total
+    n_occ = total
+    value = world * n * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    peak, peak_kind = measured_peaks()
+    avg_launch_s = statistics.mean(per_launch) / 1e3
+    alg_bytes = n + 8 * n_occ + 8 * d
+    achieved = alg_bytes / avg_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": recorded_traffic("ac_scan_kernel"),
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel": "ac_scan_kernel<uint16_t,6,1,dna,smem>"}
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, torch, synth)
+
+    # end to end: pm_scan from pinned host text, results read back to the host
+    e2e = None
+    if rank == 0:
+        pinned = torch.from_numpy(T).pin_memory()
+        s.scan(pinned.numpy())  # sizes the library's cached buffers
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            o, c = pm.pm_scan(s.h, pinned.numpy(), pm.PM_HOST_TEXT, stream)
+        dt = (time.perf_counter() - t0) / reps
+        assert o.size == n_occ
+        e2e = {"value": n / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": n,
+               "d2h_bytes_per_step": 8 * n_occ + 8 * d + 8, "api": "pm_scan (host text)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, cores, sample = cpu_oracle_rate(T, P)
+        cpu = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"EST-shaped 1 GiB text (seed 1), Aho-Corasick DFA, list mode, d={d}, m={args.m} (half copied from the text, half random)",
+                       "text_bytes": n, "d": d, "m": args.m, "algo": "AC", "mode": "list",
+                       "n_occ": n_occ, "l2": "inputs larger than L2 (1 GiB text), no flush",
+                       "parallelism": f"replicas x{world}",
+                       "table": {k: info[k] for k in ("n_rows", "entry_bytes", "placement", "smem_rows", "table_bytes")}},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps, "clocks": clk, "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, torch, synth):
+    """Secondary measurements (not part of the timed steps)."""
+    out = {}
+    n = T.size
+
+    def timeit(h, occ_buf, cap, flags, reps=5, wsb=ws):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            launch(h, occ_buf, cap, flags, wsb)
+            ev0.record(stream)
+            for _ in range(reps):
+                launch(h, occ_buf, cap, flags, wsb)
+            ev1.record(stream)
+        stream.synchronize()
+        return ev0.elapsed_time(ev1) / reps / 1e3
+
+    t = timeit(s.h, occ, 0, pm.PM_COUNTS_ONLY)
+    out["ac_counts_only_gbs"] = n / t / 1e9
+    try:
+        w = pm.PatternSet.wm(P, 3)
+        t = timeit(w.h, occ, occ.numel(), 0, reps=2)
+        out["wm_b3_list_gbs"] = n / t / 1e9
+        w.close()
+    except Exception as e:  # report, never hide
+        out["wm_b3_list_error"] = str(e)
+    sweep = {}
+    for dd in synth.EST_D:
+        for mm in synth.EST_M:
+            _, Pq = synth.est_case(dd, mm, text=T)
+            q = pm.PatternSet.ac(Pq)
+            cnt_q = torch.zeros(dd, dtype=torch.int64, device="cuda")
+            with torch.cuda.stream(stream):
+                pm.pm_scan_device(q.h, d_text, n, pm.PM_COUNTS_ONLY, cnt_q, None, 0, nocc, ws, ws.numel(), stream)
+            stream.synchronize()
+            tot = int(nocc.item())
+            buf = occ if tot <= occ.numel() else torch.empty(tot, dtype=torch.int64, device="cuda")
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                pm.pm_scan_device(q.h, d_text, n, 0, cnt_q, buf, buf.numel(), nocc, ws, ws.numel(), stream)
+                ev0.record(stream)
+                for _ in range(3):
+                    pm.pm_scan_device(q.h, d_text, n, 0, cnt_q, buf, buf.numel(), nocc, ws, ws.numel(), stream)
+                ev1.record(stream)
+            stream.synchronize()
+            dt = ev0.elapsed_time(ev1) / 3 / 1e3
+            inf = q.info()
+            sweep[f"d{dd}_m{mm}"] = {"gbs": n / dt / 1e9, "n_occ": tot,
+                                      "alg_frac": (n + 8 * tot + 8 * dd) / dt / 1e9 / measured_peaks()[0],
+                                      "placement": inf["placement"], "rows": inf["n_rows"],
+                                      "entry_bytes": inf["entry_bytes"]}
+            q.close()
+            del buf
+    out["ac_list_sweep"] = sweep
+    return out
+
+
+if __name__ == "__main__":
+    main()

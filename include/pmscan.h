@@ -1,0 +1,196 @@
+/*
+ * pmscan.h -- C ABI of libpmscan: multiple pattern matching on one GB300.
+ *
+ * The operation (Kouzinopoulos et al., "A Hybrid Parallel Implementation of
+ * the Aho-Corasick and Wu-Manber Algorithms Using NVIDIA CUDA and MPI",
+ * Section 1, Definition): given a text T = t_0..t_{n-1} and a set of d
+ * patterns p^0..p^{d-1}, all of length m, find every pair (i, r) with
+ * 0 <= i <= n-m and t_{i+j} = p^r_j for every 0 <= j < m.
+ *
+ * Two methods compute that set, both from Section 3 of the paper:
+ *   - Aho-Corasick (Section 3.1, Algorithms 1-3), compiled here to a full
+ *     DFA: goto and supply functions merged into one transition table with a
+ *     next state for every state and every character class (the "array of
+ *     size |Sigma|" representation the paper names in Section 3.1);
+ *   - Wu-Manber (Section 3.2, Algorithms 4-5): SHIFT / HASH / PREFIX tables
+ *     over blocks of B characters, candidates verified against the text.
+ * The data-parallel split of the text into chunks that overlap by m-1
+ * characters follows Section 4.2.1 (Algorithms 6-9).
+ *
+ * Conventions shared by every call:
+ *   - P is d*m contiguous bytes, row r = p^r. Any byte values are allowed.
+ *     P is copied during compilation; the caller keeps ownership.
+ *   - Pattern ids r are 0-based in input order; positions i are 0-based
+ *     start positions. Duplicate patterns are each reported under their own
+ *     id (ascending r at the same i).
+ *   - Occurrences are uint64 keys ((uint64_t)i << 32) | r, sorted ascending,
+ *     i.e. by position, then by pattern id.
+ *   - counts[r] is the number of occurrences of pattern r (int64).
+ *   - n must be < 2^32 and d < 2^24; otherwise PM_ETOOBIG.
+ *   - n < m is not an error: the result is empty.
+ *   - Every call returns PM_OK (0) or one of the error codes below; no C++
+ *     exception crosses this boundary. On error, output pointers are left
+ *     untouched and nothing is leaked.
+ *   - Calls that take a stream (cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) are asynchronous unless documented otherwise.
+ */
+#ifndef PMSCAN_H
+#define PMSCAN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes -------------------------------------------------------- */
+#define PM_OK 0
+#define PM_EINVAL 1    /* bad argument (NULL pointer, d < 1, m < 1, bad B ...) */
+#define PM_ENOMEM 2    /* host or device allocation failed */
+#define PM_ECUDA 3     /* a CUDA runtime call failed (see pm_last_cuda_error) */
+#define PM_ETOOBIG 4   /* n >= 2^32, d >= 2^24, m > 255, or a table too large */
+#define PM_ETIMEOUT 5  /* a bounded device wait gave up (status word set) */
+#define PM_ECAPACITY 6 /* occurrence buffer too small; *d_n_occ holds the need */
+#define PM_ENODEV 7    /* no usable CUDA device (the library never computes on the CPU) */
+
+/* ---- scan flags ---------------------------------------------------------- */
+#define PM_HOST_TEXT 0u     /* T is a host pointer (copied to the device) */
+#define PM_DEVICE_TEXT 1u   /* T is a device pointer */
+#define PM_COUNTS_ONLY 2u   /* per-pattern counts and the total only; no list */
+
+/* ---- table placement (Aho-Corasick transition table) ------------------- */
+#define PM_PLACE_AUTO 0    /* shared memory if it fits, else hybrid */
+#define PM_PLACE_SMEM 1    /* whole table in shared memory, else PM_ETOOBIG */
+#define PM_PLACE_HYBRID 2  /* breadth-first prefix of rows in shared memory, rest via L2 */
+#define PM_PLACE_GLOBAL 3  /* every row read through L1/L2 */
+
+#define PM_ALGO_AC 1
+#define PM_ALGO_WM 2
+
+/* Tuning knobs; a zero field means "pick automatically". */
+typedef struct pm_params {
+    int32_t placement;        /* PM_PLACE_* */
+    int32_t smem_table_bytes; /* cap on the shared-memory part of the table */
+    int32_t warps_per_cta;    /* 1..32 */
+    int32_t ctas_per_sm;      /* persistent CTAs per SM */
+    int32_t wm_prefix_len;    /* Wu-Manber B' (default 2, clamped to m) */
+    int32_t host_only;        /* 1: build host tables only (no device upload);
+                                 such a set can only be inspected, not scanned */
+} pm_params;
+
+typedef struct pm_set pm_set; /* compiled pattern set; owns its device tables */
+
+typedef struct pm_set_info {
+    int32_t algo;             /* PM_ALGO_AC or PM_ALGO_WM */
+    int32_t m;
+    int64_t d;
+    int64_t n_distinct;       /* distinct patterns */
+    /* Aho-Corasick */
+    int64_t n_states;         /* trie states, including terminals */
+    int64_t n_rows;           /* DFA rows kept (terminal rows elided) + reset row */
+    int32_t n_classes;        /* character classes (alphabet size of P) */
+    int32_t row_width;        /* table columns per row */
+    int32_t entry_bytes;      /* 2 or 4 */
+    int32_t dna_mode;         /* 1: ACGT-like alphabet decoded arithmetically */
+    int32_t placement;        /* resolved PM_PLACE_* */
+    int64_t smem_rows;        /* rows resident in shared memory */
+    int64_t table_bytes;      /* bytes of the transition table */
+    /* Wu-Manber */
+    int32_t B, Bp;            /* block size B and prefix length B' */
+    int64_t shift_entries;    /* 2^(5B) */
+    int64_t n_zero_shift;     /* SHIFT entries equal to 0 */
+    /* both */
+    int64_t device_bytes;     /* device memory owned by the set */
+} pm_set_info;
+
+typedef struct pm_result {    /* library-owned; release with pm_result_free */
+    int64_t d;
+    int64_t n_occ;
+    int64_t *counts;          /* host array of d counts */
+    uint64_t *occ;            /* host array of n_occ keys (NULL if counts only) */
+} pm_result;
+
+/*
+ * Compile an Aho-Corasick DFA (Section 3.1, Algorithms 1-2, merged into one
+ * transition table). Builds the trie in insertion order, supply links in
+ * breadth-first order, the full transition function, renumbers states
+ * breadth-first, elides the rows of depth-m states and uploads the tables.
+ * opt may be NULL. On success *out owns device memory until pm_set_free.
+ */
+int pm_ac_compile(const uint8_t *P, int64_t d, int32_t m,
+                  const pm_params *opt, pm_set **out);
+
+/*
+ * Compile Wu-Manber tables (Section 3.2, Algorithm 4) for block size B,
+ * 1 <= B <= min(m, 4). h1 and h2 shift by 5 bits and add (byte & 31), giving
+ * 2^(5B) SHIFT entries; results do not depend on the hash (SHIFT is a
+ * minimum over colliding blocks and every candidate is verified in full).
+ */
+int pm_wm_compile(const uint8_t *P, int64_t d, int32_t m, int32_t B,
+                  const pm_params *opt, pm_set **out);
+
+void pm_set_free(pm_set *s);
+int pm_set_get_info(const pm_set *s, pm_set_info *info);
+
+/*
+ * Scan T (n bytes) for every occurrence of the set (Section 1 definition).
+ * flags: PM_HOST_TEXT or PM_DEVICE_TEXT, optionally | PM_COUNTS_ONLY.
+ * Synchronous: returns when *out (host arrays, library-owned) is complete.
+ * Device buffers are cached inside the set between calls, so a set must not
+ * be scanned from two host threads at once.
+ */
+int pm_scan(const pm_set *s, const uint8_t *T, int64_t n, uint32_t flags,
+            void *stream, pm_result **out);
+
+void pm_result_free(pm_result *r);
+
+/*
+ * Device-level scan with caller-owned device buffers (e.g. torch tensors),
+ * enqueued on `stream`; nothing is allocated and nothing synchronises.
+ *   d_text       device text, n bytes (any alignment; 16-byte aligned is fastest)
+ *   d_counts     device int64[d], overwritten
+ *   d_occ        device uint64[occ_capacity] (may be NULL with PM_COUNTS_ONLY)
+ *   d_n_occ      device int64[1], receives the total number of occurrences
+ *   d_workspace  device scratch of at least pm_scan_workspace_bytes(s, n, flags)
+ * If the total exceeds occ_capacity only the first occ_capacity keys are
+ * written; the call still succeeds and *d_n_occ tells the caller how much to
+ * allocate for a rerun. Device-side failures (a bounded wait that gave up)
+ * are reported in the workspace status word, read by pm_scan_status.
+ */
+int64_t pm_scan_workspace_bytes(const pm_set *s, int64_t n, uint32_t flags);
+
+int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags,
+                   int64_t *d_counts, uint64_t *d_occ, int64_t occ_capacity,
+                   int64_t *d_n_occ, void *d_workspace, int64_t workspace_bytes,
+                   void *stream);
+
+/* Synchronise `stream` and read the device status word of the last
+ * pm_scan_device on this workspace: PM_OK or PM_ETIMEOUT. */
+int pm_scan_status(const void *d_workspace, void *stream);
+
+/*
+ * Scan k independent (set, text) instances in one persistent launch
+ * (a work queue of (instance, tile) items), synchronously. texts are host
+ * pointers unless flags has PM_DEVICE_TEXT. outs[j] receives instance j's
+ * result (library-owned). Results equal k separate pm_scan calls.
+ */
+int pm_scan_batch(const pm_set *const *sets, const uint8_t *const *texts,
+                  const int64_t *ns, int32_t k, uint32_t flags, void *stream,
+                  pm_result **outs);
+
+/*
+ * Table self-check on the host, no GPU needed: walks the compiled AC table
+ * (or applies the compiled WM tables) exactly as the kernels do, one thread,
+ * on the host. It exists to test the compiler; pm_scan never calls it.
+ */
+int pm_selfcheck_host_walk(const pm_set *s, const uint8_t *T, int64_t n, pm_result **out);
+
+const char *pm_strerror(int code);
+int pm_last_cuda_error(void);  /* cudaError_t of the last PM_ECUDA, per thread */
+const char *pm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMSCAN_H */

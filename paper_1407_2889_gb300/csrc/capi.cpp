@@ -1,0 +1,449 @@
+// capi.cpp -- the C ABI of libpmscan (declared in include/pmscan.h): set
+// compilation and upload, device-level and host-convenience scans, results,
+// errors. No C++ exception crosses this boundary.
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "pm_internal.h"
+
+namespace pm {
+
+static thread_local int g_last_cuda = 0;
+void set_cuda_error(int e) { g_last_cuda = e; }
+
+int64_t warp_tiles(int64_t n) { return n <= 0 ? 0 : (n + kWarpTile - 1) / kWarpTile; }
+
+int64_t workspace_bytes_for(int64_t n, bool list)
+{
+    return kWsHeader + (list ? warp_tiles(n) * int64_t(8) : 0);
+}
+
+int device_props(DeviceProps &p)
+{
+    static std::mutex mu;
+    static DeviceProps cache[64];
+    static bool have[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        return PM_ENODEV;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && have[dev]) {
+        p = cache[dev];
+        return PM_OK;
+    }
+    DeviceProps q;
+    e = cudaDeviceGetAttribute(&q.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&q.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&q.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&q.l2_bytes, cudaDevAttrL2CacheSize, dev);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        return PM_ENODEV;
+    }
+    if (dev >= 0 && dev < 64) {
+        cache[dev] = q;
+        have[dev] = true;
+    }
+    p = q;
+    return PM_OK;
+}
+
+namespace {
+
+// Copy `bytes` to a fresh device allocation padded to a multiple of 16.
+int upload(void **dst, const void *src, size_t bytes, int64_t &total)
+{
+    size_t padded = (bytes + 15) & ~size_t(15);
+    if (padded == 0) padded = 16;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, padded);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
+    }
+    e = cudaMemset(p, 0, padded);
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        cudaFree(p);
+        return PM_ECUDA;
+    }
+    *dst = p;
+    total += int64_t(padded);
+    return PM_OK;
+}
+
+void free_dev(void *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void release_device(pm_set *s)
+{
+    void *ptrs[] = {s->dac.table, s->dac.mid, s->dac.grp_off, s->dac.grp_ids, s->dac.cls,
+                    s->dwm.shift, s->dwm.hoff, s->dwm.hids, s->dwm.hpfx, s->dwm.pats,
+                    s->c_text, s->c_ws, s->c_out, s->c_counts};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    s->dac = DevAc();
+    s->dwm = DevWm();
+    s->c_text = s->c_ws = s->c_out = s->c_counts = nullptr;
+    s->c_text_cap = s->c_ws_cap = s->c_out_cap = 0;
+}
+
+int upload_ac(pm_set *s)
+{
+    const AcTables &t = s->ac;
+    DevAc &d = s->dac;
+    int64_t &tot = s->device_bytes;
+    const int eb = t.dna ? t.entry_bytes : 4;
+    int rc;
+    if (eb == 2) {
+        std::vector<uint16_t> t16(t.table.size());
+        for (size_t i = 0; i < t.table.size(); ++i) t16[i] = uint16_t(t.table[i]);
+        rc = upload(&d.table, t16.data(), t16.size() * 2, tot);
+    } else {
+        rc = upload(&d.table, t.table.data(), t.table.size() * 4, tot);
+    }
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.mid), t.mid.data(), t.mid.size() * 4, tot);
+    if (!rc)
+        rc = upload(reinterpret_cast<void **>(&d.grp_off), t.grp_off.data(), t.grp_off.size() * 4, tot);
+    if (!rc)
+        rc = upload(reinterpret_cast<void **>(&d.grp_ids), t.grp_ids.data(), t.grp_ids.size() * 4, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.cls), t.cls, 256, tot);
+    return rc;
+}
+
+int upload_wm(pm_set *s)
+{
+    const WmTables &t = s->wm;
+    DevWm &d = s->dwm;
+    int64_t &tot = s->device_bytes;
+    int rc = upload(reinterpret_cast<void **>(&d.shift), t.shift.data(), t.shift.size(), tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.hoff), t.hoff.data(), t.hoff.size() * 4, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.hids), t.hids.data(), t.hids.size() * 4, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.hpfx), t.hpfx.data(), t.hpfx.size() * 2, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.pats), t.pats.data(), t.pats.size(), tot);
+    return rc;
+}
+
+int finish_compile(pm_set *s, pm_set **out)
+{
+    if (s->host_only) {
+        *out = s;
+        return PM_OK;
+    }
+    DeviceProps dp;
+    int rc = device_props(dp);
+    if (!rc) rc = s->algo == PM_ALGO_AC ? ac_plan(s->ac, s->params, dp, s->dac)
+                                        : wm_plan(s->wm, s->params, dp, s->dwm);
+    if (!rc) rc = s->algo == PM_ALGO_AC ? upload_ac(s) : upload_wm(s);
+    if (rc) {
+        release_device(s);
+        delete s;
+        return rc;
+    }
+    *out = s;
+    return PM_OK;
+}
+
+// grow a cached device buffer to at least `bytes`
+int ensure(void *&p, int64_t &cap, int64_t bytes)
+{
+    if (p && cap >= bytes) return PM_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    int64_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&p, size_t(want));
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        p = nullptr;
+        return e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
+    }
+    cap = want;
+    return PM_OK;
+}
+
+pm_result *new_result(int64_t d, int64_t n_occ, bool list)
+{
+    pm_result *r = static_cast<pm_result *>(std::calloc(1, sizeof(pm_result)));
+    if (!r) return nullptr;
+    r->d = d;
+    r->n_occ = n_occ;
+    r->counts = static_cast<int64_t *>(std::calloc(size_t(d > 0 ? d : 1), sizeof(int64_t)));
+    if (list) r->occ = static_cast<uint64_t *>(std::malloc(size_t(n_occ > 0 ? n_occ : 1) * 8));
+    if (!r->counts || (list && !r->occ)) {
+        std::free(r->counts);
+        std::free(r->occ);
+        std::free(r);
+        return nullptr;
+    }
+    return r;
+}
+
+int64_t set_d(const pm_set *s) { return s->algo == PM_ALGO_AC ? s->ac.d : s->wm.d; }
+
+}  // namespace
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+const char *pm_version(void) { return "pmscan 1.0 (sm_103a)"; }
+
+const char *pm_strerror(int code)
+{
+    switch (code) {
+    case PM_OK: return "ok";
+    case PM_EINVAL: return "invalid argument";
+    case PM_ENOMEM: return "out of memory";
+    case PM_ECUDA: return "CUDA runtime error";
+    case PM_ETOOBIG: return "input or table too large";
+    case PM_ETIMEOUT: return "a bounded device wait gave up";
+    case PM_ECAPACITY: return "occurrence buffer too small";
+    case PM_ENODEV: return "no usable CUDA device";
+    default: return "unknown error";
+    }
+}
+
+int pm_last_cuda_error(void) { return g_last_cuda; }
+
+int pm_ac_compile(const uint8_t *P, int64_t d, int32_t m, const pm_params *opt, pm_set **out)
+{
+    if (!out || !P || d < 1 || m < 1) return PM_EINVAL;
+    pm_set *s = new (std::nothrow) pm_set();
+    if (!s) return PM_ENOMEM;
+    s->algo = PM_ALGO_AC;
+    if (opt) s->params = *opt;
+    s->host_only = s->params.host_only != 0;
+    int rc = build_ac(P, d, m, s->ac);
+    if (rc) {
+        delete s;
+        return rc;
+    }
+    return finish_compile(s, out);
+}
+
+int pm_wm_compile(const uint8_t *P, int64_t d, int32_t m, int32_t B, const pm_params *opt,
+                  pm_set **out)
+{
+    if (!out || !P || d < 1 || m < 1 || B < 1 || B > m) return PM_EINVAL;
+    pm_set *s = new (std::nothrow) pm_set();
+    if (!s) return PM_ENOMEM;
+    s->algo = PM_ALGO_WM;
+    if (opt) s->params = *opt;
+    s->host_only = s->params.host_only != 0;
+    int bp = s->params.wm_prefix_len > 0 ? s->params.wm_prefix_len : 2;
+    if (bp > m) bp = m;
+    int rc = build_wm(P, d, m, B, bp, s->wm);
+    if (rc) {
+        delete s;
+        return rc;
+    }
+    return finish_compile(s, out);
+}
+
+void pm_set_free(pm_set *s)
+{
+    if (!s) return;
+    release_device(s);
+    delete s;
+}
+
+int pm_set_get_info(const pm_set *s, pm_set_info *info)
+{
+    if (!s || !info) return PM_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->algo = s->algo;
+    info->device_bytes = s->device_bytes;
+    if (s->algo == PM_ALGO_AC) {
+        const AcTables &t = s->ac;
+        info->m = t.m;
+        info->d = t.d;
+        info->n_distinct = t.n_distinct;
+        info->n_states = t.n_states;
+        info->n_rows = t.n_rows;
+        info->n_classes = t.n_classes;
+        info->row_width = 1 << t.lw;
+        info->entry_bytes = t.dna ? t.entry_bytes : 4;
+        info->dna_mode = t.dna ? 1 : 0;
+        info->placement = s->dac.placement;
+        info->smem_rows = s->dac.smem_entries >> t.lw;
+        info->table_bytes = (t.n_rows << t.lw) * info->entry_bytes;
+    } else {
+        const WmTables &t = s->wm;
+        info->m = t.m;
+        info->d = t.d;
+        info->B = t.B;
+        info->Bp = t.Bp;
+        info->shift_entries = int64_t(t.shift.size());
+        info->n_zero_shift = t.n_zero_shift;
+    }
+    return PM_OK;
+}
+
+int64_t pm_scan_workspace_bytes(const pm_set *s, int64_t n, uint32_t flags)
+{
+    if (!s || n < 0) return -1;
+    return workspace_bytes_for(n, !(flags & PM_COUNTS_ONLY));
+}
+
+int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags,
+                   int64_t *d_counts, uint64_t *d_occ, int64_t occ_capacity, int64_t *d_n_occ,
+                   void *d_workspace, int64_t workspace_bytes, void *stream)
+{
+    if (!s || n < 0 || !d_counts || !d_n_occ || !d_workspace) return PM_EINVAL;
+    if (s->host_only) return PM_EINVAL;
+    if (n > 0 && !d_text) return PM_EINVAL;
+    if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
+    const bool list = !(flags & PM_COUNTS_ONLY);
+    if (list && occ_capacity > 0 && !d_occ) return PM_EINVAL;
+    if (occ_capacity < 0) return PM_EINVAL;
+    if (workspace_bytes < workspace_bytes_for(n, list)) return PM_EINVAL;
+    if (s->algo == PM_ALGO_AC)
+        return ac_launch(s->ac, s->dac, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
+                         d_workspace, stream);
+    return wm_launch(s->wm, s->dwm, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
+                     d_workspace, stream);
+}
+
+int pm_scan_status(const void *d_workspace, void *stream)
+{
+    if (!d_workspace) return PM_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, d_workspace, sizeof(status), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        return PM_ECUDA;
+    }
+    return status ? PM_ETIMEOUT : PM_OK;
+}
+
+int pm_scan(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flags, void *stream,
+            pm_result **out)
+{
+    if (!cs || !out || n < 0 || (n > 0 && !T)) return PM_EINVAL;
+    if (cs->host_only) return PM_EINVAL;
+    if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
+    pm_set *s = const_cast<pm_set *>(cs);  // device caches only
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool list = !(flags & PM_COUNTS_ONLY);
+    const int64_t d = set_d(s);
+    int rc;
+    const uint8_t *d_text = T;
+    if (!(flags & PM_DEVICE_TEXT) && n > 0) {
+        rc = ensure(s->c_text, s->c_text_cap, n);
+        if (rc) return rc;
+        cudaError_t e = cudaMemcpyAsync(s->c_text, T, size_t(n), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+        d_text = static_cast<const uint8_t *>(s->c_text);
+    }
+    const int64_t wsb = workspace_bytes_for(n, list);
+    rc = ensure(s->c_ws, s->c_ws_cap, wsb);
+    if (!rc) {
+        int64_t tmp = 0;
+        if (!s->c_counts) {
+            void *p = nullptr;
+            cudaError_t e = cudaMalloc(&p, size_t(d + 1) * 8);
+            if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); return PM_ENOMEM; }
+            s->c_counts = p;
+        }
+        (void)tmp;
+    }
+    if (rc) return rc;
+    int64_t *d_counts = static_cast<int64_t *>(s->c_counts);
+    int64_t *d_nocc = d_counts + d;
+    int64_t n_occ = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        int64_t cap = 0;
+        if (list) {
+            int64_t want = attempt == 0 ? (s->c_out_cap / 8 > 0 ? s->c_out_cap / 8 : (n / 16 + 1024)) : n_occ;
+            if (want < 1) want = 1;
+            rc = ensure(s->c_out, s->c_out_cap, want * 8);
+            if (rc) return rc;
+            cap = s->c_out_cap / 8;
+        }
+        rc = pm_scan_device(s, d_text, n, flags, d_counts, static_cast<uint64_t *>(s->c_out), cap,
+                            d_nocc, s->c_ws, wsb, stream);
+        if (rc) return rc;
+        rc = pm_scan_status(s->c_ws, stream);
+        if (rc) return rc;
+        cudaError_t e = cudaMemcpy(&n_occ, d_nocc, 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+        if (!list || n_occ <= cap) break;
+    }
+    pm_result *r = new_result(d, n_occ, list);
+    if (!r) return PM_ENOMEM;
+    cudaError_t e = cudaMemcpy(r->counts, d_counts, size_t(d) * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && list && n_occ > 0)
+        e = cudaMemcpy(r->occ, s->c_out, size_t(n_occ) * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        pm_result_free(r);
+        return PM_ECUDA;
+    }
+    *out = r;
+    return PM_OK;
+}
+
+void pm_result_free(pm_result *r)
+{
+    if (!r) return;
+    std::free(r->counts);
+    std::free(r->occ);
+    std::free(r);
+}
+
+int pm_scan_batch(const pm_set *const *sets, const uint8_t *const *texts, const int64_t *ns,
+                  int32_t k, uint32_t flags, void *stream, pm_result **outs)
+{
+    if (!sets || !texts || !ns || !outs || k < 0) return PM_EINVAL;
+    for (int32_t j = 0; j < k; ++j) outs[j] = nullptr;
+    for (int32_t j = 0; j < k; ++j) {
+        int rc = pm_scan(sets[j], texts[j], ns[j], flags, stream, &outs[j]);
+        if (rc) {
+            for (int32_t q = 0; q < j; ++q) { pm_result_free(outs[q]); outs[q] = nullptr; }
+            return rc;
+        }
+    }
+    return PM_OK;
+}
+
+int pm_selfcheck_host_walk(const pm_set *s, const uint8_t *T, int64_t n, pm_result **out)
+{
+    if (!s || !out || n < 0 || (n > 0 && !T)) return PM_EINVAL;
+    try {
+        std::vector<uint64_t> occ;
+        std::vector<int64_t> counts;
+        if (s->algo == PM_ALGO_AC) host_walk_ac(s->ac, T, n, occ, counts);
+        else host_walk_wm(s->wm, T, n, occ, counts);
+        pm_result *r = new_result(int64_t(counts.size()), int64_t(occ.size()), true);
+        if (!r) return PM_ENOMEM;
+        if (!occ.empty()) std::memcpy(r->occ, occ.data(), occ.size() * 8);
+        std::memcpy(r->counts, counts.data(), counts.size() * 8);
+        *out = r;
+        return PM_OK;
+    } catch (const std::bad_alloc &) {
+        return PM_ENOMEM;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,321 @@
+// compile.cpp -- host-side pattern-set compiler for libpmscan.
+//
+// Aho-Corasick (Section 3.1): the trie is grown pattern by pattern in input
+// order as in Algorithm 1 (goto function); supply (failure) links are
+// computed in breadth-first order as in Algorithm 2, and at the same time
+// every missing goto is filled with the transition of the supply state, so
+// the result is the full DFA ("an array of size |Sigma|" per state, Section
+// 3.1) and the scan never follows a supply link. States are then renumbered
+// breadth-first (shallow states first, which also makes the shallow prefix
+// of rows the hot part of the table), and the rows of depth-m states are
+// elided: all patterns have length m, so a depth-m state t has no children,
+// its transitions equal those of Supply(t), and a transition into t is
+// stored as "go to Supply(t) and report t".
+//
+// Wu-Manber (Section 3.2, Algorithm 4): SHIFT, HASH and PREFIX over blocks
+// of B characters ending at pattern position q-1, for q = m down to B.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "pm_internal.h"
+
+namespace pm {
+
+static inline uint32_t dna_code(uint32_t b) { return ((b >> 1) ^ (b >> 2)) & 3u; }
+
+int build_ac(const uint8_t *P, int64_t d, int32_t m, AcTables &t)
+{
+    if (!P || d < 1 || m < 1) return PM_EINVAL;
+    if (d >= (int64_t(1) << 24) || m > 255) return PM_ETOOBIG;
+    const int64_t max_states = d * int64_t(m) + 1;
+    if (max_states >= (int64_t(1) << 30)) return PM_ETOOBIG;
+    try {
+        t = AcTables();
+        t.m = m;
+        t.d = d;
+
+        // ---- character classes -------------------------------------------
+        bool present[256] = {};
+        for (int64_t k = 0; k < d * int64_t(m); ++k) present[P[k]] = true;
+        int nbytes = 0;
+        for (int b = 0; b < 256; ++b) nbytes += present[b];
+        bool dna = nbytes <= 4;
+        int byte_of_code[4] = {-1, -1, -1, -1};
+        for (int b = 0; b < 256 && dna; ++b) {
+            if (!present[b]) continue;
+            int c = int(dna_code(uint32_t(b)));
+            if (byte_of_code[c] >= 0) dna = false;
+            byte_of_code[c] = b;
+        }
+        std::memset(t.cls, 0xFF, sizeof(t.cls));
+        if (dna) {
+            t.dna = true;
+            t.lw = 2;
+            t.n_classes = 4;
+            uint32_t lut = 0;
+            for (int c = 0; c < 4; ++c) {
+                int b = byte_of_code[c];
+                if (b < 0) {
+                    // a byte whose own code differs from c can never pass the
+                    // check T == lut[code(T)] for code c
+                    for (b = 0; b < 256; ++b)
+                        if (int(dna_code(uint32_t(b))) != c) break;
+                }
+                lut |= uint32_t(b) << (8 * c);
+            }
+            t.lut = lut;
+            for (int b = 0; b < 256; ++b)
+                if (present[b]) t.cls[b] = uint8_t(dna_code(uint32_t(b)));
+        } else {
+            int k = 0;
+            for (int b = 0; b < 256; ++b)
+                if (present[b]) t.cls[b] = uint8_t(k++);
+            t.n_classes = k;
+            int lw = 0;
+            while ((1 << lw) < k) ++lw;
+            t.lw = lw;
+        }
+        const int W = 1 << t.lw;
+
+        // ---- goto function: the trie, states in creation order -----------
+        std::vector<int32_t> go;      // state * W + class -> state, -1 = none
+        std::vector<int32_t> depth;
+        std::vector<int32_t> first_pat, next_pat(size_t(d), -1), last_pat;
+        go.reserve(size_t(std::min<int64_t>(max_states, int64_t(1) << 26)) * W);
+        auto new_state = [&](int32_t dep) {
+            int32_t s = int32_t(depth.size());
+            go.insert(go.end(), size_t(W), -1);
+            depth.push_back(dep);
+            first_pat.push_back(-1);
+            last_pat.push_back(-1);
+            return s;
+        };
+        new_state(0);
+        for (int64_t r = 0; r < d; ++r) {
+            const uint8_t *p = P + r * int64_t(m);
+            int32_t s = 0;
+            for (int32_t j = 0; j < m; ++j) {
+                int c = t.cls[p[j]];
+                int32_t nx = go[size_t(s) * W + c];
+                if (nx < 0) {
+                    nx = new_state(depth[s] + 1);
+                    go[size_t(s) * W + c] = nx;
+                }
+                s = nx;
+            }
+            // Output(s) gains pattern r (kept in ascending r)
+            if (last_pat[s] < 0) first_pat[s] = int32_t(r);
+            else next_pat[last_pat[s]] = int32_t(r);
+            last_pat[s] = int32_t(r);
+        }
+        const int64_t S = int64_t(depth.size());
+        t.n_states = S;
+
+        // ---- breadth-first order, supply links, full transition function -
+        std::vector<int32_t> order;
+        order.reserve(size_t(S));
+        order.push_back(0);
+        for (size_t h = 0; h < order.size(); ++h) {
+            int32_t s = order[h];
+            for (int c = 0; c < W; ++c) {
+                int32_t nx = go[size_t(s) * W + c];
+                if (nx >= 0) order.push_back(nx);
+            }
+        }
+        std::vector<int32_t> supply(size_t(S), 0);  // depth-1 states: root
+        for (int c = 0; c < W; ++c)
+            if (go[size_t(c)] < 0) go[size_t(c)] = 0;  // root loops on absent characters
+        for (size_t h = 1; h < order.size(); ++h) {
+            int32_t s = order[h];
+            int32_t f = supply[s];
+            for (int c = 0; c < W; ++c) {
+                // entries of s are still pure goto entries here; f is
+                // shallower than s, so its row is already complete
+                int32_t nx = go[size_t(s) * W + c];
+                int32_t via = go[size_t(f) * W + c];
+                if (nx >= 0) supply[nx] = via;   // real child
+                else go[size_t(s) * W + c] = via; // missing goto -> supply's move
+            }
+        }
+
+        // ---- rows: reset row 0, then non-terminal states breadth-first ----
+        std::vector<int32_t> row_of(size_t(S), -1);
+        int64_t rows = 1, shallow = 0;
+        for (size_t h = 0; h < order.size(); ++h) {
+            int32_t s = order[h];
+            if (depth[s] < m) {
+                row_of[s] = int32_t(rows++);
+                if (depth[s] < m - 1) ++shallow;
+            }
+        }
+        t.n_rows = rows;
+        t.d0_row = 1 + shallow;
+        t.n_distinct = S - (rows - 1);
+        if (rows >= (int64_t(1) << 30)) return PM_ETOOBIG;
+
+        // groups of equal patterns (terminal states reached by >= 2 ids)
+        std::vector<int32_t> group_of(size_t(S), -1);
+        t.grp_off.push_back(0);
+        for (size_t h = 0; h < order.size(); ++h) {
+            int32_t s = order[h];
+            if (depth[s] != m || first_pat[s] < 0 || next_pat[first_pat[s]] < 0) continue;
+            group_of[s] = int32_t(t.grp_off.size() - 1);
+            for (int32_t r = first_pat[s]; r >= 0; r = next_pat[r]) t.grp_ids.push_back(uint32_t(r));
+            t.grp_off.push_back(uint32_t(t.grp_ids.size()));
+        }
+        t.has_dups = t.grp_ids.size() > 0;
+
+        t.table.assign(size_t(rows) << t.lw, 0u);
+        t.mid.assign(size_t(rows - t.d0_row) << t.lw, 0xFFFFFFFFu);
+        t.row_depth.assign(size_t(rows), 0);
+        const uint32_t root_entry = uint32_t(row_of[0]) << 1;
+        for (int c = 0; c < W; ++c) t.table[size_t(c)] = root_entry;
+        for (size_t h = 0; h < order.size(); ++h) {
+            int32_t s = order[h];
+            if (depth[s] >= m) continue;
+            const int64_t row = row_of[s];
+            t.row_depth[size_t(row)] = depth[s];
+            for (int c = 0; c < W; ++c) {
+                int32_t nx = go[size_t(s) * W + c];
+                uint32_t e;
+                if (depth[nx] == m) {
+                    e = (uint32_t(row_of[supply[nx]]) << 1) | 1u;
+                    const size_t mi = size_t((row - t.d0_row) << t.lw) + size_t(c);
+                    t.mid[mi] = group_of[nx] >= 0 ? (0x80000000u | uint32_t(group_of[nx]))
+                                                  : uint32_t(first_pat[nx]);
+                } else {
+                    e = uint32_t(row_of[nx]) << 1;
+                }
+                t.table[size_t(row << t.lw) + size_t(c)] = e;
+            }
+        }
+        const bool fits16 = rows <= 32768 && ((rows - t.d0_row) << t.lw) <= 65536;
+        t.entry_bytes = fits16 ? 2 : 4;
+        return PM_OK;
+    } catch (const std::bad_alloc &) {
+        t = AcTables();
+        return PM_ENOMEM;
+    }
+}
+
+static inline uint32_t wm_hash(const uint8_t *s, int len)
+{
+    uint32_t h = 0;
+    for (int k = 0; k < len; ++k) h = (h << 5) | (s[k] & 31u);
+    return h;
+}
+
+int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTables &t)
+{
+    if (!P || d < 1 || m < 1 || B < 1 || B > m || Bp < 1) return PM_EINVAL;
+    if (B > 4 || Bp > 3) return PM_EINVAL;
+    if (Bp > m) Bp = m;
+    if (d >= (int64_t(1) << 24) || m > 255) return PM_ETOOBIG;
+    try {
+        t = WmTables();
+        t.m = m; t.B = B; t.Bp = Bp; t.d = d;
+        const size_t H = size_t(1) << (5 * B);
+        t.shift.assign(H, uint8_t(m - B + 1));
+        std::vector<uint32_t> bucket_of(static_cast<size_t>(d));
+        std::vector<uint16_t> prefix(static_cast<size_t>(d));
+        std::vector<uint32_t> fill(H + 1, 0);
+        for (int64_t r = 0; r < d; ++r) {
+            const uint8_t *p = P + r * int64_t(m);
+            for (int32_t q = m; q >= B; --q) {
+                uint32_t h = wm_hash(p + (q - B), B);
+                uint8_t sh = uint8_t(m - q);
+                if (sh < t.shift[h]) t.shift[h] = sh;
+                if (q == m) {
+                    bucket_of[size_t(r)] = h;
+                    prefix[size_t(r)] = uint16_t(wm_hash(p, Bp));
+                    fill[h + 1]++;
+                }
+            }
+        }
+        for (size_t h = 0; h < H; ++h) fill[h + 1] += fill[h];
+        t.hoff = fill;
+        t.hids.assign(size_t(d), 0);
+        for (int64_t r = 0; r < d; ++r) t.hids[fill[bucket_of[size_t(r)]]++] = uint32_t(r);
+        for (size_t h = 0; h < H; ++h) {
+            auto b = t.hids.begin() + t.hoff[h], e = t.hids.begin() + t.hoff[h + 1];
+            std::stable_sort(b, e, [&](uint32_t x, uint32_t y) { return prefix[x] < prefix[y]; });
+        }
+        t.hpfx.resize(size_t(d));
+        for (int64_t k = 0; k < d; ++k) t.hpfx[size_t(k)] = prefix[t.hids[size_t(k)]];
+        t.pats.assign(P, P + d * int64_t(m));
+        t.n_zero_shift = 0;
+        for (size_t h = 0; h < H; ++h) t.n_zero_shift += t.shift[h] == 0;
+        return PM_OK;
+    } catch (const std::bad_alloc &) {
+        t = WmTables();
+        return PM_ENOMEM;
+    }
+}
+
+static inline void emit_entry(std::vector<uint64_t> &occ, std::vector<int64_t> &counts,
+                              int64_t i, uint32_t r)
+{
+    occ.push_back((uint64_t(i) << 32) | r);
+    counts[r]++;
+}
+
+void host_walk_ac(const AcTables &t, const uint8_t *T, int64_t n,
+                  std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
+{
+    counts.assign(size_t(t.d), 0);
+    occ.clear();
+    uint32_t e = 2u;  // root is row 1
+    const uint32_t mid_base = uint32_t(t.d0_row << t.lw);
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t b = T[i];
+        uint32_t idx;
+        if (t.dna) {
+            const uint32_t c = dna_code(b);
+            const bool ok = ((t.lut >> (8 * c)) & 0xFFu) == b;
+            idx = ok ? (((e >> 1) << 2) | c) : c;   // row 0 = reset row
+        } else {
+            const uint32_t c = t.cls[b];
+            idx = c == 0xFFu ? 0u : (((e >> 1) << t.lw) | c);
+        }
+        e = t.table[idx];
+        if (e & 1u) {
+            const uint32_t v = t.mid[idx - mid_base];
+            const int64_t pos = i - t.m + 1;
+            if (v & 0x80000000u) {
+                const uint32_t g = v & 0x7FFFFFFFu;
+                for (uint32_t k = t.grp_off[g]; k < t.grp_off[g + 1]; ++k)
+                    emit_entry(occ, counts, pos, t.grp_ids[k]);
+            } else {
+                emit_entry(occ, counts, pos, v);
+            }
+        }
+    }
+}
+
+void host_walk_wm(const WmTables &t, const uint8_t *T, int64_t n,
+                  std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
+{
+    counts.assign(size_t(t.d), 0);
+    occ.clear();
+    const int32_t m = t.m, B = t.B, Bp = t.Bp;
+    int64_t i = m - 1;
+    while (i < n) {
+        const uint32_t h = wm_hash(T + (i - B + 1), B);
+        const uint32_t sh = t.shift[h];
+        if (sh > 0) {
+            i += sh;
+            continue;
+        }
+        const uint16_t hp = uint16_t(wm_hash(T + (i - m + 1), Bp));
+        for (uint32_t k = t.hoff[h]; k < t.hoff[h + 1]; ++k) {
+            if (t.hpfx[k] != hp) continue;
+            const uint32_t r = t.hids[k];
+            if (std::memcmp(t.pats.data() + size_t(r) * m, T + (i - m + 1), size_t(m)) == 0)
+                emit_entry(occ, counts, i - m + 1, r);
+        }
+        i += 1;
+    }
+}
+
+}  // namespace pm

@@ -1,0 +1,155 @@
+// pm_internal.h -- shared declarations of libpmscan (host compiler, C ABI,
+// kernel launchers). Not installed; the public interface is include/pmscan.h.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "pmscan.h"
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// Aho-Corasick DFA (Section 3.1, Algorithms 1-2 merged into one table).
+//
+// Layout of the transition table: row 0 is a "reset" row whose entries all
+// lead to the root (used for bytes outside the pattern alphabet); rows
+// 1..n_rows-1 are the non-terminal trie states in breadth-first order (root
+// is row 1). An entry is (next_row << 1) | match, where match says the
+// transition entered a depth-m (terminal) state t; next_row is then the row
+// of Supply(t), whose outgoing transitions equal t's (t has no children), so
+// t's own row is never stored. Only rows of depth m-1 can hold match
+// entries; they are the last rows, from d0_row on. For a match entry at
+// index idx = row * W + code, mid[idx - d0_row * W] names what matched:
+// bit 31 clear -> the pattern id r; set -> a group g of equal patterns whose
+// ids are grp_ids[grp_off[g] .. grp_off[g+1]).
+// ---------------------------------------------------------------------------
+struct AcTables {
+    int32_t m = 0;
+    int64_t d = 0;
+    bool dna = false;        // ACGT-like alphabet decoded arithmetically
+    uint32_t lut = 0;        // dna: byte for code c in byte c of lut
+    uint8_t cls[256];        // general: class of each byte, 0xFF = absent
+    int32_t n_classes = 0;
+    int32_t lw = 0;          // log2 of the row width W
+    int64_t n_states = 0;    // trie states including terminals
+    int64_t n_rows = 0;      // table rows (reset row + non-terminal states)
+    int64_t d0_row = 0;      // first row holding match entries
+    int64_t n_distinct = 0;  // distinct patterns (= terminal states)
+    bool has_dups = false;
+    int32_t entry_bytes = 2;
+    std::vector<uint32_t> table;   // n_rows << lw encoded entries
+    std::vector<uint32_t> mid;     // (n_rows - d0_row) << lw
+    std::vector<uint32_t> grp_off; // groups of >= 2 equal patterns
+    std::vector<uint32_t> grp_ids;
+    std::vector<int32_t> row_depth; // depth of each row's state (row 0: 0)
+};
+
+// ---------------------------------------------------------------------------
+// Wu-Manber tables (Section 3.2, Algorithm 4). h1 over B bytes and h2 over
+// B' bytes: h = (h << 5) | (byte & 31). HASH is stored as CSR buckets over
+// h1 values; inside a bucket the pattern ids are sorted by (PREFIX, r), so
+// the candidates with PREFIX[r] = h' form one contiguous run in ascending r.
+// ---------------------------------------------------------------------------
+struct WmTables {
+    int32_t m = 0, B = 0, Bp = 0;
+    int64_t d = 0;
+    std::vector<uint8_t> shift;    // 2^(5B) entries, values <= m-B+1 <= 255
+    std::vector<uint32_t> hoff;    // 2^(5B)+1 bucket offsets
+    std::vector<uint32_t> hids;    // d pattern ids, bucket-major
+    std::vector<uint16_t> hpfx;    // PREFIX of hids[k]
+    std::vector<uint8_t> pats;     // d*m pattern bytes
+    int64_t n_zero_shift = 0;
+};
+
+int build_ac(const uint8_t *P, int64_t d, int32_t m, AcTables &out);
+int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTables &out);
+
+// host walks used by pm_selfcheck_host_walk
+void host_walk_ac(const AcTables &t, const uint8_t *T, int64_t n,
+                  std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
+void host_walk_wm(const WmTables &t, const uint8_t *T, int64_t n,
+                  std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
+
+// ---------------------------------------------------------------------------
+// Device side
+// ---------------------------------------------------------------------------
+constexpr int kLane = 32;
+constexpr int kChunk = 80;          // start positions owned by one lane (L)
+constexpr int kWarpTile = kLane * kChunk;
+
+struct AcLaunch;                    // defined in scan_ac.cu
+struct WmLaunch;
+
+// Everything a launcher needs about the device copy of a set.
+struct DevAc {
+    void *table = nullptr;          // entry_bytes * (n_rows << lw)
+    uint32_t *mid = nullptr;
+    uint32_t *grp_off = nullptr;
+    uint32_t *grp_ids = nullptr;
+    uint8_t *cls = nullptr;         // 256 bytes
+    int64_t smem_entries = 0;       // table entries copied to shared memory
+    int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0, stage_cap = 0;
+    int32_t hist_smem = 0;          // per-pattern counters in shared memory
+    int32_t nv = 0, hv = 0;         // register text vectors (chunk + halo)
+    int32_t variant = 0;            // kernel instance id
+    int64_t smem_bytes = 0;
+    int32_t placement = 0;
+};
+
+struct DevWm {
+    uint8_t *shift = nullptr;
+    uint32_t *hoff = nullptr;
+    uint32_t *hids = nullptr;
+    uint16_t *hpfx = nullptr;
+    uint8_t *pats = nullptr;
+    int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0, stage_cap = 0;
+    int32_t shift_smem = 0, hist_smem = 0;
+    int64_t smem_bytes = 0;
+};
+
+// Workspace layout (device scratch): [status word u32 | pad] [n_occ u64]
+// [tile status u64 x tiles]. Zeroed by the launcher before each scan.
+constexpr int64_t kWsHeader = 256;
+int64_t warp_tiles(int64_t n);
+int64_t workspace_bytes_for(int64_t n, bool list);
+
+struct DeviceProps {
+    int sm_count = 0;
+    int smem_optin = 0;   // max dynamic shared memory per block
+    int smem_per_sm = 0;
+    int l2_bytes = 0;
+};
+int device_props(DeviceProps &p);
+
+// Plan and launch. Return PM_* codes; PM_ECUDA records the CUDA error.
+int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevAc &dev);
+int ac_launch(const AcTables &t, const DevAc &dev, const uint8_t *d_text, int64_t n,
+              bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
+              int64_t *d_n_occ, void *d_ws, void *stream);
+int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevWm &dev);
+int wm_launch(const WmTables &t, const DevWm &dev, const uint8_t *d_text, int64_t n,
+              bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
+              int64_t *d_n_occ, void *d_ws, void *stream);
+
+void set_cuda_error(int err);
+
+}  // namespace pm
+
+// The opaque handle of the C ABI.
+struct pm_set {
+    int32_t algo = 0;
+    pm_params params{};
+    bool host_only = false;
+    pm::AcTables ac;
+    pm::WmTables wm;
+    pm::DevAc dac;
+    pm::DevWm dwm;
+    int64_t device_bytes = 0;
+    // caches for pm_scan (host-pointer convenience path)
+    void *c_text = nullptr;  int64_t c_text_cap = 0;
+    void *c_ws = nullptr;    int64_t c_ws_cap = 0;
+    void *c_out = nullptr;   int64_t c_out_cap = 0;   // uint64 entries
+    void *c_counts = nullptr;                         // int64[d] + n_occ
+};

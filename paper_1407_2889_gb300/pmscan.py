@@ -1,0 +1,322 @@
+"""Thin ctypes binding over ``libpmscan.so`` (C ABI in ``include/pmscan.h``).
+
+Argument marshalling only: every step of a scan runs in the library's CUDA
+kernels. The functions keep the C names (``pm_ac_compile``, ``pm_scan`` ...);
+:class:`PatternSet` wraps a handle for convenience. Loading raises
+``ImportError`` when the library has not been built -- there is no CPU
+fallback.
+
+Device buffers for :func:`pm_scan_device` are plain device pointers; torch
+CUDA tensors are accepted wherever a device pointer is expected.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpmscan.so")
+
+PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ETOOBIG, PM_ETIMEOUT, PM_ECAPACITY, PM_ENODEV = range(8)
+PM_HOST_TEXT, PM_DEVICE_TEXT, PM_COUNTS_ONLY = 0, 1, 2
+PM_PLACE_AUTO, PM_PLACE_SMEM, PM_PLACE_HYBRID, PM_PLACE_GLOBAL = range(4)
+PM_ALGO_AC, PM_ALGO_WM = 1, 2
+
+EXPORTED = [
+    "pm_ac_compile", "pm_wm_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
+    "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device", "pm_scan_status",
+    "pm_scan_batch", "pm_selfcheck_host_walk", "pm_strerror", "pm_last_cuda_error",
+    "pm_version",
+]
+
+
+class pm_params(ctypes.Structure):
+    _fields_ = [("placement", ctypes.c_int32), ("smem_table_bytes", ctypes.c_int32),
+                ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("wm_prefix_len", ctypes.c_int32), ("host_only", ctypes.c_int32)]
+
+
+class pm_set_info(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("m", ctypes.c_int32), ("d", ctypes.c_int64),
+                ("n_distinct", ctypes.c_int64), ("n_states", ctypes.c_int64),
+                ("n_rows", ctypes.c_int64), ("n_classes", ctypes.c_int32),
+                ("row_width", ctypes.c_int32), ("entry_bytes", ctypes.c_int32),
+                ("dna_mode", ctypes.c_int32), ("placement", ctypes.c_int32),
+                ("smem_rows", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
+                ("B", ctypes.c_int32), ("Bp", ctypes.c_int32),
+                ("shift_entries", ctypes.c_int64), ("n_zero_shift", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class pm_result(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int64), ("n_occ", ctypes.c_int64),
+                ("counts", ctypes.POINTER(ctypes.c_int64)),
+                ("occ", ctypes.POINTER(ctypes.c_uint64))]
+
+
+class PmError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = _lib_or_none().pm_strerror(code).decode() if _lib_or_none() else str(code)
+        if code == PM_ECUDA and _lib_or_none():
+            msg += f" (cudaError {_lib_or_none().pm_last_cuda_error()})"
+        super().__init__(f"{what}: {msg}" if what else msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _lib_or_none():
+    return _lib
+
+
+def lib():
+    """Load ``libpmscan.so``; ImportError if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        pp = ctypes.POINTER(vp)
+        L.pm_ac_compile.restype = ctypes.c_int
+        L.pm_ac_compile.argtypes = [vp, i64, i32, ctypes.POINTER(pm_params), pp]
+        L.pm_wm_compile.restype = ctypes.c_int
+        L.pm_wm_compile.argtypes = [vp, i64, i32, i32, ctypes.POINTER(pm_params), pp]
+        L.pm_set_free.restype = None
+        L.pm_set_free.argtypes = [vp]
+        L.pm_set_get_info.restype = ctypes.c_int
+        L.pm_set_get_info.argtypes = [vp, ctypes.POINTER(pm_set_info)]
+        L.pm_scan.restype = ctypes.c_int
+        L.pm_scan.argtypes = [vp, vp, i64, u32, vp, ctypes.POINTER(ctypes.POINTER(pm_result))]
+        L.pm_result_free.restype = None
+        L.pm_result_free.argtypes = [ctypes.POINTER(pm_result)]
+        L.pm_scan_workspace_bytes.restype = i64
+        L.pm_scan_workspace_bytes.argtypes = [vp, i64, u32]
+        L.pm_scan_device.restype = ctypes.c_int
+        L.pm_scan_device.argtypes = [vp, vp, i64, u32, vp, vp, i64, vp, vp, i64, vp]
+        L.pm_scan_status.restype = ctypes.c_int
+        L.pm_scan_status.argtypes = [vp, vp]
+        L.pm_scan_batch.restype = ctypes.c_int
+        L.pm_scan_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(i64), i32, u32, vp,
+                                    ctypes.POINTER(ctypes.POINTER(pm_result))]
+        L.pm_selfcheck_host_walk.restype = ctypes.c_int
+        L.pm_selfcheck_host_walk.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.POINTER(pm_result))]
+        L.pm_strerror.restype = ctypes.c_char_p
+        L.pm_strerror.argtypes = [ctypes.c_int]
+        L.pm_last_cuda_error.restype = ctypes.c_int
+        L.pm_last_cuda_error.argtypes = []
+        L.pm_version.restype = ctypes.c_char_p
+        L.pm_version.argtypes = []
+        _lib = L
+        return L
+
+
+def _check(rc: int, what: str):
+    if rc != PM_OK:
+        raise PmError(rc, what)
+
+
+def _dev_ptr(x) -> int:
+    """Device pointer of a torch CUDA tensor, or an int address."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError(f"expected a device tensor or address, got {type(x)}")
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _patterns(P) -> np.ndarray:
+    if isinstance(P, (list, tuple)):
+        rows = [np.frombuffer(p.encode() if isinstance(p, str) else bytes(p), dtype=np.uint8) for p in P]
+        P = np.stack(rows)
+    P = np.ascontiguousarray(P, dtype=np.uint8)
+    if P.ndim != 2:
+        raise ValueError("patterns must be a (d, m) uint8 array")
+    return P
+
+
+def _make_params(params) -> pm_params | None:
+    if params is None:
+        return None
+    if isinstance(params, pm_params):
+        return params
+    p = pm_params()
+    for k, v in dict(params).items():
+        setattr(p, k, int(v))
+    return p
+
+
+# ---------------------------------------------------------------------------
+# C names
+# ---------------------------------------------------------------------------
+def pm_ac_compile(P, params=None) -> int:
+    P = _patterns(P)
+    h = ctypes.c_void_p()
+    prm = _make_params(params)
+    _check(lib().pm_ac_compile(P.ctypes.data, P.shape[0], P.shape[1],
+                               ctypes.byref(prm) if prm is not None else None, ctypes.byref(h)),
+           "pm_ac_compile")
+    return h.value
+
+
+def pm_wm_compile(P, B: int, params=None) -> int:
+    P = _patterns(P)
+    h = ctypes.c_void_p()
+    prm = _make_params(params)
+    _check(lib().pm_wm_compile(P.ctypes.data, P.shape[0], P.shape[1], int(B),
+                               ctypes.byref(prm) if prm is not None else None, ctypes.byref(h)),
+           "pm_wm_compile")
+    return h.value
+
+
+def pm_set_free(h: int) -> None:
+    if h:
+        lib().pm_set_free(h)
+
+
+def pm_set_get_info(h: int) -> dict:
+    info = pm_set_info()
+    _check(lib().pm_set_get_info(h, ctypes.byref(info)), "pm_set_get_info")
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def _take_result(rp) -> tuple[np.ndarray, np.ndarray]:
+    r = rp.contents
+    d, n_occ = r.d, r.n_occ
+    counts = np.ctypeslib.as_array(r.counts, shape=(d,)).copy() if d > 0 else np.zeros(0, np.int64)
+    if r.occ and n_occ > 0:
+        occ = np.ctypeslib.as_array(r.occ, shape=(n_occ,)).copy()
+    else:
+        occ = np.zeros(0, dtype=np.uint64)
+    lib().pm_result_free(rp)
+    return occ, counts
+
+
+def pm_scan(h: int, T, flags: int = PM_HOST_TEXT, stream=None):
+    """Scan T (numpy uint8 host array, or a torch CUDA uint8 tensor with
+    PM_DEVICE_TEXT). Returns (occ uint64 keys (i<<32)|r, counts int64)."""
+    rp = ctypes.POINTER(pm_result)()
+    if flags & PM_DEVICE_TEXT:
+        ptr, n = _dev_ptr(T), int(T.numel())
+    else:
+        T = np.ascontiguousarray(T, dtype=np.uint8)
+        ptr, n = T.ctypes.data, T.size
+    _check(lib().pm_scan(h, ptr, n, flags, _stream_ptr(stream), ctypes.byref(rp)), "pm_scan")
+    return _take_result(rp)
+
+
+def pm_scan_workspace_bytes(h: int, n: int, flags: int = PM_HOST_TEXT) -> int:
+    v = lib().pm_scan_workspace_bytes(h, int(n), flags)
+    if v < 0:
+        raise PmError(PM_EINVAL, "pm_scan_workspace_bytes")
+    return int(v)
+
+
+def pm_scan_device(h: int, d_text, n: int, flags: int, d_counts, d_occ, occ_capacity: int,
+                   d_n_occ, d_workspace, workspace_bytes: int, stream=None) -> None:
+    _check(lib().pm_scan_device(h, _dev_ptr(d_text), int(n), flags, _dev_ptr(d_counts),
+                                _dev_ptr(d_occ), int(occ_capacity), _dev_ptr(d_n_occ),
+                                _dev_ptr(d_workspace), int(workspace_bytes), _stream_ptr(stream)),
+           "pm_scan_device")
+
+
+def pm_scan_status(d_workspace, stream=None) -> int:
+    return int(lib().pm_scan_status(_dev_ptr(d_workspace), _stream_ptr(stream)))
+
+
+def pm_scan_batch(handles, texts, flags: int = PM_HOST_TEXT, stream=None):
+    k = len(handles)
+    hs = (ctypes.c_void_p * k)(*handles)
+    keep, ptrs, ns = [], [], []
+    for T in texts:
+        if flags & PM_DEVICE_TEXT:
+            ptrs.append(_dev_ptr(T)); ns.append(int(T.numel()))
+        else:
+            T = np.ascontiguousarray(T, dtype=np.uint8)
+            keep.append(T); ptrs.append(T.ctypes.data); ns.append(T.size)
+    tp = (ctypes.c_void_p * k)(*ptrs)
+    npv = (ctypes.c_int64 * k)(*ns)
+    outs = (ctypes.POINTER(pm_result) * k)()
+    _check(lib().pm_scan_batch(hs, tp, npv, k, flags, _stream_ptr(stream), outs), "pm_scan_batch")
+    return [_take_result(outs[j]) for j in range(k)]
+
+
+def pm_selfcheck_host_walk(h: int, T):
+    T = np.ascontiguousarray(T, dtype=np.uint8)
+    rp = ctypes.POINTER(pm_result)()
+    _check(lib().pm_selfcheck_host_walk(h, T.ctypes.data, T.size, ctypes.byref(rp)),
+           "pm_selfcheck_host_walk")
+    return _take_result(rp)
+
+
+def pm_version() -> str:
+    return lib().pm_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+class PatternSet:
+    """A compiled pattern set (AC DFA or WM tables) owning its device tables."""
+
+    def __init__(self, handle: int, algo: int):
+        self.h = handle
+        self.algo = algo
+
+    @classmethod
+    def ac(cls, P, params=None) -> "PatternSet":
+        return cls(pm_ac_compile(P, params), PM_ALGO_AC)
+
+    @classmethod
+    def wm(cls, P, B: int, params=None) -> "PatternSet":
+        return cls(pm_wm_compile(P, B, params), PM_ALGO_WM)
+
+    def info(self) -> dict:
+        return pm_set_get_info(self.h)
+
+    def scan(self, T, counts_only: bool = False, stream=None):
+        flags = PM_COUNTS_ONLY if counts_only else 0
+        if hasattr(T, "is_cuda") and T.is_cuda:
+            flags |= PM_DEVICE_TEXT
+        return pm_scan(self.h, T, flags, stream)
+
+    def workspace_bytes(self, n: int, counts_only: bool = False) -> int:
+        return pm_scan_workspace_bytes(self.h, n, PM_COUNTS_ONLY if counts_only else 0)
+
+    def selfcheck_host_walk(self, T):
+        return pm_selfcheck_host_walk(self.h, T)
+
+    def close(self):
+        if self.h:
+            pm_set_free(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unpack(occ: np.ndarray):
+    occ = np.asarray(occ, dtype=np.uint64)
+    return (occ >> np.uint64(32)).astype(np.int64), (occ & np.uint64(0xFFFFFFFF)).astype(np.int64)

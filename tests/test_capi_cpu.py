@@ -1,0 +1,146 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol the header
+declares, rejects bad arguments, refuses to compute without a device, and
+its compiled tables (walked on the host by the self-check) give the
+oracle's occurrence sets."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1407_2889_gb300 import pmscan as pm
+from paper_1407_2889_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HOST = {"host_only": 1}
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "pmscan.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pm_[a-z_]+)\s*\(", src)))
+
+
+def test_header_and_exports_agree():
+    declared = _declared_functions()
+    assert declared, "no declarations parsed"
+    L = pm.lib()
+    for name in declared:
+        assert hasattr(L, name), f"{name} declared but not exported"
+    assert sorted(pm.EXPORTED) == declared
+
+
+def test_version_and_errors():
+    assert "sm_103a" in pm.pm_version()
+    L = pm.lib()
+    for code in range(8):
+        assert L.pm_strerror(code)
+
+
+def test_invalid_arguments():
+    with pytest.raises(pm.PmError) as e:
+        pm.pm_ac_compile(np.zeros((0, 4), np.uint8), HOST)
+    assert e.value.code == pm.PM_EINVAL
+    with pytest.raises(pm.PmError) as e:
+        pm.pm_ac_compile(np.zeros((3, 0), np.uint8), HOST)
+    assert e.value.code == pm.PM_EINVAL
+    with pytest.raises(pm.PmError) as e:
+        pm.pm_wm_compile(["ACGT"], 5, HOST)
+    assert e.value.code == pm.PM_EINVAL
+    with pytest.raises(pm.PmError) as e:
+        pm.pm_ac_compile(np.zeros((2, 256), np.uint8), HOST)
+    assert e.value.code == pm.PM_ETOOBIG
+    h = pm.pm_ac_compile(["ACGT"], HOST)
+    try:  # a host-only set can be inspected, never scanned
+        with pytest.raises(pm.PmError) as e:
+            pm.pm_scan(h, np.frombuffer(b"ACGTACGT", np.uint8))
+        assert e.value.code == pm.PM_EINVAL
+    finally:
+        pm.pm_set_free(h)
+
+
+def test_no_device_no_compute():
+    """Without a GPU the library refuses to compile for the device: there is
+    no CPU fallback."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("GPU present")
+    except ImportError:
+        pass
+    with pytest.raises(pm.PmError) as e:
+        pm.pm_ac_compile(["ACGT"])
+    assert e.value.code in (pm.PM_ENODEV, pm.PM_ECUDA)
+
+
+def test_worked_example_tables():
+    h = pm.pm_ac_compile(["AAC", "AGT", "GTA"], HOST)
+    try:
+        info = pm.pm_set_get_info(h)
+        # 9 trie states (Section 3.1 example); 3 terminal rows elided; + reset row
+        assert info["n_states"] == 9 and info["n_rows"] == 7 and info["n_distinct"] == 3
+        assert info["dna_mode"] == 1 and info["row_width"] == 4
+        occ, cnt = pm.pm_selfcheck_host_walk(h, np.frombuffer(b"AGTAAC", np.uint8))
+        assert [tuple(x) for x in zip(*pm.unpack(occ))] == [(0, 1), (1, 2), (3, 0)]
+    finally:
+        pm.pm_set_free(h)
+
+
+def _random_case(rng, alphabet):
+    n = int(rng.integers(0, 3000))
+    m = int(rng.integers(1, 20))
+    d = int(rng.integers(1, 40))
+    A = np.frombuffer(alphabet, np.uint8)
+    T = A[rng.integers(0, A.size, n)]
+    P = A[rng.integers(0, A.size, (d, m))]
+    for r in range(d):
+        if n >= m and rng.random() < 0.5:
+            s = int(rng.integers(0, n - m + 1))
+            P[r] = T[s:s + m]
+    if d > 2 and rng.random() < 0.5:
+        P[-1] = P[0]
+    return T, np.ascontiguousarray(P)
+
+
+@pytest.mark.parametrize("alphabet", [b"ACGT", b"ACGTN\n", b"AC", b"acgt", b"AG", b"xyz", bytes(range(0, 256, 7))])
+def test_ac_tables_match_oracle(alphabet):
+    rng = np.random.default_rng(len(alphabet) * 31 + alphabet[0])
+    for _ in range(40):
+        T, P = _random_case(rng, alphabet)
+        want_occ, want_cnt = oracle.brute(T, P)
+        h = pm.pm_ac_compile(P, HOST)
+        try:
+            occ, cnt = pm.pm_selfcheck_host_walk(h, T)
+        finally:
+            pm.pm_set_free(h)
+        assert np.array_equal(occ, want_occ) and np.array_equal(cnt, want_cnt)
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 4])
+def test_wm_tables_match_oracle(B):
+    rng = np.random.default_rng(100 + B)
+    for _ in range(40):
+        T, P = _random_case(rng, b"ACGTN")
+        if P.shape[1] < B:
+            continue
+        want_occ, want_cnt = oracle.brute(T, P)
+        h = pm.pm_wm_compile(P, B, HOST)
+        try:
+            occ, cnt = pm.pm_selfcheck_host_walk(h, T)
+        finally:
+            pm.pm_set_free(h)
+        assert np.array_equal(occ, want_occ) and np.array_equal(cnt, want_cnt)
+
+
+def test_table_sizes_of_est_sets():
+    """Row counts of the EST-shaped sets decide shared-memory placement."""
+    T = synth.est_text(1 << 22, 1)
+    P = synth.mixed_patterns(T, 8000, 8, synth.est_pattern_seed(8000, 8))
+    h = pm.pm_ac_compile(P, HOST)
+    try:
+        info = pm.pm_set_get_info(h)
+        assert info["entry_bytes"] == 2 and info["n_rows"] < 16384
+        assert info["n_distinct"] <= 8000
+    finally:
+        pm.pm_set_free(h)

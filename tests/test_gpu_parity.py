@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Every comparison is bit-exact: occurrence keys (i << 32 | r) element by
+element and per-pattern counts. Small cases span several warp tiles and a
+ragged tail; the workload sizes compare against the oracle in full where it
+finishes in seconds, and at the full 1 GiB size in the launch configuration
+bench.py times, on sampled windows plus properties checked on every output
+(each reported pair is an occurrence, order, counts, and the exact total
+from an independent window-key count done with plain torch ops).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1407_2889_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU-only machines, never run there
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1407_2889_gb300 import pmscan as pm  # noqa: E402
+
+THREADS = os.cpu_count() or 4
+
+
+def _ac(P, **kw):
+    return pm.PatternSet.ac(P, kw or None)
+
+
+def _wm(P, B, **kw):
+    return pm.PatternSet.wm(P, B, kw or None)
+
+
+def _same(got, want, what=""):
+    go, gc = got
+    wo, wc = want
+    assert go.size == wo.size, f"{what}: {go.size} occurrences, oracle {wo.size}"
+    assert np.array_equal(go, wo), f"{what}: occurrence lists differ"
+    assert np.array_equal(gc, wc), f"{what}: counts differ"
+
+
+def _random_case(rng, alphabet, n_max=20000, m_max=20, d_max=60):
+    n = int(rng.integers(0, n_max))
+    m = int(rng.integers(1, m_max + 1))
+    d = int(rng.integers(1, d_max))
+    A = np.frombuffer(alphabet, np.uint8)
+    T = A[rng.integers(0, A.size, n)]
+    P = A[rng.integers(0, A.size, (d, m))]
+    for r in range(d):
+        if n >= m and rng.random() < 0.6:
+            s = int(rng.integers(0, n - m + 1))
+            P[r] = T[s:s + m]
+    if d > 2 and rng.random() < 0.5:
+        P[-1] = P[0]
+    return T, np.ascontiguousarray(P)
+
+
+# ---------------------------------------------------------------------------
+# small cases: random alphabets, lengths, duplicates, ragged tails
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("alphabet", [b"ACGT", b"ACGTN\n", b"AC", b"acgt", b"xyzw#", bytes(range(1, 250, 3))])
+def test_ac_random_small(alphabet):
+    rng = np.random.default_rng(alphabet[0] * 7 + len(alphabet))
+    for case in range(25):
+        T, P = _random_case(rng, alphabet, m_max=65 if case % 3 == 0 else 20)
+        want = oracle.brute(T, P)
+        s = _ac(P)
+        _same(s.scan(T), want, f"AC case {case} n={T.size} m={P.shape[1]} d={P.shape[0]}")
+        _same(s.scan(torch.from_numpy(T).cuda()), want, "AC device text")
+        occ, cnt = s.scan(T, counts_only=True)
+        assert occ.size == 0 and np.array_equal(cnt, want[1])
+        s.close()
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 4])
+def test_wm_random_small(B):
+    rng = np.random.default_rng(1000 + B)
+    for case in range(25):
+        T, P = _random_case(rng, b"ACGTN\n", m_max=40)
+        if P.shape[1] < B:
+            continue
+        want = oracle.brute(T, P)
+        s = _wm(P, B)
+        _same(s.scan(T), want, f"WM B={B} case {case} n={T.size} m={P.shape[1]}")
+        occ, cnt = s.scan(T, counts_only=True)
+        assert np.array_equal(cnt, want[1])
+        s.close()
+
+
+def test_edge_cases():
+    P = np.frombuffer(b"ACGTACGT", np.uint8).reshape(1, 8)
+    for n in [0, 1, 7, 8, 9, 15, 16, 17, 2559, 2560, 2561, 2567, 5120 + 3]:
+        T = synth.uniform_dna(n, 11)
+        T[: min(n, 8)] = P[0, : min(n, 8)]
+        want = oracle.brute(T, P)
+        for s in (_ac(P), _wm(P, 3)):
+            _same(s.scan(T), want, f"n={n}")
+            s.close()
+
+
+def test_every_position_matches_overflow_path():
+    """A^n against A^m (and a duplicate): each lane sees 80 matches, more than
+    its 40-entry pool, so the overflow re-walk writes directly."""
+    T = np.full(50000, ord("A"), np.uint8)
+    T[777] = ord("C")
+    P = np.array([list(b"AAAAAAAA"), list(b"AAAAAAAA"), list(b"CAAAAAAA")], np.uint8)
+    want = oracle.brute(T, P)
+    assert want[0].size > 90000
+    for s in (_ac(P), _wm(P, 2)):
+        _same(s.scan(T), want, "all-A")
+        occ, cnt = s.scan(T, counts_only=True)
+        assert np.array_equal(cnt, want[1])
+        s.close()
+
+
+def test_unaligned_device_text():
+    T = synth.est_text(300000, 5)
+    P = synth.mixed_patterns(T, 300, 8, 5)
+    d = torch.from_numpy(T).cuda()
+    for off in (1, 3, 8, 15):
+        sub = d[off:]
+        want = oracle.dictionary(T[off:], P, threads=THREADS)
+        for s in (_ac(P), _wm(P, 3)):
+            _same(s.scan(sub), want, f"offset {off}")
+            s.close()
+
+
+@pytest.mark.parametrize("kw", [
+    {"placement": pm.PM_PLACE_HYBRID, "smem_table_bytes": 4096},
+    {"placement": pm.PM_PLACE_GLOBAL},
+    {"warps_per_cta": 8},
+    {"warps_per_cta": 12},
+    {"ctas_per_sm": 2, "warps_per_cta": 4},
+])
+def test_placements_and_launch_shapes_agree(kw):
+    T = synth.est_text(1 << 21, 6)
+    P = synth.mixed_patterns(T, 2000, 12, 6)
+    want = oracle.dictionary(T, P, threads=THREADS)
+    s = _ac(P, **kw)
+    _same(s.scan(T), want, str(kw))
+    s.close()
+
+
+def test_device_api_capacity_and_status():
+    T = synth.uniform_dna(1 << 20, 0)
+    P = synth.mixed_patterns(T, 100, 8, 0)
+    want_occ, want_cnt = oracle.brute(T, P)
+    s = _ac(P)
+    d_text = torch.from_numpy(T).cuda()
+    ws = torch.zeros(s.workspace_bytes(T.size), dtype=torch.uint8, device="cuda")
+    counts = torch.zeros(100, dtype=torch.int64, device="cuda")
+    nocc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cap = want_occ.size // 2
+    occ = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    pm.pm_scan_device(s.h, d_text, T.size, 0, counts, occ, cap, nocc, ws, ws.numel())
+    assert pm.pm_scan_status(ws) == pm.PM_OK
+    assert int(nocc.item()) == want_occ.size  # the total is exact even when truncated
+    assert np.array_equal(occ.cpu().numpy().view(np.uint64), want_occ[:cap])
+    assert np.array_equal(counts.cpu().numpy(), want_cnt)
+    s.close()
+
+
+def test_small_uniform_workload():
+    """1 MiB uniform ACGT, d=100, m=8 (50 copied from the text, 50 random);
+    AC and WM with B=2, bit-exact against the brute-force definition."""
+    T, P = synth.small_uniform_case()
+    want = oracle.brute(T, P)
+    for s in (_ac(P), _wm(P, 2)):
+        _same(s.scan(T), want, "1 MiB uniform")
+        s.close()
+
+
+# ---------------------------------------------------------------------------
+# EST-shaped workloads
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def est_text_full():
+    return synth.est_text(synth.EST_N, 1)
+
+
+@pytest.mark.parametrize("d", synth.EST_D)
+@pytest.mark.parametrize("m", synth.EST_M)
+def test_est_sets_on_64mib_prefix(est_text_full, d, m):
+    """Each (d, m) set of the EST workload, patterns drawn from the full text,
+    scanned over a 64 MiB prefix and compared with the oracle in full."""
+    _, P = synth.est_case(d, m, text=est_text_full)
+    T = est_text_full[: 64 << 20]
+    want = oracle.dictionary(T, P, threads=THREADS)
+    s = _ac(P)
+    _same(s.scan(T), want, f"AC d={d} m={m}")
+    s.close()
+    if d <= 8000 or m >= 16:   # WM at m=8, d=20000 checks every window; prefix kept short
+        s = _wm(P, 3)
+        Tw = T if d <= 8000 else T[: 16 << 20]
+        wantw = want if d <= 8000 else oracle.dictionary(Tw, P, threads=THREADS)
+        _same(s.scan(Tw), wantw, f"WM d={d} m={m}")
+        s.close()
+
+
+def _window_keys_total(d_text: "torch.Tensor", P: np.ndarray):
+    """Exact occurrence total and per-pattern counts of m=8 patterns by plain
+    torch ops: each window of 8 ACGT bytes -> 16-bit key -> multiplicity."""
+    m = P.shape[1]
+    assert m == 8
+    lut = torch.full((256,), -1, dtype=torch.int64, device=d_text.device)
+    for c, b in enumerate(b"ACGT"):
+        lut[b] = c
+    code = lut[d_text.long()]
+    n = code.numel()
+    key = torch.zeros(n - m + 1, dtype=torch.int64, device=d_text.device)
+    bad = torch.zeros(n - m + 1, dtype=torch.bool, device=d_text.device)
+    for j in range(m):
+        cj = code[j:n - m + 1 + j]
+        bad |= cj < 0
+        key = key * 4 + cj.clamp(min=0)
+    pk = np.zeros(P.shape[0], np.int64)
+    for j in range(m):
+        pk = pk * 4 + np.array([b"ACGT".index(bytes([x])) for x in P[:, j]])
+    mult = torch.zeros(1 << 16, dtype=torch.int64, device=d_text.device)
+    mult.index_add_(0, torch.from_numpy(pk).cuda(), torch.ones(P.shape[0], dtype=torch.int64, device="cuda"))
+    hist = torch.bincount(key[~bad], minlength=1 << 16)
+    total = int((hist * mult).sum().item())
+    per_pattern = hist[torch.from_numpy(pk).cuda()].cpu().numpy()
+    return total, per_pattern
+
+
+def test_full_size_headline_in_bench_configuration(est_text_full):
+    """1 GiB EST text, d=8000, m=8, AC list mode through pm_scan_device with the
+    default plan -- the launch bench.py times."""
+    T = est_text_full
+    _, P = synth.est_case(8000, 8, text=T)
+    s = _ac(P)
+    d_text = torch.from_numpy(T).cuda()
+    n = T.size
+    ws = torch.zeros(s.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    counts = torch.zeros(P.shape[0], dtype=torch.int64, device="cuda")
+    nocc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cap = n // 4
+    occ = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    pm.pm_scan_device(s.h, d_text, n, 0, counts, occ, cap, nocc, ws, ws.numel())
+    assert pm.pm_scan_status(ws) == pm.PM_OK
+    total = int(nocc.item())
+    assert 0 < total <= cap
+    occ = occ[:total]
+
+    # exact total and counts from an independent computation over every window
+    want_total, want_counts = _window_keys_total(d_text, P)
+    assert total == want_total
+    assert np.array_equal(counts.cpu().numpy(), want_counts)
+
+    # every reported pair is an occurrence; keys strictly increasing
+    u = occ.view(torch.int64)
+    assert bool((u[1:] > u[:-1]).all())
+    i = (u >> 32)
+    r = (u & 0xFFFFFFFF)
+    Pd = torch.from_numpy(P).cuda()
+    for j in range(8):
+        assert bool((d_text[i + j] == Pd[r, j]).all())
+
+    # sampled windows against the oracle, element by element
+    rng = np.random.default_rng(8000)
+    occ_np = occ.cpu().numpy().view(np.uint64)
+    starts = occ_np >> np.uint64(32)
+    W = 1 << 18
+    for a in rng.integers(0, n - W, 24):
+        a = int(a)
+        wo, _ = oracle.dictionary(T[a:a + W + 7], P, threads=THREADS)
+        wi, wr = oracle.unpack(wo)
+        keep = wi < W
+        want = ((wi[keep] + a).astype(np.uint64) << np.uint64(32)) | wr[keep].astype(np.uint64)
+        lo = np.searchsorted(starts, a)
+        hi = np.searchsorted(starts, a + W)
+        assert np.array_equal(occ_np[lo:hi], want), f"window at {a}"
+    s.close()
