@@ -148,6 +148,8 @@ def parse():
     ap.add_argument("--m", type=int, default=8)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--mode", default="list", choices=["list", "counts"],
+                    help="timed step: list mode (default) or counts only")
     ap.add_argument("--text-mib", type=int, default=0,
                     help="scan only this many MiB of the text (profiling captures); 0 = all 1 GiB")
     return ap.parse_args()
@@ -225,6 +227,8 @@ def main():
     counts = torch.zeros(d, dtype=torch.int64, device="cuda")
     nocc = torch.zeros(1, dtype=torch.int64, device="cuda")
 
+    step_flags = pm.PM_COUNTS_ONLY if args.mode == "counts" else 0
+
     def launch(h, occ_buf, cap, flags=0, wsb=ws):
         pm.pm_scan_device(h, d_text, n, flags, counts, occ_buf, cap, nocc, wsb, wsb.numel(), stream)
 
@@ -236,7 +240,7 @@ def main():
         total = int(nocc.item())
         occ = torch.empty(max(total, 1), dtype=torch.int64, device="cuda")
         for _ in range(max(args.warmup, 3)):
-            launch(s.h, occ, occ.numel())
+            launch(s.h, occ, occ.numel(), step_flags)
         stream.synchronize()
         assert pm.pm_scan_status(ws, stream) == pm.PM_OK
 
@@ -253,7 +257,7 @@ def main():
         t_all0.record(stream)
         for k in range(args.steps):
             starts[k].record(stream)
-            launch(s.h, occ, occ.numel())
+            launch(s.h, occ, occ.numel(), step_flags)
             ends[k].record(stream)
         t_all1.record(stream)
     torch.cuda.synchronize()
@@ -273,7 +277,7 @@ def main():
 
     peak, peak_kind = measured_peaks()
     avg_launch_s = statistics.mean(per_launch) / 1e3
-    alg_bytes = n + 8 * n_occ + 8 * d
+    alg_bytes = n + 8 * d + (8 * n_occ if args.mode == "list" else 0)
     achieved = alg_bytes / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
@@ -285,19 +289,24 @@ def main():
     if rank == 0 and not args.no_extras:
         extras = secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, torch, synth)
 
-    # end to end: pm_scan from pinned host text, results read back to the host
+    # end to end through the public API: pinned host text in, pinned host
+    # counts and occurrence list out (pm_scan_to_host), copies inside the timing
     e2e = None
     if rank == 0:
         pinned = torch.from_numpy(T).pin_memory()
-        s.scan(pinned.numpy())  # sizes the library's cached buffers
-        reps = 3
+        h_counts = torch.empty(d, dtype=torch.int64).pin_memory()
+        h_occ = torch.empty(max(n_occ, 1), dtype=torch.int64).pin_memory()
+        flags_e2e = pm.PM_COUNTS_ONLY if args.mode == "counts" else 0
+        pm.pm_scan_to_host(s.h, pinned, h_counts, h_occ, flags_e2e, stream)  # sizes caches
+        reps = 5
         t0 = time.perf_counter()
         for _ in range(reps):
-            o, c = pm.pm_scan(s.h, pinned.numpy(), pm.PM_HOST_TEXT, stream)
+            got = pm.pm_scan_to_host(s.h, pinned, h_counts, h_occ, flags_e2e, stream)
         dt = (time.perf_counter() - t0) / reps
-        assert o.size == n_occ
+        assert got == n_occ
         e2e = {"value": n / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": n,
-               "d2h_bytes_per_step": 8 * n_occ + 8 * d + 8, "api": "pm_scan (host text)"}
+               "d2h_bytes_per_step": (8 * n_occ if args.mode == "list" else 0) + 8 * d + 8,
+               "api": "pm_scan_to_host (pinned host text and results)"}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -310,8 +319,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"EST-shaped 1 GiB text (seed 1), Aho-Corasick DFA, list mode, d={d}, m={args.m} (half copied from the text, half random)",
-                       "text_bytes": n, "d": d, "m": args.m, "algo": "AC", "mode": "list",
+            "config": {"workload": f"EST-shaped 1 GiB text (seed 1), Aho-Corasick DFA, {args.mode} mode, d={d}, m={args.m} (half copied from the text, half random)",
+                       "text_bytes": n, "d": d, "m": args.m, "algo": "AC", "mode": args.mode,
                        "n_occ": n_occ, "l2": "inputs larger than L2 (1 GiB text), no flush",
                        "parallelism": f"replicas x{world}",
                        "table": {k: info[k] for k in ("n_rows", "entry_bytes", "placement", "smem_rows", "table_bytes")}},
@@ -355,6 +364,7 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
             _, Pq = synth.est_case(dd, mm, text=T)
             q = pm.PatternSet.ac(Pq)
             cnt_q = torch.zeros(dd, dtype=torch.int64, device="cuda")
+            ws = torch.zeros(q.workspace_bytes(n), dtype=torch.uint8, device="cuda")
             with torch.cuda.stream(stream):
                 pm.pm_scan_device(q.h, d_text, n, pm.PM_COUNTS_ONLY, cnt_q, None, 0, nocc, ws, ws.numel(), stream)
             stream.synchronize()

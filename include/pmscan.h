@@ -145,6 +145,18 @@ int pm_scan(const pm_set *s, const uint8_t *T, int64_t n, uint32_t flags,
 void pm_result_free(pm_result *r);
 
 /*
+ * pm_scan with caller-owned host result buffers (page-locked buffers give
+ * full-speed device-to-host copies; T may be page-locked for the same
+ * reason). counts_out: int64[d]; occ_out: uint64[occ_capacity] (may be NULL
+ * with PM_COUNTS_ONLY). *n_occ_out receives the total; when it exceeds
+ * occ_capacity only the first occ_capacity keys are written and the call
+ * returns PM_ECAPACITY. Synchronous.
+ */
+int pm_scan_to_host(const pm_set *s, const uint8_t *T, int64_t n, uint32_t flags,
+                    int64_t *counts_out, uint64_t *occ_out, int64_t occ_capacity,
+                    int64_t *n_occ_out, void *stream);
+
+/*
  * Device-level scan with caller-owned device buffers (e.g. torch tensors),
  * enqueued on `stream`; nothing is allocated and nothing synchronises.
  *   d_text       device text, n bytes (any alignment; 16-byte aligned is fastest)

@@ -17,9 +17,18 @@ void set_cuda_error(int e) { g_last_cuda = e; }
 
 int64_t warp_tiles(int64_t n) { return n <= 0 ? 0 : (n + kWarpTile - 1) / kWarpTile; }
 
-int64_t workspace_bytes_for(int64_t n, bool list)
+static int64_t round16(int64_t x) { return (x + 15) & ~int64_t(15); }
+
+int64_t zeroed_workspace_bytes(int64_t tiles, bool list, int64_t n_terms)
 {
-    return kWsHeader + (list ? warp_tiles(n) * int64_t(8) : 0);
+    int64_t b = kWsHeader + round16(n_terms * 8);
+    if (list) b += round16(tiles * 24);   // tile status, super sums, super prefixes
+    return b;
+}
+
+int64_t workspace_bytes_for(int64_t tiles, bool list, int64_t n_terms, int64_t scratch_bytes)
+{
+    return zeroed_workspace_bytes(tiles, list, n_terms) + (list ? round16(scratch_bytes) : 0);
 }
 
 int device_props(DeviceProps &p)
@@ -93,7 +102,8 @@ void free_dev(void *&p)
 
 void release_device(pm_set *s)
 {
-    void *ptrs[] = {s->dac.table, s->dac.mid, s->dac.grp_off, s->dac.grp_ids, s->dac.cls,
+    void *ptrs[] = {s->dac.table, s->dac.flag_mask, s->dac.flag_rank, s->dac.canon,
+                    s->dac.grp_off, s->dac.grp_ids, s->dac.cls,
                     s->dwm.shift, s->dwm.hoff, s->dwm.hids, s->dwm.hpfx, s->dwm.pats,
                     s->c_text, s->c_ws, s->c_out, s->c_counts};
     for (void *p : ptrs)
@@ -118,7 +128,21 @@ int upload_ac(pm_set *s)
     } else {
         rc = upload(&d.table, t.table.data(), t.table.size() * 4, tot);
     }
-    if (!rc) rc = upload(reinterpret_cast<void **>(&d.mid), t.mid.data(), t.mid.size() * 4, tot);
+    if (!rc)
+        rc = upload(reinterpret_cast<void **>(&d.flag_mask), t.flag_mask.data(), t.flag_mask.size() * 4, tot);
+    if (!rc) {
+        if (eb == 2) {
+            std::vector<uint16_t> r16v(t.flag_rank.begin(), t.flag_rank.end());
+            std::vector<uint16_t> c16v(t.canon.size());
+            for (size_t i = 0; i < t.canon.size(); ++i)
+                c16v[i] = uint16_t((t.canon[i] & 0x80000000u) ? (0x8000u | (t.canon[i] & 0x7FFFu)) : t.canon[i]);
+            rc = upload(&d.flag_rank, r16v.data(), r16v.size() * 2, tot);
+            if (!rc) rc = upload(&d.canon, c16v.data(), c16v.size() * 2, tot);
+        } else {
+            rc = upload(&d.flag_rank, t.flag_rank.data(), t.flag_rank.size() * 4, tot);
+            if (!rc) rc = upload(&d.canon, t.canon.data(), t.canon.size() * 4, tot);
+        }
+    }
     if (!rc)
         rc = upload(reinterpret_cast<void **>(&d.grp_off), t.grp_off.data(), t.grp_off.size() * 4, tot);
     if (!rc)
@@ -179,18 +203,44 @@ int ensure(void *&p, int64_t &cap, int64_t bytes)
     return PM_OK;
 }
 
-pm_result *new_result(int64_t d, int64_t n_occ, bool list)
+// A result and how its arrays were allocated; the public struct comes first
+// so a pm_result* is also a ResultBox*.
+struct ResultBox {
+    pm_result pub;
+    int pinned;
+};
+
+void free_array(void *p, int pinned)
 {
-    pm_result *r = static_cast<pm_result *>(std::calloc(1, sizeof(pm_result)));
-    if (!r) return nullptr;
+    if (!p) return;
+    if (pinned) cudaFreeHost(p);
+    else std::free(p);
+}
+
+// pinned = page-locked host arrays (device-to-host copies at full link speed)
+pm_result *new_result(int64_t d, int64_t n_occ, bool list, bool pinned)
+{
+    ResultBox *b = static_cast<ResultBox *>(std::calloc(1, sizeof(ResultBox)));
+    if (!b) return nullptr;
+    pm_result *r = &b->pub;
+    b->pinned = pinned ? 1 : 0;
     r->d = d;
     r->n_occ = n_occ;
-    r->counts = static_cast<int64_t *>(std::calloc(size_t(d > 0 ? d : 1), sizeof(int64_t)));
-    if (list) r->occ = static_cast<uint64_t *>(std::malloc(size_t(n_occ > 0 ? n_occ : 1) * 8));
+    const size_t cb = size_t(d > 0 ? d : 1) * sizeof(int64_t);
+    const size_t ob = size_t(n_occ > 0 ? n_occ : 1) * 8;
+    if (pinned) {
+        void *c = nullptr, *o = nullptr;
+        if (cudaMallocHost(&c, cb) == cudaSuccess) r->counts = static_cast<int64_t *>(c);
+        if (list && cudaMallocHost(&o, ob) == cudaSuccess) r->occ = static_cast<uint64_t *>(o);
+        cudaGetLastError();
+    } else {
+        r->counts = static_cast<int64_t *>(std::calloc(cb / 8, 8));
+        if (list) r->occ = static_cast<uint64_t *>(std::malloc(ob));
+    }
     if (!r->counts || (list && !r->occ)) {
-        std::free(r->counts);
-        std::free(r->occ);
-        std::free(r);
+        free_array(r->counts, b->pinned);
+        free_array(r->occ, b->pinned);
+        std::free(b);
         return nullptr;
     }
     return r;
@@ -298,10 +348,34 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
     return PM_OK;
 }
 
+static int64_t set_terms(const pm_set *s)
+{
+    return s->algo == PM_ALGO_AC ? int64_t(s->ac.canon.size()) : 0;
+}
+
+// list-mode scratch: two slots of one warp tile of entries per warp
+static int64_t set_scratch(const pm_set *s)
+{
+    if (s->algo != PM_ALGO_AC) return 0;
+    const int64_t se = (s->ac.dna ? s->ac.entry_bytes : 4) == 2 ? 4 : 8;
+    return s->dac.max_warps * 2 * int64_t(s->dac.ksub) * kWarpTile * se;
+}
+
+static int64_t set_tiles(const pm_set *s, int64_t n)
+{
+    const int64_t k = s->algo == PM_ALGO_AC ? s->dac.ksub : 1;
+    return (warp_tiles(n) + k - 1) / k;
+}
+
+static int64_t set_ws_bytes(const pm_set *s, int64_t n, bool list)
+{
+    return workspace_bytes_for(set_tiles(s, n), list, set_terms(s), set_scratch(s));
+}
+
 int64_t pm_scan_workspace_bytes(const pm_set *s, int64_t n, uint32_t flags)
 {
     if (!s || n < 0) return -1;
-    return workspace_bytes_for(n, !(flags & PM_COUNTS_ONLY));
+    return set_ws_bytes(s, n, !(flags & PM_COUNTS_ONLY));
 }
 
 int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags,
@@ -315,7 +389,7 @@ int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t f
     const bool list = !(flags & PM_COUNTS_ONLY);
     if (list && occ_capacity > 0 && !d_occ) return PM_EINVAL;
     if (occ_capacity < 0) return PM_EINVAL;
-    if (workspace_bytes < workspace_bytes_for(n, list)) return PM_EINVAL;
+    if (workspace_bytes < set_ws_bytes(s, n, list)) return PM_EINVAL;
     if (s->algo == PM_ALGO_AC)
         return ac_launch(s->ac, s->dac, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
                          d_workspace, stream);
@@ -337,13 +411,15 @@ int pm_scan_status(const void *d_workspace, void *stream)
     return status ? PM_ETIMEOUT : PM_OK;
 }
 
-int pm_scan(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flags, void *stream,
-            pm_result **out)
+}  // extern "C"
+
+namespace pm {
+namespace {
+// Runs a scan of host or device text into the set's cached device buffers.
+// On success d_counts/d_occ point at the device results and n_occ is known.
+int scan_cached(pm_set *s, const uint8_t *T, int64_t n, uint32_t flags, void *stream,
+                int64_t **d_counts_out, int64_t *n_occ_out)
 {
-    if (!cs || !out || n < 0 || (n > 0 && !T)) return PM_EINVAL;
-    if (cs->host_only) return PM_EINVAL;
-    if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
-    pm_set *s = const_cast<pm_set *>(cs);  // device caches only
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool list = !(flags & PM_COUNTS_ONLY);
     const int64_t d = set_d(s);
@@ -356,19 +432,15 @@ int pm_scan(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flags, void 
         if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
         d_text = static_cast<const uint8_t *>(s->c_text);
     }
-    const int64_t wsb = workspace_bytes_for(n, list);
+    const int64_t wsb = set_ws_bytes(s, n, list);
     rc = ensure(s->c_ws, s->c_ws_cap, wsb);
-    if (!rc) {
-        int64_t tmp = 0;
-        if (!s->c_counts) {
-            void *p = nullptr;
-            cudaError_t e = cudaMalloc(&p, size_t(d + 1) * 8);
-            if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); return PM_ENOMEM; }
-            s->c_counts = p;
-        }
-        (void)tmp;
-    }
     if (rc) return rc;
+    if (!s->c_counts) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, size_t(d + 1) * 8);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); return PM_ENOMEM; }
+        s->c_counts = p;
+    }
     int64_t *d_counts = static_cast<int64_t *>(s->c_counts);
     int64_t *d_nocc = d_counts + d;
     int64_t n_occ = 0;
@@ -390,7 +462,28 @@ int pm_scan(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flags, void 
         if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
         if (!list || n_occ <= cap) break;
     }
-    pm_result *r = new_result(d, n_occ, list);
+    *d_counts_out = d_counts;
+    *n_occ_out = n_occ;
+    return PM_OK;
+}
+}  // namespace
+}  // namespace pm
+
+extern "C" {
+
+int pm_scan(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flags, void *stream,
+            pm_result **out)
+{
+    if (!cs || !out || n < 0 || (n > 0 && !T)) return PM_EINVAL;
+    if (cs->host_only) return PM_EINVAL;
+    if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
+    pm_set *s = const_cast<pm_set *>(cs);  // device caches only
+    const bool list = !(flags & PM_COUNTS_ONLY);
+    const int64_t d = set_d(s);
+    int64_t *d_counts = nullptr, n_occ = 0;
+    int rc = scan_cached(s, T, n, flags, stream, &d_counts, &n_occ);
+    if (rc) return rc;
+    pm_result *r = new_result(d, n_occ, list, false);
     if (!r) return PM_ENOMEM;
     cudaError_t e = cudaMemcpy(r->counts, d_counts, size_t(d) * 8, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && list && n_occ > 0)
@@ -404,12 +497,36 @@ int pm_scan(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flags, void 
     return PM_OK;
 }
 
+int pm_scan_to_host(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flags,
+                    int64_t *counts_out, uint64_t *occ_out, int64_t occ_capacity,
+                    int64_t *n_occ_out, void *stream)
+{
+    if (!cs || !counts_out || !n_occ_out || n < 0 || (n > 0 && !T) || occ_capacity < 0)
+        return PM_EINVAL;
+    const bool list = !(flags & PM_COUNTS_ONLY);
+    if (list && occ_capacity > 0 && !occ_out) return PM_EINVAL;
+    if (cs->host_only) return PM_EINVAL;
+    if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
+    pm_set *s = const_cast<pm_set *>(cs);
+    const int64_t d = set_d(s);
+    int64_t *d_counts = nullptr, n_occ = 0;
+    int rc = scan_cached(s, T, n, flags, stream, &d_counts, &n_occ);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpy(counts_out, d_counts, size_t(d) * 8, cudaMemcpyDeviceToHost);
+    const int64_t k = list ? (n_occ < occ_capacity ? n_occ : occ_capacity) : 0;
+    if (e == cudaSuccess && k > 0) e = cudaMemcpy(occ_out, s->c_out, size_t(k) * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    *n_occ_out = n_occ;
+    return (list && n_occ > occ_capacity) ? PM_ECAPACITY : PM_OK;
+}
+
 void pm_result_free(pm_result *r)
 {
     if (!r) return;
-    std::free(r->counts);
-    std::free(r->occ);
-    std::free(r);
+    ResultBox *b = reinterpret_cast<ResultBox *>(r);
+    free_array(r->counts, b->pinned);
+    free_array(r->occ, b->pinned);
+    std::free(b);
 }
 
 int pm_scan_batch(const pm_set *const *sets, const uint8_t *const *texts, const int64_t *ns,
@@ -435,7 +552,7 @@ int pm_selfcheck_host_walk(const pm_set *s, const uint8_t *T, int64_t n, pm_resu
         std::vector<int64_t> counts;
         if (s->algo == PM_ALGO_AC) host_walk_ac(s->ac, T, n, occ, counts);
         else host_walk_wm(s->wm, T, n, occ, counts);
-        pm_result *r = new_result(int64_t(counts.size()), int64_t(occ.size()), true);
+        pm_result *r = new_result(int64_t(counts.size()), int64_t(occ.size()), true, false);
         if (!r) return PM_ENOMEM;
         if (!occ.empty()) std::memcpy(r->occ, occ.data(), occ.size() * 8);
         std::memcpy(r->counts, counts.data(), counts.size() * 8);

@@ -190,7 +190,25 @@ int build_ac(const uint8_t *P, int64_t d, int32_t m, AcTables &t)
                 t.table[size_t(row << t.lw) + size_t(c)] = e;
             }
         }
-        const bool fits16 = rows <= 32768 && ((rows - t.d0_row) << t.lw) <= 65536;
+        // canonical terminal ids = rank of the match entry
+        const size_t nflag = size_t(rows - t.d0_row) << t.lw;
+        const size_t nwords = (nflag + 31) / 32;
+        t.flag_mask.assign(nwords, 0u);
+        t.flag_rank.assign(nwords + 1, 0u);
+        t.canon.clear();
+        for (size_t k = 0; k < nflag; ++k) {
+            if (t.mid[k] != 0xFFFFFFFFu) {
+                t.flag_mask[k >> 5] |= 1u << (k & 31);
+                t.canon.push_back(t.mid[k]);
+            }
+        }
+        for (size_t w = 0; w < nwords; ++w)
+            t.flag_rank[w + 1] = t.flag_rank[w] + uint32_t(__builtin_popcount(t.flag_mask[w]));
+        // 16-bit entries: rows and pool codes (pattern id or group | 0x8000)
+        // must fit in 15 bits, table indices of match rows and terminal
+        // ranks in 16
+        const bool fits16 = rows <= 32768 && nflag <= 65536 && d < 32768 &&
+                            t.grp_off.size() <= 32768 && t.canon.size() < 65536;
         t.entry_bytes = fits16 ? 2 : 4;
         return PM_OK;
     } catch (const std::bad_alloc &) {

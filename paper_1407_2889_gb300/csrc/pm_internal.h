@@ -44,6 +44,16 @@ struct AcTables {
     std::vector<uint32_t> grp_off; // groups of >= 2 equal patterns
     std::vector<uint32_t> grp_ids;
     std::vector<int32_t> row_depth; // depth of each row's state (row 0: 0)
+    // Canonical terminal ids: each terminal state is entered by exactly one
+    // table entry (the trie edge into it), so numbering terminals in the
+    // order of those entries makes a terminal's id the rank of its entry
+    // among the match entries. flag_mask has one bit per entry of the match
+    // rows (from d0_row on), flag_rank the number of set bits before each
+    // 32-entry word, canon[c] the pattern id of terminal c, or
+    // 0x80000000 | group when several patterns are equal.
+    std::vector<uint32_t> flag_mask;
+    std::vector<uint32_t> flag_rank;
+    std::vector<uint32_t> canon;
 };
 
 // ---------------------------------------------------------------------------
@@ -85,17 +95,22 @@ struct WmLaunch;
 // Everything a launcher needs about the device copy of a set.
 struct DevAc {
     void *table = nullptr;          // entry_bytes * (n_rows << lw)
-    uint32_t *mid = nullptr;
     uint32_t *grp_off = nullptr;
     uint32_t *grp_ids = nullptr;
     uint8_t *cls = nullptr;         // 256 bytes
+    uint32_t *flag_mask = nullptr;
+    void *flag_rank = nullptr;      // u16 or u32 per mask word (entry_bytes)
+    void *canon = nullptr;          // u16 or u32 per terminal (entry_bytes)
     int64_t smem_entries = 0;       // table entries copied to shared memory
     int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0, stage_cap = 0;
-    int32_t hist_smem = 0;          // per-pattern counters in shared memory
+    int32_t hist_smem = 0;          // per-terminal counters in shared memory
+    int32_t ids_smem = 0;           // rank structure and canon in shared memory
     int32_t nv = 0, hv = 0;         // register text vectors (chunk + halo)
     int32_t variant = 0;            // kernel instance id
     int64_t smem_bytes = 0;
     int32_t placement = 0;
+    int64_t max_warps = 0;          // warps in the largest grid a launch uses
+    int32_t ksub = 1;               // warp tiles per look-back tile
 };
 
 struct DevWm {
@@ -109,11 +124,17 @@ struct DevWm {
     int64_t smem_bytes = 0;
 };
 
-// Workspace layout (device scratch): [status word u32 | pad] [n_occ u64]
-// [tile status u64 x tiles]. Zeroed by the launcher before each scan.
+// Workspace (device scratch), zeroed by the launcher before each scan:
+//   [header 256 B] [per-terminal counts u64 x n_terms]
+//   list mode only: [tile status u64 x tiles] [super-tile sums u64 x tiles]
+//                   [super-tile prefixes u64 x tiles]  (super-tiles <= tiles)
+//                   [Aho-Corasick: per-warp scratch slots, not zeroed]
 constexpr int64_t kWsHeader = 256;
 int64_t warp_tiles(int64_t n);
-int64_t workspace_bytes_for(int64_t n, bool list);
+// scratch_per_warp: bytes of list-mode scratch per warp of the largest grid
+// (tiles = look-back tiles; scratch_bytes = list-mode scratch of the largest grid)
+int64_t workspace_bytes_for(int64_t tiles, bool list, int64_t n_terms, int64_t scratch_bytes);
+int64_t zeroed_workspace_bytes(int64_t tiles, bool list, int64_t n_terms);
 
 struct DeviceProps {
     int sm_count = 0;

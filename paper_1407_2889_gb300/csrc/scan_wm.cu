@@ -37,7 +37,7 @@ struct WmArgs {
     long long occ_cap;
     long long *n_occ;
     dev::WsHeader *ws;
-    unsigned long long *tile_status;
+    dev::LookbackRefs lb;
 };
 
 __host__ __device__ constexpr int r16w(long long x) { return int((x + 15) & ~15LL); }
@@ -142,13 +142,13 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
     uint32_t *pl = pool + lane;
     const uint32_t cap = uint32_t(a.pool_cap);
     const int m = a.m;
-    dev::TileCursor cur;
-    long long t = cur.claim(a.ws, lane, a.ntiles);
+    dev::TileSchedule sch;
+    sch.init(a.ntiles);
     uint32_t phase = 0;
     unsigned long long my_total = 0;
-    if (t >= 0 && lane == 0) wm_stage_issue(a, t, buf, bar);
+    if (sch.cur >= 0 && lane == 0) wm_stage_issue(a, sch.cur, buf, bar);
 
-    while (t >= 0) {
+    for (long long t = sch.cur; t >= 0; t = sch.next_of(t)) {
         const bool got = __all_sync(kFull, dev::mbar_wait_bounded(bar, phase));
         if (!got) {
             if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutTma);
@@ -195,17 +195,13 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
             const uint32_t incl = dev::warp_incl_scan(cnt, lane);
             const uint32_t excl = incl - cnt;
             const uint32_t wtot = __shfl_sync(kFull, incl, 31);
-            unsigned long long base = 0;
-            int okl = 1;
-            if (lane == 0) {
-                bool ok;
-                base = dev::lookback(a.tile_status, t, wtot, ok);
-                okl = ok;
-                if (!ok) dev::set_status(a.ws, dev::kErrTimeoutLookback);
-                if (t == a.ntiles - 1) *a.n_occ = (long long)(base + wtot);
+            bool ok;
+            const unsigned long long base = dev::lookback(a.lb, t, wtot, lane, ok);
+            if (!ok) {
+                if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutLookback);
+                break;
             }
-            base = __shfl_sync(kFull, base, 0);
-            if (!__shfl_sync(kFull, okl, 0)) break;
+            if (lane == 0 && t == a.ntiles - 1) *a.n_occ = (long long)(base + wtot);
             if (!__any_sync(kFull, ovf)) {
                 uint32_t k = 0, my = excl;
                 const uint32_t S = uint32_t(a.stage_cap);
@@ -247,12 +243,10 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
             }
         }
 
-        // the buffer is free: claim and stage the next tile
-        const long long tn = cur.next(a.ws, lane, a.ntiles);
+        // the buffer is free: stage the next tile
         dev::fence_proxy_async_smem();
         __syncwarp();
-        if (tn >= 0 && lane == 0) wm_stage_issue(a, tn, buf, bar);
-        t = tn;
+        if (sch.next_of(t) >= 0 && lane == 0) wm_stage_issue(a, sch.next_of(t), buf, bar);
     }
 
     if (!a.list) {
@@ -318,7 +312,7 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
     if (e == cudaSuccess)
-        e = cudaMemsetAsync(d_ws, 0, size_t(workspace_bytes_for(n, list)), st);
+        e = cudaMemsetAsync(d_ws, 0, size_t(zeroed_workspace_bytes(ntiles, list, 0)), st);
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (n < t.m || ntiles == 0) return PM_OK;
 
@@ -359,14 +353,22 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     a.occ = reinterpret_cast<unsigned long long *>(d_occ);
     a.occ_cap = list ? occ_cap : 0;
     a.n_occ = reinterpret_cast<long long *>(d_n_occ);
-    a.ws = reinterpret_cast<dev::WsHeader *>(d_ws);
-    a.tile_status = reinterpret_cast<unsigned long long *>(static_cast<char *>(d_ws) + kWsHeader);
+    char *w = static_cast<char *>(d_ws);
+    a.ws = reinterpret_cast<dev::WsHeader *>(w);
+    a.lb.tile_st = reinterpret_cast<unsigned long long *>(w + kWsHeader);
+    a.lb.super_acc = reinterpret_cast<unsigned long long *>(w + kWsHeader + ntiles * 8);
+    a.lb.super_pre = reinterpret_cast<unsigned long long *>(w + kWsHeader + ntiles * 16);
+    a.lb.ntiles = ntiles;
 
-    long long want = (ntiles + (long long)dv.warps * dev::kClaimBatch - 1) /
-                     ((long long)dv.warps * dev::kClaimBatch);
-    long long grid = (long long)dp.sm_count * dv.ctas_per_sm;
+    // the static tile schedule needs every CTA of the grid resident at once
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, dv.warps * 32, size_t(dv.smem_bytes));
+    if (e != cudaSuccess || per_sm < 1) { set_cuda_error(int(e)); return PM_ECUDA; }
+    long long grid = (long long)dp.sm_count * std::min(per_sm, dv.ctas_per_sm);
+    const long long want = (ntiles + dv.warps - 1) / dv.warps;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
+    a.lb.super_tiles = dev::super_size_for(grid * dv.warps);
     fn<<<dim3(unsigned(grid)), dim3(unsigned(dv.warps * 32)), size_t(dv.smem_bytes), st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }

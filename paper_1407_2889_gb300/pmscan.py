@@ -27,7 +27,7 @@ PM_ALGO_AC, PM_ALGO_WM = 1, 2
 
 EXPORTED = [
     "pm_ac_compile", "pm_wm_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
-    "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device", "pm_scan_status",
+    "pm_scan_to_host", "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device", "pm_scan_status",
     "pm_scan_batch", "pm_selfcheck_host_walk", "pm_strerror", "pm_last_cuda_error",
     "pm_version",
 ]
@@ -96,6 +96,8 @@ def lib():
         L.pm_set_get_info.argtypes = [vp, ctypes.POINTER(pm_set_info)]
         L.pm_scan.restype = ctypes.c_int
         L.pm_scan.argtypes = [vp, vp, i64, u32, vp, ctypes.POINTER(ctypes.POINTER(pm_result))]
+        L.pm_scan_to_host.restype = ctypes.c_int
+        L.pm_scan_to_host.argtypes = [vp, vp, i64, u32, vp, vp, i64, ctypes.POINTER(i64), vp]
         L.pm_result_free.restype = None
         L.pm_result_free.argtypes = [ctypes.POINTER(pm_result)]
         L.pm_scan_workspace_bytes.restype = i64
@@ -222,6 +224,33 @@ def pm_scan(h: int, T, flags: int = PM_HOST_TEXT, stream=None):
         ptr, n = T.ctypes.data, T.size
     _check(lib().pm_scan(h, ptr, n, flags, _stream_ptr(stream), ctypes.byref(rp)), "pm_scan")
     return _take_result(rp)
+
+
+def pm_scan_to_host(h: int, T, counts_out, occ_out, flags: int = PM_HOST_TEXT, stream=None) -> int:
+    """Scan into caller-owned host arrays (numpy, or pinned torch CPU tensors).
+    Returns the total number of occurrences; raises PmError(PM_ECAPACITY) if
+    occ_out was too small (its first len(occ_out) keys are still written)."""
+    if flags & PM_DEVICE_TEXT:
+        ptr, n = _dev_ptr(T), int(T.numel())
+    elif hasattr(T, "data_ptr"):
+        ptr, n = int(T.data_ptr()), int(T.numel())
+    else:
+        T = np.ascontiguousarray(T, dtype=np.uint8)
+        ptr, n = T.ctypes.data, T.size
+
+    def host_ptr(x):
+        if x is None:
+            return 0, 0
+        if hasattr(x, "data_ptr"):
+            return int(x.data_ptr()), int(x.numel())
+        return x.ctypes.data, x.size
+
+    cp, _ = host_ptr(counts_out)
+    op, cap = host_ptr(occ_out)
+    total = ctypes.c_int64(0)
+    rc = lib().pm_scan_to_host(h, ptr, n, flags, cp, op, cap, ctypes.byref(total), _stream_ptr(stream))
+    _check(rc, "pm_scan_to_host")
+    return int(total.value)
 
 
 def pm_scan_workspace_bytes(h: int, n: int, flags: int = PM_HOST_TEXT) -> int:

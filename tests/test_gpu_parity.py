@@ -276,3 +276,23 @@ def test_full_size_headline_in_bench_configuration(est_text_full):
         hi = np.searchsorted(starts, a + W)
         assert np.array_equal(occ_np[lo:hi], want), f"window at {a}"
     s.close()
+
+
+def test_scan_to_host_pinned_buffers_and_capacity():
+    T = synth.est_text(1 << 21, 9)
+    P = synth.mixed_patterns(T, 500, 8, 9)
+    want_occ, want_cnt = oracle.dictionary(T, P, threads=THREADS)
+    s = _ac(P)
+    pinned = torch.from_numpy(T).pin_memory()
+    counts = torch.zeros(500, dtype=torch.int64).pin_memory()
+    occ = torch.zeros(want_occ.size, dtype=torch.int64).pin_memory()
+    total = pm.pm_scan_to_host(s.h, pinned, counts, occ)
+    assert total == want_occ.size
+    assert np.array_equal(occ.numpy().view(np.uint64), want_occ)
+    assert np.array_equal(counts.numpy(), want_cnt)
+    small = torch.zeros(10, dtype=torch.int64)
+    with pytest.raises(pm.PmError) as e:
+        pm.pm_scan_to_host(s.h, T, counts, small)
+    assert e.value.code == pm.PM_ECAPACITY
+    assert np.array_equal(small.numpy().view(np.uint64), want_occ[:10])
+    s.close()
