@@ -176,6 +176,32 @@ int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t f
                    int64_t *d_n_occ, void *d_workspace, int64_t workspace_bytes,
                    void *stream);
 
+/*
+ * Allocation-free Aho-Corasick scan. The paper has no counterpart: this is
+ * for callers that cannot allocate device memory when they scan -- a host
+ * application that owns the GPU allocator and must account for every
+ * allocation, or a latency-bound loop that reserved all of its memory up
+ * front and must not call cudaMalloc (which can block on the device and
+ * fail under fragmentation). It computes what pm_scan_device computes (same
+ * arguments, no workspace) with its scratch in one fixed device array of
+ * pm_noalloc_scratch_bytes() bytes (64 MiB) inside the library, reserved on
+ * every GPU that loads the library until the process exits. Nothing is
+ * allocated: no cudaMalloc, cudaFree or allocating library call.
+ *   - Only Aho-Corasick sets (PM_EINVAL for Wu-Manber).
+ *   - PM_ETOOBIG when the scan would need more scratch than the array holds
+ *     (large texts in list mode, or very large pattern sets); nothing runs.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture begins.
+ *   - Every call uses the same array, which keeps the last call's contents
+ *     (the call clears what must start at zero). Calls whose work overlaps
+ *     on the GPU -- other streams, other host threads -- race on it: run
+ *     them one after another.
+ */
+int pm_scan_device_noalloc(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags,
+                           int64_t *d_counts, uint64_t *d_occ, int64_t occ_capacity,
+                           int64_t *d_n_occ, void *stream);
+int64_t pm_noalloc_scratch_bytes(void);
+
 /* Synchronise `stream` and read the device status word of the last
  * pm_scan_device on this workspace: PM_OK or PM_ETIMEOUT. */
 int pm_scan_status(const void *d_workspace, void *stream);

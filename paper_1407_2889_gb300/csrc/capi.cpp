@@ -397,6 +397,22 @@ int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t f
                      d_workspace, stream);
 }
 
+int pm_scan_device_noalloc(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags,
+                           int64_t *d_counts, uint64_t *d_occ, int64_t occ_capacity,
+                           int64_t *d_n_occ, void *stream)
+{
+    if (!s || n < 0 || !d_counts || !d_n_occ) return PM_EINVAL;
+    if (s->host_only || s->algo != PM_ALGO_AC) return PM_EINVAL;
+    if (n > 0 && !d_text) return PM_EINVAL;
+    if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
+    const bool list = !(flags & PM_COUNTS_ONLY);
+    if (occ_capacity < 0 || (list && occ_capacity > 0 && !d_occ)) return PM_EINVAL;
+    return ac_launch_noalloc(s->ac, s->dac, d_text, n, list, d_counts, d_occ, occ_capacity,
+                             d_n_occ, stream);
+}
+
+int64_t pm_noalloc_scratch_bytes(void) { return ac_noalloc_limit_bytes(); }
+
 int pm_scan_status(const void *d_workspace, void *stream)
 {
     if (!d_workspace) return PM_EINVAL;

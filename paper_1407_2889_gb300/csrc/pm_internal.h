@@ -149,6 +149,11 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
 int ac_launch(const AcTables &t, const DevAc &dev, const uint8_t *d_text, int64_t n,
               bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
               int64_t *d_n_occ, void *d_ws, void *stream);
+// allocation-free variant: scratch from a fixed device array in the library
+int ac_launch_noalloc(const AcTables &t, const DevAc &dev, const uint8_t *d_text, int64_t n,
+                      bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
+                      int64_t *d_n_occ, void *stream);
+int64_t ac_noalloc_limit_bytes();
 int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevWm &dev);
 int wm_launch(const WmTables &t, const DevWm &dev, const uint8_t *d_text, int64_t n,
               bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,

@@ -28,6 +28,7 @@
 // shared-memory staging window so global stores are coalesced (the paper's
 // coalesced writes, GPU-CW).
 #include <cstdio>
+#include <mutex>
 #include <type_traits>
 
 #include "scan_common.cuh"
@@ -843,6 +844,158 @@ int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t
     if (grid < 1) grid = 1;
     if (grid * dv.warps > dv.max_warps) grid = dv.max_warps / dv.warps;
     a.lb.super_tiles = dev::super_size_for(grid * dv.warps);
+    v.fn<<<dim3(unsigned(grid)), dim3(unsigned(threads)), size_t(dv.smem_bytes), st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    return PM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free scan (pm_scan_device_noalloc).
+//
+// Some callers cannot allocate device memory when they scan: a host
+// application that owns the GPU allocator (a plugin must not add cudaMalloc
+// calls it cannot account for), or a latency-bound loop that reserved all
+// of its memory up front and must not call cudaMalloc, which can block on
+// the device and fail once memory is fragmented. For them the scratch of
+// the Aho-Corasick scan lives in one fixed array inside the library. The
+// array is reserved on every GPU that loads the library and stays reserved
+// until the process exits. Every call uses the same array and it keeps the
+// last call's contents, so the launcher clears what must start at zero, and
+// two calls whose work overlaps on the GPU (different streams, or host
+// threads) race on it. To keep the array modest the scan runs with one warp
+// tile per look-back tile (the per-warp output slots then need only two
+// warp tiles of entries).
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {};
+
+// Device address of the scratch array on the current device. The first call
+// on a device looks it up (host code cannot use the array's name as an
+// address); later calls reuse it.
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        return PM_ENODEV;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_cuda_error(int(e));
+            cudaGetLastError();
+            return PM_ECUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return PM_OK;
+}
+}  // namespace
+
+int64_t ac_noalloc_limit_bytes() { return int64_t(kNoAllocScratchBytes); }
+
+int ac_launch_noalloc(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n,
+                      bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
+                      int64_t *d_n_occ, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const int K = 1;
+    const long long nsub = warp_tiles(n);
+    const long long ntiles = nsub;
+    const long long nterms = (long long)t.canon.size();
+    const Variant &v = kVariants[dv.variant];
+    DeviceProps dp;
+    int rc = device_props(dp);
+    if (rc) return rc;
+
+    // the grid the launch will use decides the size of the output slots
+    static int attr_bytes_na[sizeof(kVariants) / sizeof(kVariants[0])] = {};
+    if (attr_bytes_na[dv.variant] < dv.smem_bytes) {
+        e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
+        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+        attr_bytes_na[dv.variant] = int(dv.smem_bytes);
+    }
+    const int threads = dv.warps * 32;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, threads, size_t(dv.smem_bytes));
+    if (e != cudaSuccess || per_sm < 1) { set_cuda_error(int(e)); return PM_ECUDA; }
+    long long grid = (long long)dp.sm_count * std::min(per_sm, dv.ctas_per_sm);
+    const long long want = (ntiles + dv.warps - 1) / dv.warps;
+    if (want < grid) grid = want;
+    if (grid < 1) grid = 1;
+    if (grid * dv.warps > dv.max_warps) grid = dv.max_warps / dv.warps;
+
+    const long long se = sizeof(uint32_t) * ((t.dna ? t.entry_bytes : 4) == 2 ? 1 : 2);
+    const long long zeroed = zeroed_workspace_bytes(ntiles, list, nterms);
+    const long long slots = list ? r16(grid * dv.warps * 2LL * K * kWarpTile * se) : 0;
+    if (zeroed + slots > (long long)kNoAllocScratchBytes) return PM_ETOOBIG;
+
+    void *ws = nullptr;
+    rc = noalloc_scratch(&ws);
+    if (rc) return rc;
+    e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, size_t(zeroed), st);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    if (n < t.m || nsub == 0) return PM_OK;
+
+    AcArgs a;
+    a.text = d_text;
+    a.n = n;
+    a.aligned = (reinterpret_cast<uintptr_t>(d_text) & 15) == 0;
+    a.table_g = dv.table;
+    a.smem_entries = int(dv.smem_entries);
+    a.mid_base = uint32_t(t.d0_row << t.lw);
+    a.mask_g = dv.flag_mask;
+    a.rank_g = dv.flag_rank;
+    a.canon_g = dv.canon;
+    a.nwords = int(t.flag_mask.size());
+    a.nterms = int(nterms);
+    a.grp_off = dv.grp_off;
+    a.grp_ids = dv.grp_ids;
+    a.cls_g = dv.cls;
+    a.m = t.m;
+    a.lw = t.lw;
+    a.lut = t.lut;
+    a.pad = 0;
+    if (t.dna) {
+        for (uint32_t b = 0; b < 256; ++b)
+            if (t.cls[b] == 0xFF) { a.pad = b; break; }
+    }
+    a.ntiles = ntiles;
+    a.nsub = nsub;
+    a.ksub = K;
+    a.pool_cap = dv.pool_cap;
+    a.stage_cap = dv.stage_cap;
+    a.list = list ? 1 : 0;
+    a.hist_smem = dv.hist_smem;
+    a.ids_smem = dv.ids_smem;
+    a.d = int(t.d);
+    a.counts = reinterpret_cast<long long *>(d_counts);
+    a.occ = reinterpret_cast<unsigned long long *>(d_occ);
+    a.occ_cap = list ? occ_cap : 0;
+    a.n_occ = reinterpret_cast<long long *>(d_n_occ);
+    char *w = static_cast<char *>(ws);
+    a.ws = reinterpret_cast<dev::WsHeader *>(w);
+    a.ccount = reinterpret_cast<unsigned long long *>(w + kWsHeader);
+    char *after = w + kWsHeader + r16(nterms * 8);
+    a.lb.tile_st = reinterpret_cast<unsigned long long *>(after);
+    a.lb.super_acc = reinterpret_cast<unsigned long long *>(after + ntiles * 8);
+    a.lb.super_pre = reinterpret_cast<unsigned long long *>(after + ntiles * 16);
+    a.lb.ntiles = ntiles;
+    a.lb.super_tiles = dev::super_size_for(grid * dv.warps);
+    a.scratch = after + r16(ntiles * 24);
     v.fn<<<dim3(unsigned(grid)), dim3(unsigned(threads)), size_t(dv.smem_bytes), st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }

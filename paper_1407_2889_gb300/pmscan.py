@@ -27,7 +27,8 @@ PM_ALGO_AC, PM_ALGO_WM = 1, 2
 
 EXPORTED = [
     "pm_ac_compile", "pm_wm_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
-    "pm_scan_to_host", "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device", "pm_scan_status",
+    "pm_scan_to_host", "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device",
+    "pm_scan_device_noalloc", "pm_noalloc_scratch_bytes", "pm_scan_status",
     "pm_scan_batch", "pm_selfcheck_host_walk", "pm_strerror", "pm_last_cuda_error",
     "pm_version",
 ]
@@ -104,6 +105,10 @@ def lib():
         L.pm_scan_workspace_bytes.argtypes = [vp, i64, u32]
         L.pm_scan_device.restype = ctypes.c_int
         L.pm_scan_device.argtypes = [vp, vp, i64, u32, vp, vp, i64, vp, vp, i64, vp]
+        L.pm_scan_device_noalloc.restype = ctypes.c_int
+        L.pm_scan_device_noalloc.argtypes = [vp, vp, i64, u32, vp, vp, i64, vp, vp]
+        L.pm_noalloc_scratch_bytes.restype = i64
+        L.pm_noalloc_scratch_bytes.argtypes = []
         L.pm_scan_status.restype = ctypes.c_int
         L.pm_scan_status.argtypes = [vp, vp]
         L.pm_scan_batch.restype = ctypes.c_int
@@ -266,6 +271,21 @@ def pm_scan_device(h: int, d_text, n: int, flags: int, d_counts, d_occ, occ_capa
                                 _dev_ptr(d_occ), int(occ_capacity), _dev_ptr(d_n_occ),
                                 _dev_ptr(d_workspace), int(workspace_bytes), _stream_ptr(stream)),
            "pm_scan_device")
+
+
+def pm_scan_device_noalloc(h: int, d_text, n: int, flags: int, d_counts, d_occ,
+                           occ_capacity: int, d_n_occ, stream=None) -> None:
+    """pm_scan_device without a workspace: for callers that cannot allocate
+    device memory while scanning (the library's fixed scratch array is used;
+    calls that overlap on the GPU race on it)."""
+    _check(lib().pm_scan_device_noalloc(h, _dev_ptr(d_text), int(n), flags, _dev_ptr(d_counts),
+                                        _dev_ptr(d_occ), int(occ_capacity), _dev_ptr(d_n_occ),
+                                        _stream_ptr(stream)),
+           "pm_scan_device_noalloc")
+
+
+def pm_noalloc_scratch_bytes() -> int:
+    return int(lib().pm_noalloc_scratch_bytes())
 
 
 def pm_scan_status(d_workspace, stream=None) -> int:
