@@ -148,6 +148,10 @@ def parse():
     ap.add_argument("--m", type=int, default=8)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--batch-k", type=int, default=4096,
+                    help="instances of the batched-vs-plain comparison (0 skips it)")
+    ap.add_argument("--only-batch", action="store_true",
+                    help="run only the batched-vs-plain comparison and print it")
     ap.add_argument("--mode", default="list", choices=["list", "counts"],
                     help="timed step: list mode (default) or counts only")
     ap.add_argument("--text-mib", type=int, default=0,
@@ -169,6 +173,10 @@ def run_reference(args, rank):
     from paper_1407_2889_gb300 import synth
     import oracle
     T = synth.est_text(synth.EST_N, 1)
+    if args.only_batch:
+        d_text = torch.from_numpy(T).cuda()
+        print(json.dumps(batched_comparison(args, T, d_text, pm, torch, synth)), flush=True)
+        return
     _, P = synth.est_case(args.d, args.m, text=T)
     cores = os.cpu_count() or 1
     sample = 8 << 20
@@ -214,6 +222,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     T = synth.est_text(synth.EST_N, 1)
+    if args.only_batch:
+        d_text = torch.from_numpy(T).cuda()
+        print(json.dumps(batched_comparison(args, T, d_text, pm, torch, synth)), flush=True)
+        return
     _, P = synth.est_case(args.d, args.m, text=T)
     if args.text_mib:
         T = T[: args.text_mib << 20]
@@ -288,6 +300,9 @@ def main():
     extras = {}
     if rank == 0 and not args.no_extras:
         extras = secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, torch, synth)
+        if args.batch_k > 0:
+            del occ
+            extras["batched"] = batched_comparison(args, T, d_text, pm, torch, synth)
 
     # end to end through the public API: pinned host text in, pinned host
     # counts and occurrence list out (pm_scan_to_host), copies inside the timing
@@ -388,6 +403,102 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
             q.close()
             del buf
     out["ac_list_sweep"] = sweep
+    return out
+
+
+def batched_comparison(args, T, d_text, pm, torch, synth):
+    """Batched form against per-instance plain launches on the same instances.
+
+    k instances (4096 by default) are slices of the resident EST text with
+    log-uniform lengths 1 KiB-4 MiB, each against its own set (d log-uniform
+    10-10^4, m uniform 8-64), list mode with exact capacities. Batched: the
+    autotuned persistent kernel replayed from a CUDA graph. Plain: one
+    pm_scan_device per instance, all k captured in one CUDA graph (so host
+    launch overhead is off both clocks). Both produce identical results.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+
+    k = args.batch_k
+    off, ln, dd, mm = synth.batch_plan(k, T.size)
+    t0 = time.perf_counter()
+
+    def make(j):
+        P = synth.batch_patterns(T, int(off[j]), int(ln[j]), int(dd[j]), int(mm[j]), synth.BATCH_SEED + j)
+        return pm.PatternSet.ac(P)
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        sets = list(ex.map(make, range(k)))
+    t_compile = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    total_bytes = int(ln.sum())
+    with torch.cuda.stream(stream):
+        b = pm.Batch.exact(sets, d_text, off, ln, stream=stream)
+        tuned_ms = b.tune(reps=2, stream=stream)
+        warps = b.warps
+        b.capture()
+        b.replay(stream)
+    stream.synchronize()
+    assert b.status(stream) == pm.PM_OK
+    n_occ = b.n_occ[:k].cpu().numpy().copy()
+    counts_b = b.counts.clone()
+
+    # plain arm: per-instance launches into the same result layout
+    ws_bytes = max(pm.pm_scan_workspace_bytes(s.h, int(n), 0) for s, n in zip(sets, ln))
+    ws = torch.zeros(ws_bytes, dtype=torch.uint8, device="cuda")
+    counts_p = torch.zeros_like(b.counts)
+    occ_p = torch.empty_like(b.occ)
+    nocc_p = torch.zeros(k, dtype=torch.int64, device="cuda")
+    base = d_text.data_ptr()
+    cptr, optr, nptr = counts_p.data_ptr(), occ_p.data_ptr(), nocc_p.data_ptr()
+
+    def plain_pass(st):
+        for j, s in enumerate(sets):
+            pm.pm_scan_device(s.h, base + int(off[j]), int(ln[j]), 0, cptr + 8 * int(b.count_off[j]),
+                              optr + 8 * int(b.occ_off[j]), int(n_occ[j]), nptr + 8 * j, ws, ws_bytes, st)
+
+    with torch.cuda.stream(stream):
+        plain_pass(stream)  # warm-up: attributes, caches
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    cap_stream = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=cap_stream, capture_error_mode="thread_local"):
+        plain_pass(cap_stream)
+    torch.cuda.synchronize()
+
+    def timed(fn, reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            fn()
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    t_batch = timed(lambda: b.replay(stream), 5)
+    t_plain = timed(lambda: g.replay(), 3)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        plain_pass(stream)
+    stream.synchronize()
+    t_plain_host = time.perf_counter() - t0
+    same = bool(torch.equal(counts_p, counts_b)) and bool(torch.equal(nocc_p, b.n_occ[:k]))
+    same = same and bool(torch.equal(occ_p, b.occ))
+    out = {
+        "k": k, "text_bytes": total_bytes, "n_occ": int(n_occ.sum()),
+        "batched_gbs": total_bytes / t_batch / 1e9, "batched_ms": t_batch * 1e3,
+        "plain_graph_gbs": total_bytes / t_plain / 1e9, "plain_graph_ms": t_plain * 1e3,
+        "plain_host_loop_ms": t_plain_host * 1e3,
+        "speedup_vs_plain_graph": t_plain / t_batch, "identical_results": same,
+        "tuned_warps": warps, "tune_best_ms": tuned_ms, "compile_s": t_compile,
+        "workload": "k slices of the EST-shaped text, lengths log-uniform 1 KiB-4 MiB (seed 4000+j), "
+                    "own set per instance: d log-uniform 10-10^4, m uniform 8-64, list mode",
+    }
+    b.close()
+    for s in sets:
+        s.close()
     return out
 
 

@@ -116,6 +116,8 @@ typedef struct pm_result {    /* library-owned; release with pm_result_free */
  * breadth-first order, the full transition function, renumbers states
  * breadth-first, elides the rows of depth-m states and uploads the tables.
  * opt may be NULL. On success *out owns device memory until pm_set_free.
+ * Device scans hold a lane's m-1 halo bytes in registers, so m <= 65 unless
+ * opt->host_only is set (PM_ETOOBIG otherwise).
  */
 int pm_ac_compile(const uint8_t *P, int64_t d, int32_t m,
                   const pm_params *opt, pm_set **out);
@@ -215,6 +217,76 @@ int pm_scan_status(const void *d_workspace, void *stream);
 int pm_scan_batch(const pm_set *const *sets, const uint8_t *const *texts,
                   const int64_t *ns, int32_t k, uint32_t flags, void *stream,
                   pm_result **outs);
+
+/*
+ * Batched device scan: k independent Aho-Corasick instances (text j against
+ * set j), each computing exactly what pm_scan_device computes for it, in one
+ * persistent launch. A CTA takes whole instances from a queue, largest text
+ * first, and runs the instance's warp tiles (the chunk-with-halo partition of
+ * Section 4.2.1) on its own warps, so no instance waits on another. The
+ * paper scans one text per run; the batch and its tuner and graph are
+ * additions of this library.
+ *
+ * pm_batch_prepare fixes the batch layout (host arrays are copied):
+ *   sets      k compiled AC sets over an ACGT-like alphabet with m <= 65
+ *             (else PM_EINVAL); a set may appear several times
+ *   text_off, text_len  int64[k] each: instance j's text is the
+ *             text_len[j] (< 2^32) bytes at text_off[j] of one device text
+ *             buffer; texts may overlap (16-byte aligned starts let the tiles
+ *             be copied by the bulk-copy engine)
+ *   occ_off   int64[k+1]: instance j's keys go to occ[occ_off[j] ..
+ *             occ_off[j+1]) (its capacity); ignored with PM_COUNTS_ONLY
+ *   flags     0 or PM_COUNTS_ONLY (PM_DEVICE_TEXT is accepted and implied)
+ * Counts of instance j land at counts[c_j .. c_j + d_j) with c_j the sum of
+ * the d of the instances before j; pm_batch_counts_total gives the sum. The
+ * sets must outlive the batch. The batch owns a small device array of
+ * descriptors until pm_batch_free.
+ */
+typedef struct pm_batch pm_batch;
+int pm_batch_prepare(const pm_set *const *sets, int32_t k, const int64_t *text_off,
+                     const int64_t *text_len, const int64_t *occ_off, uint32_t flags,
+                     pm_batch **out);
+void pm_batch_free(pm_batch *b);
+int64_t pm_batch_counts_total(const pm_batch *b);
+/* Workspace for every call below (any warp count the tuner may pick). */
+int64_t pm_batch_workspace_bytes(const pm_batch *b);
+int32_t pm_batch_warps(const pm_batch *b);  /* warps per CTA of the current plan */
+
+/*
+ * Enqueue the batched scan on `stream` (asynchronous, allocates nothing).
+ *   d_text   the device text buffer of pm_batch_prepare
+ *   d_counts int64[pm_batch_counts_total]; d_n_occ int64[k]: instance j's
+ *            total, which may exceed its capacity (then only the first
+ *            capacity keys are written, sorted, as in pm_scan_device)
+ *   d_occ    uint64[occ_off[k]] (may be NULL with PM_COUNTS_ONLY)
+ * Device-side failures are reported through pm_scan_status on d_workspace.
+ */
+int pm_batch_scan_device(const pm_batch *b, const uint8_t *d_text, int64_t *d_counts,
+                         uint64_t *d_occ, int64_t *d_n_occ, void *d_workspace,
+                         int64_t workspace_bytes, void *stream);
+
+/*
+ * Autotuner: times `reps` batched scans (after one warm-up) for each
+ * candidate warps-per-CTA (8, 12, 16; each fixes how shared memory is split
+ * between per-warp buffers and the instance's table prefix, ids and
+ * counters), keeps the fastest and returns its time per scan in *best_ms
+ * (may be NULL). Synchronises `stream`; results of every candidate are
+ * identical, and the buffers hold the last candidate's. Drops a captured graph.
+ */
+int pm_batch_tune(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_t *d_occ,
+                  int64_t *d_n_occ, void *d_workspace, int64_t workspace_bytes, int32_t reps,
+                  void *stream, float *best_ms);
+int pm_batch_set_warps(pm_batch *b, int32_t warps);  /* 1..16; drops a captured graph */
+
+/*
+ * CUDA graph of one batched scan on these buffers (the workspace memset and
+ * the persistent kernel), captured on a private stream; pm_batch_replay
+ * launches it on `stream`. Buffers are baked in: replays must use them and
+ * must not overlap each other. Capture synchronises nothing and runs nothing.
+ */
+int pm_batch_capture(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_t *d_occ,
+                     int64_t *d_n_occ, void *d_workspace, int64_t workspace_bytes);
+int pm_batch_replay(const pm_batch *b, void *stream);
 
 /*
  * Table self-check on the host, no GPU needed: walks the compiled AC table

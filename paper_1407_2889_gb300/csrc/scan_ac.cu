@@ -31,12 +31,13 @@
 #include <mutex>
 #include <type_traits>
 
-#include "scan_common.cuh"
+#include "ac_device.cuh"
 
 namespace pm {
 namespace {
 
 using dev::kFull;
+using namespace acdev;
 
 struct AcArgs {
     const uint8_t *text;
@@ -84,124 +85,6 @@ __host__ __device__ inline long long ac_ids_bytes(int nwords, int nterms, int eb
     return r16((long long)nwords * 4) + r16((long long)(nwords + 1) * eb) + r16((long long)nterms * eb);
 }
 
-template <typename E, bool HYB>
-struct TableRef {
-    const E *s;
-    const E *g;
-    uint32_t lim;
-    __device__ __forceinline__ uint32_t operator()(uint32_t idx) const
-    {
-        if (!HYB) return s[idx];
-        return idx < lim ? uint32_t(s[idx]) : uint32_t(__ldg(g + idx));
-    }
-};
-
-// Canonical terminal id and pattern code of a match entry.
-template <typename E>
-struct Ids {
-    const uint32_t *mask;
-    const E *rank;
-    const E *canon;
-    __device__ __forceinline__ uint32_t terminal(uint32_t off) const
-    {
-        const uint32_t w = off >> 5, b = off & 31u;
-        return uint32_t(rank[w]) + __popc(mask[w] & ((1u << b) - 1u));
-    }
-    __device__ __forceinline__ uint32_t code(uint32_t c) const { return canon[c]; }
-};
-
-__device__ __forceinline__ uint32_t word_of(const uint4 &v, int q)
-{
-    return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
-}
-
-// DFA walk over one lane's register text, ACGT-like alphabet. For every step
-// calls on_step(step, idx, e): idx the table index used, e the entry read
-// (bit 0 set when the transition entered a terminal state).
-template <int NV, class Tab, class F>
-__device__ __forceinline__ void walk_dna(const uint4 (&tv)[NV], int steps, uint32_t lut,
-                                         const Tab &tab, F &&on_step)
-{
-    uint32_t e = 2u;  // root (row 1)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t w = word_of(tv[v], q);
-            const uint32_t a4 = ((w >> 1) ^ (w >> 2)) & 0x03030303u;
-            const uint32_t sel = __byte_perm(a4 | (a4 >> 4), 0u, 0x4420);
-            const uint32_t x = w ^ __byte_perm(lut, 0u, sel);  // zero byte = in alphabet
-            const uint32_t y = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
-            const uint32_t vb = (y >> 7) * 0xFFu;   // 0xFF per valid byte
-            const uint32_t v2 = vb & 0xFCFCFCFCu;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int step = v * 16 + q * 4 + k;
-                if (step < kChunk || step < steps) {
-                    const uint32_t c = __byte_perm(a4, 0u, 0x4440 | k);
-                    const uint32_t vm = __byte_perm(
-                        v2, vb, (k) | ((4 + k) << 4) | ((4 + k) << 8) | ((4 + k) << 12));
-                    const uint32_t idx = ((e << 1) & vm) | c;  // invalid byte -> row 0
-                    e = tab(idx);
-                    on_step(step, idx, e);
-                }
-            }
-        }
-    }
-}
-
-// General alphabet: class map in shared memory; steps already clipped to n.
-template <int NV, class Tab, class F>
-__device__ __forceinline__ void walk_gen(const uint4 (&tv)[NV], int steps, int lw,
-                                         const uint8_t *s_cls, const Tab &tab, F &&on_step)
-{
-    uint32_t e = 2u;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t w = word_of(tv[v], q);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int step = v * 16 + q * 4 + k;
-                if (step < steps) {
-                    const uint32_t c = s_cls[(w >> (8 * k)) & 0xFFu];
-                    const uint32_t idx = c == 0xFFu ? 0u : (((e >> 1) << lw) | c);
-                    e = tab(idx);
-                    on_step(step, idx, e);
-                }
-            }
-        }
-    }
-}
-
-// Rolled re-walk of one lane's chunk straight from global memory, for the
-// rare lanes whose hit pool overflowed; same transitions as the fast walks.
-// Calls hit(step, idx) for every match.
-template <class Tab, class F>
-__device__ __forceinline__ void walk_slow(const uint8_t *text, long long n, long long g0,
-                                          int steps, bool dna, uint32_t lut, int lw,
-                                          const uint8_t *s_cls, const Tab &tab, F &&hit)
-{
-    uint32_t e = 2u;
-#pragma unroll 1
-    for (int step = 0; step < steps; ++step) {
-        const long long g = g0 + step;
-        if (g >= n) break;
-        const uint32_t b = text[g];
-        uint32_t idx;
-        if (dna) {
-            const uint32_t c = ((b >> 1) ^ (b >> 2)) & 3u;
-            idx = ((lut >> (8 * c)) & 0xFFu) == b ? (((e >> 1) << 2) | c) : c;
-        } else {
-            const uint32_t c = s_cls[b];
-            idx = c == 0xFFu ? 0u : (((e >> 1) << lw) | c);
-        }
-        e = tab(idx);
-        if (e & 1u) hit(step, idx);
-    }
-}
-
 __device__ __forceinline__ int stage_bytes(const AcArgs &a, long long t, int buf)
 {
     if (!a.aligned) return 0;
@@ -217,29 +100,6 @@ __device__ __forceinline__ void stage_issue(const AcArgs &a, long long t, uint8_
     dev::mbar_arrive_expect_tx(bar, uint32_t(bytes));
     if (bytes > 0) dev::tma_load_1d(buf, a.text + t * kWarpTile, uint32_t(bytes), bar);
 }
-
-// Iterates one lane's match steps in order from its 32-bit step bitmask.
-template <int HW>
-struct StepBits {
-    uint32_t w[HW];
-    int base;
-    // -1 if no bit is left (cannot happen when called once per recorded hit)
-    __device__ __forceinline__ int next()
-    {
-#pragma unroll
-        for (int s = 0; s < HW; ++s) {
-            if (w[0] != 0u) break;
-#pragma unroll
-            for (int j = 0; j + 1 < HW; ++j) w[j] = w[j + 1];
-            w[HW - 1] = 0u;
-            base += 32;
-        }
-        if (w[0] == 0u) return -1;
-        const int b = __ffs(int(w[0])) - 1;
-        w[0] &= w[0] - 1u;
-        return base + b;
-    }
-};
 
 template <typename E, int NV, int HV, bool DNA, bool HYB>
 __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)

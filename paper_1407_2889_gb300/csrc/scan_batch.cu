@@ -1,0 +1,789 @@
+// scan_batch.cu -- many independent Aho-Corasick scans in one persistent
+// launch (thousands of (text, pattern set) instances of uneven sizes).
+//
+// A CTA takes whole instances from a queue, largest first (the host sorts
+// the descriptors by text length, which bounds the tail at the largest
+// instance). For each instance it loads the set's transition table (its
+// breadth-first prefix when the table is larger than the CTA's table
+// budget), the canonical-terminal lookup and zeroed per-terminal counters
+// into shared memory once, then its warps walk the instance's warp tiles in
+// rounds: warp w takes tiles w, w + W, w + 2W ... Within a round the offsets
+// of the warps' outputs come from a prefix over per-warp totals in shared
+// memory, so an instance never needs a look-back across CTAs, and its
+// counts are final when the CTA leaves it. Walk, resolution of matches and
+// staged coalesced output are the same code as the plain kernel
+// (ac_device.cuh); the launch is a plain kernel plus memsets, so it can be
+// captured in a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "ac_device.cuh"
+
+namespace pm {
+
+struct BatchDesc {                 // one instance, in processing order
+    long long text_off, n;         // into the batch text buffer
+    long long count_off;           // into the batch counts buffer (d entries)
+    long long occ_off, occ_cap;    // into the batch occurrence buffer
+    long long ccount_off;          // into the workspace, when counters are global
+    long long out_slot;            // instance index (for n_occ)
+    const void *table;
+    const uint32_t *mask;
+    const void *rank;
+    const void *canon;
+    const uint32_t *grp_off;
+    const uint32_t *grp_ids;
+    int smem_entries, eb, m, nwords, nterms, d;
+    int ids_off, hist_off;         // byte offsets in the CTA's table region; -1 = global
+    uint32_t mid_base, lut, pad, pad2;
+};
+
+namespace {
+
+using dev::kFull;
+using namespace acdev;
+
+constexpr int kBatchHV = 4;                   // halo vectors: m <= 65
+constexpr int kBatchNV = 5 + kBatchHV;
+constexpr int kBatchBuf = kWarpTile + 16 * kBatchHV;
+constexpr int kBatchPool = 40;
+constexpr int kBatchStage = 128;              // u64 entries
+constexpr int kBatchMaxM = 16 * kBatchHV + 1;
+
+struct BatchArgs {
+    const BatchDesc *desc;
+    int k;
+    const uint8_t *text;
+    long long *counts;
+    unsigned long long *occ;
+    long long *n_occ;
+    dev::WsHeader *ws;
+    unsigned long long *ccount;
+    int list;
+    int region_bytes;              // per-CTA shared memory for table, ids and counters
+};
+
+__host__ __device__ constexpr long long rr16(long long x) { return (x + 15) & ~15LL; }
+
+__host__ __device__ inline long long batch_warp_bytes()
+{
+    return 16 + rr16(kBatchBuf) + rr16((long long)(kBatchPool + 1) * 32 * 4) + kBatchStage * 8;
+}
+
+__device__ __forceinline__ int bstage_bytes(const uint8_t *text, long long n, long long t)
+{
+    if (reinterpret_cast<uintptr_t>(text) & 15) return 0;
+    const long long avail = (n & ~15LL) - t * kWarpTile;
+    if (avail <= 0) return 0;
+    return avail >= kBatchBuf ? kBatchBuf : int(avail);
+}
+
+__device__ __forceinline__ void bstage_issue(const uint8_t *text, long long n, long long t,
+                                             uint8_t *buf, uint64_t *bar)
+{
+    const int bytes = bstage_bytes(text, n, t);
+    dev::mbar_arrive_expect_tx(bar, uint32_t(bytes));
+    if (bytes > 0) dev::tma_load_1d(buf, text + t * kWarpTile, uint32_t(bytes), bar);
+}
+
+struct CtaSmem {
+    unsigned char *region;          // table prefix, ids and counters of the instance
+    unsigned long long *s_tot;      // per-warp totals of a round
+    uint64_t *bar;
+    uint8_t *buf;
+    unsigned char *pool;
+    unsigned long long *stage;
+};
+
+// One instance, entry type E. All threads of the CTA call it.
+template <typename E>
+__device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSmem &S,
+                             uint32_t &phase, bool &failed)
+{
+    constexpr int NV = kBatchNV;
+    constexpr int HW = (16 * NV + 31) / 32;
+    constexpr uint32_t kGrp = sizeof(E) == 2 ? 0x8000u : 0x80000000u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const uint8_t *text = a.text + D.text_off;
+    const long long n = D.n;
+
+    // ---- per-instance tables into shared memory --------------------------
+    E *s_tab = reinterpret_cast<E *>(S.region);
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(D.table);
+        uint4 *dst = reinterpret_cast<uint4 *>(s_tab);
+        const int nvec = int(((long long)D.smem_entries * sizeof(E) + 15) / 16);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
+    }
+    Ids<E> ids;
+    if (D.ids_off >= 0) {
+        unsigned char *ip = S.region + D.ids_off;
+        uint32_t *mk = reinterpret_cast<uint32_t *>(ip);
+        E *rk = reinterpret_cast<E *>(ip + rr16((long long)D.nwords * 4));
+        E *cn = reinterpret_cast<E *>(reinterpret_cast<unsigned char *>(rk) +
+                                      rr16((long long)(D.nwords + 1) * sizeof(E)));
+        for (int i = threadIdx.x; i < D.nwords; i += blockDim.x) mk[i] = D.mask[i];
+        for (int i = threadIdx.x; i <= D.nwords; i += blockDim.x) rk[i] = reinterpret_cast<const E *>(D.rank)[i];
+        for (int i = threadIdx.x; i < D.nterms; i += blockDim.x) cn[i] = reinterpret_cast<const E *>(D.canon)[i];
+        ids.mask = mk;
+        ids.rank = rk;
+        ids.canon = cn;
+    } else {
+        ids.mask = D.mask;
+        ids.rank = reinterpret_cast<const E *>(D.rank);
+        ids.canon = reinterpret_cast<const E *>(D.canon);
+    }
+    uint32_t *s_hist = D.hist_off >= 0 ? reinterpret_cast<uint32_t *>(S.region + D.hist_off) : nullptr;
+    unsigned long long *g_hist = a.ccount + D.ccount_off;
+    if (s_hist)
+        for (int i = threadIdx.x; i < D.nterms; i += blockDim.x) s_hist[i] = 0u;
+    __syncthreads();
+
+    const TableRef<E, true> tab{s_tab, reinterpret_cast<const E *>(D.table), uint32_t(D.smem_entries)};
+    E *pl = reinterpret_cast<E *>(S.pool) + lane;
+    const uint32_t cap = kBatchPool;
+    const int m = D.m;
+    const long long nsub = (n + kWarpTile - 1) / kWarpTile;
+    auto count_terminal = [&](uint32_t c) {
+        if (s_hist) atomicAdd(&s_hist[c], 1u);
+        else atomicAdd(&g_hist[c], 1ull);
+    };
+    auto mult_of = [&](uint32_t code) -> uint32_t {
+        if (!(code & kGrp)) return 1u;
+        const uint32_t g = code & ~kGrp;
+        return __ldg(D.grp_off + g + 1) - __ldg(D.grp_off + g);
+    };
+
+    long long t = warp;
+    bool inflight = false;
+    if (t < nsub) {
+        if (lane == 0) bstage_issue(text, n, t, S.buf, S.bar);
+        inflight = true;
+    }
+    unsigned long long running = 0;
+    const unsigned long long obase = (unsigned long long)D.occ_off;
+    const unsigned long long ocap = (unsigned long long)D.occ_cap;
+    const long long rounds = (nsub + W - 1) / W;
+    for (long long rd = 0; rd < rounds; ++rd, t += W) {
+        const bool active = t < nsub && !failed;
+        uint32_t nh = 0, cnt = 0;
+        bool ovf = false;
+        uint32_t hw[HW];
+#pragma unroll
+        for (int j = 0; j < HW; ++j) hw[j] = 0u;
+        long long g0 = 0;
+        if (active) {
+            const bool got = __all_sync(kFull, dev::mbar_wait_bounded(S.bar, phase));
+            if (!got) {
+                if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutTma);
+                failed = true;  // the copy stays in flight: waited for below
+            } else {
+                inflight = false;
+                phase ^= 1u;
+                const long long tile0 = t * kWarpTile;
+                const int got_bytes = bstage_bytes(text, n, t);
+                if (got_bytes < kBatchBuf) {
+                    for (int b = got_bytes + lane; b < kBatchBuf; b += 32) {
+                        const long long g = tile0 + b;
+                        S.buf[b] = g < n ? text[g] : uint8_t(D.pad);
+                    }
+                    __syncwarp();
+                }
+                uint4 tv[NV];
+                {
+                    const uint4 *bv = reinterpret_cast<const uint4 *>(S.buf + lane * kChunk);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) tv[v] = bv[v];
+                }
+                dev::fence_proxy_async_smem();
+                __syncwarp();
+                if (t + W < nsub) {
+                    if (lane == 0) bstage_issue(text, n, t + W, S.buf, S.bar);
+                    inflight = true;
+                }
+                g0 = tile0 + (long long)lane * kChunk;
+                const int steps = kChunk + m - 1;
+                uint32_t kslot = 0;
+                auto rec = [&](int step, uint32_t idx, uint32_t e) {
+                    const uint32_t h = e & 1u;
+                    pl[kslot * 32] = E(idx - D.mid_base);
+                    kslot = min(kslot + h, cap);
+                    hw[step >> 5] |= h << (step & 31);
+                };
+                walk_dna<NV>(tv, steps, D.lut, tab, rec);
+#pragma unroll
+                for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
+                ovf = nh > cap;
+                if (!ovf) {
+                    for (uint32_t k = 0; k < nh; ++k) {
+                        const uint32_t c = ids.terminal(pl[k * 32]);
+                        const uint32_t code = ids.code(c);
+                        count_terminal(c);
+                        cnt += mult_of(code);
+                        pl[k * 32] = E(code);
+                    }
+                } else {
+                    walk_slow(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
+                              [&](int, uint32_t idx) {
+                                  const uint32_t c = ids.terminal(idx - D.mid_base);
+                                  count_terminal(c);
+                                  cnt += mult_of(ids.code(c));
+                              });
+                }
+            }
+        }
+        // ---- offsets of this round: prefix over the warps' totals ----------
+        const uint32_t incl = dev::warp_incl_scan(cnt, lane);
+        const uint32_t wtot = __shfl_sync(kFull, incl, 31);
+        if (lane == 0) S.s_tot[warp] = wtot;
+        __syncthreads();
+        unsigned long long before = 0, all = 0;
+        for (int w = 0; w < W; ++w) {
+            const unsigned long long v = S.s_tot[w];
+            if (w < warp) before += v;
+            all += v;
+        }
+        const unsigned long long base = running + before;
+        running += all;
+        if (a.list && active && !failed && wtot > 0) {
+            const uint32_t excl = incl - cnt;
+            auto put = [&](unsigned long long oi, long long pos, uint32_t r) {
+                if (oi < ocap) a.occ[obase + oi] = ((unsigned long long)pos << 32) | r;
+            };
+            if (!__any_sync(kFull, ovf)) {
+                StepBits<HW> it;
+#pragma unroll
+                for (int j = 0; j < HW; ++j) it.w[j] = hw[j];
+                it.base = 0;
+                uint32_t k = 0, my = excl;
+                bool have = false, single = true;
+                uint32_t rs = 0, glo = 0, ghi = 0;
+                long long pos = 0;
+                for (uint32_t w0 = 0; w0 < wtot; w0 += kBatchStage) {
+                    const uint32_t wend = min(w0 + (uint32_t)kBatchStage, wtot);
+                    const uint32_t lim = min(wend, incl);
+                    while (my < lim) {
+                        if (!have) {
+                            const int st = it.next();
+                            if (st < 0) dev::set_status(a.ws, dev::kErrInternal);
+                            pos = g0 + st - (m - 1);
+                            const uint32_t code = pl[k * 32];
+                            ++k;
+                            single = !(code & kGrp);
+                            if (single) {
+                                rs = code;
+                            } else {
+                                const uint32_t g = code & ~kGrp;
+                                glo = __ldg(D.grp_off + g);
+                                ghi = __ldg(D.grp_off + g + 1);
+                            }
+                            have = true;
+                        }
+                        const uint32_t r = single ? rs : __ldg(D.grp_ids + glo);
+                        S.stage[my - w0] = ((unsigned long long)pos << 32) | r;
+                        ++my;
+                        if (single || ++glo >= ghi) have = false;
+                    }
+                    __syncwarp();
+                    for (uint32_t q = w0 + lane; q < wend; q += 32) {
+                        const unsigned long long oi = base + q;
+                        if (oi < ocap) a.occ[obase + oi] = S.stage[q - w0];
+                    }
+                    __syncwarp();
+                }
+            } else {
+                unsigned long long oi = base + excl;
+                auto put_code = [&](long long pos, uint32_t code) {
+                    if (code & kGrp) {
+                        const uint32_t g = code & ~kGrp;
+                        const uint32_t hi = __ldg(D.grp_off + g + 1);
+                        for (uint32_t j = __ldg(D.grp_off + g); j < hi; ++j) put(oi++, pos, __ldg(D.grp_ids + j));
+                    } else {
+                        put(oi++, pos, code);
+                    }
+                };
+                if (!ovf) {
+                    StepBits<HW> it;
+#pragma unroll
+                    for (int j = 0; j < HW; ++j) it.w[j] = hw[j];
+                    it.base = 0;
+                    for (uint32_t k = 0; k < nh; ++k) {
+                        const int st = it.next();
+                        if (st < 0) dev::set_status(a.ws, dev::kErrInternal);
+                        put_code(g0 + st - (m - 1), pl[k * 32]);
+                    }
+                } else {
+                    walk_slow(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
+                              [&](int step, uint32_t idx) {
+                                  put_code(g0 + step - (m - 1), ids.code(ids.terminal(idx - D.mid_base)));
+                              });
+                }
+            }
+        }
+        __syncthreads();  // s_tot is rewritten next round
+    }
+    if (inflight) {  // only after a failure: let the last copy land before reuse
+        (void)dev::mbar_wait_bounded(S.bar, phase);
+        phase ^= 1u;
+    }
+
+    // ---- results of the instance -----------------------------------------
+    if (threadIdx.x == 0) a.n_occ[D.out_slot] = (long long)running;
+    long long *cnt_out = a.counts + D.count_off;
+    const E *cg = reinterpret_cast<const E *>(D.canon);
+    for (int c = threadIdx.x; c < D.nterms; c += blockDim.x) {
+        const unsigned long long v = s_hist ? (unsigned long long)s_hist[c] : g_hist[c];
+        const uint32_t code = cg[c];
+        if (code & kGrp) {
+            const uint32_t g = code & ~kGrp;
+            for (uint32_t j = D.grp_off[g]; j < D.grp_off[g + 1]; ++j) cnt_out[D.grp_ids[j]] = (long long)v;
+        } else {
+            cnt_out[code] = (long long)v;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(512, 1) ac_batch_kernel(const BatchArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    __shared__ int s_next;
+    __shared__ unsigned long long s_tot[32];
+    CtaSmem S;
+    unsigned char *p = smem;
+    S.region = p;
+    p += a.region_bytes;
+    p += warp * batch_warp_bytes();
+    S.bar = reinterpret_cast<uint64_t *>(p);
+    S.buf = p + 16;
+    S.pool = S.buf + rr16(kBatchBuf);
+    S.stage = reinterpret_cast<unsigned long long *>(S.pool + rr16((long long)(kBatchPool + 1) * 32 * 4));
+    S.s_tot = s_tot;
+    (void)W;
+    if (lane == 0) dev::mbar_init(S.bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    dev::fence_proxy_async_smem();
+    __syncthreads();
+
+    uint32_t phase = 0;
+    bool failed = false;
+    while (true) {
+        if (threadIdx.x == 0) {
+            const unsigned long long j = atomicAdd(&a.ws->queue, 1ull);
+            s_next = j < (unsigned long long)a.k ? int(j) : -1;
+        }
+        __syncthreads();
+        const int j = s_next;
+        __syncthreads();
+        if (j < 0) break;
+        const BatchDesc D = a.desc[j];
+        if (D.eb == 2) run_instance<uint16_t>(a, D, S, phase, failed);
+        else run_instance<uint32_t>(a, D, S, phase, failed);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+constexpr int kBatchWarpChoices[] = {8, 12, 16};   // autotuner candidates
+constexpr int kBatchMaxWarps = 16;
+
+struct BatchPlan {
+    int warps = 12;
+    int region_bytes = 0;
+    long long smem_bytes = 0;
+};
+
+// Per-CTA shared memory: one block of per-warp buffers, the rest is the
+// instance region (table prefix, ids, counters).
+static BatchPlan plan_batch(int warps, long long smem_optin)
+{
+    BatchPlan p;
+    p.warps = warps;
+    const long long budget = smem_optin - 2048;   // static shared memory and slack
+    long long room = budget - (long long)warps * batch_warp_bytes();
+    if (room < 4096) room = 4096;
+    p.region_bytes = int(room & ~15LL);
+    p.smem_bytes = (long long)p.region_bytes + (long long)warps * batch_warp_bytes();
+    return p;
+}
+
+struct InstLayout {
+    int smem_entries, ids_off, hist_off;
+};
+
+// Where an instance's tables go inside the region. Everything when it fits;
+// otherwise counters and ids stay in shared memory only while each takes at
+// most a quarter of the region, and the table gets the rest (its
+// breadth-first prefix: the rows a walk visits most).
+static InstLayout layout_of(const AcTables &t, int region)
+{
+    const int eb = t.entry_bytes;
+    const long long entries = (long long)t.n_rows << t.lw;
+    const long long nw = (long long)t.flag_mask.size(), nt = (long long)t.canon.size();
+    const long long tb = rr16(entries * eb);
+    const long long ib = rr16(nw * 4) + rr16((nw + 1) * eb) + rr16(nt * eb);
+    const long long hb = rr16(nt * 4);
+    InstLayout L;
+    if (tb + ib + hb <= region) {
+        L.smem_entries = int(entries);
+        L.ids_off = int(tb);
+        L.hist_off = int(tb + ib);
+        return L;
+    }
+    long long off = region;
+    L.hist_off = L.ids_off = -1;
+    if (hb <= region / 4) { off -= hb; L.hist_off = int(off); }
+    if (ib <= region / 4) { off -= ib; L.ids_off = int(off); }
+    long long se = off / eb;
+    se &= ~((long long)(16 / eb) - 1);
+    L.smem_entries = int(std::min(entries, se));
+    return L;
+}
+
+}  // namespace pm
+
+// The prepared batch of the C ABI.
+struct pm_batch {
+    int32_t k = 0;
+    std::vector<const pm_set *> sets;
+    std::vector<int64_t> text_off, text_len, occ_off, count_off, ccount_off;
+    std::vector<int32_t> order;       // processing order (largest text first)
+    pm::BatchDesc *d_desc = nullptr;
+    int64_t ccount_total = 0;
+    int64_t ws_bytes = 0;             // enough for every candidate plan
+    int64_t d_total = 0;
+    pm::BatchPlan plan;
+    uint32_t flags = 0;
+    cudaGraphExec_t graph = nullptr;  // captured launch, see pm_batch_capture
+};
+
+namespace pm {
+
+// Global per-terminal counters (workspace) for the instances whose counters
+// stay out of shared memory under `plan`.
+static int64_t ccount_for(const pm_batch &b, const BatchPlan &plan, std::vector<int64_t> *off)
+{
+    int64_t tot = 0;
+    if (off) off->assign(size_t(b.k) + 1, 0);
+    for (int32_t j = 0; j < b.k; ++j) {
+        const AcTables &t = b.sets[size_t(j)]->ac;
+        if (layout_of(t, plan.region_bytes).hist_off < 0) tot += int64_t(t.canon.size());
+        if (off) (*off)[size_t(j) + 1] = tot;
+    }
+    return tot;
+}
+
+static void fill_desc(const pm_batch &b, std::vector<BatchDesc> &out)
+{
+    out.resize(size_t(b.k));
+    for (int32_t q = 0; q < b.k; ++q) {
+        const int32_t j = b.order[size_t(q)];
+        const pm_set *s = b.sets[size_t(j)];
+        const AcTables &t = s->ac;
+        const DevAc &dv = s->dac;
+        BatchDesc &D = out[size_t(q)];
+        std::memset(&D, 0, sizeof(D));
+        D.text_off = b.text_off[size_t(j)];
+        D.n = b.text_len[size_t(j)];
+        D.count_off = b.count_off[size_t(j)];
+        D.occ_off = b.occ_off[size_t(j)];
+        D.occ_cap = b.occ_off[size_t(j) + 1] - b.occ_off[size_t(j)];
+        D.ccount_off = b.ccount_off[size_t(j)];
+        D.out_slot = j;
+        D.table = dv.table;
+        D.mask = dv.flag_mask;
+        D.rank = dv.flag_rank;
+        D.canon = dv.canon;
+        D.grp_off = dv.grp_off;
+        D.grp_ids = dv.grp_ids;
+        D.eb = t.entry_bytes;
+        const InstLayout L = layout_of(t, b.plan.region_bytes);
+        D.smem_entries = L.smem_entries;
+        D.ids_off = L.ids_off;
+        D.hist_off = L.hist_off;
+        D.m = t.m;
+        D.nwords = int(t.flag_mask.size());
+        D.nterms = int(t.canon.size());
+        D.d = int(t.d);
+        D.mid_base = uint32_t(t.d0_row << t.lw);
+        D.lut = t.lut;
+        D.pad = 0;
+        for (uint32_t x = 0; x < 256; ++x)  // a byte outside the alphabet
+            if (t.cls[x] == 0xFF) { D.pad = x; break; }
+    }
+}
+
+// Lay the batch out for `warps` warps per CTA and upload the descriptors
+// (into the existing device array once there is one).
+static int apply_plan(pm_batch *b, int warps)
+{
+    DeviceProps dp;
+    int rc = device_props(dp);
+    if (rc) return rc;
+    b->plan = plan_batch(warps, dp.smem_optin);
+    b->ccount_total = ccount_for(*b, b->plan, &b->ccount_off);
+    if (b->k == 0) return PM_OK;
+    std::vector<BatchDesc> h;
+    fill_desc(*b, h);
+    cudaError_t e = cudaSuccess;
+    if (!b->d_desc) e = cudaMalloc(&b->d_desc, h.size() * sizeof(BatchDesc));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, h.data(), h.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
+    }
+    return PM_OK;
+}
+
+static int ensure_batch_attr(long long smem_bytes)
+{
+    static std::mutex mu;
+    static long long attr[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) { set_cuda_error(int(e)); return PM_ECUDA; }
+    std::lock_guard<std::mutex> lk(mu);
+    if (attr[dev] < smem_bytes) {
+        e = cudaFuncSetAttribute(ac_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes));
+        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+        attr[dev] = smem_bytes;
+    }
+    return PM_OK;
+}
+
+struct BatchBufs {
+    const uint8_t *text;
+    int64_t *counts;
+    uint64_t *occ;
+    int64_t *n_occ;
+    void *ws;
+};
+
+// Enqueue one batched scan: a memset of the queue, status and global
+// counters, then the persistent kernel. Nothing else touches the host, so the
+// pair can be captured in a graph.
+static int batch_enqueue(const pm_batch *b, const BatchBufs &o, int sm_count, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(o.ws, 0, size_t(kWsHeader + b->ccount_total * 8), st);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    if (b->k == 0) return PM_OK;
+    BatchArgs a;
+    a.desc = b->d_desc;
+    a.k = b->k;
+    a.text = o.text;
+    a.counts = reinterpret_cast<long long *>(o.counts);
+    a.occ = reinterpret_cast<unsigned long long *>(o.occ);
+    a.n_occ = reinterpret_cast<long long *>(o.n_occ);
+    a.ws = reinterpret_cast<dev::WsHeader *>(o.ws);
+    a.ccount = reinterpret_cast<unsigned long long *>(static_cast<char *>(o.ws) + kWsHeader);
+    a.list = (b->flags & PM_COUNTS_ONLY) ? 0 : 1;
+    a.region_bytes = b->plan.region_bytes;
+    const int grid = std::min(sm_count, b->k);
+    ac_batch_kernel<<<dim3(unsigned(grid)), dim3(unsigned(b->plan.warps * 32)),
+                      size_t(b->plan.smem_bytes), st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    return PM_OK;
+}
+
+static int batch_check(const pm_batch *b, const BatchBufs &o, int64_t ws_bytes)
+{
+    if (!b) return PM_EINVAL;
+    if (b->k > 0 && (!o.text || !o.n_occ || !o.ws || (b->d_total > 0 && !o.counts))) return PM_EINVAL;
+    if (!(b->flags & PM_COUNTS_ONLY) && b->occ_off[size_t(b->k)] > 0 && !o.occ) return PM_EINVAL;
+    if (ws_bytes < b->ws_bytes) return PM_EINVAL;
+    return PM_OK;
+}
+
+static void drop_graph(pm_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+int pm_batch_prepare(const pm_set *const *sets, int32_t k, const int64_t *text_off,
+                     const int64_t *text_len, const int64_t *occ_off, uint32_t flags,
+                     pm_batch **out)
+{
+    if (!out || k < 0 || (k > 0 && (!sets || !text_off || !text_len || !occ_off))) return PM_EINVAL;
+    if (flags & ~(PM_DEVICE_TEXT | PM_COUNTS_ONLY)) return PM_EINVAL;
+    if (k > 0 && occ_off[0] < 0) return PM_EINVAL;
+    for (int32_t j = 0; j < k; ++j) {
+        const pm_set *s = sets[j];
+        if (!s || s->host_only || s->algo != PM_ALGO_AC || !s->ac.dna || s->ac.m > kBatchMaxM) return PM_EINVAL;
+        if (text_off[j] < 0 || text_len[j] < 0 || occ_off[j + 1] < occ_off[j]) return PM_EINVAL;
+        if (text_len[j] >= (int64_t(1) << 32)) return PM_ETOOBIG;
+    }
+    pm_batch *b = new (std::nothrow) pm_batch();
+    if (!b) return PM_ENOMEM;
+    try {
+        b->k = k;
+        b->flags = flags;
+        b->sets.assign(sets, sets + k);
+        b->text_off.assign(text_off, text_off + k);
+        b->text_len.assign(text_len, text_len + k);
+        b->occ_off.assign(occ_off, occ_off + k + 1);
+        b->count_off.assign(size_t(k) + 1, 0);
+        for (int32_t j = 0; j < k; ++j)
+            b->count_off[size_t(j) + 1] = b->count_off[size_t(j)] + sets[j]->ac.d;
+        b->d_total = b->count_off[size_t(k)];
+        b->order.resize(size_t(k));
+        std::iota(b->order.begin(), b->order.end(), 0);
+        std::stable_sort(b->order.begin(), b->order.end(),
+                         [&](int32_t x, int32_t y) { return text_len[x] > text_len[y]; });
+        DeviceProps dp;
+        int rc = device_props(dp);
+        if (rc) { delete b; return rc; }
+        // the largest warp count leaves the smallest region, hence the most
+        // counters in the workspace: size the workspace for it
+        b->ws_bytes = kWsHeader + 8 * ccount_for(*b, plan_batch(kBatchMaxWarps, dp.smem_optin), nullptr);
+        rc = apply_plan(b, 12);
+        if (rc) { pm_batch_free(b); return rc; }
+    } catch (const std::bad_alloc &) {
+        pm_batch_free(b);
+        return PM_ENOMEM;
+    }
+    *out = b;
+    return PM_OK;
+}
+
+void pm_batch_free(pm_batch *b)
+{
+    if (!b) return;
+    drop_graph(b);
+    if (b->d_desc) cudaFree(b->d_desc);
+    delete b;
+}
+
+int64_t pm_batch_workspace_bytes(const pm_batch *b) { return b ? b->ws_bytes : -1; }
+
+int64_t pm_batch_counts_total(const pm_batch *b) { return b ? b->d_total : -1; }
+
+int32_t pm_batch_warps(const pm_batch *b) { return b ? b->plan.warps : -1; }
+
+int pm_batch_set_warps(pm_batch *b, int32_t warps)
+{
+    if (!b || warps < 1 || warps > kBatchMaxWarps) return PM_EINVAL;
+    drop_graph(b);
+    return apply_plan(b, warps);
+}
+
+int pm_batch_scan_device(const pm_batch *b, const uint8_t *d_text, int64_t *d_counts,
+                         uint64_t *d_occ, int64_t *d_n_occ, void *d_workspace,
+                         int64_t workspace_bytes, void *stream)
+{
+    const BatchBufs o{d_text, d_counts, d_occ, d_n_occ, d_workspace};
+    int rc = batch_check(b, o, workspace_bytes);
+    if (rc) return rc;
+    DeviceProps dp;
+    rc = device_props(dp);
+    if (rc) return rc;
+    rc = ensure_batch_attr(b->plan.smem_bytes);
+    if (rc) return rc;
+    return batch_enqueue(b, o, dp.sm_count, static_cast<cudaStream_t>(stream));
+}
+
+int pm_batch_tune(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_t *d_occ,
+                  int64_t *d_n_occ, void *d_workspace, int64_t workspace_bytes, int32_t reps,
+                  void *stream, float *best_ms)
+{
+    const BatchBufs o{d_text, d_counts, d_occ, d_n_occ, d_workspace};
+    int rc = batch_check(b, o, workspace_bytes);
+    if (rc) return rc;
+    if (reps < 1) reps = 1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DeviceProps dp;
+    rc = device_props(dp);
+    if (rc) return rc;
+    drop_graph(b);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        if (e0) cudaEventDestroy(e0);
+        return PM_ECUDA;
+    }
+    int best_w = b->plan.warps;
+    float best = -1.0f;
+    for (int w : kBatchWarpChoices) {
+        rc = apply_plan(b, w);
+        if (!rc) rc = ensure_batch_attr(b->plan.smem_bytes);
+        if (!rc) rc = batch_enqueue(b, o, dp.sm_count, st);  // warm-up
+        if (!rc) {
+            e = cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && !rc && e == cudaSuccess; ++r) rc = batch_enqueue(b, o, dp.sm_count, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) { set_cuda_error(int(e)); rc = PM_ECUDA; }
+            if (!rc && pm_scan_status(d_workspace, stream) != PM_OK) rc = PM_ETIMEOUT;
+            if (!rc && (best < 0.0f || ms < best)) { best = ms; best_w = w; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (best_ms) *best_ms = best / float(reps);
+    return apply_plan(b, best_w);
+}
+
+int pm_batch_capture(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_t *d_occ,
+                     int64_t *d_n_occ, void *d_workspace, int64_t workspace_bytes)
+{
+    const BatchBufs o{d_text, d_counts, d_occ, d_n_occ, d_workspace};
+    int rc = batch_check(b, o, workspace_bytes);
+    if (rc) return rc;
+    DeviceProps dp;
+    rc = device_props(dp);
+    if (!rc) rc = ensure_batch_attr(b->plan.smem_bytes);
+    if (rc) return rc;
+    drop_graph(b);
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = batch_enqueue(b, o, dp.sm_count, cs);
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (!rc && e2 != cudaSuccess) e = e2;
+    }
+    if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (!rc && e != cudaSuccess) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        b->graph = nullptr;
+        rc = PM_ECUDA;
+    }
+    return rc;
+}
+
+int pm_batch_replay(const pm_batch *b, void *stream)
+{
+    if (!b || !b->graph) return PM_EINVAL;
+    const cudaError_t e = cudaGraphLaunch(b->graph, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    return PM_OK;
+}
+
+}  // extern "C"

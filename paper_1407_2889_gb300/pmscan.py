@@ -29,8 +29,10 @@ EXPORTED = [
     "pm_ac_compile", "pm_wm_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
     "pm_scan_to_host", "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device",
     "pm_scan_device_noalloc", "pm_noalloc_scratch_bytes", "pm_scan_status",
-    "pm_scan_batch", "pm_selfcheck_host_walk", "pm_strerror", "pm_last_cuda_error",
-    "pm_version",
+    "pm_scan_batch", "pm_batch_prepare", "pm_batch_free", "pm_batch_counts_total",
+    "pm_batch_workspace_bytes", "pm_batch_warps", "pm_batch_scan_device", "pm_batch_tune",
+    "pm_batch_set_warps", "pm_batch_capture", "pm_batch_replay",
+    "pm_selfcheck_host_walk", "pm_strerror", "pm_last_cuda_error", "pm_version",
 ]
 
 
@@ -115,6 +117,26 @@ def lib():
         L.pm_scan_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp),
                                     ctypes.POINTER(i64), i32, u32, vp,
                                     ctypes.POINTER(ctypes.POINTER(pm_result))]
+        L.pm_batch_prepare.restype = ctypes.c_int
+        L.pm_batch_prepare.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, u32, pp]
+        L.pm_batch_free.restype = None
+        L.pm_batch_free.argtypes = [vp]
+        L.pm_batch_counts_total.restype = i64
+        L.pm_batch_counts_total.argtypes = [vp]
+        L.pm_batch_workspace_bytes.restype = i64
+        L.pm_batch_workspace_bytes.argtypes = [vp]
+        L.pm_batch_warps.restype = i32
+        L.pm_batch_warps.argtypes = [vp]
+        L.pm_batch_scan_device.restype = ctypes.c_int
+        L.pm_batch_scan_device.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
+        L.pm_batch_tune.restype = ctypes.c_int
+        L.pm_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp, i64, i32, vp, ctypes.POINTER(ctypes.c_float)]
+        L.pm_batch_set_warps.restype = ctypes.c_int
+        L.pm_batch_set_warps.argtypes = [vp, i32]
+        L.pm_batch_capture.restype = ctypes.c_int
+        L.pm_batch_capture.argtypes = [vp, vp, vp, vp, vp, vp, i64]
+        L.pm_batch_replay.restype = ctypes.c_int
+        L.pm_batch_replay.argtypes = [vp, vp]
         L.pm_selfcheck_host_walk.restype = ctypes.c_int
         L.pm_selfcheck_host_walk.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.POINTER(pm_result))]
         L.pm_strerror.restype = ctypes.c_char_p
@@ -309,6 +331,73 @@ def pm_scan_batch(handles, texts, flags: int = PM_HOST_TEXT, stream=None):
     return [_take_result(outs[j]) for j in range(k)]
 
 
+def pm_batch_prepare(handles, text_off, text_len, occ_off, flags: int = 0) -> int:
+    """Prepared batch: instance j scans text_len[j] bytes at text_off[j] of one
+    device buffer with set handles[j]; its keys go to occ[occ_off[j]:occ_off[j+1]]."""
+    k = len(handles)
+    hs = (ctypes.c_void_p * max(k, 1))(*handles)
+    to = np.ascontiguousarray(text_off, dtype=np.int64)
+    tl = np.ascontiguousarray(text_len, dtype=np.int64)
+    oo = np.ascontiguousarray(occ_off, dtype=np.int64)
+    if to.size != k or tl.size != k or oo.size != k + 1:
+        raise ValueError("text_off and text_len need k entries, occ_off k+1")
+    b = ctypes.c_void_p()
+    _check(lib().pm_batch_prepare(hs, k, to.ctypes.data, tl.ctypes.data, oo.ctypes.data, flags,
+                                  ctypes.byref(b)),
+           "pm_batch_prepare")
+    return int(b.value)
+
+
+def pm_batch_free(b: int) -> None:
+    if b:
+        lib().pm_batch_free(b)
+
+
+def pm_batch_counts_total(b: int) -> int:
+    return int(lib().pm_batch_counts_total(b))
+
+
+def pm_batch_workspace_bytes(b: int) -> int:
+    return int(lib().pm_batch_workspace_bytes(b))
+
+
+def pm_batch_warps(b: int) -> int:
+    return int(lib().pm_batch_warps(b))
+
+
+def pm_batch_scan_device(b: int, d_text, d_counts, d_occ, d_n_occ, d_workspace,
+                         workspace_bytes: int, stream=None) -> None:
+    _check(lib().pm_batch_scan_device(b, _dev_ptr(d_text), _dev_ptr(d_counts), _dev_ptr(d_occ),
+                                      _dev_ptr(d_n_occ), _dev_ptr(d_workspace), int(workspace_bytes),
+                                      _stream_ptr(stream)),
+           "pm_batch_scan_device")
+
+
+def pm_batch_tune(b: int, d_text, d_counts, d_occ, d_n_occ, d_workspace, workspace_bytes: int,
+                  reps: int = 3, stream=None) -> float:
+    ms = ctypes.c_float(0.0)
+    _check(lib().pm_batch_tune(b, _dev_ptr(d_text), _dev_ptr(d_counts), _dev_ptr(d_occ),
+                               _dev_ptr(d_n_occ), _dev_ptr(d_workspace), int(workspace_bytes),
+                               int(reps), _stream_ptr(stream), ctypes.byref(ms)),
+           "pm_batch_tune")
+    return float(ms.value)
+
+
+def pm_batch_set_warps(b: int, warps: int) -> None:
+    _check(lib().pm_batch_set_warps(b, int(warps)), "pm_batch_set_warps")
+
+
+def pm_batch_capture(b: int, d_text, d_counts, d_occ, d_n_occ, d_workspace,
+                     workspace_bytes: int) -> None:
+    _check(lib().pm_batch_capture(b, _dev_ptr(d_text), _dev_ptr(d_counts), _dev_ptr(d_occ),
+                                  _dev_ptr(d_n_occ), _dev_ptr(d_workspace), int(workspace_bytes)),
+           "pm_batch_capture")
+
+
+def pm_batch_replay(b: int, stream=None) -> None:
+    _check(lib().pm_batch_replay(b, _stream_ptr(stream)), "pm_batch_replay")
+
+
 def pm_selfcheck_host_walk(h: int, T):
     T = np.ascontiguousarray(T, dtype=np.uint8)
     rp = ctypes.POINTER(pm_result)()
@@ -358,6 +447,105 @@ class PatternSet:
         if self.h:
             pm_set_free(self.h)
             self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """k Aho-Corasick instances over one device text, scanned in one launch.
+
+    Owns its device result buffers (torch tensors: device memory only).
+    ``occ_caps`` gives each instance's key capacity; ``None`` means counts
+    only. :meth:`exact` sizes the capacities with a counts-only pass first.
+    """
+
+    def __init__(self, sets, d_text, text_off, text_len, occ_caps=None):
+        import torch
+
+        self.sets = list(sets)
+        self.k = len(self.sets)
+        self.d_text = d_text
+        self.text_off = np.asarray(text_off, dtype=np.int64)
+        self.text_len = np.asarray(text_len, dtype=np.int64)
+        self.counts_only = occ_caps is None
+        caps = np.zeros(self.k, np.int64) if occ_caps is None else np.asarray(occ_caps, np.int64)
+        self.occ_off = np.zeros(self.k + 1, np.int64)
+        np.cumsum(caps, out=self.occ_off[1:])
+        flags = PM_COUNTS_ONLY if self.counts_only else 0
+        self.b = pm_batch_prepare([s.h for s in self.sets], self.text_off, self.text_len,
+                                  self.occ_off, flags)
+        dev = d_text.device
+        self.count_off = np.zeros(self.k + 1, np.int64)
+        np.cumsum([s.info()["d"] for s in self.sets], out=self.count_off[1:])
+        self.counts = torch.empty(max(1, pm_batch_counts_total(self.b)), dtype=torch.int64, device=dev)
+        self.n_occ = torch.empty(max(1, self.k), dtype=torch.int64, device=dev)
+        self.occ = torch.empty(max(1, int(self.occ_off[-1])), dtype=torch.int64, device=dev)
+        self.ws_bytes = pm_batch_workspace_bytes(self.b)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+
+    @classmethod
+    def exact(cls, sets, d_text, text_off, text_len, stream=None) -> "Batch":
+        """List-mode batch whose capacities are the exact totals (one
+        counts-only batched scan, synchronised, sizes them)."""
+        import torch
+
+        probe = cls(sets, d_text, text_off, text_len, None)
+        probe.scan(stream)
+        torch.cuda.synchronize()
+        caps = probe.n_occ[: probe.k].cpu().numpy().copy()
+        probe.close()
+        return cls(sets, d_text, text_off, text_len, caps)
+
+    def _bufs(self):
+        return (self.d_text, self.counts, None if self.counts_only else self.occ, self.n_occ, self.ws,
+                self.ws_bytes)
+
+    def scan(self, stream=None) -> None:
+        pm_batch_scan_device(self.b, *self._bufs(), stream=stream)
+
+    def tune(self, reps: int = 3, stream=None) -> float:
+        return pm_batch_tune(self.b, *self._bufs(), reps=reps, stream=stream)
+
+    def set_warps(self, warps: int) -> None:
+        pm_batch_set_warps(self.b, warps)
+
+    @property
+    def warps(self) -> int:
+        return pm_batch_warps(self.b)
+
+    def capture(self) -> None:
+        pm_batch_capture(self.b, *self._bufs())
+
+    def replay(self, stream=None) -> None:
+        pm_batch_replay(self.b, stream)
+
+    def status(self, stream=None) -> int:
+        return pm_scan_status(self.ws, stream)
+
+    def results(self):
+        """[(occ uint64 array, counts int64 array)] per instance (synchronises)."""
+        n_occ = self.n_occ[: self.k].cpu().numpy()
+        counts = self.counts.cpu().numpy()
+        occ = None if self.counts_only else self.occ.cpu().numpy().view(np.uint64)
+        out = []
+        for j in range(self.k):
+            c = counts[self.count_off[j]:self.count_off[j + 1]].copy()
+            if occ is None:
+                o = np.empty(0, np.uint64)
+            else:
+                cap = int(self.occ_off[j + 1] - self.occ_off[j])
+                o = occ[self.occ_off[j]:self.occ_off[j] + min(cap, int(n_occ[j]))].copy()
+            out.append((o, c, int(n_occ[j])))
+        return out
+
+    def close(self):
+        if getattr(self, "b", 0):
+            pm_batch_free(self.b)
+            self.b = 0
 
     def __del__(self):
         try:

@@ -217,3 +217,50 @@ def large_set(d: int, text: np.ndarray, m: int = 32):
     """Large pattern set (d = 1e5 -> seed 200, 5e5 -> seed 201) over an EST text."""
     seed = {100000: 200, 500000: 201}.get(d, 202)
     return mixed_patterns(text, d, m, seed)
+
+
+# ---------------------------------------------------------------------------
+# Batched workload: many independent (text, pattern set) instances
+# ---------------------------------------------------------------------------
+BATCH_K = 4096
+BATCH_SEED = 4000
+BATCH_N = (1 << 10, 1 << 22)     # text length, log-uniform
+BATCH_D = (10, 10000)            # patterns per set, log-uniform
+BATCH_M = (8, 64)                # pattern length, uniform integer
+BATCH_SAMPLE_SPAN = 1 << 16      # sampled patterns come from this much text
+
+
+def _log_uniform(u: float, lo: int, hi: int) -> int:
+    return int(min(hi, max(lo, round(lo * (hi / lo) ** u))))
+
+
+def batch_plan(k: int, base_n: int, seed: int = BATCH_SEED, n_range=BATCH_N,
+               d_range=BATCH_D, m_range=BATCH_M):
+    """Shapes of k instances over one EST-shaped base text of base_n bytes.
+
+    Instance j draws from its own seed (seed + j): a text length log-uniform
+    in n_range, a start uniform in [0, base_n - length] rounded down to a
+    multiple of 16, d log-uniform in d_range and m uniform in m_range. Texts
+    are slices of the base text, so they keep its EST shape and may overlap.
+    Returns int64 arrays (off, length, d, m).
+    """
+    off = np.empty(k, np.int64)
+    ln = np.empty(k, np.int64)
+    d = np.empty(k, np.int64)
+    m = np.empty(k, np.int64)
+    for j in range(k):
+        u = uniform01(seed + j, SID_MISC, 4)
+        ln[j] = min(_log_uniform(float(u[0]), *n_range), base_n)
+        off[j] = (int(u[1] * (base_n - ln[j] + 1)) // 16) * 16
+        d[j] = _log_uniform(float(u[2]), *d_range)
+        m[j] = m_range[0] + min(int(u[3] * (m_range[1] - m_range[0] + 1)), m_range[1] - m_range[0])
+    return off, ln, d, m
+
+
+def batch_patterns(base: np.ndarray, off: int, length: int, d: int, m: int, seed: int) -> np.ndarray:
+    """Pattern set of one instance: d//2 windows sampled from the base text
+    starting at the instance's slice (at least BATCH_SAMPLE_SPAN bytes of it,
+    so that short slices still offer ACGT-only windows), the rest random."""
+    span = max(length, BATCH_SAMPLE_SPAN)
+    lo = max(0, min(off, base.size - span))
+    return mixed_patterns(base[lo:lo + span], d, m, seed)
