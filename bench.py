@@ -34,7 +34,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "text GB/s scanned on 1 GB300 (AC & WM), batched vs plain; % of HBM roofline"
-KERNEL_SOURCES = ["paper_1407_2889_gb300/csrc/scan_ac.cu", "paper_1407_2889_gb300/csrc/scan_common.cuh"]
+KERNEL_SOURCES = ["paper_1407_2889_gb300/csrc/scan_ac.cu", "paper_1407_2889_gb300/csrc/ac_device.cuh",
+                  "paper_1407_2889_gb300/csrc/scan_common.cuh"]
 
 
 def kernel_hash() -> str:
@@ -53,7 +54,7 @@ def measured_peaks() -> tuple[float, str]:
     return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel_name: str):
+def recorded_traffic(kernel_name: str, workload: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel source and the same workload; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -62,7 +63,7 @@ def recorded_traffic(kernel_name: str):
     with open(p) as f:
         rec = json.load(f)
     e = rec.get(kernel_name)
-    if not e or e.get("kernel_hash") != kernel_hash():
+    if not e or e.get("kernel_hash") != kernel_hash() or e.get("workload") != workload:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -159,6 +160,12 @@ def parse():
     return ap.parse_args()
 
 
+def workload_name(args) -> str:
+    mib = args.text_mib or 1024
+    return (f"EST-shaped {mib} MiB text (seed 1), Aho-Corasick DFA, {args.mode} mode, "
+            f"d={args.d}, m={args.m} (half copied from the text, half random)")
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -173,10 +180,6 @@ def run_reference(args, rank):
     from paper_1407_2889_gb300 import synth
     import oracle
     T = synth.est_text(synth.EST_N, 1)
-    if args.only_batch:
-        d_text = torch.from_numpy(T).cuda()
-        print(json.dumps(batched_comparison(args, T, d_text, pm, torch, synth)), flush=True)
-        return
     _, P = synth.est_case(args.d, args.m, text=T)
     cores = os.cpu_count() or 1
     sample = 8 << 20
@@ -195,8 +198,9 @@ def run_reference(args, rank):
         "n_gpus": args.gpus, "steps": len(times), "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"EST-shaped text, AC list mode, d={args.d}, m={args.m}; oracle dictionary route on {sample >> 20} MiB samples",
-                   "text_bytes": sample, "d": args.d, "m": args.m},
+        "config": {"workload": workload_name(args), "text_bytes": T.size, "d": args.d, "m": args.m,
+                   "algo": "AC", "mode": args.mode,
+                   "timed": f"oracle (sorted-dictionary route) on {sample >> 20} MiB samples of the text"},
         "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
                          "sample": f"{len(times)} samples of {sample >> 20} MiB of the 1 GiB EST text"},
         "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -293,7 +297,7 @@ def main():
     achieved = alg_bytes / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": recorded_traffic("ac_scan_kernel"),
+                "traffic": recorded_traffic("ac_scan_kernel", f"est1gib_d{d}_m{args.m}_{args.mode}_n{n}"),
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": "ac_scan_kernel<uint16_t,6,1,dna,smem>"}
 
@@ -334,7 +338,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"EST-shaped 1 GiB text (seed 1), Aho-Corasick DFA, {args.mode} mode, d={d}, m={args.m} (half copied from the text, half random)",
+            "config": {"workload": workload_name(args),
                        "text_bytes": n, "d": d, "m": args.m, "algo": "AC", "mode": args.mode,
                        "n_occ": n_occ, "l2": "inputs larger than L2 (1 GiB text), no flush",
                        "parallelism": f"replicas x{world}",

@@ -363,7 +363,7 @@ static int64_t set_scratch(const pm_set *s)
 
 static int64_t set_tiles(const pm_set *s, int64_t n)
 {
-    const int64_t k = s->algo == PM_ALGO_AC ? s->dac.ksub : 1;
+    const int64_t k = s->algo == PM_ALGO_AC ? ac_ksub_for(s->dac, n) : 1;
     return (warp_tiles(n) + k - 1) / k;
 }
 

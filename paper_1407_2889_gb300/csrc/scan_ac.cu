@@ -619,6 +619,14 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     return PM_OK;
 }
 
+int ac_ksub_for(const DevAc &dv, int64_t n)
+{
+    const long long nsub = warp_tiles(n);
+    int k = dv.ksub < 1 ? 1 : dv.ksub;
+    while (k > 1 && (nsub + k - 1) / k < dv.max_warps) k >>= 1;
+    return k;
+}
+
 int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n, bool list,
               int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
               void *stream)
@@ -626,7 +634,8 @@ int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     const long long nsub = warp_tiles(n);
-    const long long ntiles = (nsub + dv.ksub - 1) / dv.ksub;
+    const int K = ac_ksub_for(dv, n);
+    const long long ntiles = (nsub + K - 1) / K;
     const long long nterms = (long long)t.canon.size();
     e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
@@ -672,7 +681,7 @@ int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t
     }
     a.ntiles = ntiles;
     a.nsub = nsub;
-    a.ksub = dv.ksub;
+    a.ksub = K;
     a.pool_cap = dv.pool_cap;
     a.stage_cap = dv.stage_cap;
     a.list = list ? 1 : 0;
