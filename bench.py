@@ -153,6 +153,10 @@ def parse():
                     help="instances of the batched-vs-plain comparison (0 skips it)")
     ap.add_argument("--only-batch", action="store_true",
                     help="run only the batched-vs-plain comparison and print it")
+    ap.add_argument("--serve-seconds", type=float, default=6.0,
+                    help="length of the Poisson request stream of the serving run (0 skips it)")
+    ap.add_argument("--only-serve", action="store_true",
+                    help="run only the serving measurement and print it")
     ap.add_argument("--mode", default="list", choices=["list", "counts"],
                     help="timed step: list mode (default) or counts only")
     ap.add_argument("--text-mib", type=int, default=0,
@@ -229,6 +233,9 @@ def main():
     if args.only_batch:
         d_text = torch.from_numpy(T).cuda()
         print(json.dumps(batched_comparison(args, T, d_text, pm, torch, synth)), flush=True)
+        return
+    if args.only_serve:
+        print(json.dumps(serving_run(args, torch.from_numpy(T).pin_memory(), pm, torch, synth)), flush=True)
         return
     _, P = synth.est_case(args.d, args.m, text=T)
     if args.text_mib:
@@ -326,6 +333,9 @@ def main():
         e2e = {"value": n / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": n,
                "d2h_bytes_per_step": (8 * n_occ if args.mode == "list" else 0) + 8 * d + 8,
                "api": "pm_scan_to_host (pinned host text and results)"}
+
+    if rank == 0 and not args.no_extras and args.serve_seconds > 0:
+        extras["serving"] = serving_run(args, pinned, pm, torch, synth)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -504,6 +514,88 @@ def batched_comparison(args, T, d_text, pm, torch, synth):
     for s in sets:
         s.close()
     return out
+
+
+def serving_run(args, pinned, pm, torch, synth):
+    """Serving measurement: a Poisson stream of requests (mean 2000/s) over
+    64 device-resident sets (d log-uniform 100-10^5, m in {8, 16, 24, 32},
+    seed 5000+j), each request a slice of the pinned EST text with length
+    log-uniform 1 KiB-16 MiB (seed 5000), submitted at its arrival time from
+    one thread and waited on from another; latency is submit -> result in
+    host memory. A sample of results is compared with solo scans."""
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+
+    T = pinned.numpy()
+    nsets = 64
+    u = synth.uniform01(5000, synth.SID_MISC, 2 * nsets).reshape(nsets, 2)
+    shapes = [(int(round(100 * 1000 ** float(a))), (8, 16, 24, 32)[min(3, int(b * 4))]) for a, b in u]
+
+    def make(j):
+        d, m = shapes[j]
+        off = (j * 104729 * 4096) % (T.size - (1 << 20))
+        return pm.PatternSet.ac(synth.batch_patterns(T, off, 1 << 20, d, m, 5000 + j))
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        sets = list(ex.map(make, range(nsets)))
+    t_compile = time.perf_counter() - t0
+    rate, secs = 2000.0, float(args.serve_seconds)
+    k = int(rate * secs)
+    r = synth.uniform01(5001, synth.SID_MISC, 4 * k).reshape(k, 4)
+    gaps = -np.log(np.maximum(r[:, 0], 1e-12)) / rate
+    arrive = np.cumsum(gaps)
+    lens = np.rint(1024 * (16384.0 ** r[:, 1])).astype(np.int64)
+    offs = (r[:, 2] * (T.size - lens)).astype(np.int64)
+    which = np.minimum((r[:, 3] * nsets).astype(np.int64), nsets - 1)
+    srv = pm.Server(budget_bytes=8 << 30, max_batch=256, max_inflight=3)
+    tickets = [None] * k
+    submitted = threading.Semaphore(0)
+    results = {}
+    sample = set(range(0, k, max(1, k // 24)))
+
+    def producer():
+        start = time.perf_counter()
+        for j in range(k):
+            now = time.perf_counter() - start
+            if arrive[j] > now:
+                time.sleep(arrive[j] - now)
+            tickets[j] = srv.submit(sets[which[j]], pinned[offs[j]:offs[j] + lens[j]])
+            submitted.release()
+
+    def consumer():
+        for j in range(k):
+            submitted.acquire()
+            res = srv.wait(tickets[j])
+            if j in sample:
+                results[j] = res
+
+    pt = threading.Thread(target=producer)
+    ct = threading.Thread(target=consumer)
+    t0 = time.perf_counter()
+    pt.start()
+    ct.start()
+    pt.join()
+    ct.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    same = True
+    for j, (occ, cnt) in results.items():
+        so, sc = sets[which[j]].scan(T[offs[j]:offs[j] + lens[j]])
+        same = same and bool(np.array_equal(so, occ)) and bool(np.array_equal(sc, cnt))
+    for s_ in sets:
+        s_.close()
+    return {
+        "requests": k, "offered_req_per_s": rate, "seconds": secs, "wall_s": wall,
+        "offered_gbs": float(lens.sum()) / float(arrive[-1]) / 1e9,
+        "sustained_gbs": st["gbs"], "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+        "mean_ms": st["mean_us"] / 1e3, "batches": st["batches"], "mean_batch": st["mean_batch"],
+        "reruns": st["reruns"], "peak_inflight": st["peak_inflight"],
+        "identical_to_solo_on_sample": same, "sampled": len(results), "compile_s": t_compile,
+        "workload": "Poisson 2000 req/s; text log-uniform 1 KiB-16 MiB slices of the pinned EST text (H2D and D2H "
+                    "inside the latency); 64 sets d log-uniform 100-1e5, m in {8,16,24,32}; list mode",
+    }
 
 
 if __name__ == "__main__":

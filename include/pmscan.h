@@ -289,6 +289,65 @@ int pm_batch_capture(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint
 int pm_batch_replay(const pm_batch *b, void *stream);
 
 /*
+ * Serving loop with continuous batching (the paper has no counterpart; it
+ * scans one text per run). A server owns a device arena of
+ * device_budget_bytes for the texts, counts and occurrence buffers of the
+ * requests in flight, and two host threads:
+ *   - a dispatcher admits queued requests in arrival order while their
+ *     memory fits the arena, and launches everything admitted as one batched
+ *     scan (pm_batch_scan_device's kernel) on a free stream slot; up to
+ *     max_inflight batches run at once, so requests that arrive while others
+ *     are on the GPU start as soon as memory and a slot free up;
+ *   - a completer copies each finished batch's results to host memory
+ *     (re-running, with the exact capacity, the rare request whose
+ *     occurrence estimate was short), frees its memory, records latencies and
+ *     wakes waiters.
+ * A request's result equals a solo scan of the same text with the same set
+ * (pm_scan): instances never share counters or outputs.
+ */
+typedef struct pm_server pm_server;
+typedef struct pm_server_params {
+    int64_t device_budget_bytes;  /* arena size (default 4 GiB) */
+    int32_t max_batch;            /* requests per batched launch (default 512) */
+    int32_t max_inflight;         /* batches in flight, one stream each (default 3, max 16) */
+    int32_t warps_per_cta;        /* batched kernel shape, 1..16 (default 12) */
+    int32_t pad;
+    int64_t counter_words;        /* per-slot workspace for global per-terminal
+                                     counters, in 8-byte words (default 4 Mi) */
+} pm_server_params;
+typedef struct pm_server_stats {
+    int64_t completed;            /* requests finished with PM_OK */
+    int64_t bytes;                /* text bytes of those requests */
+    int64_t batches;              /* batched launches */
+    int64_t reruns;               /* requests re-run with an exact capacity */
+    int64_t peak_inflight;        /* most requests admitted at once */
+    int64_t pending;              /* requests waiting for admission now */
+    int64_t arena_used;           /* arena bytes held now */
+    double mean_batch;            /* requests per launch */
+    double p50_us, p99_us, mean_us; /* latency, submit -> result on the host */
+    double gbs;                   /* text bytes / (last completion - first submit) */
+} pm_server_stats;
+
+/* params may be NULL (all defaults). Allocates the arena and per-slot
+ * buffers on the current device and starts the two threads. */
+int pm_server_create(const pm_server_params *params, pm_server **out);
+/*
+ * Queue a scan of host text T (n bytes) against `set` (an AC set the batched
+ * scan accepts, else PM_EINVAL); flags: 0 or PM_COUNTS_ONLY. T and set must
+ * stay valid until pm_server_wait returns for the ticket. PM_ETOOBIG when
+ * the request alone could never fit the arena. Never blocks on the GPU.
+ */
+int pm_server_submit(pm_server *s, const pm_set *set, const uint8_t *T, int64_t n,
+                     uint32_t flags, int64_t *ticket);
+/* Block until the request is done; returns its status and hands over its
+ * result (library-owned; pm_result_free). Each ticket is waited on once. */
+int pm_server_wait(pm_server *s, int64_t ticket, pm_result **out);
+int pm_server_get_stats(pm_server *s, pm_server_stats *st);
+/* Finishes every queued and running request, then frees everything
+ * (results never waited on are freed too). */
+void pm_server_destroy(pm_server *s);
+
+/*
  * Table self-check on the host, no GPU needed: walks the compiled AC table
  * (or applies the compiled WM tables) exactly as the kernels do, one thread,
  * on the host. It exists to test the compiler; pm_scan never calls it.

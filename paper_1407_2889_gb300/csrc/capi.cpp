@@ -249,6 +249,8 @@ pm_result *new_result(int64_t d, int64_t n_occ, bool list, bool pinned)
 int64_t set_d(const pm_set *s) { return s->algo == PM_ALGO_AC ? s->ac.d : s->wm.d; }
 
 }  // namespace
+
+pm_result *make_result(int64_t d, int64_t n_occ, bool list) { return new_result(d, n_occ, list, false); }
 }  // namespace pm
 
 using namespace pm;
@@ -353,23 +355,27 @@ static int64_t set_terms(const pm_set *s)
     return s->algo == PM_ALGO_AC ? int64_t(s->ac.canon.size()) : 0;
 }
 
-// list-mode scratch: two slots of one warp tile of entries per warp
-static int64_t set_scratch(const pm_set *s)
-{
-    if (s->algo != PM_ALGO_AC) return 0;
-    const int64_t se = (s->ac.dna ? s->ac.entry_bytes : 4) == 2 ? 4 : 8;
-    return s->dac.max_warps * 2 * int64_t(s->dac.ksub) * kWarpTile * se;
-}
-
 static int64_t set_tiles(const pm_set *s, int64_t n)
 {
     const int64_t k = s->algo == PM_ALGO_AC ? ac_ksub_for(s->dac, n) : 1;
     return (warp_tiles(n) + k - 1) / k;
 }
 
+// list-mode scratch: two slots of K warp tiles of entries for every warp of
+// the grid a scan of n bytes launches (at most one warp per look-back tile,
+// rounded up to whole CTAs, and at most the largest grid)
+static int64_t set_scratch(const pm_set *s, int64_t n)
+{
+    if (s->algo != PM_ALGO_AC) return 0;
+    const int64_t se = (s->ac.dna ? s->ac.entry_bytes : 4) == 2 ? 4 : 8;
+    const int64_t w = std::max<int64_t>(1, s->dac.warps);
+    const int64_t grid_warps = std::min<int64_t>(s->dac.max_warps, (set_tiles(s, n) + w - 1) / w * w);
+    return grid_warps * 2 * int64_t(ac_ksub_for(s->dac, n)) * kWarpTile * se;
+}
+
 static int64_t set_ws_bytes(const pm_set *s, int64_t n, bool list)
 {
-    return workspace_bytes_for(set_tiles(s, n), list, set_terms(s), set_scratch(s));
+    return workspace_bytes_for(set_tiles(s, n), list, set_terms(s), set_scratch(s, n));
 }
 
 int64_t pm_scan_workspace_bytes(const pm_set *s, int64_t n, uint32_t flags)

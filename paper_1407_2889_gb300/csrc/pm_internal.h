@@ -163,6 +163,59 @@ int wm_launch(const WmTables &t, const DevWm &dev, const uint8_t *d_text, int64_
               int64_t *d_n_occ, void *d_ws, void *stream);
 
 void set_cuda_error(int err);
+// a library-owned result (plain host arrays), released by pm_result_free
+pm_result *make_result(int64_t d, int64_t n_occ, bool list);
+
+}  // namespace pm
+
+struct pm_set;
+
+namespace pm {
+
+// ---------------------------------------------------------------------------
+// Batched Aho-Corasick scan (scan_batch.cu): many (text, set) instances in
+// one persistent launch. Offsets are relative to the base pointers given to
+// batch_launch_raw: bytes for the text, elements for counts and occ.
+// ---------------------------------------------------------------------------
+struct BatchDesc {                 // one instance, in processing order
+    long long text_off, n;         // text bytes [text_off, text_off + n)
+    long long count_off;           // counts of the instance start here (d entries)
+    long long occ_off, occ_cap;    // occurrence keys go here (capacity occ_cap)
+    long long ccount_off;          // into the workspace, when counters are global
+    long long out_slot;            // n_occ[out_slot] receives the total
+    const void *table;
+    const uint32_t *mask;
+    const void *rank;
+    const void *canon;
+    const uint32_t *grp_off;
+    const uint32_t *grp_ids;
+    int smem_entries, eb, m, nwords, nterms, d;
+    int ids_off, hist_off;         // byte offsets in the CTA's table region; -1 = global
+    uint32_t mid_base, lut, pad, pad2;
+};
+
+struct BatchShape {                // launch shape and shared-memory split
+    int warps = 12;
+    int region_bytes = 0;          // per-CTA table / ids / counters region
+    long long smem_bytes = 0;
+    int sm_count = 0;
+};
+
+struct BatchInst {
+    const pm_set *set;
+    int64_t text_off, text_len, count_off, occ_off, occ_cap, out_slot;
+};
+
+int batch_shape(int warps, BatchShape &out);
+bool batch_supports(const pm_set *s);   // AC, ACGT-like alphabet, m <= 65, device tables
+// Descriptors of k instances in the order given (out may be NULL); returns
+// the number of global counter words the workspace needs.
+int64_t batch_fill(const BatchInst *inst, int k, const BatchShape &sh, BatchDesc *out);
+inline int64_t batch_ws_bytes(int64_t ccount_words) { return kWsHeader + 8 * ccount_words; }
+int batch_prepare_launch(const BatchShape &sh);  // host-side set-up, before any capture
+int batch_launch_raw(const BatchDesc *d_desc, int k, const uint8_t *text, int64_t *counts,
+                     uint64_t *occ, int64_t *n_occ, void *ws, int64_t ccount_total,
+                     const BatchShape &sh, bool list, void *stream);
 
 }  // namespace pm
 

@@ -25,22 +25,6 @@
 
 namespace pm {
 
-struct BatchDesc {                 // one instance, in processing order
-    long long text_off, n;         // into the batch text buffer
-    long long count_off;           // into the batch counts buffer (d entries)
-    long long occ_off, occ_cap;    // into the batch occurrence buffer
-    long long ccount_off;          // into the workspace, when counters are global
-    long long out_slot;            // instance index (for n_occ)
-    const void *table;
-    const uint32_t *mask;
-    const void *rank;
-    const void *canon;
-    const uint32_t *grp_off;
-    const uint32_t *grp_ids;
-    int smem_entries, eb, m, nwords, nterms, d;
-    int ids_off, hist_off;         // byte offsets in the CTA's table region; -1 = global
-    uint32_t mid_base, lut, pad, pad2;
-};
 
 namespace {
 
@@ -395,26 +379,6 @@ __global__ void __launch_bounds__(512, 1) ac_batch_kernel(const BatchArgs a)
 constexpr int kBatchWarpChoices[] = {8, 12, 16};   // autotuner candidates
 constexpr int kBatchMaxWarps = 16;
 
-struct BatchPlan {
-    int warps = 12;
-    int region_bytes = 0;
-    long long smem_bytes = 0;
-};
-
-// Per-CTA shared memory: one block of per-warp buffers, the rest is the
-// instance region (table prefix, ids, counters).
-static BatchPlan plan_batch(int warps, long long smem_optin)
-{
-    BatchPlan p;
-    p.warps = warps;
-    const long long budget = smem_optin - 2048;   // static shared memory and slack
-    long long room = budget - (long long)warps * batch_warp_bytes();
-    if (room < 4096) room = 4096;
-    p.region_bytes = int(room & ~15LL);
-    p.smem_bytes = (long long)p.region_bytes + (long long)warps * batch_warp_bytes();
-    return p;
-}
-
 struct InstLayout {
     int smem_entries, ids_off, hist_off;
 };
@@ -448,56 +412,50 @@ static InstLayout layout_of(const AcTables &t, int region)
     return L;
 }
 
-}  // namespace pm
-
-// The prepared batch of the C ABI.
-struct pm_batch {
-    int32_t k = 0;
-    std::vector<const pm_set *> sets;
-    std::vector<int64_t> text_off, text_len, occ_off, count_off, ccount_off;
-    std::vector<int32_t> order;       // processing order (largest text first)
-    pm::BatchDesc *d_desc = nullptr;
-    int64_t ccount_total = 0;
-    int64_t ws_bytes = 0;             // enough for every candidate plan
-    int64_t d_total = 0;
-    pm::BatchPlan plan;
-    uint32_t flags = 0;
-    cudaGraphExec_t graph = nullptr;  // captured launch, see pm_batch_capture
-};
-
-namespace pm {
-
-// Global per-terminal counters (workspace) for the instances whose counters
-// stay out of shared memory under `plan`.
-static int64_t ccount_for(const pm_batch &b, const BatchPlan &plan, std::vector<int64_t> *off)
+// Per-CTA shared memory: one block of per-warp buffers, the rest is the
+// instance region (table prefix, ids, counters).
+int batch_shape(int warps, BatchShape &out)
 {
-    int64_t tot = 0;
-    if (off) off->assign(size_t(b.k) + 1, 0);
-    for (int32_t j = 0; j < b.k; ++j) {
-        const AcTables &t = b.sets[size_t(j)]->ac;
-        if (layout_of(t, plan.region_bytes).hist_off < 0) tot += int64_t(t.canon.size());
-        if (off) (*off)[size_t(j) + 1] = tot;
-    }
-    return tot;
+    if (warps < 1 || warps > kBatchMaxWarps) return PM_EINVAL;
+    DeviceProps dp;
+    const int rc = device_props(dp);
+    if (rc) return rc;
+    out.warps = warps;
+    const long long budget = (long long)dp.smem_optin - 2048;   // static shared memory and slack
+    long long room = budget - (long long)warps * batch_warp_bytes();
+    if (room < 4096) room = 4096;
+    out.region_bytes = int(room & ~15LL);
+    out.smem_bytes = (long long)out.region_bytes + (long long)warps * batch_warp_bytes();
+    out.sm_count = dp.sm_count;
+    return PM_OK;
 }
 
-static void fill_desc(const pm_batch &b, std::vector<BatchDesc> &out)
+bool batch_supports(const pm_set *s)
 {
-    out.resize(size_t(b.k));
-    for (int32_t q = 0; q < b.k; ++q) {
-        const int32_t j = b.order[size_t(q)];
-        const pm_set *s = b.sets[size_t(j)];
-        const AcTables &t = s->ac;
-        const DevAc &dv = s->dac;
-        BatchDesc &D = out[size_t(q)];
+    return s && !s->host_only && s->algo == PM_ALGO_AC && s->ac.dna && s->ac.m <= kBatchMaxM;
+}
+
+int64_t batch_fill(const BatchInst *inst, int k, const BatchShape &sh, BatchDesc *out)
+{
+    int64_t ccount = 0;
+    for (int q = 0; q < k; ++q) {
+        const BatchInst &I = inst[q];
+        const AcTables &t = I.set->ac;
+        const InstLayout L = layout_of(t, sh.region_bytes);
+        const int64_t nt = int64_t(t.canon.size());
+        const int64_t coff = ccount;
+        if (L.hist_off < 0) ccount += nt;
+        if (!out) continue;
+        const DevAc &dv = I.set->dac;
+        BatchDesc &D = out[q];
         std::memset(&D, 0, sizeof(D));
-        D.text_off = b.text_off[size_t(j)];
-        D.n = b.text_len[size_t(j)];
-        D.count_off = b.count_off[size_t(j)];
-        D.occ_off = b.occ_off[size_t(j)];
-        D.occ_cap = b.occ_off[size_t(j) + 1] - b.occ_off[size_t(j)];
-        D.ccount_off = b.ccount_off[size_t(j)];
-        D.out_slot = j;
+        D.text_off = I.text_off;
+        D.n = I.text_len;
+        D.count_off = I.count_off;
+        D.occ_off = I.occ_off;
+        D.occ_cap = I.occ_cap;
+        D.ccount_off = coff;
+        D.out_slot = I.out_slot;
         D.table = dv.table;
         D.mask = dv.flag_mask;
         D.rank = dv.flag_rank;
@@ -505,13 +463,12 @@ static void fill_desc(const pm_batch &b, std::vector<BatchDesc> &out)
         D.grp_off = dv.grp_off;
         D.grp_ids = dv.grp_ids;
         D.eb = t.entry_bytes;
-        const InstLayout L = layout_of(t, b.plan.region_bytes);
         D.smem_entries = L.smem_entries;
         D.ids_off = L.ids_off;
         D.hist_off = L.hist_off;
         D.m = t.m;
         D.nwords = int(t.flag_mask.size());
-        D.nterms = int(t.canon.size());
+        D.nterms = int(nt);
         D.d = int(t.d);
         D.mid_base = uint32_t(t.d0_row << t.lw);
         D.lut = t.lut;
@@ -519,29 +476,7 @@ static void fill_desc(const pm_batch &b, std::vector<BatchDesc> &out)
         for (uint32_t x = 0; x < 256; ++x)  // a byte outside the alphabet
             if (t.cls[x] == 0xFF) { D.pad = x; break; }
     }
-}
-
-// Lay the batch out for `warps` warps per CTA and upload the descriptors
-// (into the existing device array once there is one).
-static int apply_plan(pm_batch *b, int warps)
-{
-    DeviceProps dp;
-    int rc = device_props(dp);
-    if (rc) return rc;
-    b->plan = plan_batch(warps, dp.smem_optin);
-    b->ccount_total = ccount_for(*b, b->plan, &b->ccount_off);
-    if (b->k == 0) return PM_OK;
-    std::vector<BatchDesc> h;
-    fill_desc(*b, h);
-    cudaError_t e = cudaSuccess;
-    if (!b->d_desc) e = cudaMalloc(&b->d_desc, h.size() * sizeof(BatchDesc));
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, h.data(), h.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        set_cuda_error(int(e));
-        cudaGetLastError();
-        return e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
-    }
-    return PM_OK;
+    return ccount;
 }
 
 static int ensure_batch_attr(long long smem_bytes)
@@ -560,6 +495,76 @@ static int ensure_batch_attr(long long smem_bytes)
     return PM_OK;
 }
 
+int batch_prepare_launch(const BatchShape &sh) { return ensure_batch_attr(sh.smem_bytes); }
+
+// A memset of the queue, status and global counters, then the persistent
+// kernel. Nothing else touches the host, so the pair can be captured in a
+// graph (batch_prepare_launch must have run for the shape).
+int batch_launch_raw(const BatchDesc *d_desc, int k, const uint8_t *text, int64_t *counts,
+                     uint64_t *occ, int64_t *n_occ, void *ws, int64_t ccount_total,
+                     const BatchShape &sh, bool list, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(ws, 0, size_t(batch_ws_bytes(ccount_total)), st);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    if (k == 0) return PM_OK;
+    BatchArgs a;
+    a.desc = d_desc;
+    a.k = k;
+    a.text = text;
+    a.counts = reinterpret_cast<long long *>(counts);
+    a.occ = reinterpret_cast<unsigned long long *>(occ);
+    a.n_occ = reinterpret_cast<long long *>(n_occ);
+    a.ws = reinterpret_cast<dev::WsHeader *>(ws);
+    a.ccount = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + kWsHeader);
+    a.list = list ? 1 : 0;
+    a.region_bytes = sh.region_bytes;
+    const int grid = std::min(sh.sm_count, k);
+    ac_batch_kernel<<<dim3(unsigned(grid)), dim3(unsigned(sh.warps * 32)), size_t(sh.smem_bytes), st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    return PM_OK;
+}
+
+}  // namespace pm
+
+// The prepared batch of the C ABI.
+struct pm_batch {
+    int32_t k = 0;
+    std::vector<int64_t> occ_off, count_off;
+    std::vector<pm::BatchInst> inst;  // processing order (largest text first)
+    pm::BatchDesc *d_desc = nullptr;
+    int64_t ccount_total = 0;
+    int64_t ws_bytes = 0;             // enough for every candidate shape
+    int64_t d_total = 0;
+    pm::BatchShape shape;
+    uint32_t flags = 0;
+    cudaGraphExec_t graph = nullptr;  // captured launch, see pm_batch_capture
+};
+
+namespace pm {
+
+// Lay the batch out for `warps` warps per CTA and upload the descriptors
+// (into the existing device array once there is one).
+static int apply_plan(pm_batch *b, int warps)
+{
+    int rc = batch_shape(warps, b->shape);
+    if (rc) return rc;
+    b->ccount_total = batch_fill(b->inst.data(), b->k, b->shape, nullptr);
+    if (b->k == 0) return PM_OK;
+    std::vector<BatchDesc> h(size_t(b->k));
+    batch_fill(b->inst.data(), b->k, b->shape, h.data());
+    cudaError_t e = cudaSuccess;
+    if (!b->d_desc) e = cudaMalloc(&b->d_desc, h.size() * sizeof(BatchDesc));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, h.data(), h.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
+    }
+    return PM_OK;
+}
+
 struct BatchBufs {
     const uint8_t *text;
     int64_t *counts;
@@ -568,31 +573,10 @@ struct BatchBufs {
     void *ws;
 };
 
-// Enqueue one batched scan: a memset of the queue, status and global
-// counters, then the persistent kernel. Nothing else touches the host, so the
-// pair can be captured in a graph.
-static int batch_enqueue(const pm_batch *b, const BatchBufs &o, int sm_count, cudaStream_t st)
+static int batch_enqueue(const pm_batch *b, const BatchBufs &o, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(o.ws, 0, size_t(kWsHeader + b->ccount_total * 8), st);
-    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-    if (b->k == 0) return PM_OK;
-    BatchArgs a;
-    a.desc = b->d_desc;
-    a.k = b->k;
-    a.text = o.text;
-    a.counts = reinterpret_cast<long long *>(o.counts);
-    a.occ = reinterpret_cast<unsigned long long *>(o.occ);
-    a.n_occ = reinterpret_cast<long long *>(o.n_occ);
-    a.ws = reinterpret_cast<dev::WsHeader *>(o.ws);
-    a.ccount = reinterpret_cast<unsigned long long *>(static_cast<char *>(o.ws) + kWsHeader);
-    a.list = (b->flags & PM_COUNTS_ONLY) ? 0 : 1;
-    a.region_bytes = b->plan.region_bytes;
-    const int grid = std::min(sm_count, b->k);
-    ac_batch_kernel<<<dim3(unsigned(grid)), dim3(unsigned(b->plan.warps * 32)),
-                      size_t(b->plan.smem_bytes), st>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-    return PM_OK;
+    return batch_launch_raw(b->d_desc, b->k, o.text, o.counts, o.occ, o.n_occ, o.ws, b->ccount_total,
+                            b->shape, !(b->flags & PM_COUNTS_ONLY), st);
 }
 
 static int batch_check(const pm_batch *b, const BatchBufs &o, int64_t ws_bytes)
@@ -624,8 +608,7 @@ int pm_batch_prepare(const pm_set *const *sets, int32_t k, const int64_t *text_o
     if (flags & ~(PM_DEVICE_TEXT | PM_COUNTS_ONLY)) return PM_EINVAL;
     if (k > 0 && occ_off[0] < 0) return PM_EINVAL;
     for (int32_t j = 0; j < k; ++j) {
-        const pm_set *s = sets[j];
-        if (!s || s->host_only || s->algo != PM_ALGO_AC || !s->ac.dna || s->ac.m > kBatchMaxM) return PM_EINVAL;
+        if (!batch_supports(sets[j])) return PM_EINVAL;
         if (text_off[j] < 0 || text_len[j] < 0 || occ_off[j + 1] < occ_off[j]) return PM_EINVAL;
         if (text_len[j] >= (int64_t(1) << 32)) return PM_ETOOBIG;
     }
@@ -634,24 +617,27 @@ int pm_batch_prepare(const pm_set *const *sets, int32_t k, const int64_t *text_o
     try {
         b->k = k;
         b->flags = flags;
-        b->sets.assign(sets, sets + k);
-        b->text_off.assign(text_off, text_off + k);
-        b->text_len.assign(text_len, text_len + k);
         b->occ_off.assign(occ_off, occ_off + k + 1);
         b->count_off.assign(size_t(k) + 1, 0);
         for (int32_t j = 0; j < k; ++j)
             b->count_off[size_t(j) + 1] = b->count_off[size_t(j)] + sets[j]->ac.d;
         b->d_total = b->count_off[size_t(k)];
-        b->order.resize(size_t(k));
-        std::iota(b->order.begin(), b->order.end(), 0);
-        std::stable_sort(b->order.begin(), b->order.end(),
+        std::vector<int32_t> order(static_cast<size_t>(k));
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
                          [&](int32_t x, int32_t y) { return text_len[x] > text_len[y]; });
-        DeviceProps dp;
-        int rc = device_props(dp);
-        if (rc) { delete b; return rc; }
+        b->inst.resize(size_t(k));
+        for (int32_t q = 0; q < k; ++q) {
+            const int32_t j = order[size_t(q)];
+            b->inst[size_t(q)] = BatchInst{sets[j], text_off[j], text_len[j], b->count_off[size_t(j)],
+                                           occ_off[j], occ_off[j + 1] - occ_off[j], j};
+        }
         // the largest warp count leaves the smallest region, hence the most
         // counters in the workspace: size the workspace for it
-        b->ws_bytes = kWsHeader + 8 * ccount_for(*b, plan_batch(kBatchMaxWarps, dp.smem_optin), nullptr);
+        BatchShape widest;
+        int rc = batch_shape(kBatchMaxWarps, widest);
+        if (rc) { delete b; return rc; }
+        b->ws_bytes = batch_ws_bytes(batch_fill(b->inst.data(), k, widest, nullptr));
         rc = apply_plan(b, 12);
         if (rc) { pm_batch_free(b); return rc; }
     } catch (const std::bad_alloc &) {
@@ -674,7 +660,7 @@ int64_t pm_batch_workspace_bytes(const pm_batch *b) { return b ? b->ws_bytes : -
 
 int64_t pm_batch_counts_total(const pm_batch *b) { return b ? b->d_total : -1; }
 
-int32_t pm_batch_warps(const pm_batch *b) { return b ? b->plan.warps : -1; }
+int32_t pm_batch_warps(const pm_batch *b) { return b ? b->shape.warps : -1; }
 
 int pm_batch_set_warps(pm_batch *b, int32_t warps)
 {
@@ -690,12 +676,9 @@ int pm_batch_scan_device(const pm_batch *b, const uint8_t *d_text, int64_t *d_co
     const BatchBufs o{d_text, d_counts, d_occ, d_n_occ, d_workspace};
     int rc = batch_check(b, o, workspace_bytes);
     if (rc) return rc;
-    DeviceProps dp;
-    rc = device_props(dp);
+    rc = batch_prepare_launch(b->shape);
     if (rc) return rc;
-    rc = ensure_batch_attr(b->plan.smem_bytes);
-    if (rc) return rc;
-    return batch_enqueue(b, o, dp.sm_count, static_cast<cudaStream_t>(stream));
+    return batch_enqueue(b, o, static_cast<cudaStream_t>(stream));
 }
 
 int pm_batch_tune(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_t *d_occ,
@@ -707,9 +690,6 @@ int pm_batch_tune(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_
     if (rc) return rc;
     if (reps < 1) reps = 1;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    DeviceProps dp;
-    rc = device_props(dp);
-    if (rc) return rc;
     drop_graph(b);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
@@ -719,15 +699,15 @@ int pm_batch_tune(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_
         if (e0) cudaEventDestroy(e0);
         return PM_ECUDA;
     }
-    int best_w = b->plan.warps;
+    int best_w = b->shape.warps;
     float best = -1.0f;
     for (int w : kBatchWarpChoices) {
         rc = apply_plan(b, w);
-        if (!rc) rc = ensure_batch_attr(b->plan.smem_bytes);
-        if (!rc) rc = batch_enqueue(b, o, dp.sm_count, st);  // warm-up
+        if (!rc) rc = batch_prepare_launch(b->shape);
+        if (!rc) rc = batch_enqueue(b, o, st);  // warm-up
         if (!rc) {
             e = cudaEventRecord(e0, st);
-            for (int r = 0; r < reps && !rc && e == cudaSuccess; ++r) rc = batch_enqueue(b, o, dp.sm_count, st);
+            for (int r = 0; r < reps && !rc && e == cudaSuccess; ++r) rc = batch_enqueue(b, o, st);
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.0f;
@@ -750,10 +730,7 @@ int pm_batch_capture(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint
 {
     const BatchBufs o{d_text, d_counts, d_occ, d_n_occ, d_workspace};
     int rc = batch_check(b, o, workspace_bytes);
-    if (rc) return rc;
-    DeviceProps dp;
-    rc = device_props(dp);
-    if (!rc) rc = ensure_batch_attr(b->plan.smem_bytes);
+    if (!rc) rc = batch_prepare_launch(b->shape);
     if (rc) return rc;
     drop_graph(b);
     cudaStream_t cs = nullptr;
@@ -762,7 +739,7 @@ int pm_batch_capture(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = batch_enqueue(b, o, dp.sm_count, cs);
+        rc = batch_enqueue(b, o, cs);
         const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         if (!rc && e2 != cudaSuccess) e = e2;
     }

@@ -1,0 +1,722 @@
+// serve.cpp -- request loop with continuous batching over the batched
+// Aho-Corasick scan.
+//
+// Requests (a pattern set already compiled on the device plus a host text)
+// enter a FIFO. A dispatcher thread admits requests from the head while
+// their device memory (text, counts, an occurrence buffer of estimated size)
+// fits a fixed device arena, forms a batch from everything admitted, and
+// launches it on a free stream slot: one copy per text, the descriptors, the
+// persistent batched kernel, and a copy of the per-instance totals back. Up
+// to max_inflight batches run at once on their own streams, so requests that
+// arrive while others are on the GPU are admitted as soon as memory and a
+// slot free up, and their copies and kernels overlap the running batches.
+// A completion thread takes finished batches (a host callback on the stream
+// marks them), re-runs the few instances whose occurrence estimate was too
+// small with the exact capacity, copies results to host memory, frees the
+// arena blocks, records each request's latency and wakes its waiter.
+//
+// Each request's result is computed by the same per-instance arithmetic as a
+// solo scan (an instance never shares counters or outputs with another), so
+// results are identical alone and in any mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "pm_internal.h"
+
+namespace pm {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+constexpr int64_t kAlign = 256;
+// Requests at least this long run as their own whole-GPU scan (the plain
+// kernel, decoupled look-back over all SMs); shorter ones share a batched
+// launch, where one CTA takes a whole request.
+constexpr int64_t kPlainMin = int64_t(256) << 10;
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// First-fit allocator over one device block; bookkeeping on the host.
+class Arena {
+ public:
+    int init(int64_t bytes)
+    {
+        bytes = round_up(bytes, kAlign);
+        const cudaError_t e = cudaMalloc(&base_, size_t(bytes));
+        if (e != cudaSuccess) {
+            set_cuda_error(int(e));
+            cudaGetLastError();
+            base_ = nullptr;
+            return PM_ENOMEM;
+        }
+        cap_ = bytes;
+        free_[0] = bytes;
+        return PM_OK;
+    }
+    void release()
+    {
+        if (base_) cudaFree(base_);
+        base_ = nullptr;
+    }
+    // offset of a block of at least `bytes`, or -1
+    int64_t alloc(int64_t bytes)
+    {
+        bytes = round_up(std::max<int64_t>(bytes, 1), kAlign);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes) continue;
+            const int64_t off = it->first, left = it->second - bytes;
+            free_.erase(it);
+            if (left > 0) free_[off + bytes] = left;
+            used_ += bytes;
+            return off;
+        }
+        return -1;
+    }
+    void free(int64_t off, int64_t bytes)
+    {
+        if (off < 0) return;
+        bytes = round_up(std::max<int64_t>(bytes, 1), kAlign);
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    uint8_t *base() const { return static_cast<uint8_t *>(base_); }
+    int64_t capacity() const { return cap_; }
+    int64_t used() const { return used_; }
+
+ private:
+    void *base_ = nullptr;
+    int64_t cap_ = 0, used_ = 0;
+    std::map<int64_t, int64_t> free_;  // offset -> size, coalesced
+};
+
+struct Req {
+    int64_t id = 0;
+    const pm_set *set = nullptr;
+    const uint8_t *T = nullptr;
+    int64_t n = 0;
+    bool list = true;
+    Clock::time_point t_submit;
+    int64_t text_blk = -1, text_bytes = 0;
+    int64_t cnt_blk = -1, cnt_bytes = 0;
+    int64_t occ_blk = -1, occ_bytes = 0, occ_cap = 0;
+    int64_t ws_blk = -1, ws_bytes = 0; // workspace of a whole-GPU scan
+    bool plain = false;
+    void *occ_ext = nullptr;           // re-run buffer outside the arena
+    int64_t n_occ = 0;
+    int status = PM_OK;
+    bool done = false;
+    pm_result *res = nullptr;
+};
+
+struct Slot {
+    cudaStream_t st = nullptr;
+    BatchDesc *h_desc = nullptr;       // pinned, max_batch
+    int64_t *h_nocc = nullptr;         // pinned, max_batch
+    BatchDesc *d_desc = nullptr;
+    int64_t *d_nocc = nullptr;
+    void *d_ws = nullptr;
+    int64_t ws_words = 0;              // global counter words the workspace holds
+    bool busy = false;
+    std::vector<Req *> reqs;
+    std::atomic<bool> ready{false};
+    Clock::time_point t_launch;
+};
+
+}  // namespace
+}  // namespace pm
+
+struct pm_server {
+    pm_server_params p{};
+    int device = 0;
+    pm::BatchShape shape;
+    pm::Arena arena;
+    std::vector<pm::Slot *> slots;
+    std::mutex mu;
+    std::condition_variable cv_dispatch, cv_complete, cv_done;
+    std::deque<pm::Req *> pending;
+    std::unordered_map<int64_t, pm::Req *> by_id;
+    std::unordered_map<const pm_set *, double> rate;   // occurrences per text byte seen
+    int64_t next_id = 1;
+    bool stopping = false;
+    std::thread dispatcher, completer;
+    // statistics
+    std::vector<double> lat_us;
+    int64_t bytes_done = 0, batches = 0, batched_reqs = 0, reruns = 0, peak_inflight = 0;
+    int64_t inflight_reqs = 0;
+    bool have_first = false;
+    pm::Clock::time_point t_first, t_last;
+};
+
+namespace pm {
+namespace {
+
+void CUDART_CB on_batch_done(void *arg)
+{
+    // runs on a CUDA callback thread: no CUDA calls here
+    auto *pr = static_cast<std::pair<pm_server *, Slot *> *>(arg);
+    {
+        std::lock_guard<std::mutex> lk(pr->first->mu);
+        pr->second->ready.store(true);
+    }
+    pr->first->cv_complete.notify_all();
+    delete pr;
+}
+
+int64_t est_cap(pm_server *s, const Req &r)
+{
+    if (!r.list) return 0;
+    auto it = s->rate.find(r.set);
+    const double rate = it == s->rate.end() ? 1.0 / 16.0 : it->second;
+    return int64_t(double(r.n) * rate * 1.25) + 256;
+}
+
+// Arena blocks of one request; false (nothing held) when they do not fit.
+bool admit(pm_server *s, Req &r)
+{
+    const int64_t d = r.set->ac.d;
+    r.text_bytes = std::max<int64_t>(r.n, 1);
+    r.cnt_bytes = d * 8;
+    r.occ_cap = est_cap(s, r);
+    r.occ_bytes = r.list ? std::max<int64_t>(r.occ_cap, 1) * 8 : 0;
+    r.plain = r.n >= kPlainMin;
+    r.ws_bytes = r.plain ? pm_scan_workspace_bytes(r.set, r.n, r.list ? 0u : PM_COUNTS_ONLY) : 0;
+    if (r.plain) {
+        r.ws_blk = s->arena.alloc(r.ws_bytes);
+        if (r.ws_blk < 0) return false;
+    }
+    r.text_blk = s->arena.alloc(r.text_bytes);
+    if (r.text_blk < 0) {
+        s->arena.free(r.ws_blk, r.ws_bytes);
+        r.ws_blk = -1;
+        return false;
+    }
+    r.cnt_blk = s->arena.alloc(r.cnt_bytes);
+    if (r.cnt_blk < 0) {
+        s->arena.free(r.text_blk, r.text_bytes);
+        s->arena.free(r.ws_blk, r.ws_bytes);
+        r.text_blk = r.ws_blk = -1;
+        return false;
+    }
+    if (r.list) {
+        r.occ_blk = s->arena.alloc(r.occ_bytes);
+        if (r.occ_blk < 0) {
+            s->arena.free(r.text_blk, r.text_bytes);
+            s->arena.free(r.cnt_blk, r.cnt_bytes);
+            s->arena.free(r.ws_blk, r.ws_bytes);
+            r.text_blk = r.cnt_blk = r.ws_blk = -1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// Arena blocks back to the free list (caller holds the lock; a buffer
+// outside the arena is handed back for cudaFree after the lock is dropped:
+// a CUDA call under the lock could wait on a stream callback that waits on
+// the lock).
+void *release(pm_server *s, Req &r)
+{
+    s->arena.free(r.text_blk, r.text_bytes);
+    s->arena.free(r.cnt_blk, r.cnt_bytes);
+    if (r.occ_blk >= 0) s->arena.free(r.occ_blk, r.occ_bytes);
+    s->arena.free(r.ws_blk, r.ws_bytes);
+    r.text_blk = r.cnt_blk = r.occ_blk = r.ws_blk = -1;
+    void *ext = r.occ_ext;
+    r.occ_ext = nullptr;
+    return ext;
+}
+
+int64_t counter_words(const pm_server *s, const Req &r)
+{
+    if (r.n >= kPlainMin) return 0;  // a whole-GPU scan has its own workspace
+    BatchInst I{r.set, 0, r.n, 0, 0, 0, 0};
+    return batch_fill(&I, 1, s->shape, nullptr);
+}
+
+// A whole-GPU scan of one request, its keys going to `occ`, its total to
+// d_nocc (asynchronous on the stream).
+int launch_plain(pm_server *s, const Req &r, uint64_t *occ, int64_t cap, int64_t *d_nocc, cudaStream_t st)
+{
+    uint8_t *base = s->arena.base();
+    return ac_launch(r.set->ac, r.set->dac, base + r.text_blk, r.n, r.list,
+                     reinterpret_cast<int64_t *>(base + r.cnt_blk), r.list ? occ : nullptr, cap, d_nocc,
+                     base + r.ws_blk, st);
+}
+
+// Enqueue the batch of slot `sl` (texts in, kernel, totals out); the caller
+// holds no lock. Returns a PM code.
+int launch_slot(pm_server *s, Slot &sl)
+{
+    const int k = int(sl.reqs.size());
+    std::vector<int> order;
+    for (int j = 0; j < k; ++j)
+        if (!sl.reqs[size_t(j)]->plain) order.push_back(j);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return sl.reqs[size_t(x)]->n > sl.reqs[size_t(y)]->n; });
+    const int kb = int(order.size());
+    std::vector<BatchInst> inst(static_cast<size_t>(kb));
+    for (int q = 0; q < kb; ++q) {
+        const int j = order[size_t(q)];
+        const Req &r = *sl.reqs[size_t(j)];
+        const int64_t occ_off = r.list ? r.occ_blk / 8 : 0;
+        inst[size_t(q)] = BatchInst{r.set, r.text_blk, r.n, r.cnt_blk / 8, occ_off, r.list ? r.occ_cap : 0, j};
+    }
+    const int64_t words = batch_fill(inst.data(), kb, s->shape, sl.h_desc);
+    if (words > sl.ws_words) return PM_EINVAL;  // admission keeps this from happening
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < k && e == cudaSuccess; ++j) {
+        const Req &r = *sl.reqs[size_t(j)];
+        if (r.n > 0)
+            e = cudaMemcpyAsync(s->arena.base() + r.text_blk, r.T, size_t(r.n), cudaMemcpyHostToDevice, sl.st);
+    }
+    if (e == cudaSuccess && kb > 0)
+        e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, size_t(kb) * sizeof(BatchDesc), cudaMemcpyHostToDevice, sl.st);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    uint8_t *base = s->arena.base();
+    int rc = PM_OK;
+    if (kb > 0)
+        rc = batch_launch_raw(sl.d_desc, kb, base, reinterpret_cast<int64_t *>(base),
+                              reinterpret_cast<uint64_t *>(base), sl.d_nocc, sl.d_ws, words, s->shape,
+                              true, sl.st);
+    for (int j = 0; j < k && rc == PM_OK; ++j) {
+        const Req &r = *sl.reqs[size_t(j)];
+        if (r.plain)
+            rc = launch_plain(s, r, reinterpret_cast<uint64_t *>(base + r.occ_blk), r.occ_cap, sl.d_nocc + j, sl.st);
+    }
+    if (rc) return rc;
+    e = cudaMemcpyAsync(sl.h_nocc, sl.d_nocc, size_t(k) * 8, cudaMemcpyDeviceToHost, sl.st);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    return PM_OK;
+}
+
+void finish(pm_server *s, Req &r, int status)
+{
+    // caller holds the lock
+    r.status = status;
+    r.done = true;
+    const auto now = Clock::now();
+    if (status == PM_OK) {
+        s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r.t_submit).count());
+        s->bytes_done += r.n;
+        s->t_last = now;
+    }
+}
+
+void dispatcher_main(pm_server *s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        Slot *free_slot = nullptr;
+        for (Slot *sl : s->slots)
+            if (!sl->busy) { free_slot = sl; break; }
+        if (s->stopping && s->pending.empty()) break;
+        if (!free_slot || s->pending.empty()) {
+            s->cv_dispatch.wait(lk);
+            continue;
+        }
+        // admit from the head while memory, batch size and counters allow
+        std::vector<Req *> batch;
+        int64_t words = 0;
+        while (!s->pending.empty() && int(batch.size()) < s->p.max_batch) {
+            Req *r = s->pending.front();
+            const int64_t w = counter_words(s, *r);
+            if (words + w > free_slot->ws_words && !batch.empty()) break;
+            if (!admit(s, *r)) break;
+            words += w;
+            batch.push_back(r);
+            s->pending.pop_front();
+        }
+        if (batch.empty()) {
+            bool any_busy = false;
+            for (Slot *sl : s->slots) any_busy = any_busy || sl->busy;
+            if (!any_busy) {
+                // nothing holds memory and the head still does not fit (its
+                // estimate grew since it was accepted): it never will
+                Req *r = s->pending.front();
+                s->pending.pop_front();
+                finish(s, *r, PM_ENOMEM);
+                s->cv_done.notify_all();
+                continue;
+            }
+            // the head does not fit while batches hold memory: wait for one
+            s->cv_dispatch.wait(lk);
+            continue;
+        }
+        free_slot->busy = true;
+        free_slot->ready.store(false);
+        free_slot->reqs = batch;
+        free_slot->t_launch = Clock::now();
+        s->inflight_reqs += int64_t(batch.size());
+        s->peak_inflight = std::max(s->peak_inflight, s->inflight_reqs);
+        s->batches += 1;
+        s->batched_reqs += int64_t(batch.size());
+        lk.unlock();
+        int rc = launch_slot(s, *free_slot);
+        if (rc == PM_OK) {
+            auto *arg = new (std::nothrow) std::pair<pm_server *, Slot *>(s, free_slot);
+            cudaError_t e = arg ? cudaLaunchHostFunc(free_slot->st, on_batch_done, arg) : cudaErrorMemoryAllocation;
+            if (e != cudaSuccess) {
+                delete arg;
+                set_cuda_error(int(e));
+                rc = PM_ECUDA;
+            }
+        }
+        lk.lock();
+        if (rc != PM_OK) {
+            // the stream may still hold copies: drain it, then fail the batch
+            lk.unlock();
+            cudaStreamSynchronize(free_slot->st);
+            cudaGetLastError();
+            lk.lock();
+            for (Req *r : free_slot->reqs) {
+                release(s, *r);  // nothing outside the arena before a re-run
+                finish(s, *r, rc);
+            }
+            s->inflight_reqs -= int64_t(free_slot->reqs.size());
+            free_slot->reqs.clear();
+            free_slot->busy = false;
+            s->cv_done.notify_all();
+        }
+    }
+}
+
+// One instance again with the exact capacity, its keys going to `occ`
+// (arena or not): a batch of one whose occurrence base is that buffer.
+// Synchronous on the slot's stream; the slot's batch has finished.
+int rerun_one(pm_server *s, Slot &sl, Req &r, uint64_t *occ)
+{
+    cudaError_t e = cudaSuccess;
+    int rc = PM_OK;
+    if (r.plain) {
+        rc = launch_plain(s, r, occ, r.occ_cap, sl.d_nocc, sl.st);
+    } else {
+        BatchInst I{r.set, r.text_blk, r.n, r.cnt_blk / 8, 0, r.occ_cap, 0};
+        const int64_t words = batch_fill(&I, 1, s->shape, sl.h_desc);
+        e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(BatchDesc), cudaMemcpyHostToDevice, sl.st);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+        uint8_t *base = s->arena.base();
+        rc = batch_launch_raw(sl.d_desc, 1, base, reinterpret_cast<int64_t *>(base), occ, sl.d_nocc,
+                              sl.d_ws, words, s->shape, true, sl.st);
+    }
+    if (rc) return rc;
+    e = cudaMemcpyAsync(sl.h_nocc, sl.d_nocc, 8, cudaMemcpyDeviceToHost, sl.st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sl.st);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    if (pm_scan_status(r.plain ? static_cast<void *>(s->arena.base() + r.ws_blk) : sl.d_ws, sl.st) != PM_OK)
+        return PM_ETIMEOUT;
+    return sl.h_nocc[0] == r.n_occ ? PM_OK : PM_ECUDA;  // same scan, same total
+}
+
+// Finish one completed slot: re-runs, host copies, bookkeeping.
+void complete_slot(pm_server *s, Slot &sl, std::unique_lock<std::mutex> &lk)
+{
+    const int k = int(sl.reqs.size());
+    std::vector<Req *> over;
+    for (int j = 0; j < k; ++j) {
+        Req &r = *sl.reqs[size_t(j)];
+        r.n_occ = sl.h_nocc[j];
+        if (r.list && r.n_occ > r.occ_cap) over.push_back(&r);
+    }
+    int rc = PM_OK;
+    lk.unlock();
+    if (pm_scan_status(sl.d_ws, sl.st) != PM_OK) rc = PM_ETIMEOUT;
+    for (Req *r : sl.reqs)
+        if (rc == PM_OK && r->plain && pm_scan_status(s->arena.base() + r->ws_blk, sl.st) != PM_OK)
+            rc = PM_ETIMEOUT;
+    if (!over.empty() && rc == PM_OK) {
+        // exact capacity for the instances whose estimate was short: a new
+        // arena block, else a buffer of its own
+        lk.lock();
+        for (Req *r : over) {
+            s->arena.free(r->occ_blk, r->occ_bytes);
+            r->occ_bytes = r->n_occ * 8;
+            r->occ_cap = r->n_occ;
+            r->occ_blk = s->arena.alloc(r->occ_bytes);
+        }
+        s->reruns += int64_t(over.size());
+        lk.unlock();
+        for (Req *r : over) {
+            if (rc != PM_OK) break;
+            if (r->occ_blk < 0) {
+                const cudaError_t e = cudaMalloc(&r->occ_ext, size_t(r->occ_bytes));
+                if (e != cudaSuccess) { cudaGetLastError(); r->occ_ext = nullptr; rc = PM_ENOMEM; break; }
+            }
+            uint64_t *o = r->occ_ext ? static_cast<uint64_t *>(r->occ_ext)
+                                     : reinterpret_cast<uint64_t *>(s->arena.base() + r->occ_blk);
+            rc = rerun_one(s, sl, *r, o);
+        }
+    }
+    // results to host memory
+    std::vector<int> rcs(static_cast<size_t>(k), rc);
+    for (int j = 0; j < k; ++j) {
+        Req &r = *sl.reqs[size_t(j)];
+        if (rcs[size_t(j)] != PM_OK) continue;
+        r.res = make_result(r.set->ac.d, r.list ? r.n_occ : 0, r.list);
+        if (!r.res) { rcs[size_t(j)] = PM_ENOMEM; continue; }
+        r.res->n_occ = r.n_occ;
+        cudaError_t e = cudaMemcpyAsync(r.res->counts, s->arena.base() + r.cnt_blk, size_t(r.cnt_bytes),
+                                        cudaMemcpyDeviceToHost, sl.st);
+        if (e == cudaSuccess && r.list && r.n_occ > 0) {
+            const uint8_t *o = r.occ_ext ? static_cast<uint8_t *>(r.occ_ext) : s->arena.base() + r.occ_blk;
+            e = cudaMemcpyAsync(r.res->occ, o, size_t(r.n_occ) * 8, cudaMemcpyDeviceToHost, sl.st);
+        }
+        if (e != cudaSuccess) { set_cuda_error(int(e)); rcs[size_t(j)] = PM_ECUDA; }
+    }
+    if (cudaStreamSynchronize(sl.st) != cudaSuccess) {
+        cudaGetLastError();
+        for (int &x : rcs) if (x == PM_OK) x = PM_ECUDA;
+    }
+    lk.lock();
+    std::vector<void *> ext;
+    for (int j = 0; j < k; ++j) {
+        Req &r = *sl.reqs[size_t(j)];
+        if (rcs[size_t(j)] != PM_OK && r.res) {
+            pm_result_free(r.res);
+            r.res = nullptr;
+        }
+        if (r.list && rcs[size_t(j)] == PM_OK && r.n > 0) {
+            const double obs = double(r.n_occ) / double(r.n);
+            auto it = s->rate.find(r.set);
+            const double prev = it == s->rate.end() ? obs : it->second;
+            s->rate[r.set] = std::max(obs, 0.98 * prev);
+        }
+        if (void *x = release(s, r)) ext.push_back(x);
+        finish(s, r, rcs[size_t(j)]);
+    }
+    s->inflight_reqs -= int64_t(k);
+    sl.reqs.clear();
+    sl.busy = false;
+    s->cv_done.notify_all();
+    s->cv_dispatch.notify_all();
+    if (!ext.empty()) {
+        lk.unlock();
+        for (void *x : ext) cudaFree(x);
+        lk.lock();
+    }
+}
+
+void completer_main(pm_server *s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        Slot *ready = nullptr;
+        bool any_busy = false;
+        for (Slot *sl : s->slots) {
+            if (sl->busy) any_busy = true;
+            if (sl->busy && sl->ready.load()) { ready = sl; break; }
+        }
+        if (ready) {
+            ready->ready.store(false);
+            complete_slot(s, *ready, lk);
+            continue;
+        }
+        if (s->stopping && !any_busy && s->pending.empty()) break;
+        s->cv_complete.wait_for(lk, std::chrono::milliseconds(50));
+    }
+}
+
+void destroy(pm_server *s)
+{
+    for (Slot *sl : s->slots) {
+        if (sl->st) cudaStreamDestroy(sl->st);
+        if (sl->h_desc) cudaFreeHost(sl->h_desc);
+        if (sl->h_nocc) cudaFreeHost(sl->h_nocc);
+        if (sl->d_desc) cudaFree(sl->d_desc);
+        if (sl->d_nocc) cudaFree(sl->d_nocc);
+        if (sl->d_ws) cudaFree(sl->d_ws);
+        delete sl;
+    }
+    s->slots.clear();
+    s->arena.release();
+    for (auto &kv : s->by_id) {
+        if (kv.second->res) pm_result_free(kv.second->res);
+        delete kv.second;
+    }
+    s->by_id.clear();
+    delete s;
+}
+
+}  // namespace
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+int pm_server_create(const pm_server_params *params, pm_server **out)
+{
+    if (!out) return PM_EINVAL;
+    pm_server_params p{};
+    if (params) p = *params;
+    if (p.device_budget_bytes <= 0) p.device_budget_bytes = int64_t(4) << 30;
+    if (p.max_batch <= 0) p.max_batch = 512;
+    if (p.max_inflight <= 0) p.max_inflight = 3;
+    if (p.warps_per_cta <= 0) p.warps_per_cta = 12;
+    if (p.counter_words <= 0) p.counter_words = int64_t(4) << 20;
+    if (p.max_inflight > 16 || p.max_batch > (1 << 20)) return PM_EINVAL;
+    pm_server *s = new (std::nothrow) pm_server();
+    if (!s) return PM_ENOMEM;
+    s->p = p;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); delete s; return PM_ENODEV; }
+    int rc = batch_shape(p.warps_per_cta, s->shape);
+    if (!rc) rc = batch_prepare_launch(s->shape);
+    if (!rc) rc = s->arena.init(p.device_budget_bytes);
+    for (int i = 0; i < p.max_inflight && !rc; ++i) {
+        Slot *sl = new (std::nothrow) Slot();
+        if (!sl) { rc = PM_ENOMEM; break; }
+        s->slots.push_back(sl);
+        sl->ws_words = p.counter_words;
+        e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_desc), size_t(p.max_batch) * sizeof(BatchDesc));
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_nocc), size_t(p.max_batch) * 8);
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&sl->d_desc), size_t(p.max_batch) * sizeof(BatchDesc));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&sl->d_nocc), size_t(p.max_batch) * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&sl->d_ws, size_t(batch_ws_bytes(p.counter_words)));
+        if (e != cudaSuccess) {
+            set_cuda_error(int(e));
+            cudaGetLastError();
+            rc = e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
+        }
+    }
+    if (rc) { destroy(s); return rc; }
+    try {
+        s->dispatcher = std::thread(dispatcher_main, s);
+        s->completer = std::thread(completer_main, s);
+    } catch (...) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->stopping = true;
+        }
+        s->cv_dispatch.notify_all();
+        s->cv_complete.notify_all();
+        if (s->dispatcher.joinable()) s->dispatcher.join();
+        if (s->completer.joinable()) s->completer.join();
+        destroy(s);
+        return PM_ENOMEM;
+    }
+    *out = s;
+    return PM_OK;
+}
+
+int pm_server_submit(pm_server *s, const pm_set *set, const uint8_t *T, int64_t n, uint32_t flags,
+                     int64_t *ticket)
+{
+    if (!s || !ticket || n < 0 || (n > 0 && !T)) return PM_EINVAL;
+    if (flags & ~(PM_HOST_TEXT | PM_COUNTS_ONLY)) return PM_EINVAL;
+    if (!batch_supports(set)) return PM_EINVAL;
+    if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
+    Req *r = new (std::nothrow) Req();
+    if (!r) return PM_ENOMEM;
+    r->set = set;
+    r->T = T;
+    r->n = n;
+    r->list = !(flags & PM_COUNTS_ONLY);
+    int64_t need = round_up(std::max<int64_t>(n, 1), kAlign) + round_up(set->ac.d * 8, kAlign) +
+                   (r->list ? round_up((est_cap(s, *r) + 1) * 8, kAlign) : 0);
+    if (n >= kPlainMin) need += round_up(pm_scan_workspace_bytes(set, n, r->list ? 0u : PM_COUNTS_ONLY), kAlign);
+    if (need > s->arena.capacity() || counter_words(s, *r) > s->p.counter_words) {
+        delete r;
+        return PM_ETOOBIG;  // could never be admitted
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stopping) { delete r; return PM_EINVAL; }
+        r->id = s->next_id++;
+        r->t_submit = Clock::now();
+        if (!s->have_first) { s->have_first = true; s->t_first = r->t_submit; }
+        s->by_id[r->id] = r;
+        s->pending.push_back(r);
+        *ticket = r->id;
+    }
+    s->cv_dispatch.notify_all();
+    return PM_OK;
+}
+
+int pm_server_wait(pm_server *s, int64_t ticket, pm_result **out)
+{
+    if (!s || !out) return PM_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->by_id.find(ticket);
+    if (it == s->by_id.end()) return PM_EINVAL;
+    Req *r = it->second;
+    s->cv_done.wait(lk, [&] { return r->done; });
+    const int rc = r->status;
+    *out = r->res;
+    r->res = nullptr;
+    s->by_id.erase(ticket);
+    delete r;
+    return rc;
+}
+
+int pm_server_get_stats(pm_server *s, pm_server_stats *st)
+{
+    if (!s || !st) return PM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(st, 0, sizeof(*st));
+    st->completed = int64_t(s->lat_us.size());
+    st->bytes = s->bytes_done;
+    st->batches = s->batches;
+    st->mean_batch = s->batches ? double(s->batched_reqs) / double(s->batches) : 0.0;
+    st->reruns = s->reruns;
+    st->peak_inflight = s->peak_inflight;
+    st->pending = int64_t(s->pending.size());
+    st->arena_used = s->arena.used();
+    if (!s->lat_us.empty()) {
+        std::vector<double> v = s->lat_us;
+        auto pct = [&](double q) {
+            const size_t i = std::min(v.size() - 1, size_t(q * double(v.size() - 1) + 0.5));
+            std::nth_element(v.begin(), v.begin() + long(i), v.end());
+            return v[i];
+        };
+        st->p50_us = pct(0.50);
+        st->p99_us = pct(0.99);
+        double sum = 0.0;
+        for (double x : s->lat_us) sum += x;
+        st->mean_us = sum / double(s->lat_us.size());
+        const double span = std::chrono::duration<double>(s->t_last - s->t_first).count();
+        st->gbs = span > 0.0 ? double(s->bytes_done) / span / 1e9 : 0.0;
+    }
+    return PM_OK;
+}
+
+void pm_server_destroy(pm_server *s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stopping = true;
+    }
+    s->cv_dispatch.notify_all();
+    s->cv_complete.notify_all();
+    if (s->dispatcher.joinable()) s->dispatcher.join();
+    if (s->completer.joinable()) s->completer.join();
+    destroy(s);
+}
+
+}  // extern "C"

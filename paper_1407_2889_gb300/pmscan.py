@@ -32,6 +32,8 @@ EXPORTED = [
     "pm_scan_batch", "pm_batch_prepare", "pm_batch_free", "pm_batch_counts_total",
     "pm_batch_workspace_bytes", "pm_batch_warps", "pm_batch_scan_device", "pm_batch_tune",
     "pm_batch_set_warps", "pm_batch_capture", "pm_batch_replay",
+    "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
+    "pm_server_destroy",
     "pm_selfcheck_host_walk", "pm_strerror", "pm_last_cuda_error", "pm_version",
 ]
 
@@ -58,6 +60,19 @@ class pm_result(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int64), ("n_occ", ctypes.c_int64),
                 ("counts", ctypes.POINTER(ctypes.c_int64)),
                 ("occ", ctypes.POINTER(ctypes.c_uint64))]
+
+
+class pm_server_params(ctypes.Structure):
+    _fields_ = [("device_budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("max_inflight", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("counter_words", ctypes.c_int64)]
+
+
+class pm_server_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("bytes", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("reruns", ctypes.c_int64), ("peak_inflight", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("arena_used", ctypes.c_int64), ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("gbs", ctypes.c_double)]
 
 
 class PmError(RuntimeError):
@@ -137,6 +152,16 @@ def lib():
         L.pm_batch_capture.argtypes = [vp, vp, vp, vp, vp, vp, i64]
         L.pm_batch_replay.restype = ctypes.c_int
         L.pm_batch_replay.argtypes = [vp, vp]
+        L.pm_server_create.restype = ctypes.c_int
+        L.pm_server_create.argtypes = [ctypes.POINTER(pm_server_params), pp]
+        L.pm_server_submit.restype = ctypes.c_int
+        L.pm_server_submit.argtypes = [vp, vp, vp, i64, u32, ctypes.POINTER(i64)]
+        L.pm_server_wait.restype = ctypes.c_int
+        L.pm_server_wait.argtypes = [vp, i64, ctypes.POINTER(ctypes.POINTER(pm_result))]
+        L.pm_server_get_stats.restype = ctypes.c_int
+        L.pm_server_get_stats.argtypes = [vp, ctypes.POINTER(pm_server_stats)]
+        L.pm_server_destroy.restype = None
+        L.pm_server_destroy.argtypes = [vp]
         L.pm_selfcheck_host_walk.restype = ctypes.c_int
         L.pm_selfcheck_host_walk.argtypes = [vp, vp, i64, ctypes.POINTER(ctypes.POINTER(pm_result))]
         L.pm_strerror.restype = ctypes.c_char_p
@@ -546,6 +571,66 @@ class Batch:
         if getattr(self, "b", 0):
             pm_batch_free(self.b)
             self.b = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The library's serving loop (pm_server_*): submit host texts against
+    device-resident sets, wait for results; continuous batching inside."""
+
+    def __init__(self, budget_bytes: int = 4 << 30, max_batch: int = 512, max_inflight: int = 3,
+                 warps: int = 12, counter_words: int = 0):
+        p = pm_server_params(int(budget_bytes), int(max_batch), int(max_inflight), int(warps), 0,
+                             int(counter_words))
+        h = ctypes.c_void_p()
+        _check(lib().pm_server_create(ctypes.byref(p), ctypes.byref(h)), "pm_server_create")
+        self.h = int(h.value)
+        self._keep = {}
+        self._klock = threading.Lock()
+
+    def submit(self, pset, T, counts_only: bool = False) -> int:
+        """Queue a scan of host text T (numpy uint8 or CPU tensor, kept alive
+        until its wait) against a PatternSet; returns the ticket."""
+        if hasattr(T, "data_ptr"):
+            ptr, n = int(T.data_ptr()), int(T.numel())
+        else:
+            T = np.ascontiguousarray(T, dtype=np.uint8)
+            ptr, n = T.ctypes.data, T.size
+        t = ctypes.c_int64(0)
+        _check(lib().pm_server_submit(self.h, pset.h, ptr, n, PM_COUNTS_ONLY if counts_only else 0,
+                                      ctypes.byref(t)),
+               "pm_server_submit")
+        with self._klock:
+            self._keep[t.value] = (T, pset)
+        return int(t.value)
+
+    def wait(self, ticket: int):
+        """(occ uint64 array, counts int64 array) of the request."""
+        rp = ctypes.POINTER(pm_result)()
+        rc = lib().pm_server_wait(self.h, int(ticket), ctypes.byref(rp))
+        with self._klock:
+            self._keep.pop(int(ticket), None)
+        if rc != PM_OK:
+            if rp:
+                lib().pm_result_free(rp)
+            raise PmError(rc, "pm_server_wait")
+        return _take_result(rp)
+
+    def stats(self) -> dict:
+        st = pm_server_stats()
+        _check(lib().pm_server_get_stats(self.h, ctypes.byref(st)), "pm_server_get_stats")
+        return {f: getattr(st, f) for f, _ in pm_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", 0):
+            lib().pm_server_destroy(self.h)
+            self.h = 0
+            self._keep.clear()
 
     def __del__(self):
         try:

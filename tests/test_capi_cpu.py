@@ -74,6 +74,26 @@ def test_no_device_no_compute():
     assert e.value.code in (pm.PM_ENODEV, pm.PM_ECUDA)
 
 
+def test_batch_and_server_refuse_without_device():
+    """The batched scan and the serving loop are device-only too."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("GPU present")
+    except ImportError:
+        pass
+    with pytest.raises(pm.PmError) as e:
+        pm.Server(budget_bytes=1 << 20)
+    assert e.value.code in (pm.PM_ENODEV, pm.PM_ECUDA)
+    h = pm.pm_ac_compile(["ACGTACGT"], HOST)
+    try:  # a host-only set is never batched
+        with pytest.raises(pm.PmError) as e:
+            pm.pm_batch_prepare([h], [0], [16], [0, 4])
+        assert e.value.code == pm.PM_EINVAL
+    finally:
+        pm.pm_set_free(h)
+
+
 def test_worked_example_tables():
     h = pm.pm_ac_compile(["AAC", "AGT", "GTA"], HOST)
     try:
