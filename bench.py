@@ -417,6 +417,62 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
             q.close()
             del buf
     out["ac_list_sweep"] = sweep
+    out["large_sets"] = large_sets(T, d_text, stream, nocc, pm, torch, synth)
+    return out
+
+
+def large_sets(T, d_text, stream, nocc, pm, torch, synth):
+    """Large pattern sets (d = 1e5, 5e5; m = 32) on the same text: AC with a
+    u32 table whose BFS prefix sits in shared memory and the rest in L2/HBM
+    (full 1 GiB, list mode), WM with B = 4 (2^20 SHIFT entries) on a prefix."""
+    out = {}
+    n = T.size
+    peak = measured_peaks()[0]
+    for d in (100000, 500000):
+        P = synth.large_set(d, T)
+        t0 = time.perf_counter()
+        q = pm.PatternSet.ac(P)
+        t_comp = time.perf_counter() - t0
+        inf = q.info()
+        cnt = torch.zeros(d, dtype=torch.int64, device="cuda")
+        ws = torch.zeros(q.workspace_bytes(n), dtype=torch.uint8, device="cuda")
+        with torch.cuda.stream(stream):
+            pm.pm_scan_device(q.h, d_text, n, pm.PM_COUNTS_ONLY, cnt, None, 0, nocc, ws, ws.numel(), stream)
+        stream.synchronize()
+        tot = int(nocc.item())
+        buf = torch.empty(max(tot, 1), dtype=torch.int64, device="cuda")
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            pm.pm_scan_device(q.h, d_text, n, 0, cnt, buf, buf.numel(), nocc, ws, ws.numel(), stream)
+            ev0.record(stream)
+            for _ in range(3):
+                pm.pm_scan_device(q.h, d_text, n, 0, cnt, buf, buf.numel(), nocc, ws, ws.numel(), stream)
+            ev1.record(stream)
+        stream.synchronize()
+        assert pm.pm_scan_status(ws, stream) == pm.PM_OK
+        dt = ev0.elapsed_time(ev1) / 3 / 1e3
+        entry = {"ac_gbs": n / dt / 1e9, "ac_alg_frac": (n + 8 * tot + 8 * d) / dt / 1e9 / peak,
+                 "n_occ": tot, "rows": inf["n_rows"], "table_bytes": inf["table_bytes"],
+                 "smem_rows": inf["smem_rows"], "placement": inf["placement"], "compile_s": t_comp}
+        q.close()
+        del ws, buf
+        nw = (64 << 20) if d == 100000 else (8 << 20)
+        w = pm.PatternSet.wm(P, 4)
+        dw = d_text[:nw]
+        wsw = torch.zeros(w.workspace_bytes(nw), dtype=torch.uint8, device="cuda")
+        bw = torch.empty(max(tot, 1 << 16), dtype=torch.int64, device="cuda")
+        with torch.cuda.stream(stream):
+            pm.pm_scan_device(w.h, dw, nw, 0, cnt, bw, bw.numel(), nocc, wsw, wsw.numel(), stream)
+            ev0.record(stream)
+            pm.pm_scan_device(w.h, dw, nw, 0, cnt, bw, bw.numel(), nocc, wsw, wsw.numel(), stream)
+            ev1.record(stream)
+        stream.synchronize()
+        assert pm.pm_scan_status(wsw, stream) == pm.PM_OK
+        entry["wm_b4_gbs"] = nw / (ev0.elapsed_time(ev1) / 1e3) / 1e9
+        entry["wm_text_bytes"] = nw
+        w.close()
+        out[f"d{d}_m32"] = entry
     return out
 
 
@@ -580,6 +636,18 @@ def serving_run(args, pinned, pm, torch, synth):
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
+
+    # saturation: the same kind of requests, all queued at once (closed
+    # loop), so batches form while others run; sustained capacity
+    ks = min(k, 3000)
+    sat = pm.Server(budget_bytes=8 << 30, max_batch=256, max_inflight=3)
+    t0 = time.perf_counter()
+    tk = [sat.submit(sets[which[j]], pinned[offs[j]:offs[j] + lens[j]]) for j in range(ks)]
+    for t in tk:
+        sat.wait(t)
+    sat_wall = time.perf_counter() - t0
+    ss = sat.stats()
+    sat.close()
     same = True
     for j, (occ, cnt) in results.items():
         so, sc = sets[which[j]].scan(T[offs[j]:offs[j] + lens[j]])
@@ -593,6 +661,10 @@ def serving_run(args, pinned, pm, torch, synth):
         "mean_ms": st["mean_us"] / 1e3, "batches": st["batches"], "mean_batch": st["mean_batch"],
         "reruns": st["reruns"], "peak_inflight": st["peak_inflight"],
         "identical_to_solo_on_sample": same, "sampled": len(results), "compile_s": t_compile,
+        "saturated": {"requests": ks, "gbs": ss["gbs"], "wall_s": sat_wall, "mean_batch": ss["mean_batch"],
+                      "batches": ss["batches"], "p50_ms": ss["p50_us"] / 1e3, "p99_ms": ss["p99_us"] / 1e3,
+                      "peak_inflight": ss["peak_inflight"], "dispatch_busy_s": ss["dispatch_busy_s"],
+                      "complete_busy_s": ss["complete_busy_s"]},
         "workload": "Poisson 2000 req/s; text log-uniform 1 KiB-16 MiB slices of the pinned EST text (H2D and D2H "
                     "inside the latency); 64 sets d log-uniform 100-1e5, m in {8,16,24,32}; list mode",
     }

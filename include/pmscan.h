@@ -302,6 +302,9 @@ int pm_batch_replay(const pm_batch *b, void *stream);
  *     (re-running, with the exact capacity, the rare request whose
  *     occurrence estimate was short), frees its memory, records latencies and
  *     wakes waiters.
+ * Requests of 256 KiB or more run as whole-GPU scans (the plain kernel) on
+ * the slot's stream, sharing one per-slot workspace outside the arena; the
+ * rest share one batched launch.
  * A request's result equals a solo scan of the same text with the same set
  * (pm_scan): instances never share counters or outputs.
  */
@@ -314,6 +317,9 @@ typedef struct pm_server_params {
     int32_t pad;
     int64_t counter_words;        /* per-slot workspace for global per-terminal
                                      counters, in 8-byte words (default 4 Mi) */
+    int64_t host_pool_bytes;      /* page-locked host pool for result arrays
+                                     (default 1 GiB; < 0: none, plain memory);
+                                     results may outlive the server */
 } pm_server_params;
 typedef struct pm_server_stats {
     int64_t completed;            /* requests finished with PM_OK */
@@ -326,6 +332,8 @@ typedef struct pm_server_stats {
     double mean_batch;            /* requests per launch */
     double p50_us, p99_us, mean_us; /* latency, submit -> result on the host */
     double gbs;                   /* text bytes / (last completion - first submit) */
+    double dispatch_busy_s;       /* dispatcher time spent enqueueing batches */
+    double complete_busy_s;       /* completer time spent finishing batches */
 } pm_server_stats;
 
 /* params may be NULL (all defaults). Allocates the arena and per-slot

@@ -208,6 +208,8 @@ int ensure(void *&p, int64_t &cap, int64_t bytes)
 struct ResultBox {
     pm_result pub;
     int pinned;
+    ResultRelease release;  // arrays owned by an allocator of the caller's
+    void *ctx;
 };
 
 void free_array(void *p, int pinned)
@@ -251,6 +253,20 @@ int64_t set_d(const pm_set *s) { return s->algo == PM_ALGO_AC ? s->ac.d : s->wm.
 }  // namespace
 
 pm_result *make_result(int64_t d, int64_t n_occ, bool list) { return new_result(d, n_occ, list, false); }
+
+pm_result *make_result_owned(int64_t d, int64_t n_occ, int64_t *counts, uint64_t *occ,
+                             ResultRelease release, void *ctx)
+{
+    ResultBox *b = static_cast<ResultBox *>(std::calloc(1, sizeof(ResultBox)));
+    if (!b) return nullptr;
+    b->pub.d = d;
+    b->pub.n_occ = n_occ;
+    b->pub.counts = counts;
+    b->pub.occ = occ;
+    b->release = release;
+    b->ctx = ctx;
+    return &b->pub;
+}
 }  // namespace pm
 
 using namespace pm;
@@ -546,8 +562,12 @@ void pm_result_free(pm_result *r)
 {
     if (!r) return;
     ResultBox *b = reinterpret_cast<ResultBox *>(r);
-    free_array(r->counts, b->pinned);
-    free_array(r->occ, b->pinned);
+    if (b->release) {
+        b->release(b->ctx, r->counts, r->occ);
+    } else {
+        free_array(r->counts, b->pinned);
+        free_array(r->occ, b->pinned);
+    }
     std::free(b);
 }
 

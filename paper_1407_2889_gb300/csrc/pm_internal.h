@@ -165,6 +165,11 @@ int wm_launch(const WmTables &t, const DevWm &dev, const uint8_t *d_text, int64_
 void set_cuda_error(int err);
 // a library-owned result (plain host arrays), released by pm_result_free
 pm_result *make_result(int64_t d, int64_t n_occ, bool list);
+// a result whose arrays came from another allocator: pm_result_free hands
+// them to release(ctx, counts, occ)
+typedef void (*ResultRelease)(void *ctx, void *counts, void *occ);
+pm_result *make_result_owned(int64_t d, int64_t n_occ, int64_t *counts, uint64_t *occ,
+                             ResultRelease release, void *ctx);
 
 }  // namespace pm
 

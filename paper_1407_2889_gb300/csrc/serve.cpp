@@ -47,27 +47,15 @@ constexpr int64_t kPlainMin = int64_t(256) << 10;
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-// First-fit allocator over one device block; bookkeeping on the host.
-class Arena {
+// First-fit offset allocator with coalescing free list.
+class FreeList {
  public:
-    int init(int64_t bytes)
+    void reset(int64_t cap)
     {
-        bytes = round_up(bytes, kAlign);
-        const cudaError_t e = cudaMalloc(&base_, size_t(bytes));
-        if (e != cudaSuccess) {
-            set_cuda_error(int(e));
-            cudaGetLastError();
-            base_ = nullptr;
-            return PM_ENOMEM;
-        }
-        cap_ = bytes;
-        free_[0] = bytes;
-        return PM_OK;
-    }
-    void release()
-    {
-        if (base_) cudaFree(base_);
-        base_ = nullptr;
+        free_.clear();
+        free_[0] = cap;
+        cap_ = cap;
+        used_ = 0;
     }
     // offset of a block of at least `bytes`, or -1
     int64_t alloc(int64_t bytes)
@@ -102,14 +90,94 @@ class Arena {
             }
         }
     }
-    uint8_t *base() const { return static_cast<uint8_t *>(base_); }
     int64_t capacity() const { return cap_; }
     int64_t used() const { return used_; }
 
  private:
-    void *base_ = nullptr;
     int64_t cap_ = 0, used_ = 0;
     std::map<int64_t, int64_t> free_;  // offset -> size, coalesced
+};
+
+// Device memory of the requests in flight.
+class Arena {
+ public:
+    int init(int64_t bytes)
+    {
+        bytes = round_up(bytes, kAlign);
+        const cudaError_t e = cudaMalloc(&base_, size_t(bytes));
+        if (e != cudaSuccess) {
+            set_cuda_error(int(e));
+            cudaGetLastError();
+            base_ = nullptr;
+            return PM_ENOMEM;
+        }
+        fl_.reset(bytes);
+        return PM_OK;
+    }
+    void release()
+    {
+        if (base_) cudaFree(base_);
+        base_ = nullptr;
+    }
+    int64_t alloc(int64_t bytes) { return fl_.alloc(bytes); }
+    void free(int64_t off, int64_t bytes) { fl_.free(off, bytes); }
+    uint8_t *base() const { return static_cast<uint8_t *>(base_); }
+    int64_t capacity() const { return fl_.capacity(); }
+    int64_t used() const { return fl_.used(); }
+
+ private:
+    void *base_ = nullptr;
+    FreeList fl_;
+};
+
+// Page-locked host memory for result arrays, so results leave the device at
+// full link speed straight into the arrays the caller receives. Results may
+// outlive the server: the pool is freed when the server and every array
+// handed out are gone.
+struct HostPool {
+    std::mutex mu;
+    uint8_t *base = nullptr;
+    FreeList fl;
+    std::unordered_map<int64_t, int64_t> sizes;  // offset -> bytes of live arrays
+    int64_t refs = 1;                            // the server + live arrays
+
+    // NULL when the pool is full (the caller falls back to plain memory)
+    void *get(int64_t bytes)
+    {
+        if (!base) return nullptr;
+        std::lock_guard<std::mutex> lk(mu);
+        const int64_t off = fl.alloc(bytes);
+        if (off < 0) return nullptr;
+        sizes[off] = bytes;
+        ++refs;
+        return base + off;
+    }
+    static void drop(HostPool *p, void *ptr)
+    {
+        bool last = false;
+        {
+            std::lock_guard<std::mutex> lk(p->mu);
+            if (ptr) {
+                const int64_t off = static_cast<uint8_t *>(ptr) - p->base;
+                auto it = p->sizes.find(off);
+                if (it != p->sizes.end()) {
+                    p->fl.free(off, it->second);
+                    p->sizes.erase(it);
+                }
+            }
+            last = --p->refs == 0;
+        }
+        if (last) {
+            if (p->base) cudaFreeHost(p->base);
+            delete p;
+        }
+    }
+    static void release_result(void *ctx, void *counts, void *occ)
+    {
+        HostPool *p = static_cast<HostPool *>(ctx);
+        if (counts) drop(p, counts);
+        if (occ) drop(p, occ);
+    }
 };
 
 struct Req {
@@ -122,7 +190,7 @@ struct Req {
     int64_t text_blk = -1, text_bytes = 0;
     int64_t cnt_blk = -1, cnt_bytes = 0;
     int64_t occ_blk = -1, occ_bytes = 0, occ_cap = 0;
-    int64_t ws_blk = -1, ws_bytes = 0; // workspace of a whole-GPU scan
+    int64_t ws_bytes = 0;              // workspace of a whole-GPU scan (the slot's)
     bool plain = false;
     void *occ_ext = nullptr;           // re-run buffer outside the arena
     int64_t n_occ = 0;
@@ -139,6 +207,10 @@ struct Slot {
     int64_t *d_nocc = nullptr;
     void *d_ws = nullptr;
     int64_t ws_words = 0;              // global counter words the workspace holds
+    uint32_t *h_bstat = nullptr;       // pinned: the batched scan's status word
+    void *d_pws = nullptr;             // workspace shared by the slot's whole-GPU scans
+    int64_t pws_bytes = 0;
+    uint32_t *h_pstat = nullptr;       // pinned, max_batch: their status words
     bool busy = false;
     std::vector<Req *> reqs;
     std::atomic<bool> ready{false};
@@ -161,11 +233,14 @@ struct pm_server {
     std::unordered_map<const pm_set *, double> rate;   // occurrences per text byte seen
     int64_t next_id = 1;
     bool stopping = false;
-    std::thread dispatcher, completer;
+    std::thread dispatcher;
+    std::vector<std::thread> completers;   // one per slot
+    pm::HostPool *pool = nullptr;
     // statistics
     std::vector<double> lat_us;
     int64_t bytes_done = 0, batches = 0, batched_reqs = 0, reruns = 0, peak_inflight = 0;
     int64_t inflight_reqs = 0;
+    double dispatch_busy_s = 0.0, complete_busy_s = 0.0;
     bool have_first = false;
     pm::Clock::time_point t_first, t_last;
 };
@@ -203,21 +278,12 @@ bool admit(pm_server *s, Req &r)
     r.occ_bytes = r.list ? std::max<int64_t>(r.occ_cap, 1) * 8 : 0;
     r.plain = r.n >= kPlainMin;
     r.ws_bytes = r.plain ? pm_scan_workspace_bytes(r.set, r.n, r.list ? 0u : PM_COUNTS_ONLY) : 0;
-    if (r.plain) {
-        r.ws_blk = s->arena.alloc(r.ws_bytes);
-        if (r.ws_blk < 0) return false;
-    }
     r.text_blk = s->arena.alloc(r.text_bytes);
-    if (r.text_blk < 0) {
-        s->arena.free(r.ws_blk, r.ws_bytes);
-        r.ws_blk = -1;
-        return false;
-    }
+    if (r.text_blk < 0) return false;
     r.cnt_blk = s->arena.alloc(r.cnt_bytes);
     if (r.cnt_blk < 0) {
         s->arena.free(r.text_blk, r.text_bytes);
-        s->arena.free(r.ws_blk, r.ws_bytes);
-        r.text_blk = r.ws_blk = -1;
+        r.text_blk = -1;
         return false;
     }
     if (r.list) {
@@ -225,8 +291,7 @@ bool admit(pm_server *s, Req &r)
         if (r.occ_blk < 0) {
             s->arena.free(r.text_blk, r.text_bytes);
             s->arena.free(r.cnt_blk, r.cnt_bytes);
-            s->arena.free(r.ws_blk, r.ws_bytes);
-            r.text_blk = r.cnt_blk = r.ws_blk = -1;
+            r.text_blk = r.cnt_blk = -1;
             return false;
         }
     }
@@ -242,8 +307,7 @@ void *release(pm_server *s, Req &r)
     s->arena.free(r.text_blk, r.text_bytes);
     s->arena.free(r.cnt_blk, r.cnt_bytes);
     if (r.occ_blk >= 0) s->arena.free(r.occ_blk, r.occ_bytes);
-    s->arena.free(r.ws_blk, r.ws_bytes);
-    r.text_blk = r.cnt_blk = r.occ_blk = r.ws_blk = -1;
+    r.text_blk = r.cnt_blk = r.occ_blk = -1;
     void *ext = r.occ_ext;
     r.occ_ext = nullptr;
     return ext;
@@ -258,12 +322,32 @@ int64_t counter_words(const pm_server *s, const Req &r)
 
 // A whole-GPU scan of one request, its keys going to `occ`, its total to
 // d_nocc (asynchronous on the stream).
-int launch_plain(pm_server *s, const Req &r, uint64_t *occ, int64_t cap, int64_t *d_nocc, cudaStream_t st)
+int launch_plain(pm_server *s, const Req &r, uint64_t *occ, int64_t cap, int64_t *d_nocc, void *ws,
+                 cudaStream_t st)
 {
     uint8_t *base = s->arena.base();
     return ac_launch(r.set->ac, r.set->dac, base + r.text_blk, r.n, r.list,
                      reinterpret_cast<int64_t *>(base + r.cnt_blk), r.list ? occ : nullptr, cap, d_nocc,
-                     base + r.ws_blk, st);
+                     ws, st);
+}
+
+// The slot's whole-GPU scans run one after another on its stream and share
+// one workspace; grow it when a request needs more (the slot is idle here).
+int ensure_pws(Slot &sl, int64_t need)
+{
+    if (need <= sl.pws_bytes) return PM_OK;
+    if (sl.d_pws) cudaFree(sl.d_pws);
+    sl.d_pws = nullptr;
+    sl.pws_bytes = 0;
+    const cudaError_t e = cudaMalloc(&sl.d_pws, size_t(need));
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        sl.d_pws = nullptr;
+        return PM_ENOMEM;
+    }
+    sl.pws_bytes = need;
+    return PM_OK;
 }
 
 // Enqueue the batch of slot `sl` (texts in, kernel, totals out); the caller
@@ -297,14 +381,30 @@ int launch_slot(pm_server *s, Slot &sl)
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     uint8_t *base = s->arena.base();
     int rc = PM_OK;
-    if (kb > 0)
+    *sl.h_bstat = 0;
+    if (kb > 0) {
         rc = batch_launch_raw(sl.d_desc, kb, base, reinterpret_cast<int64_t *>(base),
                               reinterpret_cast<uint64_t *>(base), sl.d_nocc, sl.d_ws, words, s->shape,
                               true, sl.st);
+        if (rc == PM_OK) {
+            e = cudaMemcpyAsync(sl.h_bstat, sl.d_ws, 4, cudaMemcpyDeviceToHost, sl.st);
+            if (e != cudaSuccess) { set_cuda_error(int(e)); rc = PM_ECUDA; }
+        }
+    }
+    int64_t pws = 0;
+    for (const Req *r : sl.reqs)
+        if (r->plain) pws = std::max(pws, r->ws_bytes);
+    if (rc == PM_OK && pws > 0) rc = ensure_pws(sl, pws);
     for (int j = 0; j < k && rc == PM_OK; ++j) {
         const Req &r = *sl.reqs[size_t(j)];
-        if (r.plain)
-            rc = launch_plain(s, r, reinterpret_cast<uint64_t *>(base + r.occ_blk), r.occ_cap, sl.d_nocc + j, sl.st);
+        if (!r.plain) continue;
+        rc = launch_plain(s, r, reinterpret_cast<uint64_t *>(base + r.occ_blk), r.occ_cap, sl.d_nocc + j,
+                          sl.d_pws, sl.st);
+        // the next scan clears the shared status word: keep this one's
+        if (rc == PM_OK) {
+            e = cudaMemcpyAsync(sl.h_pstat + j, sl.d_pws, 4, cudaMemcpyDeviceToHost, sl.st);
+            if (e != cudaSuccess) { set_cuda_error(int(e)); rc = PM_ECUDA; }
+        }
     }
     if (rc) return rc;
     e = cudaMemcpyAsync(sl.h_nocc, sl.d_nocc, size_t(k) * 8, cudaMemcpyDeviceToHost, sl.st);
@@ -375,6 +475,7 @@ void dispatcher_main(pm_server *s)
         s->batches += 1;
         s->batched_reqs += int64_t(batch.size());
         lk.unlock();
+        const auto tb0 = Clock::now();
         int rc = launch_slot(s, *free_slot);
         if (rc == PM_OK) {
             auto *arg = new (std::nothrow) std::pair<pm_server *, Slot *>(s, free_slot);
@@ -386,6 +487,7 @@ void dispatcher_main(pm_server *s)
             }
         }
         lk.lock();
+        s->dispatch_busy_s += std::chrono::duration<double>(Clock::now() - tb0).count();
         if (rc != PM_OK) {
             // the stream may still hold copies: drain it, then fail the batch
             lk.unlock();
@@ -412,7 +514,8 @@ int rerun_one(pm_server *s, Slot &sl, Req &r, uint64_t *occ)
     cudaError_t e = cudaSuccess;
     int rc = PM_OK;
     if (r.plain) {
-        rc = launch_plain(s, r, occ, r.occ_cap, sl.d_nocc, sl.st);
+        rc = ensure_pws(sl, r.ws_bytes);
+        if (rc == PM_OK) rc = launch_plain(s, r, occ, r.occ_cap, sl.d_nocc, sl.d_pws, sl.st);
     } else {
         BatchInst I{r.set, r.text_blk, r.n, r.cnt_blk / 8, 0, r.occ_cap, 0};
         const int64_t words = batch_fill(&I, 1, s->shape, sl.h_desc);
@@ -426,8 +529,7 @@ int rerun_one(pm_server *s, Slot &sl, Req &r, uint64_t *occ)
     e = cudaMemcpyAsync(sl.h_nocc, sl.d_nocc, 8, cudaMemcpyDeviceToHost, sl.st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sl.st);
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-    if (pm_scan_status(r.plain ? static_cast<void *>(s->arena.base() + r.ws_blk) : sl.d_ws, sl.st) != PM_OK)
-        return PM_ETIMEOUT;
+    if (pm_scan_status(r.plain ? sl.d_pws : sl.d_ws, sl.st) != PM_OK) return PM_ETIMEOUT;
     return sl.h_nocc[0] == r.n_occ ? PM_OK : PM_ECUDA;  // same scan, same total
 }
 
@@ -443,10 +545,9 @@ void complete_slot(pm_server *s, Slot &sl, std::unique_lock<std::mutex> &lk)
     }
     int rc = PM_OK;
     lk.unlock();
-    if (pm_scan_status(sl.d_ws, sl.st) != PM_OK) rc = PM_ETIMEOUT;
-    for (Req *r : sl.reqs)
-        if (rc == PM_OK && r->plain && pm_scan_status(s->arena.base() + r->ws_blk, sl.st) != PM_OK)
-            rc = PM_ETIMEOUT;
+    if (*sl.h_bstat != 0) rc = PM_ETIMEOUT;
+    for (int j = 0; j < k; ++j)
+        if (rc == PM_OK && sl.reqs[size_t(j)]->plain && sl.h_pstat[j] != 0) rc = PM_ETIMEOUT;
     if (!over.empty() && rc == PM_OK) {
         // exact capacity for the instances whose estimate was short: a new
         // arena block, else a buffer of its own
@@ -475,7 +576,17 @@ void complete_slot(pm_server *s, Slot &sl, std::unique_lock<std::mutex> &lk)
     for (int j = 0; j < k; ++j) {
         Req &r = *sl.reqs[size_t(j)];
         if (rcs[size_t(j)] != PM_OK) continue;
-        r.res = make_result(r.set->ac.d, r.list ? r.n_occ : 0, r.list);
+        const int64_t d = r.set->ac.d, no = r.list ? r.n_occ : 0;
+        void *pc = s->pool->get(d * 8);
+        void *po = r.list ? s->pool->get(std::max<int64_t>(no, 1) * 8) : nullptr;
+        if (pc && (po || !r.list)) {
+            r.res = make_result_owned(d, r.n_occ, static_cast<int64_t *>(pc), static_cast<uint64_t *>(po),
+                                      &HostPool::release_result, s->pool);
+            if (!r.res) HostPool::release_result(s->pool, pc, po);
+        } else {
+            HostPool::release_result(s->pool, pc, po);
+            r.res = make_result(d, no, r.list);  // pool full: plain host arrays
+        }
         if (!r.res) { rcs[size_t(j)] = PM_ENOMEM; continue; }
         r.res->n_occ = r.n_occ;
         cudaError_t e = cudaMemcpyAsync(r.res->counts, s->arena.base() + r.cnt_blk, size_t(r.cnt_bytes),
@@ -519,23 +630,21 @@ void complete_slot(pm_server *s, Slot &sl, std::unique_lock<std::mutex> &lk)
     }
 }
 
-void completer_main(pm_server *s)
+// One completion thread per slot, so batches that finish together are
+// finished in parallel (their copies run on their own streams).
+void completer_main(pm_server *s, Slot *sl)
 {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        Slot *ready = nullptr;
-        bool any_busy = false;
-        for (Slot *sl : s->slots) {
-            if (sl->busy) any_busy = true;
-            if (sl->busy && sl->ready.load()) { ready = sl; break; }
-        }
-        if (ready) {
-            ready->ready.store(false);
-            complete_slot(s, *ready, lk);
+        if (sl->busy && sl->ready.load()) {
+            sl->ready.store(false);
+            const auto tb0 = Clock::now();
+            complete_slot(s, *sl, lk);
+            s->complete_busy_s += std::chrono::duration<double>(Clock::now() - tb0).count();
             continue;
         }
-        if (s->stopping && !any_busy && s->pending.empty()) break;
+        if (s->stopping && !sl->busy && s->pending.empty()) break;
         s->cv_complete.wait_for(lk, std::chrono::milliseconds(50));
     }
 }
@@ -546,6 +655,9 @@ void destroy(pm_server *s)
         if (sl->st) cudaStreamDestroy(sl->st);
         if (sl->h_desc) cudaFreeHost(sl->h_desc);
         if (sl->h_nocc) cudaFreeHost(sl->h_nocc);
+        if (sl->h_pstat) cudaFreeHost(sl->h_pstat);
+        if (sl->h_bstat) cudaFreeHost(sl->h_bstat);
+        if (sl->d_pws) cudaFree(sl->d_pws);
         if (sl->d_desc) cudaFree(sl->d_desc);
         if (sl->d_nocc) cudaFree(sl->d_nocc);
         if (sl->d_ws) cudaFree(sl->d_ws);
@@ -553,6 +665,8 @@ void destroy(pm_server *s)
     }
     s->slots.clear();
     s->arena.release();
+    if (s->pool) HostPool::drop(s->pool, nullptr);  // the server's reference
+    s->pool = nullptr;
     for (auto &kv : s->by_id) {
         if (kv.second->res) pm_result_free(kv.second->res);
         delete kv.second;
@@ -578,6 +692,7 @@ int pm_server_create(const pm_server_params *params, pm_server **out)
     if (p.max_inflight <= 0) p.max_inflight = 3;
     if (p.warps_per_cta <= 0) p.warps_per_cta = 12;
     if (p.counter_words <= 0) p.counter_words = int64_t(4) << 20;
+    if (p.host_pool_bytes == 0) p.host_pool_bytes = int64_t(1) << 30;
     if (p.max_inflight > 16 || p.max_batch > (1 << 20)) return PM_EINVAL;
     pm_server *s = new (std::nothrow) pm_server();
     if (!s) return PM_ENOMEM;
@@ -587,6 +702,20 @@ int pm_server_create(const pm_server_params *params, pm_server **out)
     int rc = batch_shape(p.warps_per_cta, s->shape);
     if (!rc) rc = batch_prepare_launch(s->shape);
     if (!rc) rc = s->arena.init(p.device_budget_bytes);
+    if (!rc) {
+        s->pool = new (std::nothrow) HostPool();
+        if (!s->pool) rc = PM_ENOMEM;
+    }
+    if (!rc && p.host_pool_bytes > 0) {
+        const int64_t hb = round_up(p.host_pool_bytes, kAlign);
+        void *hp = nullptr;
+        if (cudaMallocHost(&hp, size_t(hb)) == cudaSuccess) {
+            s->pool->base = static_cast<uint8_t *>(hp);
+            s->pool->fl.reset(hb);
+        } else {
+            cudaGetLastError();  // no page-locked pool: results use plain memory
+        }
+    }
     for (int i = 0; i < p.max_inflight && !rc; ++i) {
         Slot *sl = new (std::nothrow) Slot();
         if (!sl) { rc = PM_ENOMEM; break; }
@@ -595,6 +724,8 @@ int pm_server_create(const pm_server_params *params, pm_server **out)
         e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_desc), size_t(p.max_batch) * sizeof(BatchDesc));
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_nocc), size_t(p.max_batch) * 8);
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_pstat), size_t(p.max_batch) * 4);
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_bstat), 4);
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&sl->d_desc), size_t(p.max_batch) * sizeof(BatchDesc));
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&sl->d_nocc), size_t(p.max_batch) * 8);
         if (e == cudaSuccess) e = cudaMalloc(&sl->d_ws, size_t(batch_ws_bytes(p.counter_words)));
@@ -607,7 +738,7 @@ int pm_server_create(const pm_server_params *params, pm_server **out)
     if (rc) { destroy(s); return rc; }
     try {
         s->dispatcher = std::thread(dispatcher_main, s);
-        s->completer = std::thread(completer_main, s);
+        for (Slot *sl : s->slots) s->completers.emplace_back(completer_main, s, sl);
     } catch (...) {
         {
             std::lock_guard<std::mutex> lk(s->mu);
@@ -616,7 +747,7 @@ int pm_server_create(const pm_server_params *params, pm_server **out)
         s->cv_dispatch.notify_all();
         s->cv_complete.notify_all();
         if (s->dispatcher.joinable()) s->dispatcher.join();
-        if (s->completer.joinable()) s->completer.join();
+        for (auto &t : s->completers) if (t.joinable()) t.join();
         destroy(s);
         return PM_ENOMEM;
     }
@@ -639,7 +770,6 @@ int pm_server_submit(pm_server *s, const pm_set *set, const uint8_t *T, int64_t 
     r->list = !(flags & PM_COUNTS_ONLY);
     int64_t need = round_up(std::max<int64_t>(n, 1), kAlign) + round_up(set->ac.d * 8, kAlign) +
                    (r->list ? round_up((est_cap(s, *r) + 1) * 8, kAlign) : 0);
-    if (n >= kPlainMin) need += round_up(pm_scan_workspace_bytes(set, n, r->list ? 0u : PM_COUNTS_ONLY), kAlign);
     if (need > s->arena.capacity() || counter_words(s, *r) > s->p.counter_words) {
         delete r;
         return PM_ETOOBIG;  // could never be admitted
@@ -687,6 +817,8 @@ int pm_server_get_stats(pm_server *s, pm_server_stats *st)
     st->peak_inflight = s->peak_inflight;
     st->pending = int64_t(s->pending.size());
     st->arena_used = s->arena.used();
+    st->dispatch_busy_s = s->dispatch_busy_s;
+    st->complete_busy_s = s->complete_busy_s;
     if (!s->lat_us.empty()) {
         std::vector<double> v = s->lat_us;
         auto pct = [&](double q) {
@@ -715,7 +847,7 @@ void pm_server_destroy(pm_server *s)
     s->cv_dispatch.notify_all();
     s->cv_complete.notify_all();
     if (s->dispatcher.joinable()) s->dispatcher.join();
-    if (s->completer.joinable()) s->completer.join();
+    for (auto &t : s->completers) if (t.joinable()) t.join();
     destroy(s);
 }
 

@@ -65,14 +65,16 @@ class pm_result(ctypes.Structure):
 class pm_server_params(ctypes.Structure):
     _fields_ = [("device_budget_bytes", ctypes.c_int64), ("max_batch", ctypes.c_int32),
                 ("max_inflight", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("counter_words", ctypes.c_int64)]
+                ("pad", ctypes.c_int32), ("counter_words", ctypes.c_int64),
+                ("host_pool_bytes", ctypes.c_int64)]
 
 
 class pm_server_stats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("bytes", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("reruns", ctypes.c_int64), ("peak_inflight", ctypes.c_int64), ("pending", ctypes.c_int64),
                 ("arena_used", ctypes.c_int64), ("mean_batch", ctypes.c_double), ("p50_us", ctypes.c_double),
-                ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("gbs", ctypes.c_double)]
+                ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("gbs", ctypes.c_double),
+                ("dispatch_busy_s", ctypes.c_double), ("complete_busy_s", ctypes.c_double)]
 
 
 class PmError(RuntimeError):
@@ -584,9 +586,9 @@ class Server:
     device-resident sets, wait for results; continuous batching inside."""
 
     def __init__(self, budget_bytes: int = 4 << 30, max_batch: int = 512, max_inflight: int = 3,
-                 warps: int = 12, counter_words: int = 0):
+                 warps: int = 12, counter_words: int = 0, host_pool_bytes: int = 0):
         p = pm_server_params(int(budget_bytes), int(max_batch), int(max_inflight), int(warps), 0,
-                             int(counter_words))
+                             int(counter_words), int(host_pool_bytes))
         h = ctypes.c_void_p()
         _check(lib().pm_server_create(ctypes.byref(p), ctypes.byref(h)), "pm_server_create")
         self.h = int(h.value)

@@ -278,6 +278,29 @@ def test_full_size_headline_in_bench_configuration(est_text_full):
     s.close()
 
 
+@pytest.mark.parametrize("d", [100000, 500000])
+def test_large_sets_full_text(est_text_full, d):
+    """Large pattern sets (m=32): the AC table (u32, 2.3M / 11M rows) only
+    fits shared memory as a breadth-first prefix; the rest is read through
+    L2/HBM. Full 1 GiB text against the oracle in full; WM with B=4 (2^20
+    SHIFT entries) on a prefix (on ACGT text every 4-byte block ends some
+    pattern when d is this large, so WM verifies at every position)."""
+    T = est_text_full
+    P = synth.large_set(d, T)
+    s = _ac(P)
+    info = s.info()
+    assert info["entry_bytes"] == 4 and info["placement"] == pm.PM_PLACE_HYBRID
+    assert info["smem_rows"] < info["n_rows"]
+    want = oracle.dictionary(T, P, threads=THREADS)
+    _same(s.scan(torch.from_numpy(T).cuda()), want, f"AC d={d}")
+    s.close()
+    nw = (16 << 20) if d == 100000 else (2 << 20)
+    w = _wm(P, 4)
+    assert w.info()["shift_entries"] == 1 << 20
+    _same(w.scan(T[:nw]), oracle.dictionary(T[:nw], P, threads=THREADS), f"WM B=4 d={d}")
+    w.close()
+
+
 def test_scan_to_host_pinned_buffers_and_capacity():
     T = synth.est_text(1 << 21, 9)
     P = synth.mixed_patterns(T, 500, 8, 9)

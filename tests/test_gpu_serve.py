@@ -162,3 +162,24 @@ def test_rejected_requests(base, sets):
             assert occ.size == 0 and cnt.sum() == 0
     finally:
         srv.close()
+
+
+def test_results_outlive_the_server(base, sets):
+    """Result arrays come from the server's page-locked pool; a result freed
+    after pm_server_destroy is still intact (the pool lives until then)."""
+    import ctypes
+    L = pm.lib()
+    T = base[: 1 << 20]
+    want = sets[2][1].scan(T)
+    srv = pm.Server(budget_bytes=64 << 20, host_pool_bytes=64 << 20)
+    t = srv.submit(sets[2][1], T)
+    rp = ctypes.POINTER(pm.pm_result)()
+    assert L.pm_server_wait(srv.h, t, ctypes.byref(rp)) == pm.PM_OK
+    srv._keep.clear()
+    srv.close()
+    r = rp.contents
+    cnt = np.ctypeslib.as_array(r.counts, shape=(r.d,)).copy()
+    occ = np.ctypeslib.as_array(r.occ, shape=(r.n_occ,)).copy() if r.n_occ else np.zeros(0, np.uint64)
+    L.pm_result_free(rp)
+    _same((occ, cnt), want, 0)
+
