@@ -170,6 +170,19 @@ def workload_name(args) -> str:
             f"d={args.d}, m={args.m} (half copied from the text, half random)")
 
 
+def max_over_ranks(elapsed_ms: float, dist, torch, device) -> float:
+    """The slowest rank's timed region (every rank calls this)."""
+    tt = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(bytes_per_rank: int, steps: int, world: int, elapsed_ms: float) -> float:
+    """Whole-job GB/s: every replica scans its own copy of the workload
+    (weak scaling), all ranks' bytes over the slowest rank's time."""
+    return world * bytes_per_rank * steps / (elapsed_ms / 1e3) / 1e9
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -290,13 +303,11 @@ def main():
     elapsed_ms = t_all0.elapsed_time(t_all1)
     per_launch = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     if dist:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+        elapsed_ms = max_over_ranks(elapsed_ms, dist, torch, "cuda")
     assert pm.pm_scan_status(ws, stream) == pm.PM_OK
     assert int(nocc.item()) == total
     n_occ = total
-    value = world * n * args.steps / (elapsed_ms / 1e3) / 1e9
+    value = job_rate(n, args.steps, world, elapsed_ms)
 
     peak, peak_kind = measured_peaks()
     avg_launch_s = statistics.mean(per_launch) / 1e3
@@ -306,7 +317,7 @@ def main():
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": recorded_traffic("ac_scan_kernel", f"est1gib_d{d}_m{args.m}_{args.mode}_n{n}"),
                 "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel": "ac_scan_kernel<uint16_t,6,1,dna,smem>"}
+                "kernel": "ac_scan_kernel<uint16_t,6,1,dna,smem> + tile_offsets_kernel + expand_kernel (list mode)"}
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -354,7 +365,7 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "table": {k: info[k] for k in ("n_rows", "entry_bytes", "placement", "smem_rows", "table_bytes")}},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps, "clocks": clk, "extras": extras,
+            "gpu_launches": args.steps * (3 if args.mode == "list" else 1), "clocks": clk, "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -366,32 +366,11 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
     return PM_OK;
 }
 
-static int64_t set_terms(const pm_set *s)
-{
-    return s->algo == PM_ALGO_AC ? int64_t(s->ac.canon.size()) : 0;
-}
-
-static int64_t set_tiles(const pm_set *s, int64_t n)
-{
-    const int64_t k = s->algo == PM_ALGO_AC ? ac_ksub_for(s->dac, n) : 1;
-    return (warp_tiles(n) + k - 1) / k;
-}
-
-// list-mode scratch: two slots of K warp tiles of entries for every warp of
-// the grid a scan of n bytes launches (at most one warp per look-back tile,
-// rounded up to whole CTAs, and at most the largest grid)
-static int64_t set_scratch(const pm_set *s, int64_t n)
-{
-    if (s->algo != PM_ALGO_AC) return 0;
-    const int64_t se = (s->ac.dna ? s->ac.entry_bytes : 4) == 2 ? 4 : 8;
-    const int64_t w = std::max<int64_t>(1, s->dac.warps);
-    const int64_t grid_warps = std::min<int64_t>(s->dac.max_warps, (set_tiles(s, n) + w - 1) / w * w);
-    return grid_warps * 2 * int64_t(ac_ksub_for(s->dac, n)) * kWarpTile * se;
-}
-
+// Wu-Manber: look-back tiles are warp tiles; no scratch
 static int64_t set_ws_bytes(const pm_set *s, int64_t n, bool list)
 {
-    return workspace_bytes_for(set_tiles(s, n), list, set_terms(s), set_scratch(s, n));
+    if (s->algo == PM_ALGO_AC) return ac_workspace_bytes(s->ac, n, list);
+    return workspace_bytes_for(warp_tiles(n), list, 0, 0);
 }
 
 int64_t pm_scan_workspace_bytes(const pm_set *s, int64_t n, uint32_t flags)

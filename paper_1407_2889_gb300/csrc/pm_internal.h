@@ -110,7 +110,6 @@ struct DevAc {
     int64_t smem_bytes = 0;
     int32_t placement = 0;
     int64_t max_warps = 0;          // warps in the largest grid a launch uses
-    int32_t ksub = 1;               // warp tiles per look-back tile
 };
 
 struct DevWm {
@@ -154,9 +153,8 @@ int ac_launch_noalloc(const AcTables &t, const DevAc &dev, const uint8_t *d_text
                       bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
                       int64_t *d_n_occ, void *stream);
 int64_t ac_noalloc_limit_bytes();
-// warp tiles per look-back tile for a text of n bytes: the set's value,
-// halved while that would leave warps of the largest grid without a tile
-int ac_ksub_for(const DevAc &dev, int64_t n);
+// device workspace of an Aho-Corasick scan of n bytes
+int64_t ac_workspace_bytes(const AcTables &t, int64_t n, bool list);
 int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevWm &dev);
 int wm_launch(const WmTables &t, const DevWm &dev, const uint8_t *d_text, int64_t n,
               bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,

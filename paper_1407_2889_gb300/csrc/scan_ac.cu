@@ -6,10 +6,10 @@
 // [tile + 80 l, tile + 80 l + 80) and walks the DFA from the root over those
 // bytes plus the m-1 that follow (the paper's m-1 overlap), so every start
 // position belongs to exactly one lane and a match is reported by the lane
-// that owns its start. A warp claims tiles from a global counter in
-// increasing order, stages each tile (plus halo) into its own shared-memory
-// buffer with one 1-D TMA bulk copy, loads its 80+16*HV bytes into
-// registers, and immediately prefetches the next tile into the same buffer.
+// that owns its start. Warp w of the grid takes tiles w, w + G, w + 2G ...,
+// stages each tile (plus halo) into its own shared-memory buffer with one
+// 1-D TMA bulk copy, loads its 80+16*HV bytes into registers, and
+// immediately prefetches its next tile into the same buffer.
 //
 // The transition table (Section 3.1, goto and supply merged) is loaded into
 // shared memory once per CTA; with hybrid placement only its breadth-first
@@ -22,11 +22,17 @@
 // terminal state and the table index of that transition (pool, shared
 // memory). Afterwards each match is resolved to its terminal's canonical id
 // (the rank of its table entry among match entries, from a bitmap with
-// prefix counts) and to the pattern id, per-terminal counters are bumped,
-// per-lane offsets come from a warp scan and the tile's global offset from a
-// two-level decoupled look-back, and the sorted (i, r) keys leave through a
-// shared-memory staging window so global stores are coalesced (the paper's
-// coalesced writes, GPU-CW).
+// prefix counts) and to the pattern code, and per-terminal counters are
+// bumped; the last CTA turns them into counts[r].
+//
+// List mode writes the output in three launches, so that no warp ever waits
+// for another: the scan writes each warp tile's matches, in text order, to
+// that tile's own slot of kWarpTile entries (at most one distinct pattern
+// string starts at a position) with the tile's totals; a one-CTA kernel turns
+// the totals into each tile's offset in the output; an expand kernel with
+// many resident warps copies the slots to the sorted (i, r) keys, one key per
+// pattern of a group of equal patterns (the paper's coalesced writes,
+// GPU-CW).
 #include <cstdio>
 #include <mutex>
 #include <type_traits>
@@ -56,28 +62,43 @@ struct AcArgs {
     int m, lw;
     uint32_t lut;
     uint32_t pad;
-    long long ntiles;             // look-back tiles of ksub warp tiles each
     long long nsub;               // warp tiles (2560 text bytes each)
-    int ksub;
-    int pool_cap, stage_cap;
+    int pool_cap;
     int list, hist_smem, ids_smem, d;
     long long *counts;
-    unsigned long long *occ;
-    long long occ_cap;
     long long *n_occ;
     dev::WsHeader *ws;
     unsigned long long *ccount;   // per-terminal totals
-    dev::LookbackRefs lb;
-    void *scratch;                // list mode: 2 slots of ksub * kWarpTile entries per warp
+    uint32_t *tile_ent;           // list: entries (one per matching position) per warp tile
+    uint32_t *tile_out;           // list: outputs (keys, groups expanded) per warp tile
+    void *slots;                  // list: kWarpTile entries per warp tile
+};
+
+// Workspace carve-up shared by the launchers and the workspace size:
+//   [header][per-terminal counters] -- zeroed by every scan
+//   list mode: [tile_ent u32][tile_out u32][tile offsets u64][slots]
+struct AcWsLayout {
+    long long zeroed, tile_ent, tile_out, tile_base, slots, total;
 };
 
 __host__ __device__ constexpr long long r16(long long x) { return (x + 15) & ~15LL; }
 
-__host__ __device__ inline long long ac_warp_bytes(int hv, int pool_cap, int eb, int stage_cap)
+__host__ __device__ inline long long ac_warp_bytes(int hv, int pool_cap, int eb)
 {
-    // barrier | text buffer | pool (pool_cap + 1 slots per lane) | staging
-    return 16 + r16(kWarpTile + 16 * hv) + r16((long long)(pool_cap + 1) * 32 * eb) +
-           (long long)stage_cap * 8;
+    // barrier | text buffer | pool (pool_cap + 1 slots per lane)
+    return 16 + r16(kWarpTile + 16 * hv) + r16((long long)(pool_cap + 1) * 32 * eb);
+}
+
+AcWsLayout ac_ws_layout(long long nsub, bool list, long long nterms, int slot_entry_bytes)
+{
+    AcWsLayout L;
+    L.zeroed = kWsHeader + r16(nterms * 8);
+    L.tile_ent = L.zeroed;
+    L.tile_out = L.tile_ent + (list ? r16(nsub * 4) : 0);
+    L.tile_base = L.tile_out + (list ? r16(nsub * 4) : 0);
+    L.slots = L.tile_base + (list ? r16(nsub * 8) : 0);
+    L.total = L.slots + (list ? r16(nsub * kWarpTile * (long long)slot_entry_bytes) : 0);
+    return L;
 }
 
 __host__ __device__ inline long long ac_ids_bytes(int nwords, int nterms, int eb)
@@ -132,12 +153,10 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
     p += a.hist_smem ? r16((long long)a.nterms * 4) : 0;
     uint8_t *s_cls = p;
     p += DNA ? 0 : 256;
-    p += warp * ac_warp_bytes(HV, a.pool_cap, sizeof(E), a.stage_cap);
+    p += warp * ac_warp_bytes(HV, a.pool_cap, sizeof(E));
     uint64_t *bar = reinterpret_cast<uint64_t *>(p);
     uint8_t *buf = p + 16;
     E *pool = reinterpret_cast<E *>(buf + r16(BUF));
-    unsigned long long *stage = reinterpret_cast<unsigned long long *>(
-        reinterpret_cast<unsigned char *>(pool) + r16((long long)(a.pool_cap + 1) * 32 * sizeof(E)));
 
     {   // table prefix -> shared memory (16-byte vectors; the global copy is padded)
         const uint4 *src = reinterpret_cast<const uint4 *>(a.table_g);
@@ -181,276 +200,147 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
         return __ldg(a.grp_off + g + 1) - __ldg(a.grp_off + g);
     };
 
-    // scratch entries: (start offset in the tile, pattern code)
+    // slot entries: (start offset in the tile, pattern code)
     typedef typename std::conditional<sizeof(E) == 2, uint32_t, unsigned long long>::type SE;
     constexpr int kOffShift = sizeof(E) == 2 ? 16 : 32;
-    const int K = a.ksub;
-    const long long slot_len = (long long)K * kWarpTile;
+    const long long G = (long long)gridDim.x * (blockDim.x >> 5);
     const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    SE *slots = reinterpret_cast<SE *>(a.scratch) + gwarp * 2 * slot_len;
-    SE *sstage = reinterpret_cast<SE *>(stage);  // staging window, SE entries
-    const uint32_t S = uint32_t(a.stage_cap) * 8u / sizeof(SE);
+    SE *slots = reinterpret_cast<SE *>(a.slots);
 
-    dev::TileSchedule sch;
-    sch.init(a.ntiles);
     uint32_t phase = 0;
     bool inflight = false;
     bool failed = false;
     unsigned long long my_total = 0;
-    // the tile whose output is written one round later (list mode)
-    long long prev = -1;
-    uint32_t prev_entries = 0, prev_slot = 0, cur_slot = 0;
-    unsigned long long prev_outputs = 0;
-    bool prev_group = false;
 
-    // Emits tile u from its scratch slot once its offset is known.
-    auto emit_deferred = [&](long long u, uint32_t entries, unsigned long long outputs,
-                             bool group, uint32_t slot) -> bool {
-        bool ok;
-        const unsigned long long B = dev::tile_base(a.lb, u, lane, ok);
-        if (!ok) return false;
-        const long long tile0 = u * slot_len;
-        const SE *sl = slots + (long long)slot * slot_len;
-        if (!group) {
-            // coalesced copy with 16 independent scratch loads in flight per lane
-            constexpr int U = sizeof(SE) == 4 ? 16 : 8;
-            const unsigned long long cap_occ = (unsigned long long)a.occ_cap;
-            for (uint32_t j0 = 0; j0 < entries; j0 += 32 * U) {
-                SE v[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint32_t j = j0 + u * 32 + lane;
-                    v[u] = j < entries ? __ldcg(sl + j) : (SE)0;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint32_t j = j0 + u * 32 + lane;
-                    const unsigned long long gi = B + j;
-                    if (j < entries && gi < cap_occ)
-                        a.occ[gi] = ((unsigned long long)(tile0 + (long long)(v[u] >> kOffShift)) << 32) |
-                                    (uint32_t)(v[u] & (((SE)1 << kOffShift) - 1));
-                }
-            }
-        } else {
-            unsigned long long run = 0;
-            for (uint32_t w0 = 0; w0 < entries; w0 += 32) {
-                const uint32_t j = w0 + lane;
-                SE v = 0;
-                uint32_t mult = 0, code = 0, lo = 0;
-                if (j < entries) {
-                    v = sl[j];
-                    code = uint32_t(v & (((SE)1 << kOffShift) - 1));
-                    if (code & kGrp) {
-                        const uint32_t g = code & ~kGrp;
-                        lo = __ldg(a.grp_off + g);
-                        mult = __ldg(a.grp_off + g + 1) - lo;
-                    } else {
-                        mult = 1;
-                    }
-                }
-                const uint32_t inc = dev::warp_incl_scan(mult, lane);
-                const unsigned long long key_hi =
-                    (unsigned long long)(tile0 + (long long)(v >> kOffShift)) << 32;
-                for (uint32_t k = 0; k < mult; ++k) {
-                    const uint32_t r = (code & kGrp) ? __ldg(a.grp_ids + lo + k) : code;
-                    const unsigned long long gi = B + run + (inc - mult) + k;
-                    if (gi < (unsigned long long)a.occ_cap) a.occ[gi] = key_hi | r;
-                }
-                run += __shfl_sync(kFull, inc, 31);
-            }
-        }
-        if (lane == 0 && u == a.ntiles - 1) *a.n_occ = (long long)(B + outputs);
-        return true;
-    };
-
-    if (sch.cur >= 0) {
-        if (lane == 0) stage_issue(a, sch.cur * K, buf, bar, BUF);
+    if (gwarp < a.nsub) {
+        if (lane == 0) stage_issue(a, gwarp, buf, bar, BUF);
         inflight = true;
     }
 
-    for (long long t = sch.cur; t >= 0 && !failed; t = sch.next_of(t)) {
-        const long long tn = sch.next_of(t);
-        uint32_t e_base = 0;           // entries of this tile written so far
-        unsigned long long o_sum = 0;  // outputs of this tile (with multiplicity)
-        bool grp_tile = false;
-        SE *slot = slots + (long long)cur_slot * slot_len;
-
-        for (int sub = 0; sub < K; ++sub) {
-            const long long stile = t * K + sub;  // warp tile index
-            if (stile >= a.nsub) break;
-            const bool got = __all_sync(kFull, dev::mbar_wait_bounded(bar, phase));
-            if (!got) {
-                if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutTma);
-                inflight = false;  // the copy never completed; nothing to wait for
-                failed = true;
-                break;
-            }
-            inflight = false;
-            phase ^= 1u;
-            const long long tile0 = stile * kWarpTile;
-            const int got_bytes = stage_bytes(a, stile, BUF);
-            if (got_bytes < BUF) {  // tail of the text, or an unaligned text
-                for (int b = got_bytes + lane; b < BUF; b += 32) {
-                    const long long g = tile0 + b;
-                    buf[b] = g < a.n ? a.text[g] : uint8_t(a.pad);
-                }
-                __syncwarp();
-            }
-            uint4 tv[NV];
-            {
-                const uint4 *bv = reinterpret_cast<const uint4 *>(buf + lane * kChunk);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) tv[v] = bv[v];
-            }
-            dev::fence_proxy_async_smem();
-            __syncwarp();
-            const long long snext =
-                (sub + 1 < K && stile + 1 < a.nsub) ? stile + 1 : (tn >= 0 ? tn * K : -1);
-            if (snext >= 0) {
-                if (lane == 0) stage_issue(a, snext, buf, bar, BUF);
-                inflight = true;
-            }
-
-            // ---- walk: branch-free recording of match steps ----------------
-            const long long g0 = tile0 + (long long)lane * kChunk;
-            int steps = kChunk + m - 1;
-            if (!DNA) {
-                const long long left = a.n - g0;
-                steps = left <= 0 ? 0 : (left < steps ? int(left) : steps);
-            }
-            uint32_t hw[HW];
-#pragma unroll
-            for (int j = 0; j < HW; ++j) hw[j] = 0u;
-            uint32_t kslot = 0;
-            // pool slot `cap` absorbs the stores of an overflowing lane
-            auto rec = [&](int step, uint32_t idx, uint32_t e) {
-                const uint32_t h = e & 1u;
-                pl[kslot * 32] = E(idx - a.mid_base);
-                kslot = min(kslot + h, cap);
-                hw[step >> 5] |= h << (step & 31);
-            };
-            if (DNA) walk_dna<NV>(tv, steps, a.lut, tab, rec);
-            else walk_gen<NV>(tv, steps, a.lw, s_cls, tab, rec);
-            uint32_t nh = 0;
-#pragma unroll
-            for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
-            const bool ovf = nh > cap;
-
-            // ---- resolve: match entry -> terminal -> pattern code -----------
-            uint32_t cnt = 0;
-            bool grp = false;
-            if (!ovf) {
-                for (uint32_t k0 = 0; k0 < nh; k0 += 4) {
-                    uint32_t c4[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        c4[j] = ids.terminal(k0 + j < nh ? uint32_t(pl[(k0 + j) * 32]) : 0u);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (k0 + j < nh) {
-                            const uint32_t code = ids.code(c4[j]);
-                            count_terminal(c4[j]);
-                            grp |= (code & kGrp) != 0;
-                            cnt += mult_of(code);
-                            pl[(k0 + j) * 32] = E(code);
-                        }
-                    }
-                }
-            } else {
-                walk_slow(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
-                          [&](int, uint32_t idx) {
-                              const uint32_t c = ids.terminal(idx - a.mid_base);
-                              const uint32_t code = ids.code(c);
-                              count_terminal(c);
-                              grp |= (code & kGrp) != 0;
-                              cnt += mult_of(code);
-                          });
-            }
-
-            if (!a.list) {
-                my_total += cnt;
-                continue;
-            }
-
-            // ---- entries of this warp tile -> scratch slot, in text order ---
-            const uint32_t e_incl = dev::warp_incl_scan(nh, lane);
-            const uint32_t e_excl = e_incl - nh;
-            const uint32_t e_tot = __shfl_sync(kFull, e_incl, 31);
-            unsigned long long o_tot = cnt;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) o_tot += __shfl_xor_sync(kFull, o_tot, o);
-            grp_tile |= __any_sync(kFull, grp);
-            SE *dst = slot + e_base;
-            // start offset (in the tile) of a match whose last byte is `step`
-            const uint32_t off0 = uint32_t(sub * kWarpTile + lane * kChunk - (m - 1));
-            if (!__any_sync(kFull, ovf)) {
-                StepBits<HW> it;
-#pragma unroll
-                for (int j = 0; j < HW; ++j) it.w[j] = hw[j];
-                it.base = 0;
-                uint32_t k = 0, my = e_excl;
-                for (uint32_t w0 = 0; w0 < e_tot; w0 += S) {
-                    const uint32_t wend = min(w0 + S, e_tot);
-                    const uint32_t lim = min(wend, e_incl);  // this lane's entries in the window
-                    while (my < lim) {
-                        const int stp = it.next();
-                        if (stp < 0) dev::set_status(a.ws, dev::kErrInternal);
-                        sstage[my - w0] = ((SE)(off0 + uint32_t(stp)) << kOffShift) | (SE)pl[k * 32];
-                        ++k;
-                        ++my;
-                    }
-                    __syncwarp();
-                    for (uint32_t qq = w0 + lane; qq < wend; qq += 32) dst[qq] = sstage[qq - w0];
-                    __syncwarp();
-                }
-            } else {
-                // a lane overflowed its pool: every lane writes its entries directly
-                uint32_t j = e_excl;
-                if (!ovf) {
-                    StepBits<HW> it;
-#pragma unroll
-                    for (int jj = 0; jj < HW; ++jj) it.w[jj] = hw[jj];
-                    it.base = 0;
-                    for (uint32_t k = 0; k < nh; ++k) {
-                        const int stp = it.next();
-                        if (stp < 0) dev::set_status(a.ws, dev::kErrInternal);
-                        dst[j++] = ((SE)(off0 + uint32_t(stp)) << kOffShift) | (SE)pl[k * 32];
-                    }
-                } else {
-                    walk_slow(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
-                              [&](int step, uint32_t idx) {
-                                  const uint32_t code = ids.code(ids.terminal(idx - a.mid_base));
-                                  dst[j++] = ((SE)(off0 + uint32_t(step)) << kOffShift) | (SE)code;
-                              });
-                }
-                __syncwarp();
-            }
-            e_base += e_tot;
-            o_sum += o_tot;
-        }
-        if (failed || !a.list) continue;
-
-        dev::publish_tile(a.lb, t, o_sum, lane);
-        // ---- output of the previous tile, whose predecessors are done -------
-        if (prev >= 0 && !emit_deferred(prev, prev_entries, prev_outputs, prev_group, prev_slot)) {
-            if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutLookback);
-            failed = true;
+    for (long long st = gwarp; st < a.nsub && !failed; st += G) {
+        const bool got = __all_sync(kFull, dev::mbar_wait_bounded(bar, phase));
+        if (!got) {
+            if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutTma);
+            failed = true;  // the copy stays in flight: waited for below
             break;
         }
-        prev = t;
-        prev_entries = e_base;
-        prev_outputs = o_sum;
-        prev_group = grp_tile;
-        prev_slot = cur_slot;
-        cur_slot ^= 1u;
-    }
-    if (!failed && prev >= 0 &&
-        !emit_deferred(prev, prev_entries, prev_outputs, prev_group, prev_slot)) {
-        if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutLookback);
+        inflight = false;
+        phase ^= 1u;
+        const long long tile0 = st * kWarpTile;
+        const int got_bytes = stage_bytes(a, st, BUF);
+        if (got_bytes < BUF) {  // tail of the text, or an unaligned text
+            for (int b = got_bytes + lane; b < BUF; b += 32) {
+                const long long g = tile0 + b;
+                buf[b] = g < a.n ? a.text[g] : uint8_t(a.pad);
+            }
+            __syncwarp();
+        }
+        uint4 tv[NV];
+        {
+            const uint4 *bv = reinterpret_cast<const uint4 *>(buf + lane * kChunk);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) tv[v] = bv[v];
+        }
+        dev::fence_proxy_async_smem();
+        __syncwarp();
+        if (st + G < a.nsub) {
+            if (lane == 0) stage_issue(a, st + G, buf, bar, BUF);
+            inflight = true;
+        }
+
+        // ---- walk: branch-free recording of match steps --------------------
+        const long long g0 = tile0 + (long long)lane * kChunk;
+        int steps = kChunk + m - 1;
+        if (!DNA) {
+            const long long left = a.n - g0;
+            steps = left <= 0 ? 0 : (left < steps ? int(left) : steps);
+        }
+        uint32_t hw[HW];
+#pragma unroll
+        for (int j = 0; j < HW; ++j) hw[j] = 0u;
+        uint32_t kslot = 0;
+        // pool slot `cap` absorbs the stores of an overflowing lane
+        auto rec = [&](int step, uint32_t idx, uint32_t e) {
+            const uint32_t h = e & 1u;
+            pl[kslot * 32] = E(idx - a.mid_base);
+            kslot = min(kslot + h, cap);
+            hw[step >> 5] |= h << (step & 31);
+        };
+        if (DNA) walk_dna<NV>(tv, steps, a.lut, tab, rec);
+        else walk_gen<NV>(tv, steps, a.lw, s_cls, tab, rec);
+        uint32_t nh = 0;  // exact even when the pool overflowed
+#pragma unroll
+        for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
+        const bool ovf = nh > cap;
+
+        // ---- resolve: match entry -> terminal -> pattern code ---------------
+        uint32_t cnt = 0;
+        if (!ovf) {
+            for (uint32_t k0 = 0; k0 < nh; k0 += 4) {
+                uint32_t c4[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    c4[j] = ids.terminal(k0 + j < nh ? uint32_t(pl[(k0 + j) * 32]) : 0u);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (k0 + j < nh) {
+                        const uint32_t code = ids.code(c4[j]);
+                        count_terminal(c4[j]);
+                        cnt += mult_of(code);
+                        pl[(k0 + j) * 32] = E(code);
+                    }
+                }
+            }
+        } else {
+            walk_slow(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
+                      [&](int, uint32_t idx) {
+                          const uint32_t c = ids.terminal(idx - a.mid_base);
+                          count_terminal(c);
+                          cnt += mult_of(ids.code(c));
+                      });
+        }
+
+        if (!a.list) {
+            my_total += cnt;
+            continue;
+        }
+
+        // ---- this tile's matches -> its slot, in text order -----------------
+        const uint32_t e_incl = dev::warp_incl_scan(nh, lane);
+        const uint32_t e_excl = e_incl - nh;
+        uint32_t o_tot = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) o_tot += __shfl_xor_sync(kFull, o_tot, o);
+        SE *dst = slots + st * kWarpTile + e_excl;
+        // start offset (in the tile) of a match whose last byte is `step`
+        const uint32_t off0 = uint32_t(lane * kChunk - (m - 1));
+        if (!ovf) {
+            StepBits<HW> it;
+#pragma unroll
+            for (int j = 0; j < HW; ++j) it.w[j] = hw[j];
+            it.base = 0;
+            for (uint32_t k = 0; k < nh; ++k) {
+                const int stp = it.next();
+                if (stp < 0) dev::set_status(a.ws, dev::kErrInternal);
+                dst[k] = ((SE)(off0 + uint32_t(stp)) << kOffShift) | (SE)pl[k * 32];
+            }
+        } else {
+            uint32_t k = 0;
+            walk_slow(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
+                      [&](int step, uint32_t idx) {
+                          const uint32_t code = ids.code(ids.terminal(idx - a.mid_base));
+                          if (k < nh) dst[k] = ((SE)(off0 + uint32_t(step)) << kOffShift) | (SE)code;
+                          ++k;
+                      });
+        }
+        if (lane == 31) {
+            a.tile_ent[st] = e_incl;
+            a.tile_out[st] = o_tot;
+        }
     }
 
-    // a prefetch issued before an error exit: wait for it (bounded) so no
-    // copy is still writing this CTA's shared memory when it exits
+    // a copy still in flight after an error exit: wait for it (bounded) so
+    // it is not still writing this CTA's shared memory when the CTA exits
     if (inflight) (void)dev::mbar_wait_bounded(bar, phase);
 
     if (!a.list) {
@@ -485,6 +375,151 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
                     a.counts[a.grp_ids[j]] = (long long)v;
             } else {
                 a.counts[code] = (long long)v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// List mode, step 2: exclusive prefix of the tiles' output counts (one CTA;
+// each round loads 8 counts per thread with two 16-byte loads, the next
+// round's loads issued before this round's scan), and the total.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads, 1)
+tile_offsets_kernel(const uint32_t *__restrict__ tile_out, unsigned long long *__restrict__ tile_base,
+                    long long nsub, long long *n_occ)
+{
+    __shared__ unsigned long long s_warp[kScanThreads / 32];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr long long kPer = 8, kRound = kScanThreads * kPer;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    auto load8 = [&](long long r0, uint32_t (&v)[kPer]) {
+        const long long i0 = r0 + tid * kPer;
+        if (i0 + kPer <= nsub && ((reinterpret_cast<uintptr_t>(tile_out + i0) & 15) == 0)) {
+            const uint4 x = *reinterpret_cast<const uint4 *>(tile_out + i0);
+            const uint4 y = *reinterpret_cast<const uint4 *>(tile_out + i0 + 4);
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+            v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) v[q] = i0 + q < nsub ? tile_out[i0 + q] : 0u;
+        }
+    };
+    uint32_t cur[kPer], nxt[kPer];
+    load8(0, cur);
+    for (long long r0 = 0; r0 < nsub; r0 += kRound) {
+        if (r0 + kRound < nsub) load8(r0 + kRound, nxt);
+        unsigned long long mine = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) mine += cur[q];
+        unsigned long long inc = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += u;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long u = __shfl_up_sync(kFull, w, o);
+                if (lane >= o) w += u;
+            }
+            s_warp[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        unsigned long long run = s_carry + (warp ? s_warp[warp - 1] : 0ull) + inc - mine;
+        const long long i0 = r0 + tid * kPer;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            if (i0 + q < nsub) tile_base[i0 + q] = run;
+            run += cur[q];
+        }
+        __syncthreads();
+        if (tid == kScanThreads - 1) s_carry = run;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) cur[q] = nxt[q];
+    }
+    if (tid == 0) *n_occ = (long long)s_carry;
+}
+
+// ---------------------------------------------------------------------------
+// List mode, step 3: slots -> sorted keys ((i << 32) | r). One warp per tile,
+// U slot entries per lane in flight; a chunk with a group of equal patterns
+// takes a running prefix over the entries' multiplicities.
+// ---------------------------------------------------------------------------
+template <typename SE, int kOffShift, uint32_t kGrp>
+__global__ void __launch_bounds__(512)
+expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_ent,
+              const unsigned long long *__restrict__ tile_base, long long nsub,
+              const uint32_t *__restrict__ grp_off, const uint32_t *__restrict__ grp_ids,
+              unsigned long long *__restrict__ occ, long long occ_cap)
+{
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const long long G = (long long)gridDim.x * (blockDim.x >> 5);
+    const unsigned long long cap = (unsigned long long)occ_cap;
+    for (long long st = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); st < nsub; st += G) {
+        const uint32_t ent = min(tile_ent[st], uint32_t(kWarpTile));
+        unsigned long long run = tile_base[st];
+        const SE *src = slots + st * kWarpTile;
+        const long long tile0 = st * kWarpTile;
+        for (uint32_t j0 = 0; j0 < ent; j0 += 32 * U) {
+            SE v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = j0 + u * 32 + lane;
+                v[u] = j < ent ? __ldcs(src + j) : (SE)0;
+            }
+            bool any_grp = false;
+#pragma unroll
+            for (int u = 0; u < U; ++u) any_grp |= (uint32_t(v[u] & (((SE)1 << kOffShift) - 1)) & kGrp) != 0;
+            if (!__any_sync(kFull, any_grp)) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const uint32_t j = j0 + u * 32 + lane;
+                    const unsigned long long gi = run + (j - j0);
+                    if (j < ent && gi < cap)
+                        occ[gi] = ((unsigned long long)(tile0 + (long long)(v[u] >> kOffShift)) << 32) |
+                                  uint32_t(v[u] & (((SE)1 << kOffShift) - 1));
+                }
+                run += min(ent - j0, uint32_t(32 * U));
+                continue;
+            }
+            uint32_t lo[U], mult[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t j = j0 + u * 32 + lane;
+                const uint32_t code = uint32_t(v[u] & (((SE)1 << kOffShift) - 1));
+                lo[u] = code;
+                mult[u] = j < ent ? 1u : 0u;
+                if (j < ent && (code & kGrp)) {
+                    const uint32_t g = code & ~kGrp;
+                    lo[u] = __ldg(grp_off + g);
+                    mult[u] = __ldg(grp_off + g + 1) - lo[u];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t code = uint32_t(v[u] & (((SE)1 << kOffShift) - 1));
+                const uint32_t inc = dev::warp_incl_scan(mult[u], lane);
+                const unsigned long long key_hi =
+                    (unsigned long long)(tile0 + (long long)(v[u] >> kOffShift)) << 32;
+                const unsigned long long gb = run + (inc - mult[u]);
+                if (!(code & kGrp)) {
+                    if (mult[u] && gb < cap) occ[gb] = key_hi | code;
+                } else {
+                    for (uint32_t k = 0; k < mult[u]; ++k)
+                        if (gb + k < cap) occ[gb + k] = key_hi | __ldg(grp_ids + lo[u] + k);
+                }
+                run += __shfl_sync(kFull, inc, 31);
             }
         }
     }
@@ -527,7 +562,7 @@ int hv_slot(int hv) { return hv == 1 ? 0 : hv == 2 ? 1 : 2; }
 
 struct Layout {
     long long smem_entries;
-    int warps, hist, ids, stage;
+    int warps, hist, ids;
 };
 
 long long ac_smem_bytes(const AcTables &t, int eb, const Layout &L, int hv, int pool_cap)
@@ -536,7 +571,7 @@ long long ac_smem_bytes(const AcTables &t, int eb, const Layout &L, int hv, int 
     const int nterms = int(t.canon.size());
     return r16(L.smem_entries * eb) + (L.ids ? ac_ids_bytes(nwords, nterms, eb) : 0) +
            (L.hist ? r16((long long)nterms * 4) : 0) + (t.dna ? 0 : 256) +
-           (long long)L.warps * ac_warp_bytes(hv, pool_cap, eb, L.stage);
+           (long long)L.warps * ac_warp_bytes(hv, pool_cap, eb);
 }
 
 }  // namespace
@@ -561,7 +596,7 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
                need * dev.ctas_per_sm + 1024LL * dev.ctas_per_sm <= (long long)dp.smem_per_sm;
     };
 
-    Layout best{0, 0, 0, 0, 0};
+    Layout best{0, 0, 0, 0};
     bool chosen = false;
     if ((place == PM_PLACE_AUTO || place == PM_PLACE_SMEM) &&
         (opt.smem_table_bytes <= 0 || entries * eb <= opt.smem_table_bytes)) {
@@ -570,14 +605,11 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
         const int ids_hist[3][2] = {{1, 1}, {1, 0}, {0, 0}};
         for (int minw : {12, 4}) {
             for (int o = 0; o < 3 && !chosen; ++o) {
-                for (int stage : {128, 64}) {
-                    const int hi = forced_warps ? forced_warps : 16;
-                    const int lo = forced_warps ? forced_warps : minw;
-                    for (int w = hi; w >= lo; --w) {
-                        Layout L{entries, w, ids_hist[o][1], ids_hist[o][0], stage};
-                        if (fits(L)) { best = L; chosen = true; break; }
-                    }
-                    if (chosen) break;
+                const int hi = forced_warps ? forced_warps : 16;
+                const int lo = forced_warps ? forced_warps : minw;
+                for (int w = hi; w >= lo; --w) {
+                    Layout L{entries, w, ids_hist[o][1], ids_hist[o][0]};
+                    if (fits(L)) { best = L; chosen = true; break; }
                 }
             }
             if (chosen) break;
@@ -588,7 +620,7 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     if (!chosen) {
         // hybrid / global: breadth-first prefix of rows in shared memory
         const int w = forced_warps ? forced_warps : 16;
-        Layout L{0, w, 0, 0, 128};
+        Layout L{0, w, 0, 0};
         const long long fixed = ac_smem_bytes(t, eb, L, hv, pool_cap);
         long long room = budget - fixed;
         if (dev.ctas_per_sm > 1)
@@ -605,7 +637,7 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     dev.warps = best.warps;
     dev.hist_smem = best.hist;
     dev.ids_smem = best.ids;
-    dev.stage_cap = best.stage;
+    dev.stage_cap = 0;
     dev.smem_entries = best.smem_entries;
     const bool hyb = dev.smem_entries < entries || !t.dna || eb == 4;
     int group;
@@ -615,41 +647,41 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     dev.variant = group * 3 + hv_slot(hv);
     dev.smem_bytes = ac_smem_bytes(t, eb, best, hv, pool_cap);
     dev.max_warps = (long long)dp.sm_count * dev.ctas_per_sm * dev.warps;
-    dev.ksub = 8;
     return PM_OK;
 }
 
-int ac_ksub_for(const DevAc &dv, int64_t n)
-{
-    const long long nsub = warp_tiles(n);
-    int k = dv.ksub < 1 ? 1 : dv.ksub;
-    while (k > 1 && (nsub + k - 1) / k < dv.max_warps) k >>= 1;
-    return k;
-}
+namespace {
 
-int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n, bool list,
-              int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
-              void *stream)
+int slot_entry_bytes(const AcTables &t) { return (t.dna ? t.entry_bytes : 4) == 2 ? 4 : 8; }
+
+// Enqueue a whole scan on `st` with workspace `d_ws` (laid out by ac_ws_layout).
+int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n, bool list,
+               int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
+               cudaStream_t st)
 {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     const long long nsub = warp_tiles(n);
-    const int K = ac_ksub_for(dv, n);
-    const long long ntiles = (nsub + K - 1) / K;
     const long long nterms = (long long)t.canon.size();
+    const int se = slot_entry_bytes(t);
+    const AcWsLayout L = ac_ws_layout(nsub, list, nterms, se);
     e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(d_ws, 0, size_t(zeroed_workspace_bytes(ntiles, list, nterms)), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ws, 0, size_t(L.zeroed), st);
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (n < t.m || nsub == 0) return PM_OK;
 
     const Variant &v = kVariants[dv.variant];
-    static int attr_bytes[sizeof(kVariants) / sizeof(kVariants[0])] = {};
-    if (attr_bytes[dv.variant] < dv.smem_bytes) {
-        e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
-        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-        attr_bytes[dv.variant] = int(dv.smem_bytes);
+    {
+        static std::mutex mu;
+        static int attr_bytes[64][sizeof(kVariants) / sizeof(kVariants[0])] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && attr_bytes[dev][dv.variant] < dv.smem_bytes) {
+            e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
+            if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+            attr_bytes[dev][dv.variant] = int(dv.smem_bytes);
+        }
     }
     DeviceProps dp;
     int rc = device_props(dp);
@@ -679,44 +711,68 @@ int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t
         for (uint32_t b = 0; b < 256; ++b)
             if (t.cls[b] == 0xFF) { a.pad = b; break; }
     }
-    a.ntiles = ntiles;
     a.nsub = nsub;
-    a.ksub = K;
     a.pool_cap = dv.pool_cap;
-    a.stage_cap = dv.stage_cap;
     a.list = list ? 1 : 0;
     a.hist_smem = dv.hist_smem;
     a.ids_smem = dv.ids_smem;
     a.d = int(t.d);
     a.counts = reinterpret_cast<long long *>(d_counts);
-    a.occ = reinterpret_cast<unsigned long long *>(d_occ);
-    a.occ_cap = list ? occ_cap : 0;
     a.n_occ = reinterpret_cast<long long *>(d_n_occ);
     char *w = static_cast<char *>(d_ws);
     a.ws = reinterpret_cast<dev::WsHeader *>(w);
     a.ccount = reinterpret_cast<unsigned long long *>(w + kWsHeader);
-    char *after = w + kWsHeader + r16(nterms * 8);
-    a.lb.tile_st = reinterpret_cast<unsigned long long *>(after);
-    a.lb.super_acc = reinterpret_cast<unsigned long long *>(after + ntiles * 8);
-    a.lb.super_pre = reinterpret_cast<unsigned long long *>(after + ntiles * 16);
-    a.lb.ntiles = ntiles;
-    a.scratch = after + r16(ntiles * 24);
+    a.tile_ent = reinterpret_cast<uint32_t *>(w + L.tile_ent);
+    a.tile_out = reinterpret_cast<uint32_t *>(w + L.tile_out);
+    a.slots = w + L.slots;
 
-    // the static tile schedule needs every CTA of the grid resident at once
     const int threads = dv.warps * 32;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, threads, size_t(dv.smem_bytes));
     if (e != cudaSuccess || per_sm < 1) { set_cuda_error(int(e)); return PM_ECUDA; }
     long long grid = (long long)dp.sm_count * std::min(per_sm, dv.ctas_per_sm);
-    const long long want = (ntiles + dv.warps - 1) / dv.warps;  // look-back tiles
+    const long long want = (nsub + dv.warps - 1) / dv.warps;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    if (grid * dv.warps > dv.max_warps) grid = dv.max_warps / dv.warps;
-    a.lb.super_tiles = dev::super_size_for(grid * dv.warps);
     v.fn<<<dim3(unsigned(grid)), dim3(unsigned(threads)), size_t(dv.smem_bytes), st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    if (!list) return PM_OK;
+
+    unsigned long long *tile_base = reinterpret_cast<unsigned long long *>(w + L.tile_base);
+    tile_offsets_kernel<<<1, kScanThreads, 0, st>>>(a.tile_out, tile_base, nsub, a.n_occ);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    long long grid3 = (long long)dp.sm_count * 4;
+    const long long want3 = (nsub + 15) / 16;
+    if (want3 < grid3) grid3 = want3;
+    unsigned long long *occ = reinterpret_cast<unsigned long long *>(d_occ);
+    const long long cap = d_occ ? occ_cap : 0;
+    if (se == 4)
+        expand_kernel<uint32_t, 16, 0x8000u><<<unsigned(grid3), 512, 0, st>>>(
+            static_cast<const uint32_t *>(a.slots), a.tile_ent, tile_base, nsub, dv.grp_off, dv.grp_ids, occ, cap);
+    else
+        expand_kernel<unsigned long long, 32, 0x80000000u><<<unsigned(grid3), 512, 0, st>>>(
+            static_cast<const unsigned long long *>(a.slots), a.tile_ent, tile_base, nsub, dv.grp_off,
+            dv.grp_ids, occ, cap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     return PM_OK;
+}
+
+}  // namespace
+
+int64_t ac_workspace_bytes(const AcTables &t, int64_t n, bool list)
+{
+    return ac_ws_layout(warp_tiles(n), list, (long long)t.canon.size(), slot_entry_bytes(t)).total;
+}
+
+int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n, bool list,
+              int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
+              void *stream)
+{
+    return ac_enqueue(t, dv, d_text, n, list, d_counts, d_occ, occ_cap, d_n_occ, d_ws,
+                      static_cast<cudaStream_t>(stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -726,15 +782,15 @@ int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t
 // application that owns the GPU allocator (a plugin must not add cudaMalloc
 // calls it cannot account for), or a latency-bound loop that reserved all
 // of its memory up front and must not call cudaMalloc, which can block on
-// the device and fail once memory is fragmented. For them the scratch of
+// the device and fail once memory is fragmented. For them the workspace of
 // the Aho-Corasick scan lives in one fixed array inside the library. The
 // array is reserved on every GPU that loads the library and stays reserved
 // until the process exits. Every call uses the same array and it keeps the
 // last call's contents, so the launcher clears what must start at zero, and
 // two calls whose work overlaps on the GPU (different streams, or host
-// threads) race on it. To keep the array modest the scan runs with one warp
-// tile per look-back tile (the per-warp output slots then need only two
-// warp tiles of entries).
+// threads) race on it. List mode needs 4 or 8 bytes of the array per text
+// byte (one slot entry per start position), so list-mode texts are limited
+// to a few MiB.
 // ---------------------------------------------------------------------------
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -777,98 +833,12 @@ int ac_launch_noalloc(const AcTables &t, const DevAc &dv, const uint8_t *d_text,
                       bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
                       int64_t *d_n_occ, void *stream)
 {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    const int K = 1;
-    const long long nsub = warp_tiles(n);
-    const long long ntiles = nsub;
-    const long long nterms = (long long)t.canon.size();
-    const Variant &v = kVariants[dv.variant];
-    DeviceProps dp;
-    int rc = device_props(dp);
-    if (rc) return rc;
-
-    // the grid the launch will use decides the size of the output slots
-    static int attr_bytes_na[sizeof(kVariants) / sizeof(kVariants[0])] = {};
-    if (attr_bytes_na[dv.variant] < dv.smem_bytes) {
-        e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
-        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-        attr_bytes_na[dv.variant] = int(dv.smem_bytes);
-    }
-    const int threads = dv.warps * 32;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, threads, size_t(dv.smem_bytes));
-    if (e != cudaSuccess || per_sm < 1) { set_cuda_error(int(e)); return PM_ECUDA; }
-    long long grid = (long long)dp.sm_count * std::min(per_sm, dv.ctas_per_sm);
-    const long long want = (ntiles + dv.warps - 1) / dv.warps;
-    if (want < grid) grid = want;
-    if (grid < 1) grid = 1;
-    if (grid * dv.warps > dv.max_warps) grid = dv.max_warps / dv.warps;
-
-    const long long se = sizeof(uint32_t) * ((t.dna ? t.entry_bytes : 4) == 2 ? 1 : 2);
-    const long long zeroed = zeroed_workspace_bytes(ntiles, list, nterms);
-    const long long slots = list ? r16(grid * dv.warps * 2LL * K * kWarpTile * se) : 0;
-    if (zeroed + slots > (long long)kNoAllocScratchBytes) return PM_ETOOBIG;
-
+    if (ac_workspace_bytes(t, n, list) > (int64_t)kNoAllocScratchBytes) return PM_ETOOBIG;
     void *ws = nullptr;
-    rc = noalloc_scratch(&ws);
+    const int rc = noalloc_scratch(&ws);
     if (rc) return rc;
-    e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ws, 0, size_t(zeroed), st);
-    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-    if (n < t.m || nsub == 0) return PM_OK;
-
-    AcArgs a;
-    a.text = d_text;
-    a.n = n;
-    a.aligned = (reinterpret_cast<uintptr_t>(d_text) & 15) == 0;
-    a.table_g = dv.table;
-    a.smem_entries = int(dv.smem_entries);
-    a.mid_base = uint32_t(t.d0_row << t.lw);
-    a.mask_g = dv.flag_mask;
-    a.rank_g = dv.flag_rank;
-    a.canon_g = dv.canon;
-    a.nwords = int(t.flag_mask.size());
-    a.nterms = int(nterms);
-    a.grp_off = dv.grp_off;
-    a.grp_ids = dv.grp_ids;
-    a.cls_g = dv.cls;
-    a.m = t.m;
-    a.lw = t.lw;
-    a.lut = t.lut;
-    a.pad = 0;
-    if (t.dna) {
-        for (uint32_t b = 0; b < 256; ++b)
-            if (t.cls[b] == 0xFF) { a.pad = b; break; }
-    }
-    a.ntiles = ntiles;
-    a.nsub = nsub;
-    a.ksub = K;
-    a.pool_cap = dv.pool_cap;
-    a.stage_cap = dv.stage_cap;
-    a.list = list ? 1 : 0;
-    a.hist_smem = dv.hist_smem;
-    a.ids_smem = dv.ids_smem;
-    a.d = int(t.d);
-    a.counts = reinterpret_cast<long long *>(d_counts);
-    a.occ = reinterpret_cast<unsigned long long *>(d_occ);
-    a.occ_cap = list ? occ_cap : 0;
-    a.n_occ = reinterpret_cast<long long *>(d_n_occ);
-    char *w = static_cast<char *>(ws);
-    a.ws = reinterpret_cast<dev::WsHeader *>(w);
-    a.ccount = reinterpret_cast<unsigned long long *>(w + kWsHeader);
-    char *after = w + kWsHeader + r16(nterms * 8);
-    a.lb.tile_st = reinterpret_cast<unsigned long long *>(after);
-    a.lb.super_acc = reinterpret_cast<unsigned long long *>(after + ntiles * 8);
-    a.lb.super_pre = reinterpret_cast<unsigned long long *>(after + ntiles * 16);
-    a.lb.ntiles = ntiles;
-    a.lb.super_tiles = dev::super_size_for(grid * dv.warps);
-    a.scratch = after + r16(ntiles * 24);
-    v.fn<<<dim3(unsigned(grid)), dim3(unsigned(threads)), size_t(dv.smem_bytes), st>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-    return PM_OK;
+    return ac_enqueue(t, dv, d_text, n, list, d_counts, d_occ, occ_cap, d_n_occ, ws,
+                      static_cast<cudaStream_t>(stream));
 }
 
 }  // namespace pm

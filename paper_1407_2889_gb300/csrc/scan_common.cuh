@@ -178,6 +178,7 @@ __device__ __forceinline__ bool wait_sum2(const unsigned long long *p, long long
             return true;
         }
         if (clock64() - t0 > kSpinLimit) return false;
+        __nanosleep(200);  // leave the issue slots to warps that have work
     }
 }
 
@@ -251,6 +252,7 @@ __device__ __forceinline__ unsigned long long tile_base(const LookbackRefs &L, l
         else { nh = kFull; nl = kFull; }
         if ((rl & nl) != nl || (rh & nh) != nh) {
             if (clock64() - t0 > kSpinLimit) { ok = false; return 0; }
+            __nanosleep(200);
             continue;
         }
         unsigned long long x = (((nl >> lane) & 1u) ? vl : 0ull) + (((nh >> lane) & 1u) ? vh : 0ull);

@@ -45,7 +45,7 @@ def _noalloc(s, d_text, n, flags, d, cap):
 
 @pytest.mark.parametrize("flags", [0, pm.PM_COUNTS_ONLY])
 def test_noalloc_matches_regular_scan_on_two_calls(flags):
-    T = synth.est_text(24 << 20, 31)
+    T = synth.est_text(12 << 20, 31)  # list mode: 4 bytes of the array per text byte
     P = synth.mixed_patterns(T, 3000, 8, 31)
     P = np.concatenate([P, P[:20]])  # duplicates exercise the group path
     d = P.shape[0]
