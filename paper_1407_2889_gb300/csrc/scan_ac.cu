@@ -71,15 +71,27 @@ struct AcArgs {
     unsigned long long *ccount;   // per-terminal totals
     uint32_t *tile_ent;           // list: entries (one per matching position) per warp tile
     uint32_t *tile_out;           // list: outputs (keys, groups expanded) per warp tile
+    unsigned long long *seg_sum;  // list: outputs per segment of seg_tiles warp tiles
+    long long seg_tiles;
     void *slots;                  // list: kWarpTile entries per warp tile
 };
 
 // Workspace carve-up shared by the launchers and the workspace size:
-//   [header][per-terminal counters] -- zeroed by every scan
-//   list mode: [tile_ent u32][tile_out u32][tile offsets u64][slots]
+//   [header][per-terminal counters][list: segment sums u64] -- zeroed by every scan
+//   list mode: [tile_ent u32][tile_out u32][slots]
 struct AcWsLayout {
-    long long zeroed, tile_ent, tile_out, tile_base, slots, total;
+    long long seg_sum, zeroed, tile_ent, tile_out, slots, total;
 };
+
+// Output segments of the list mode: one expand CTA per segment of
+// consecutive warp tiles (two CTAs per SM, at least 64 tiles each).
+inline long long ac_segments(long long nsub, int sm_count)
+{
+    long long b = 2LL * (sm_count > 0 ? sm_count : 1);
+    const long long most = (nsub + 63) / 64;
+    if (most < b) b = most;
+    return b < 1 ? 1 : b;
+}
 
 __host__ __device__ constexpr long long r16(long long x) { return (x + 15) & ~15LL; }
 
@@ -89,14 +101,14 @@ __host__ __device__ inline long long ac_warp_bytes(int hv, int pool_cap, int eb)
     return 16 + r16(kWarpTile + 16 * hv) + r16((long long)(pool_cap + 1) * 32 * eb);
 }
 
-AcWsLayout ac_ws_layout(long long nsub, bool list, long long nterms, int slot_entry_bytes)
+AcWsLayout ac_ws_layout(long long nsub, bool list, long long nterms, int slot_entry_bytes, int sm_count)
 {
     AcWsLayout L;
-    L.zeroed = kWsHeader + r16(nterms * 8);
+    L.seg_sum = kWsHeader + r16(nterms * 8);
+    L.zeroed = L.seg_sum + (list ? r16(ac_segments(nsub, sm_count) * 8) : 0);
     L.tile_ent = L.zeroed;
     L.tile_out = L.tile_ent + (list ? r16(nsub * 4) : 0);
-    L.tile_base = L.tile_out + (list ? r16(nsub * 4) : 0);
-    L.slots = L.tile_base + (list ? r16(nsub * 8) : 0);
+    L.slots = L.tile_out + (list ? r16(nsub * 4) : 0);
     L.total = L.slots + (list ? r16(nsub * kWarpTile * (long long)slot_entry_bytes) : 0);
     return L;
 }
@@ -336,6 +348,7 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
         if (lane == 31) {
             a.tile_ent[st] = e_incl;
             a.tile_out[st] = o_tot;
+            if (o_tot) atomicAdd(&a.seg_sum[st / a.seg_tiles], (unsigned long long)o_tot);
         }
     }
 
@@ -381,146 +394,138 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// List mode, step 2: exclusive prefix of the tiles' output counts (one CTA;
-// each round loads 8 counts per thread with two 16-byte loads, the next
-// round's loads issued before this round's scan), and the total.
+// List mode, step 2: slots -> sorted keys ((i << 32) | r). CTA b owns the
+// warp tiles of segment b: its output base is the sum of the earlier
+// segments' totals (added up by the scan), each tile's offset inside the
+// segment comes from a block scan of the tiles' totals kept in shared
+// memory, and its warps then copy one tile at a time with 16-byte slot
+// loads. A chunk that names a group of equal patterns takes a running prefix
+// over the entries' multiplicities instead. The last CTA writes the total.
 // ---------------------------------------------------------------------------
-constexpr int kScanThreads = 1024;
+constexpr int kExpandThreads = 512;
 
-__global__ void __launch_bounds__(kScanThreads, 1)
-tile_offsets_kernel(const uint32_t *__restrict__ tile_out, unsigned long long *__restrict__ tile_base,
-                    long long nsub, long long *n_occ)
-{
-    __shared__ unsigned long long s_warp[kScanThreads / 32];
-    __shared__ unsigned long long s_carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr long long kPer = 8, kRound = kScanThreads * kPer;
-    if (tid == 0) s_carry = 0;
-    __syncthreads();
-    auto load8 = [&](long long r0, uint32_t (&v)[kPer]) {
-        const long long i0 = r0 + tid * kPer;
-        if (i0 + kPer <= nsub && ((reinterpret_cast<uintptr_t>(tile_out + i0) & 15) == 0)) {
-            const uint4 x = *reinterpret_cast<const uint4 *>(tile_out + i0);
-            const uint4 y = *reinterpret_cast<const uint4 *>(tile_out + i0 + 4);
-            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-            v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
-        } else {
-#pragma unroll
-            for (int q = 0; q < kPer; ++q) v[q] = i0 + q < nsub ? tile_out[i0 + q] : 0u;
-        }
-    };
-    uint32_t cur[kPer], nxt[kPer];
-    load8(0, cur);
-    for (long long r0 = 0; r0 < nsub; r0 += kRound) {
-        if (r0 + kRound < nsub) load8(r0 + kRound, nxt);
-        unsigned long long mine = 0;
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) mine += cur[q];
-        unsigned long long inc = mine;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long u = __shfl_up_sync(kFull, inc, o);
-            if (lane >= o) inc += u;
-        }
-        if (lane == 31) s_warp[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            unsigned long long w = s_warp[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long u = __shfl_up_sync(kFull, w, o);
-                if (lane >= o) w += u;
-            }
-            s_warp[lane] = w;  // inclusive over warps
-        }
-        __syncthreads();
-        unsigned long long run = s_carry + (warp ? s_warp[warp - 1] : 0ull) + inc - mine;
-        const long long i0 = r0 + tid * kPer;
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            if (i0 + q < nsub) tile_base[i0 + q] = run;
-            run += cur[q];
-        }
-        __syncthreads();
-        if (tid == kScanThreads - 1) s_carry = run;
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) cur[q] = nxt[q];
-    }
-    if (tid == 0) *n_occ = (long long)s_carry;
-}
-
-// ---------------------------------------------------------------------------
-// List mode, step 3: slots -> sorted keys ((i << 32) | r). One warp per tile,
-// U slot entries per lane in flight; a chunk with a group of equal patterns
-// takes a running prefix over the entries' multiplicities.
-// ---------------------------------------------------------------------------
 template <typename SE, int kOffShift, uint32_t kGrp>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(kExpandThreads)
 expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_ent,
-              const unsigned long long *__restrict__ tile_base, long long nsub,
+              const uint32_t *__restrict__ tile_out, const unsigned long long *__restrict__ seg_sum,
+              long long nseg, long long seg_tiles, long long nsub,
               const uint32_t *__restrict__ grp_off, const uint32_t *__restrict__ grp_ids,
-              unsigned long long *__restrict__ occ, long long occ_cap)
+              unsigned long long *__restrict__ occ, long long occ_cap, long long *n_occ)
 {
-    constexpr int U = 8;
-    const int lane = threadIdx.x & 31;
-    const long long G = (long long)gridDim.x * (blockDim.x >> 5);
+    extern __shared__ __align__(16) unsigned char esm[];
+    unsigned long long *s_off = reinterpret_cast<unsigned long long *>(esm);  // seg_tiles + 1
+    uint32_t *s_ent = reinterpret_cast<uint32_t *>(s_off + seg_tiles + 1);
+    __shared__ unsigned long long s_red[kExpandThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kExpandThreads / 32;
+    const long long seg = blockIdx.x;
+    const long long t0 = seg * seg_tiles;
+    const long long nt = min(seg_tiles, nsub - t0);
+    if (nt <= 0) return;
+
+    // base of the segment: sum of the earlier segments
+    unsigned long long part = 0;
+    for (long long q = tid; q < seg; q += kExpandThreads) part += seg_sum[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+    if (lane == 0) s_red[warp] = part;
+    __syncthreads();
+    unsigned long long seg_base = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) seg_base += s_red[w];
+    __syncthreads();
+
+    // per-tile offsets: each thread scans a run of consecutive tiles
+    const long long per = (nt + kExpandThreads - 1) / kExpandThreads;
+    const long long r0 = min(nt, (long long)tid * per), r1 = min(nt, r0 + per);
+    unsigned long long mine = 0;
+    for (long long q = r0; q < r1; ++q) {
+        const uint32_t o = tile_out[t0 + q];
+        s_ent[q] = min(tile_ent[t0 + q], uint32_t(kWarpTile));
+        s_off[q] = o;  // the tile's own total, replaced by its offset below
+        mine += o;
+    }
+    unsigned long long inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) s_red[warp] = inc;
+    __syncthreads();
+    unsigned long long run = seg_base + inc - mine;
+    for (int w = 0; w < warp; ++w) run += s_red[w];
+    for (long long q = r0; q < r1; ++q) {
+        const unsigned long long o = s_off[q];
+        s_off[q] = run;
+        run += o;
+    }
+    if (tid == kExpandThreads - 1 && t0 + nt == nsub) *n_occ = (long long)run;  // the last tile's CTA
+    __syncthreads();
+
     const unsigned long long cap = (unsigned long long)occ_cap;
-    for (long long st = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); st < nsub; st += G) {
-        const uint32_t ent = min(tile_ent[st], uint32_t(kWarpTile));
-        unsigned long long run = tile_base[st];
+    constexpr int PER = 4;  // slot entries per lane per chunk (one or two 16-byte loads)
+    for (long long q = warp; q < nt; q += NW) {
+        const long long st = t0 + q;
+        const uint32_t ent = s_ent[q];
+        unsigned long long base = s_off[q];
         const SE *src = slots + st * kWarpTile;
-        const long long tile0 = st * kWarpTile;
-        for (uint32_t j0 = 0; j0 < ent; j0 += 32 * U) {
-            SE v[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t j = j0 + u * 32 + lane;
-                v[u] = j < ent ? __ldcs(src + j) : (SE)0;
+        const uint32_t tile0 = uint32_t(st * kWarpTile);
+        for (uint32_t j0 = 0; j0 < ent; j0 += 32 * PER) {
+            const uint32_t j = j0 + lane * PER;
+            SE v[PER];
+            if (sizeof(SE) == 4) {
+                const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src + j));
+                v[0] = (SE)x.x; v[1] = (SE)x.y; v[2] = (SE)x.z; v[3] = (SE)x.w;
+            } else {
+                const ulonglong2 x = __ldcs(reinterpret_cast<const ulonglong2 *>(src + j));
+                const ulonglong2 y = __ldcs(reinterpret_cast<const ulonglong2 *>(src + j) + 1);
+                v[0] = (SE)x.x; v[1] = (SE)x.y; v[2] = (SE)y.x; v[3] = (SE)y.y;
             }
-            bool any_grp = false;
+            bool grp = false;
 #pragma unroll
-            for (int u = 0; u < U; ++u) any_grp |= (uint32_t(v[u] & (((SE)1 << kOffShift) - 1)) & kGrp) != 0;
-            if (!__any_sync(kFull, any_grp)) {
+            for (int u = 0; u < PER; ++u)
+                grp |= j + u < ent && (uint32_t(v[u] & (((SE)1 << kOffShift) - 1)) & kGrp);
+            if (!__any_sync(kFull, grp)) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const uint32_t j = j0 + u * 32 + lane;
-                    const unsigned long long gi = run + (j - j0);
-                    if (j < ent && gi < cap)
-                        occ[gi] = ((unsigned long long)(tile0 + (long long)(v[u] >> kOffShift)) << 32) |
+                for (int u = 0; u < PER; ++u) {
+                    const unsigned long long gi = base + (j - j0) + u;
+                    if (j + u < ent && gi < cap)
+                        occ[gi] = ((unsigned long long)(tile0 + uint32_t(v[u] >> kOffShift)) << 32) |
                                   uint32_t(v[u] & (((SE)1 << kOffShift) - 1));
                 }
-                run += min(ent - j0, uint32_t(32 * U));
+                base += min(ent - j0, uint32_t(32 * PER));
                 continue;
             }
-            uint32_t lo[U], mult[U];
+            // multiplicities, then the lane's keys in entry order
+            uint32_t lo[PER], mult[PER], msum = 0;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t j = j0 + u * 32 + lane;
+            for (int u = 0; u < PER; ++u) {
                 const uint32_t code = uint32_t(v[u] & (((SE)1 << kOffShift) - 1));
                 lo[u] = code;
-                mult[u] = j < ent ? 1u : 0u;
-                if (j < ent && (code & kGrp)) {
+                mult[u] = j + u < ent ? 1u : 0u;
+                if (j + u < ent && (code & kGrp)) {
                     const uint32_t g = code & ~kGrp;
                     lo[u] = __ldg(grp_off + g);
                     mult[u] = __ldg(grp_off + g + 1) - lo[u];
                 }
+                msum += mult[u];
             }
+            const uint32_t incl = dev::warp_incl_scan(msum, lane);
+            unsigned long long gb = base + (incl - msum);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < PER; ++u) {
                 const uint32_t code = uint32_t(v[u] & (((SE)1 << kOffShift) - 1));
-                const uint32_t inc = dev::warp_incl_scan(mult[u], lane);
-                const unsigned long long key_hi =
-                    (unsigned long long)(tile0 + (long long)(v[u] >> kOffShift)) << 32;
-                const unsigned long long gb = run + (inc - mult[u]);
+                const unsigned long long key_hi = (unsigned long long)(tile0 + uint32_t(v[u] >> kOffShift)) << 32;
                 if (!(code & kGrp)) {
                     if (mult[u] && gb < cap) occ[gb] = key_hi | code;
                 } else {
                     for (uint32_t k = 0; k < mult[u]; ++k)
                         if (gb + k < cap) occ[gb + k] = key_hi | __ldg(grp_ids + lo[u] + k);
                 }
-                run += __shfl_sync(kFull, inc, 31);
+                gb += mult[u];
             }
+            base += __shfl_sync(kFull, incl, 31);
         }
     }
 }
@@ -663,7 +668,13 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     const long long nsub = warp_tiles(n);
     const long long nterms = (long long)t.canon.size();
     const int se = slot_entry_bytes(t);
-    const AcWsLayout L = ac_ws_layout(nsub, list, nterms, se);
+    DeviceProps dp;
+    int rc = device_props(dp);
+    if (rc) return rc;
+    const AcWsLayout L = ac_ws_layout(nsub, list, nterms, se, dp.sm_count);
+    // every segment non-empty: at most ac_segments() of them
+    const long long seg_tiles = (nsub + ac_segments(nsub, dp.sm_count) - 1) / ac_segments(nsub, dp.sm_count);
+    const long long nseg = (nsub + seg_tiles - 1) / seg_tiles;
     e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ws, 0, size_t(L.zeroed), st);
@@ -683,10 +694,6 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
             attr_bytes[dev][dv.variant] = int(dv.smem_bytes);
         }
     }
-    DeviceProps dp;
-    int rc = device_props(dp);
-    if (rc) return rc;
-
     AcArgs a;
     a.text = d_text;
     a.n = n;
@@ -724,6 +731,8 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     a.ccount = reinterpret_cast<unsigned long long *>(w + kWsHeader);
     a.tile_ent = reinterpret_cast<uint32_t *>(w + L.tile_ent);
     a.tile_out = reinterpret_cast<uint32_t *>(w + L.tile_out);
+    a.seg_sum = reinterpret_cast<unsigned long long *>(w + L.seg_sum);
+    a.seg_tiles = seg_tiles;
     a.slots = w + L.slots;
 
     const int threads = dv.warps * 32;
@@ -739,22 +748,26 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (!list) return PM_OK;
 
-    unsigned long long *tile_base = reinterpret_cast<unsigned long long *>(w + L.tile_base);
-    tile_offsets_kernel<<<1, kScanThreads, 0, st>>>(a.tile_out, tile_base, nsub, a.n_occ);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-    long long grid3 = (long long)dp.sm_count * 4;
-    const long long want3 = (nsub + 15) / 16;
-    if (want3 < grid3) grid3 = want3;
+    // shared memory of the expand kernel: 12 bytes per tile of a segment
+    // (above 48 KB only for texts of more than about 3 GB)
     unsigned long long *occ = reinterpret_cast<unsigned long long *>(d_occ);
     const long long cap = d_occ ? occ_cap : 0;
+    const size_t esmem = size_t((seg_tiles + 1) * 8 + seg_tiles * 4);
+    if (esmem > (size_t(48) << 10)) {
+        e = se == 4 ? cudaFuncSetAttribute(expand_kernel<uint32_t, 16, 0x8000u>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem))
+                    : cudaFuncSetAttribute(expand_kernel<unsigned long long, 32, 0x80000000u>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem));
+        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    }
     if (se == 4)
-        expand_kernel<uint32_t, 16, 0x8000u><<<unsigned(grid3), 512, 0, st>>>(
-            static_cast<const uint32_t *>(a.slots), a.tile_ent, tile_base, nsub, dv.grp_off, dv.grp_ids, occ, cap);
+        expand_kernel<uint32_t, 16, 0x8000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
+            static_cast<const uint32_t *>(a.slots), a.tile_ent, a.tile_out, a.seg_sum, nseg, seg_tiles, nsub,
+            dv.grp_off, dv.grp_ids, occ, cap, a.n_occ);
     else
-        expand_kernel<unsigned long long, 32, 0x80000000u><<<unsigned(grid3), 512, 0, st>>>(
-            static_cast<const unsigned long long *>(a.slots), a.tile_ent, tile_base, nsub, dv.grp_off,
-            dv.grp_ids, occ, cap);
+        expand_kernel<unsigned long long, 32, 0x80000000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
+            static_cast<const unsigned long long *>(a.slots), a.tile_ent, a.tile_out, a.seg_sum, nseg,
+            seg_tiles, nsub, dv.grp_off, dv.grp_ids, occ, cap, a.n_occ);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     return PM_OK;
@@ -764,7 +777,9 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
 
 int64_t ac_workspace_bytes(const AcTables &t, int64_t n, bool list)
 {
-    return ac_ws_layout(warp_tiles(n), list, (long long)t.canon.size(), slot_entry_bytes(t)).total;
+    DeviceProps dp;
+    if (device_props(dp)) dp.sm_count = 1024;  // an upper bound on the segments
+    return ac_ws_layout(warp_tiles(n), list, (long long)t.canon.size(), slot_entry_bytes(t), dp.sm_count).total;
 }
 
 int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n, bool list,
