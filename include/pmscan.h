@@ -91,7 +91,8 @@ typedef struct pm_set_info {
     int32_t n_classes;        /* character classes (alphabet size of P) */
     int32_t row_width;        /* table columns per row */
     int32_t entry_bytes;      /* 2 or 4 */
-    int32_t dna_mode;         /* 1: ACGT-like alphabet decoded arithmetically */
+    int32_t dna_mode;         /* 1: ACGT-like alphabet decoded arithmetically
+                                 (Wu-Manber: exact 2-bit-code tables in use) */
     int32_t placement;        /* resolved PM_PLACE_* */
     int64_t smem_rows;        /* rows resident in shared memory */
     int64_t table_bytes;      /* bytes of the transition table */

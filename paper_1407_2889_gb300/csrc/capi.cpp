@@ -105,6 +105,7 @@ void release_device(pm_set *s)
     void *ptrs[] = {s->dac.table, s->dac.flag_mask, s->dac.flag_rank, s->dac.canon,
                     s->dac.grp_off, s->dac.grp_ids, s->dac.cls,
                     s->dwm.shift, s->dwm.hoff, s->dwm.hids, s->dwm.hpfx, s->dwm.pats,
+                    s->dwm.shift2, s->dwm.dir, s->dwm.ccode, s->dwm.cr,
                     s->c_text, s->c_ws, s->c_out, s->c_counts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -161,6 +162,12 @@ int upload_wm(pm_set *s)
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.hids), t.hids.data(), t.hids.size() * 4, tot);
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.hpfx), t.hpfx.data(), t.hpfx.size() * 2, tot);
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.pats), t.pats.data(), t.pats.size(), tot);
+    if (!rc && t.dna) {
+        rc = upload(reinterpret_cast<void **>(&d.shift2), t.shift2.data(), t.shift2.size(), tot);
+        if (!rc) rc = upload(reinterpret_cast<void **>(&d.dir), t.dir.data(), t.dir.size() * 4, tot);
+        if (!rc) rc = upload(reinterpret_cast<void **>(&d.ccode), t.ccode.data(), t.ccode.size() * 8, tot);
+        if (!rc) rc = upload(reinterpret_cast<void **>(&d.cr), t.cr.data(), t.cr.size() * 4, tot);
+    }
     return rc;
 }
 
@@ -362,6 +369,7 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
         info->Bp = t.Bp;
         info->shift_entries = int64_t(t.shift.size());
         info->n_zero_shift = t.n_zero_shift;
+        info->dna_mode = t.dna ? 1 : 0;  // exact 2-bit-code tables in use
     }
     return PM_OK;
 }

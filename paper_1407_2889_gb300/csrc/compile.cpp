@@ -224,6 +224,74 @@ static inline uint32_t wm_hash(const uint8_t *s, int len)
     return h;
 }
 
+// The exact-code tables of an ACGT-like set (see WmTables): the same SHIFT
+// rule (the minimum over every block occurrence of m - q, initialised to
+// m - B + 1) and the same HASH / PREFIX partition as Algorithm 4, with the
+// 2-bit codes of the B-character block and of the B'-character prefix as h1
+// and h2. A run holds the patterns of one (block, prefix) pair sorted by
+// (packed pattern, r), so equal patterns are adjacent in ascending r.
+static void build_wm_packed(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp,
+                            WmTables &t)
+{
+    t.dna = false;
+    if (m > 32 || B + Bp > 6) return;
+    bool present[256] = {};
+    for (int64_t k = 0; k < d * int64_t(m); ++k) present[P[k]] = true;
+    int byte_of_code[4] = {-1, -1, -1, -1};
+    for (int b = 0; b < 256; ++b) {
+        if (!present[b]) continue;
+        const int c = int(dna_code(uint32_t(b)));
+        if (byte_of_code[c] >= 0) return;  // two bytes share a code: not ACGT-like
+        byte_of_code[c] = b;
+    }
+    uint32_t lut = 0;
+    for (int c = 0; c < 4; ++c) {
+        int b = byte_of_code[c];
+        if (b < 0)  // a byte whose own code is not c never passes the check
+            for (b = 0; b < 256; ++b)
+                if (int(dna_code(uint32_t(b))) != c) break;
+        lut |= uint32_t(b) << (8 * c);
+    }
+    const size_t NB = size_t(1) << (2 * B), NK = size_t(1) << (2 * (B + Bp));
+    std::vector<uint8_t> shift2(NB, uint8_t(m - B + 1));
+    std::vector<uint64_t> code(static_cast<size_t>(d));
+    std::vector<uint32_t> key(static_cast<size_t>(d));
+    std::vector<uint32_t> fill(NK + 1, 0);
+    for (int64_t r = 0; r < d; ++r) {
+        const uint8_t *p = P + r * int64_t(m);
+        uint64_t c = 0;
+        for (int32_t j = 0; j < m; ++j) c = (c << 2) | dna_code(p[j]);
+        code[size_t(r)] = c;
+        for (int32_t q = m; q >= B; --q) {
+            uint32_t h = 0;
+            for (int32_t j = q - B; j < q; ++j) h = (h << 2) | dna_code(p[j]);
+            if (uint8_t(m - q) < shift2[h]) shift2[h] = uint8_t(m - q);
+        }
+        const uint32_t blk = uint32_t(c & (NB - 1));
+        const uint32_t pre = uint32_t(c >> (2 * (m - Bp)));
+        key[size_t(r)] = (blk << (2 * Bp)) | pre;
+        fill[key[size_t(r)] + 1]++;
+    }
+    for (size_t k = 0; k < NK; ++k) fill[k + 1] += fill[k];
+    std::vector<uint32_t> order(static_cast<size_t>(d));
+    for (int64_t r = 0; r < d; ++r) order[size_t(r)] = uint32_t(r);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        if (key[x] != key[y]) return key[x] < key[y];
+        if (code[x] != code[y]) return code[x] < code[y];
+        return x < y;
+    });
+    t.shift2 = std::move(shift2);
+    t.dir = std::move(fill);
+    t.ccode.resize(static_cast<size_t>(d));
+    t.cr.resize(static_cast<size_t>(d));
+    for (int64_t k = 0; k < d; ++k) {
+        t.ccode[size_t(k)] = code[order[size_t(k)]];
+        t.cr[size_t(k)] = order[size_t(k)];
+    }
+    t.lut = lut;
+    t.dna = true;
+}
+
 int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTables &t)
 {
     if (!P || d < 1 || m < 1 || B < 1 || B > m || Bp < 1) return PM_EINVAL;
@@ -264,6 +332,7 @@ int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTa
         t.pats.assign(P, P + d * int64_t(m));
         t.n_zero_shift = 0;
         for (size_t h = 0; h < H; ++h) t.n_zero_shift += t.shift[h] == 0;
+        build_wm_packed(P, d, m, B, Bp, t);
         return PM_OK;
     } catch (const std::bad_alloc &) {
         t = WmTables();
@@ -311,9 +380,40 @@ void host_walk_ac(const AcTables &t, const uint8_t *T, int64_t n,
     }
 }
 
+// Algorithm 5 over the exact-code tables, as the device runs it (one text,
+// one walk): the same window ends, SHIFT values and verification result.
+static void host_walk_wm_packed(const WmTables &t, const uint8_t *T, int64_t n,
+                                std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
+{
+    const int32_t m = t.m, B = t.B, Bp = t.Bp;
+    const uint64_t mask = m >= 32 ? ~uint64_t(0) : ((uint64_t(1) << (2 * m)) - 1);
+    const uint32_t bmask = (1u << (2 * B)) - 1u;
+    uint64_t code = 0;
+    int64_t bad = -1, skip = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t b = T[i], c = dna_code(b);
+        if (((t.lut >> (8 * c)) & 0xFFu) != b) bad = i;
+        code = ((code << 2) | c) & mask;
+        if (i < m - 1) continue;
+        if (skip > 0) { --skip; continue; }
+        const uint32_t sh = bad > i - B ? uint32_t(m - B + 1) : t.shift2[uint32_t(code) & bmask];
+        if (sh > 0) { skip = int64_t(sh) - 1; continue; }
+        if (bad > i - m) continue;
+        const uint32_t key = ((uint32_t(code) & bmask) << (2 * Bp)) | uint32_t(code >> (2 * (m - Bp)));
+        for (uint32_t k = t.dir[key]; k < t.dir[key + 1]; ++k)
+            if (t.ccode[k] == code) emit_entry(occ, counts, i - m + 1, t.cr[k]);
+    }
+}
+
 void host_walk_wm(const WmTables &t, const uint8_t *T, int64_t n,
                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
 {
+    if (t.dna) {
+        counts.assign(size_t(t.d), 0);
+        occ.clear();
+        host_walk_wm_packed(t, T, n, occ, counts);
+        return;
+    }
     counts.assign(size_t(t.d), 0);
     occ.clear();
     const int32_t m = t.m, B = t.B, Bp = t.Bp;

@@ -71,6 +71,18 @@ struct WmTables {
     std::vector<uint16_t> hpfx;    // PREFIX of hids[k]
     std::vector<uint8_t> pats;     // d*m pattern bytes
     int64_t n_zero_shift = 0;
+    // ACGT-like sets with m <= 32 (and B + B' <= 6) also get tables over the
+    // exact 2-bit codes of the blocks (an injective h1 / h2): SHIFT over the
+    // 4^B blocks, a directory of the candidate runs of each (block, prefix)
+    // pair, and each candidate's whole pattern packed 2 bits per character
+    // (first character in the high bits), so that verification is one
+    // comparison with the window's packed code.
+    bool dna = false;
+    uint32_t lut = 0;              // byte of code c in byte c
+    std::vector<uint8_t> shift2;   // 4^B
+    std::vector<uint32_t> dir;     // 4^(B+B') + 1 run offsets, key = block << 2B' | prefix
+    std::vector<uint64_t> ccode;   // d packed patterns, run order (code, then r)
+    std::vector<uint32_t> cr;      // their pattern ids
 };
 
 int build_ac(const uint8_t *P, int64_t d, int32_t m, AcTables &out);
@@ -118,8 +130,12 @@ struct DevWm {
     uint32_t *hids = nullptr;
     uint16_t *hpfx = nullptr;
     uint8_t *pats = nullptr;
+    uint8_t *shift2 = nullptr;      // exact-code tables (WmTables::dna)
+    uint32_t *dir = nullptr;
+    uint64_t *ccode = nullptr;
+    uint32_t *cr = nullptr;
     int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0, stage_cap = 0;
-    int32_t shift_smem = 0, hist_smem = 0;
+    int32_t shift_smem = 0, hist_smem = 0, dna = 0;
     int64_t smem_bytes = 0;
 };
 

@@ -38,6 +38,13 @@ struct WmArgs {
     long long *n_occ;
     dev::WsHeader *ws;
     dev::LookbackRefs lb;
+    // exact-code tables (ACGT-like sets, m <= 32)
+    uint32_t lut;
+    const uint8_t *shift2_g;
+    const uint32_t *dir_g;
+    const unsigned long long *ccode;
+    const uint32_t *cr;
+    int nkey;                     // 4^(B + B')
 };
 
 __host__ __device__ constexpr int r16w(long long x) { return int((x + 15) & ~15LL); }
@@ -108,7 +115,49 @@ __device__ __forceinline__ void wm_walk(const WmArgs &a, const uint8_t *s_shift,
     }
 }
 
-template <bool SHIFT_SMEM>
+// Algorithm 5 over one lane's windows on an ACGT-like set, with h1 and h2
+// the exact 2-bit codes of the block and the prefix. The lane keeps the
+// packed code of its last m characters (first character in the high bits)
+// and the offset of its last byte outside the alphabet; the window ends
+// Algorithm 5 visits are the same as with the byte hash (a block holding a
+// byte outside the alphabet occurs in no pattern: SHIFT m-B+1), and each
+// candidate of the (block, prefix) run is verified by one comparison of
+// packed codes (equal patterns are adjacent in the run, in ascending r).
+template <class F>
+__device__ __forceinline__ void wm_walk_dna(const WmArgs &a, const uint8_t *s_shift2,
+                                            const uint32_t *s_dir, const uint8_t *w, int lim, F &&hit)
+{
+    const int m = a.m, B = a.B, Bp = a.Bp;
+    const unsigned long long mask = m >= 32 ? ~0ull : ((1ull << (2 * m)) - 1ull);
+    const uint32_t bmask = (1u << (2 * B)) - 1u;
+    const int pshift = 2 * (m - Bp);
+    unsigned long long code = 0;
+    int bad = -1;   // last offset holding a byte outside the alphabet
+    int skip = 0;   // window ends still to pass over after a SHIFT > 1
+    for (int i = 0; i < lim; ++i) {
+        const uint32_t b = w[i];
+        const uint32_t c = ((b >> 1) ^ (b >> 2)) & 3u;
+        if (((a.lut >> (8 * c)) & 0xFFu) != b) bad = i;
+        code = ((code << 2) | c) & mask;
+        if (i < m - 1) continue;
+        if (skip > 0) { --skip; continue; }
+        const uint32_t sh = bad > i - B ? uint32_t(m - B + 1) : uint32_t(s_shift2[uint32_t(code) & bmask]);
+        if (sh > 0) { skip = int(sh) - 1; continue; }
+        if (bad > i - m) continue;  // the window holds a byte no pattern has
+        const uint32_t key = ((uint32_t(code) & bmask) << (2 * Bp)) | uint32_t(code >> pshift);
+        const uint32_t lo = s_dir[key], hi = s_dir[key + 1];
+        for (uint32_t k0 = lo; k0 < hi; k0 += 4) {
+            unsigned long long cc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cc[u] = k0 + u < hi ? __ldg(a.ccode + k0 + u) : ~code;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (cc[u] == code) hit(i - (m - 1), __ldg(a.cr + k0 + u));
+        }
+    }
+}
+
+template <bool SHIFT_SMEM, bool DNA>
 __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -116,7 +165,11 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
     const int warp = threadIdx.x >> 5;
     unsigned char *p = smem;
     uint8_t *s_shift = p;
-    p += SHIFT_SMEM ? r16w(1LL << a.hbits) : 0;
+    p += (SHIFT_SMEM && !DNA) ? r16w(1LL << a.hbits) : 0;
+    uint8_t *s_shift2 = p;
+    p += DNA ? r16w(1LL << (2 * a.B)) : 0;
+    uint32_t *s_dir = reinterpret_cast<uint32_t *>(p);
+    p += DNA ? r16w((long long)(a.nkey + 1) * 4) : 0;
     uint32_t *s_hist = a.hist_smem ? reinterpret_cast<uint32_t *>(p) : nullptr;
     p += a.hist_smem ? r16w((long long)a.d * 4) : 0;
     p += warp * wm_warp_bytes(a.m, a.pool_cap, a.stage_cap);
@@ -126,7 +179,10 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
     unsigned long long *stage = reinterpret_cast<unsigned long long *>(
         reinterpret_cast<unsigned char *>(pool) + r16w((long long)a.pool_cap * 32 * 4));
 
-    if (SHIFT_SMEM) {
+    if (DNA) {
+        for (int i = threadIdx.x; i < (1 << (2 * a.B)); i += blockDim.x) s_shift2[i] = a.shift2_g[i];
+        for (int i = threadIdx.x; i <= a.nkey; i += blockDim.x) s_dir[i] = a.dir_g[i];
+    } else if (SHIFT_SMEM) {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.shift_g);
         uint4 *dst = reinterpret_cast<uint4 *>(s_shift);
         const int nvec = int(((1LL << a.hbits) + 15) / 16);
@@ -174,10 +230,12 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
         }
         const uint8_t *w = buf + cs;
         uint32_t nh = 0;
-        wm_walk<SHIFT_SMEM>(a, s_shift, w, lim, [&](int off, uint32_t r) {
+        auto rec = [&](int off, uint32_t r) {
             if (nh < cap) pl[nh * 32] = (uint32_t(off) << 24) | r;
             ++nh;
-        });
+        };
+        if (DNA) wm_walk_dna(a, s_shift2, s_dir, w, lim, rec);
+        else wm_walk<SHIFT_SMEM>(a, s_shift, w, lim, rec);
         const bool ovf = nh > cap;
         const uint32_t cnt = nh;
 
@@ -186,9 +244,9 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
                 for (uint32_t k = 0; k < nh; ++k)
                     dev::count_pattern(pl[k * 32] & 0xFFFFFFu, s_hist, a.counts);
             } else {
-                wm_walk<SHIFT_SMEM>(a, s_shift, w, lim, [&](int, uint32_t r) {
-                    dev::count_pattern(r, s_hist, a.counts);
-                });
+                auto cnt_hit = [&](int, uint32_t r) { dev::count_pattern(r, s_hist, a.counts); };
+                if (DNA) wm_walk_dna(a, s_shift2, s_dir, w, lim, cnt_hit);
+                else wm_walk<SHIFT_SMEM>(a, s_shift, w, lim, cnt_hit);
             }
             my_total += cnt;
         } else {
@@ -237,8 +295,9 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
                         put(g0 + (v >> 24), v & 0xFFFFFFu);
                     }
                 } else {
-                    wm_walk<SHIFT_SMEM>(a, s_shift, w, lim,
-                                        [&](int off, uint32_t r) { put(g0 + off, r); });
+                    auto put_hit = [&](int off, uint32_t r) { put(g0 + off, r); };
+                    if (DNA) wm_walk_dna(a, s_shift2, s_dir, w, lim, put_hit);
+                    else wm_walk<SHIFT_SMEM>(a, s_shift, w, lim, put_hit);
                 }
             }
         }
@@ -265,10 +324,11 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
 }
 
 long long wm_smem_bytes(int hbits, bool shift_smem, int hist, int d, int warps, int m,
-                        int pool_cap, int stage_cap)
+                        int pool_cap, int stage_cap, bool dna, int B, int nkey)
 {
-    return (shift_smem ? r16w(1LL << hbits) : 0) + (hist ? r16w((long long)d * 4) : 0) +
-           (long long)warps * wm_warp_bytes(m, pool_cap, stage_cap);
+    const long long tables = dna ? r16w(1LL << (2 * B)) + r16w((long long)(nkey + 1) * 4)
+                                 : (shift_smem ? r16w(1LL << hbits) : 0);
+    return tables + (hist ? r16w((long long)d * 4) : 0) + (long long)warps * wm_warp_bytes(m, pool_cap, stage_cap);
 }
 
 }  // namespace
@@ -287,12 +347,13 @@ int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevW
         for (int wi = 0; wi < 3; ++wi) {
             const int w = forced ? forced : choices[wi];
             const int hist = pass == 0 ? 1 : 0;
-            const long long need = wm_smem_bytes(hbits, shift_smem, hist, int(t.d), w, t.m,
-                                                 dev.pool_cap, dev.stage_cap);
+            const long long need = wm_smem_bytes(hbits, shift_smem, hist, int(t.d), w, t.m, dev.pool_cap,
+                                                 dev.stage_cap, t.dna, t.B, 1 << (2 * (t.B + t.Bp)));
             if (need <= budget) {
                 dev.warps = w;
                 dev.hist_smem = hist;
                 dev.shift_smem = shift_smem;
+                dev.dna = t.dna ? 1 : 0;
                 dev.smem_bytes = need;
                 return PM_OK;
             }
@@ -317,9 +378,10 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     if (n < t.m || ntiles == 0) return PM_OK;
 
     typedef void (*K)(const WmArgs);
-    K fn = dv.shift_smem ? wm_scan_kernel<true> : wm_scan_kernel<false>;
-    static int attr_bytes[2] = {0, 0};
-    const int slot = dv.shift_smem ? 1 : 0;
+    K fn = dv.dna ? wm_scan_kernel<false, true>
+                  : (dv.shift_smem ? wm_scan_kernel<true, false> : wm_scan_kernel<false, false>);
+    static int attr_bytes[3] = {0, 0, 0};
+    const int slot = dv.dna ? 2 : (dv.shift_smem ? 1 : 0);
     if (attr_bytes[slot] < dv.smem_bytes) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
         if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
@@ -359,6 +421,12 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     a.lb.super_acc = reinterpret_cast<unsigned long long *>(w + kWsHeader + ntiles * 8);
     a.lb.super_pre = reinterpret_cast<unsigned long long *>(w + kWsHeader + ntiles * 16);
     a.lb.ntiles = ntiles;
+    a.lut = t.lut;
+    a.shift2_g = dv.shift2;
+    a.dir_g = dv.dir;
+    a.ccode = reinterpret_cast<const unsigned long long *>(dv.ccode);
+    a.cr = dv.cr;
+    a.nkey = t.dna ? (1 << (2 * (t.B + t.Bp))) : 0;
 
     // the static tile schedule needs every CTA of the grid resident at once
     int per_sm = 0;

@@ -153,6 +153,41 @@ def test_wm_tables_match_oracle(B):
         assert np.array_equal(occ, want_occ) and np.array_equal(cnt, want_cnt)
 
 
+@pytest.mark.parametrize("B", [1, 2, 3, 4])
+def test_wm_packed_tables_match_oracle(B):
+    """ACGT pattern sets (m <= 32) get exact-code WM tables; their host walk
+    over texts with bytes outside the alphabet equals the definition."""
+    rng = np.random.default_rng(200 + B)
+    A = np.frombuffer(b"ACGT", np.uint8)
+    checked = 0
+    for trial in range(40):
+        m = int(rng.integers(max(B, 1), 33))
+        d = int(rng.integers(1, 80))
+        n = int(rng.integers(0, 6000))
+        T = np.frombuffer(b"ACGTN\n", np.uint8)[rng.choice(6, n, p=[.24, .24, .24, .24, .02, .02])]
+        P = A[rng.integers(0, 4, (d, m))]
+        for r in range(d):
+            if n >= m and rng.random() < 0.6:
+                s0 = int(rng.integers(0, n - m + 1))
+                if all(x in b"ACGT" for x in T[s0:s0 + m].tobytes()):
+                    P[r] = T[s0:s0 + m]
+        if d > 2:
+            P[-1] = P[0]
+        P = np.ascontiguousarray(P)
+        Bp = 2 if B <= 4 else 1
+        h = pm.pm_wm_compile(P, B, {"host_only": 1, "wm_prefix_len": min(Bp, 6 - B)})
+        try:
+            info = pm.pm_set_get_info(h)
+            assert info["dna_mode"] == 1
+            occ, cnt = pm.pm_selfcheck_host_walk(h, T)
+        finally:
+            pm.pm_set_free(h)
+        want_occ, want_cnt = oracle.brute(T, P) if n * d <= 200000 else oracle.dictionary(T, P)
+        assert np.array_equal(occ, want_occ) and np.array_equal(cnt, want_cnt), (m, d, n)
+        checked += 1
+    assert checked == 40
+
+
 def test_table_sizes_of_est_sets():
     """Row counts of the EST-shaped sets decide shared-memory placement."""
     T = synth.est_text(1 << 22, 1)
