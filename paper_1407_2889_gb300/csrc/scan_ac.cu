@@ -327,14 +327,17 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
         // start offset (in the tile) of a match whose last byte is `step`
         const uint32_t off0 = uint32_t(lane * kChunk - (m - 1));
         if (!ovf) {
-            StepBits<HW> it;
+            // the lane's match steps in order, word by word of its step mask
+            uint32_t k = 0;
 #pragma unroll
-            for (int j = 0; j < HW; ++j) it.w[j] = hw[j];
-            it.base = 0;
-            for (uint32_t k = 0; k < nh; ++k) {
-                const int stp = it.next();
-                if (stp < 0) dev::set_status(a.ws, dev::kErrInternal);
-                dst[k] = ((SE)(off0 + uint32_t(stp)) << kOffShift) | (SE)pl[k * 32];
+            for (int j = 0; j < HW; ++j) {
+                uint32_t wj = hw[j];
+                while (wj) {
+                    const uint32_t b = uint32_t(__ffs(int(wj))) - 1u;
+                    wj &= wj - 1u;
+                    dst[k] = ((SE)(off0 + uint32_t(j * 32) + b) << kOffShift) | (SE)pl[k * 32];
+                    ++k;
+                }
             }
         } else {
             uint32_t k = 0;
@@ -464,68 +467,84 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
     __syncthreads();
 
     const unsigned long long cap = (unsigned long long)occ_cap;
-    constexpr int PER = 4;  // slot entries per lane per chunk (one or two 16-byte loads)
+    constexpr int PER = 4;   // slot entries per lane per chunk (one or two 16-byte loads)
+    constexpr int NCH = 4;   // chunks loaded together (512 entries)
+    constexpr uint32_t kMask = (uint32_t)((((SE)1) << kOffShift) - 1);
     for (long long q = warp; q < nt; q += NW) {
         const long long st = t0 + q;
         const uint32_t ent = s_ent[q];
         unsigned long long base = s_off[q];
         const SE *src = slots + st * kWarpTile;
         const uint32_t tile0 = uint32_t(st * kWarpTile);
-        for (uint32_t j0 = 0; j0 < ent; j0 += 32 * PER) {
-            const uint32_t j = j0 + lane * PER;
-            SE v[PER];
-            if (sizeof(SE) == 4) {
-                const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src + j));
-                v[0] = (SE)x.x; v[1] = (SE)x.y; v[2] = (SE)x.z; v[3] = (SE)x.w;
-            } else {
-                const ulonglong2 x = __ldcs(reinterpret_cast<const ulonglong2 *>(src + j));
-                const ulonglong2 y = __ldcs(reinterpret_cast<const ulonglong2 *>(src + j) + 1);
-                v[0] = (SE)x.x; v[1] = (SE)x.y; v[2] = (SE)y.x; v[3] = (SE)y.y;
-            }
-            bool grp = false;
+        for (uint32_t g0 = 0; g0 < ent; g0 += NCH * 32 * PER) {
+            SE v[NCH][PER];
 #pragma unroll
-            for (int u = 0; u < PER; ++u)
-                grp |= j + u < ent && (uint32_t(v[u] & (((SE)1 << kOffShift) - 1)) & kGrp);
-            if (!__any_sync(kFull, grp)) {
+            for (int ch = 0; ch < NCH; ++ch) {
+                const uint32_t j = g0 + ch * 32 * PER + lane * PER;
+                if (g0 + ch * 32 * PER < ent) {
+                    if (sizeof(SE) == 4) {
+                        const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src + j));
+                        v[ch][0] = (SE)x.x; v[ch][1] = (SE)x.y; v[ch][2] = (SE)x.z; v[ch][3] = (SE)x.w;
+                    } else {
+                        const ulonglong2 x = __ldcs(reinterpret_cast<const ulonglong2 *>(src + j));
+                        const ulonglong2 y = __ldcs(reinterpret_cast<const ulonglong2 *>(src + j) + 1);
+                        v[ch][0] = (SE)x.x; v[ch][1] = (SE)x.y; v[ch][2] = (SE)y.x; v[ch][3] = (SE)y.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int u = 0; u < PER; ++u) v[ch][u] = 0;
+                }
+            }
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
+                const uint32_t j0 = g0 + ch * 32 * PER;
+                if (j0 >= ent) break;
+                const uint32_t j = j0 + lane * PER;
+                bool grp = false;
+#pragma unroll
+                for (int u = 0; u < PER; ++u) grp |= j + u < ent && (uint32_t(v[ch][u] & kMask) & kGrp);
+                if (!__any_sync(kFull, grp)) {
+#pragma unroll
+                    for (int u = 0; u < PER; ++u) {
+                        const unsigned long long gi = base + (j - j0) + u;
+                        if (j + u < ent && gi < cap)
+                            occ[gi] = ((unsigned long long)(tile0 + uint32_t(v[ch][u] >> kOffShift)) << 32) |
+                                      uint32_t(v[ch][u] & kMask);
+                    }
+                    base += min(ent - j0, uint32_t(32 * PER));
+                    continue;
+                }
+                // multiplicities, then the lane's keys in entry order
+                uint32_t lo[PER], mult[PER], msum = 0;
 #pragma unroll
                 for (int u = 0; u < PER; ++u) {
-                    const unsigned long long gi = base + (j - j0) + u;
-                    if (j + u < ent && gi < cap)
-                        occ[gi] = ((unsigned long long)(tile0 + uint32_t(v[u] >> kOffShift)) << 32) |
-                                  uint32_t(v[u] & (((SE)1 << kOffShift) - 1));
+                    const uint32_t code = uint32_t(v[ch][u] & kMask);
+                    lo[u] = code;
+                    mult[u] = j + u < ent ? 1u : 0u;
+                    if (j + u < ent && (code & kGrp)) {
+                        const uint32_t g = code & ~kGrp;
+                        lo[u] = __ldg(grp_off + g);
+                        mult[u] = __ldg(grp_off + g + 1) - lo[u];
+                    }
+                    msum += mult[u];
                 }
-                base += min(ent - j0, uint32_t(32 * PER));
-                continue;
-            }
-            // multiplicities, then the lane's keys in entry order
-            uint32_t lo[PER], mult[PER], msum = 0;
+                const uint32_t incl = dev::warp_incl_scan(msum, lane);
+                unsigned long long gb = base + (incl - msum);
 #pragma unroll
-            for (int u = 0; u < PER; ++u) {
-                const uint32_t code = uint32_t(v[u] & (((SE)1 << kOffShift) - 1));
-                lo[u] = code;
-                mult[u] = j + u < ent ? 1u : 0u;
-                if (j + u < ent && (code & kGrp)) {
-                    const uint32_t g = code & ~kGrp;
-                    lo[u] = __ldg(grp_off + g);
-                    mult[u] = __ldg(grp_off + g + 1) - lo[u];
+                for (int u = 0; u < PER; ++u) {
+                    const uint32_t code = uint32_t(v[ch][u] & kMask);
+                    const unsigned long long key_hi =
+                        (unsigned long long)(tile0 + uint32_t(v[ch][u] >> kOffShift)) << 32;
+                    if (!(code & kGrp)) {
+                        if (mult[u] && gb < cap) occ[gb] = key_hi | code;
+                    } else {
+                        for (uint32_t k = 0; k < mult[u]; ++k)
+                            if (gb + k < cap) occ[gb + k] = key_hi | __ldg(grp_ids + lo[u] + k);
+                    }
+                    gb += mult[u];
                 }
-                msum += mult[u];
+                base += __shfl_sync(kFull, incl, 31);
             }
-            const uint32_t incl = dev::warp_incl_scan(msum, lane);
-            unsigned long long gb = base + (incl - msum);
-#pragma unroll
-            for (int u = 0; u < PER; ++u) {
-                const uint32_t code = uint32_t(v[u] & (((SE)1 << kOffShift) - 1));
-                const unsigned long long key_hi = (unsigned long long)(tile0 + uint32_t(v[u] >> kOffShift)) << 32;
-                if (!(code & kGrp)) {
-                    if (mult[u] && gb < cap) occ[gb] = key_hi | code;
-                } else {
-                    for (uint32_t k = 0; k < mult[u]; ++k)
-                        if (gb + k < cap) occ[gb + k] = key_hi | __ldg(grp_ids + lo[u] + k);
-                }
-                gb += mult[u];
-            }
-            base += __shfl_sync(kFull, incl, 31);
         }
     }
 }
