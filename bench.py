@@ -157,6 +157,7 @@ def parse():
                     help="length of the Poisson request stream of the serving run (0 skips it)")
     ap.add_argument("--only-serve", action="store_true",
                     help="run only the serving measurement and print it")
+    ap.add_argument("--no-tune", action="store_true", help="keep the planner's default launch plan")
     ap.add_argument("--mode", default="list", choices=["list", "counts"],
                     help="timed step: list mode (default) or counts only")
     ap.add_argument("--text-mib", type=int, default=0,
@@ -256,9 +257,13 @@ def main():
     n = T.size
     d = P.shape[0]
     s = pm.PatternSet.ac(P)
-    info = s.info()
     stream = torch.cuda.Stream()
     d_text = torch.from_numpy(T).cuda()
+    tuned = None
+    if not args.no_tune:  # the autotuner picks the launch plan (not timed)
+        params, tms = s.tune(d_text, counts_only=args.mode == "counts", reps=3)
+        tuned = {"ms_per_scan": tms, **{k: params[k] for k in ("placement", "warps_per_cta", "counters", "ids_place")}}
+    info = s.info()
     ws = torch.zeros(s.workspace_bytes(n), dtype=torch.uint8, device="cuda")
     counts = torch.zeros(d, dtype=torch.int64, device="cuda")
     nocc = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -319,13 +324,6 @@ def main():
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": "ac_scan_kernel<uint16_t,6,1,dna,smem> + tile_offsets_kernel + expand_kernel (list mode)"}
 
-    extras = {}
-    if rank == 0 and not args.no_extras:
-        extras = secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, torch, synth)
-        if args.batch_k > 0:
-            del occ
-            extras["batched"] = batched_comparison(args, T, d_text, pm, torch, synth)
-
     # end to end through the public API: pinned host text in, pinned host
     # counts and occurrence list out (pm_scan_to_host), copies inside the timing
     e2e = None
@@ -345,6 +343,15 @@ def main():
                "d2h_bytes_per_step": (8 * n_occ if args.mode == "list" else 0) + 8 * d + 8,
                "api": "pm_scan_to_host (pinned host text and results)"}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras = secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, torch, synth)
+        torch.cuda.empty_cache()
+        if args.batch_k > 0:
+            del occ
+            extras["batched"] = batched_comparison(args, T, d_text, pm, torch, synth)
+            torch.cuda.empty_cache()
+
     if rank == 0 and not args.no_extras and args.serve_seconds > 0:
         extras["serving"] = serving_run(args, pinned, pm, torch, synth)
 
@@ -363,7 +370,8 @@ def main():
                        "text_bytes": n, "d": d, "m": args.m, "algo": "AC", "mode": args.mode,
                        "n_occ": n_occ, "l2": "inputs larger than L2 (1 GiB text), no flush",
                        "parallelism": f"replicas x{world}",
-                       "table": {k: info[k] for k in ("n_rows", "entry_bytes", "placement", "smem_rows", "table_bytes")}},
+                       "table": {k: info[k] for k in ("n_rows", "entry_bytes", "placement", "smem_rows", "table_bytes")},
+                       "plan": tuned or "planner default"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * (3 if args.mode == "list" else 1), "clocks": clk, "extras": extras,
         }
@@ -403,6 +411,8 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
         for mm in synth.EST_M:
             _, Pq = synth.est_case(dd, mm, text=T)
             q = pm.PatternSet.ac(Pq)
+            if not args.no_tune:
+                q.tune(d_text, reps=2)
             cnt_q = torch.zeros(dd, dtype=torch.int64, device="cuda")
             ws = torch.zeros(q.workspace_bytes(n), dtype=torch.uint8, device="cuda")
             with torch.cuda.stream(stream):
@@ -426,7 +436,8 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
                                       "placement": inf["placement"], "rows": inf["n_rows"],
                                       "entry_bytes": inf["entry_bytes"]}
             q.close()
-            del buf
+            del buf, ws
+            torch.cuda.empty_cache()
     out["ac_list_sweep"] = sweep
     out["large_sets"] = large_sets(T, d_text, stream, nocc, pm, torch, synth)
     return out
@@ -483,6 +494,8 @@ def large_sets(T, d_text, stream, nocc, pm, torch, synth):
         entry["wm_b4_gbs"] = nw / (ev0.elapsed_time(ev1) / 1e3) / 1e9
         entry["wm_text_bytes"] = nw
         w.close()
+        del wsw, bw
+        torch.cuda.empty_cache()
         out[f"d{d}_m32"] = entry
     return out
 
@@ -616,6 +629,12 @@ def serving_run(args, pinned, pm, torch, synth):
     offs = (r[:, 2] * (T.size - lens)).astype(np.int64)
     which = np.minimum((r[:, 3] * nsets).astype(np.int64), nsets - 1)
     srv = pm.Server(budget_bytes=8 << 30, max_batch=256, max_inflight=3)
+    # warm-up (not measured): every set once at the largest request size, so
+    # kernels are loaded and per-slot workspaces have their final size
+    big = 16 << 20
+    for t in [srv.submit(q, pinned[j * big:(j + 1) * big]) for j, q in enumerate(sets)]:
+        srv.wait(t)
+    srv.reset_stats()
     tickets = [None] * k
     submitted = threading.Semaphore(0)
     results = {}
@@ -652,6 +671,9 @@ def serving_run(args, pinned, pm, torch, synth):
     # loop), so batches form while others run; sustained capacity
     ks = min(k, 3000)
     sat = pm.Server(budget_bytes=8 << 30, max_batch=256, max_inflight=3)
+    for t in [sat.submit(q, pinned[j * big:(j + 1) * big]) for j, q in enumerate(sets)]:
+        sat.wait(t)
+    sat.reset_stats()
     t0 = time.perf_counter()
     tk = [sat.submit(sets[which[j]], pinned[offs[j]:offs[j] + lens[j]]) for j in range(ks)]
     for t in tk:
@@ -677,7 +699,8 @@ def serving_run(args, pinned, pm, torch, synth):
                       "peak_inflight": ss["peak_inflight"], "dispatch_busy_s": ss["dispatch_busy_s"],
                       "complete_busy_s": ss["complete_busy_s"]},
         "workload": "Poisson 2000 req/s; text log-uniform 1 KiB-16 MiB slices of the pinned EST text (H2D and D2H "
-                    "inside the latency); 64 sets d log-uniform 100-1e5, m in {8,16,24,32}; list mode",
+                    "inside the latency); 64 sets d log-uniform 100-1e5, m in {8,16,24,32}; list mode; "
+                    "after a warm-up of one 16 MiB request per set",
     }
 
 

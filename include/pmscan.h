@@ -76,6 +76,11 @@ typedef struct pm_params {
     int32_t wm_prefix_len;    /* Wu-Manber B' (default 2, clamped to m) */
     int32_t host_only;        /* 1: build host tables only (no device upload);
                                  such a set can only be inspected, not scanned */
+    int32_t counters;         /* AC per-terminal counters: 0 auto, 1 32-bit in
+                                 shared memory, 2 16-bit in shared memory,
+                                 3 64-bit in device memory */
+    int32_t ids_place;        /* AC terminal-id structure: 0 auto, 1 shared
+                                 memory, 2 device memory (through L1/L2) */
 } pm_params;
 
 typedef struct pm_set pm_set; /* compiled pattern set; owns its device tables */
@@ -204,6 +209,21 @@ int pm_scan_device_noalloc(const pm_set *s, const uint8_t *d_text, int64_t n, ui
                            int64_t *d_counts, uint64_t *d_occ, int64_t occ_capacity,
                            int64_t *d_n_occ, void *stream);
 int64_t pm_noalloc_scratch_bytes(void);
+
+/*
+ * Autotuner for the plain Aho-Corasick scan (the paper's kernels fix their
+ * launch shape by hand; this picks it by measurement). Times `reps` scans of
+ * the device text (after one warm-up each) for every distinct launch plan
+ * the planner accepts over table placement (shared memory / hybrid prefix),
+ * warps per CTA (auto, 16, 12, 8), per-terminal counters (32-bit or 16-bit
+ * in shared memory, or device memory) and the terminal-id structure (shared
+ * or device memory), and keeps the fastest for the set: later scans use it.
+ * Results never depend on the plan. Allocates its own scratch, synchronises
+ * `stream`. *best_out / *best_ms (may be NULL) receive the chosen pm_params
+ * and its time per scan. PM_EINVAL for Wu-Manber and host-only sets.
+ */
+int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t reps,
+            void *stream, pm_params *best_out, float *best_ms);
 
 /* Synchronise `stream` and read the device status word of the last
  * pm_scan_device on this workspace: PM_OK or PM_ETIMEOUT. */
@@ -352,6 +372,9 @@ int pm_server_submit(pm_server *s, const pm_set *set, const uint8_t *T, int64_t 
  * result (library-owned; pm_result_free). Each ticket is waited on once. */
 int pm_server_wait(pm_server *s, int64_t ticket, pm_result **out);
 int pm_server_get_stats(pm_server *s, pm_server_stats *st);
+/* Forget the statistics so far (e.g. after a warm-up); requests in flight
+ * are counted when they finish. */
+int pm_server_reset_stats(pm_server *s);
 /* Finishes every queued and running request, then frees everything
  * (results never waited on are freed too). */
 void pm_server_destroy(pm_server *s);

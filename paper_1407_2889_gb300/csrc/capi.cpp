@@ -299,9 +299,18 @@ const char *pm_strerror(int code)
 
 int pm_last_cuda_error(void) { return g_last_cuda; }
 
+static bool params_ok(const pm_params *p)
+{
+    if (!p) return true;
+    return p->placement >= 0 && p->placement <= PM_PLACE_GLOBAL && p->smem_table_bytes >= 0 &&
+           p->warps_per_cta >= 0 && p->warps_per_cta <= 32 && p->ctas_per_sm >= 0 &&
+           p->ctas_per_sm <= 8 && p->wm_prefix_len >= 0 && p->wm_prefix_len <= 3 &&
+           p->counters >= 0 && p->counters <= 3 && p->ids_place >= 0 && p->ids_place <= 2;
+}
+
 int pm_ac_compile(const uint8_t *P, int64_t d, int32_t m, const pm_params *opt, pm_set **out)
 {
-    if (!out || !P || d < 1 || m < 1) return PM_EINVAL;
+    if (!out || !P || d < 1 || m < 1 || !params_ok(opt)) return PM_EINVAL;
     pm_set *s = new (std::nothrow) pm_set();
     if (!s) return PM_ENOMEM;
     s->algo = PM_ALGO_AC;
@@ -318,7 +327,7 @@ int pm_ac_compile(const uint8_t *P, int64_t d, int32_t m, const pm_params *opt, 
 int pm_wm_compile(const uint8_t *P, int64_t d, int32_t m, int32_t B, const pm_params *opt,
                   pm_set **out)
 {
-    if (!out || !P || d < 1 || m < 1 || B < 1 || B > m) return PM_EINVAL;
+    if (!out || !P || d < 1 || m < 1 || B < 1 || B > m || !params_ok(opt)) return PM_EINVAL;
     pm_set *s = new (std::nothrow) pm_set();
     if (!s) return PM_ENOMEM;
     s->algo = PM_ALGO_WM;
@@ -421,6 +430,104 @@ int pm_scan_device_noalloc(const pm_set *s, const uint8_t *d_text, int64_t n, ui
 }
 
 int64_t pm_noalloc_scratch_bytes(void) { return ac_noalloc_limit_bytes(); }
+
+int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t reps,
+            void *stream, pm_params *best_out, float *best_ms)
+{
+    if (!s || s->host_only || s->algo != PM_ALGO_AC || !d_text || n <= 0) return PM_EINVAL;
+    if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
+    if (reps < 1) reps = 1;
+    const bool list = !(flags & PM_COUNTS_ONLY);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DeviceProps dp;
+    int rc = device_props(dp);
+    if (rc) return rc;
+    const AcTables &t = s->ac;
+    void *ws = nullptr, *counts = nullptr, *nocc = nullptr, *occ = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int64_t n_occ = 0;
+    auto cleanup = [&]() {
+        if (ws) cudaFree(ws);
+        if (counts) cudaFree(counts);
+        if (nocc) cudaFree(nocc);
+        if (occ) cudaFree(occ);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = cudaMalloc(&ws, size_t(ac_workspace_bytes(t, n, list)));
+    if (e == cudaSuccess) e = cudaMalloc(&counts, size_t(t.d) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&nocc, 8);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && list) {
+        // size the occurrence buffer with one counts-only scan
+        rc = ac_launch(t, s->dac, d_text, n, false, static_cast<int64_t *>(counts), nullptr, 0,
+                       static_cast<int64_t *>(nocc), ws, st);
+        if (!rc) e = cudaMemcpyAsync(&n_occ, nocc, 8, cudaMemcpyDeviceToHost, st);
+        if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (!rc && e == cudaSuccess) e = cudaMalloc(&occ, size_t(std::max<int64_t>(n_occ, 1)) * 8);
+    }
+    if (e != cudaSuccess || rc) {
+        if (e != cudaSuccess) set_cuda_error(int(e));
+        cudaGetLastError();
+        cleanup();
+        return rc ? rc : (e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA);
+    }
+    // candidate plans: the current one, then placement x warps x counters x ids
+    std::vector<pm_params> cand;
+    cand.push_back(s->params);
+    for (int place : {PM_PLACE_AUTO, PM_PLACE_HYBRID})
+        for (int w : {0, 16, 12, 8})
+            for (int c : {0, 1, 2, 3})
+                for (int idp : {0, 1, 2}) {
+                    pm_params p = s->params;
+                    p.placement = place;
+                    p.warps_per_cta = w;
+                    p.counters = c;
+                    p.ids_place = idp;
+                    p.smem_table_bytes = 0;
+                    cand.push_back(p);
+                }
+    struct Tried { DevAc plan; pm_params params; float ms; };
+    std::vector<Tried> tried;
+    const DevAc saved = s->dac;
+    for (const pm_params &p : cand) {
+        DevAc plan = saved;
+        if (ac_plan(t, p, dp, plan) != PM_OK) continue;
+        bool dup = false;
+        for (const Tried &x : tried)
+            dup = dup || (x.plan.warps == plan.warps && x.plan.hist_smem == plan.hist_smem &&
+                          x.plan.ids_smem == plan.ids_smem && x.plan.smem_entries == plan.smem_entries &&
+                          x.plan.variant == plan.variant && x.plan.ctas_per_sm == plan.ctas_per_sm);
+        if (dup) continue;
+        auto run = [&]() {
+            return ac_launch(t, plan, d_text, n, list, static_cast<int64_t *>(counts),
+                             static_cast<uint64_t *>(occ), n_occ, static_cast<int64_t *>(nocc), ws, st);
+        };
+        rc = run();  // warm-up
+        if (!rc) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && !rc && e == cudaSuccess; ++r) rc = run();
+        if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); rc = PM_ECUDA; }
+        if (!rc && pm_scan_status(ws, stream) != PM_OK) rc = PM_ETIMEOUT;
+        if (rc) break;
+        tried.push_back(Tried{plan, p, ms / float(reps)});
+    }
+    cleanup();
+    if (rc) return rc;
+    if (tried.empty()) return PM_ETOOBIG;
+    size_t bi = 0;
+    for (size_t i = 1; i < tried.size(); ++i)
+        if (tried[i].ms < tried[bi].ms) bi = i;
+    s->dac = tried[bi].plan;  // same device tables, new launch plan
+    s->params = tried[bi].params;
+    if (best_out) *best_out = tried[bi].params;
+    if (best_ms) *best_ms = tried[bi].ms;
+    return PM_OK;
+}
 
 int pm_scan_status(const void *d_workspace, void *stream)
 {

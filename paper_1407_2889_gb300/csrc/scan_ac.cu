@@ -161,8 +161,11 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
         ids.rank = reinterpret_cast<const E *>(a.rank_g);
         ids.canon = reinterpret_cast<const E *>(a.canon_g);
     }
+    // per-terminal counters: 32-bit (hist_smem 1) or two 16-bit halves per
+    // word (hist_smem 2) in shared memory, else 64-bit in the workspace
     uint32_t *s_hist = a.hist_smem ? reinterpret_cast<uint32_t *>(p) : nullptr;
-    p += a.hist_smem ? r16((long long)a.nterms * 4) : 0;
+    const long long hist_words = a.hist_smem == 2 ? (a.nterms + 1) / 2 : a.nterms;
+    p += a.hist_smem ? r16(hist_words * 4) : 0;
     uint8_t *s_cls = p;
     p += DNA ? 0 : 256;
     p += warp * ac_warp_bytes(HV, a.pool_cap, sizeof(E));
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
         for (int i = threadIdx.x; i < a.nterms; i += blockDim.x) cn[i] = cg[i];
     }
     if (s_hist)
-        for (int i = threadIdx.x; i < a.nterms; i += blockDim.x) s_hist[i] = 0u;
+        for (int i = threadIdx.x; i < hist_words; i += blockDim.x) s_hist[i] = 0u;
     if (!DNA)
         for (int i = threadIdx.x; i < 256; i += blockDim.x) s_cls[i] = a.cls_g[i];
     if (lane == 0) dev::mbar_init(bar, 1);
@@ -202,8 +205,21 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
     const int m = a.m;
 
     auto count_terminal = [&](uint32_t c) {
-        if (s_hist) atomicAdd(&s_hist[c], 1u);
-        else atomicAdd(&a.ccount[c], 1ull);
+        if (a.hist_smem == 1) {
+            atomicAdd(&s_hist[c], 1u);
+        } else if (a.hist_smem == 2) {
+            // the add that takes a half to 0x8000 moves 0x8000 to the global
+            // counter, so a half never wraps (it would take 0x8000 more adds
+            // between that add and the move)
+            const uint32_t sh = (c & 1u) << 4;
+            const uint32_t old = atomicAdd(&s_hist[c >> 1], 1u << sh);
+            if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
+                atomicSub(&s_hist[c >> 1], 0x8000u << sh);
+                atomicAdd(&a.ccount[c], 0x8000ull);
+            }
+        } else {
+            atomicAdd(&a.ccount[c], 1ull);
+        }
     };
     // multiplicity of a pattern code (1, or the size of its group)
     auto mult_of = [&](uint32_t code) -> uint32_t {
@@ -370,7 +386,7 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
     __syncthreads();
     if (s_hist) {
         for (int c = threadIdx.x; c < a.nterms; c += blockDim.x) {
-            const uint32_t v = s_hist[c];
+            const uint32_t v = a.hist_smem == 2 ? (s_hist[c >> 1] >> ((c & 1) << 4)) & 0xFFFFu : s_hist[c];
             if (v) atomicAdd(&a.ccount[c], (unsigned long long)v);
         }
     }
@@ -589,12 +605,17 @@ struct Layout {
     int warps, hist, ids;
 };
 
+long long ac_hist_bytes(int hist, long long nterms)
+{
+    return hist == 1 ? r16(nterms * 4) : hist == 2 ? r16((nterms + 1) / 2 * 4) : 0;
+}
+
 long long ac_smem_bytes(const AcTables &t, int eb, const Layout &L, int hv, int pool_cap)
 {
     const int nwords = int(t.flag_mask.size());
     const int nterms = int(t.canon.size());
     return r16(L.smem_entries * eb) + (L.ids ? ac_ids_bytes(nwords, nterms, eb) : 0) +
-           (L.hist ? r16((long long)nterms * 4) : 0) + (t.dna ? 0 : 256) +
+           ac_hist_bytes(L.hist, nterms) + (t.dna ? 0 : 256) +
            (long long)L.warps * ac_warp_bytes(hv, pool_cap, eb);
 }
 
@@ -614,6 +635,12 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     dev.hv = hv;
     dev.nv = 5 + hv;
     dev.ctas_per_sm = opt.ctas_per_sm > 0 ? opt.ctas_per_sm : 1;
+    // pm_params.counters: 0 auto, 1 32-bit shared, 2 16-bit shared, 3 global;
+    // pm_params.ids_place: 0 auto, 1 shared, 2 global
+    auto hist_ok = [&](int h) {
+        return opt.counters == 0 || (opt.counters == 3 ? h == 0 : h == opt.counters);
+    };
+    auto ids_ok = [&](int i) { return opt.ids_place == 0 || (opt.ids_place == 1) == (i == 1); };
     auto fits = [&](const Layout &L) {
         const long long need = ac_smem_bytes(t, eb, L, hv, pool_cap);
         return need <= budget &&
@@ -625,10 +652,12 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     if ((place == PM_PLACE_AUTO || place == PM_PLACE_SMEM) &&
         (opt.smem_table_bytes <= 0 || entries * eb <= opt.smem_table_bytes)) {
         // whole table in shared memory; prefer the id structure and the
-        // counters there too, then the most warps (at least 12 if possible)
-        const int ids_hist[3][2] = {{1, 1}, {1, 0}, {0, 0}};
+        // counters there too (32-bit, else 16-bit), then the most warps (at
+        // least 12 if possible); pm_params can pin either choice
+        const int ids_hist[6][2] = {{1, 1}, {1, 2}, {0, 1}, {0, 2}, {1, 0}, {0, 0}};
         for (int minw : {12, 4}) {
-            for (int o = 0; o < 3 && !chosen; ++o) {
+            for (int o = 0; o < 6 && !chosen; ++o) {
+                if (!ids_ok(ids_hist[o][0]) || !hist_ok(ids_hist[o][1])) continue;
                 const int hi = forced_warps ? forced_warps : 16;
                 const int lo = forced_warps ? forced_warps : minw;
                 for (int w = hi; w >= lo; --w) {
@@ -644,8 +673,11 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     if (!chosen) {
         // hybrid / global: breadth-first prefix of rows in shared memory
         const int w = forced_warps ? forced_warps : 16;
-        Layout L{0, w, 0, 0};
+        // counters / ids only when pinned by pm_params (the table prefix
+        // gets the room otherwise)
+        Layout L{0, w, opt.counters == 1 ? 1 : opt.counters == 2 ? 2 : 0, opt.ids_place == 1 ? 1 : 0};
         const long long fixed = ac_smem_bytes(t, eb, L, hv, pool_cap);
+        if (fixed > budget) return PM_ETOOBIG;
         long long room = budget - fixed;
         if (dev.ctas_per_sm > 1)
             room = std::min(room, (long long)dp.smem_per_sm / dev.ctas_per_sm - 1024 - fixed);

@@ -837,6 +837,19 @@ int pm_server_get_stats(pm_server *s, pm_server_stats *st)
     return PM_OK;
 }
 
+int pm_server_reset_stats(pm_server *s)
+{
+    if (!s) return PM_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->lat_us.clear();
+    s->bytes_done = 0;
+    s->batches = s->batched_reqs = s->reruns = 0;
+    s->peak_inflight = s->inflight_reqs;
+    s->dispatch_busy_s = s->complete_busy_s = 0.0;
+    s->have_first = false;
+    return PM_OK;
+}
+
 void pm_server_destroy(pm_server *s)
 {
     if (!s) return;

@@ -32,8 +32,8 @@ EXPORTED = [
     "pm_scan_batch", "pm_batch_prepare", "pm_batch_free", "pm_batch_counts_total",
     "pm_batch_workspace_bytes", "pm_batch_warps", "pm_batch_scan_device", "pm_batch_tune",
     "pm_batch_set_warps", "pm_batch_capture", "pm_batch_replay",
-    "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
-    "pm_server_destroy",
+    "pm_tune", "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
+    "pm_server_reset_stats", "pm_server_destroy",
     "pm_selfcheck_host_walk", "pm_strerror", "pm_last_cuda_error", "pm_version",
 ]
 
@@ -41,7 +41,8 @@ EXPORTED = [
 class pm_params(ctypes.Structure):
     _fields_ = [("placement", ctypes.c_int32), ("smem_table_bytes", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("wm_prefix_len", ctypes.c_int32), ("host_only", ctypes.c_int32)]
+                ("wm_prefix_len", ctypes.c_int32), ("host_only", ctypes.c_int32),
+                ("counters", ctypes.c_int32), ("ids_place", ctypes.c_int32)]
 
 
 class pm_set_info(ctypes.Structure):
@@ -154,6 +155,9 @@ def lib():
         L.pm_batch_capture.argtypes = [vp, vp, vp, vp, vp, vp, i64]
         L.pm_batch_replay.restype = ctypes.c_int
         L.pm_batch_replay.argtypes = [vp, vp]
+        L.pm_tune.restype = ctypes.c_int
+        L.pm_tune.argtypes = [vp, vp, i64, u32, i32, vp, ctypes.POINTER(pm_params),
+                              ctypes.POINTER(ctypes.c_float)]
         L.pm_server_create.restype = ctypes.c_int
         L.pm_server_create.argtypes = [ctypes.POINTER(pm_server_params), pp]
         L.pm_server_submit.restype = ctypes.c_int
@@ -162,6 +166,8 @@ def lib():
         L.pm_server_wait.argtypes = [vp, i64, ctypes.POINTER(ctypes.POINTER(pm_result))]
         L.pm_server_get_stats.restype = ctypes.c_int
         L.pm_server_get_stats.argtypes = [vp, ctypes.POINTER(pm_server_stats)]
+        L.pm_server_reset_stats.restype = ctypes.c_int
+        L.pm_server_reset_stats.argtypes = [vp]
         L.pm_server_destroy.restype = None
         L.pm_server_destroy.argtypes = [vp]
         L.pm_selfcheck_host_walk.restype = ctypes.c_int
@@ -358,6 +364,15 @@ def pm_scan_batch(handles, texts, flags: int = PM_HOST_TEXT, stream=None):
     return [_take_result(outs[j]) for j in range(k)]
 
 
+def pm_tune(h: int, d_text, n: int, flags: int = 0, reps: int = 3, stream=None):
+    """Autotune the set's launch plan on a device text; returns (params dict, ms)."""
+    p = pm_params()
+    ms = ctypes.c_float(0.0)
+    _check(lib().pm_tune(h, _dev_ptr(d_text), int(n), flags, int(reps), _stream_ptr(stream),
+                         ctypes.byref(p), ctypes.byref(ms)), "pm_tune")
+    return {f: getattr(p, f) for f, _ in pm_params._fields_}, float(ms.value)
+
+
 def pm_batch_prepare(handles, text_off, text_len, occ_off, flags: int = 0) -> int:
     """Prepared batch: instance j scans text_len[j] bytes at text_off[j] of one
     device buffer with set handles[j]; its keys go to occ[occ_off[j]:occ_off[j+1]]."""
@@ -463,6 +478,11 @@ class PatternSet:
         if hasattr(T, "is_cuda") and T.is_cuda:
             flags |= PM_DEVICE_TEXT
         return pm_scan(self.h, T, flags, stream)
+
+    def tune(self, d_text, counts_only: bool = False, reps: int = 3, stream=None):
+        """Autotune the launch plan on a device text (AC sets); (params, ms)."""
+        return pm_tune(self.h, d_text, int(d_text.numel()), PM_COUNTS_ONLY if counts_only else 0,
+                       reps, stream)
 
     def workspace_bytes(self, n: int, counts_only: bool = False) -> int:
         return pm_scan_workspace_bytes(self.h, n, PM_COUNTS_ONLY if counts_only else 0)
@@ -627,6 +647,9 @@ class Server:
         st = pm_server_stats()
         _check(lib().pm_server_get_stats(self.h, ctypes.byref(st)), "pm_server_get_stats")
         return {f: getattr(st, f) for f, _ in pm_server_stats._fields_}
+
+    def reset_stats(self) -> None:
+        _check(lib().pm_server_reset_stats(self.h), "pm_server_reset_stats")
 
     def close(self):
         if getattr(self, "h", 0):

@@ -145,6 +145,43 @@ def test_placements_and_launch_shapes_agree(kw):
     s.close()
 
 
+@pytest.mark.parametrize("counters", [1, 2, 3])
+@pytest.mark.parametrize("ids_place", [1, 2])
+def test_counter_and_id_placements_agree(counters, ids_place):
+    """Per-terminal counters (32-bit / 16-bit shared, device memory) and the
+    terminal-id structure (shared / device) give identical results; the
+    16-bit counters overflow into the device counter many times here."""
+    T = synth.est_text(4 << 20, 21)
+    P = synth.mixed_patterns(T, 3000, 8, 21)
+    P = np.concatenate([P, P[:7]])
+    want = oracle.dictionary(T, P, threads=THREADS)
+    s = _ac(P, counters=counters, ids_place=ids_place)
+    _same(s.scan(T), want, f"counters={counters} ids={ids_place}")
+    s.close()
+    n = 8 << 20
+    A = np.full(n, ord("A"), np.uint8)
+    s = _ac(np.full((2, 8), ord("A"), np.uint8), counters=counters, ids_place=ids_place)
+    occ, cnt = s.scan(A, counts_only=True)
+    assert cnt.tolist() == [n - 7, n - 7]
+    s.close()
+
+
+def test_autotuner_keeps_results():
+    T = synth.est_text(16 << 20, 22)
+    P = synth.mixed_patterns(T, 8000, 8, 22)
+    want = oracle.dictionary(T, P, threads=THREADS)
+    s = _ac(P)
+    params, ms = s.tune(torch.from_numpy(T).cuda(), reps=2)
+    assert ms > 0 and params["counters"] in (0, 1, 2, 3)
+    _same(s.scan(T), want, f"tuned {params}")
+    _same(s.scan(T, counts_only=True), (np.zeros(0, np.uint64), want[1]), "tuned counts")
+    s.close()
+    w = _wm(P, 3)
+    with pytest.raises(pm.PmError):
+        w.tune(torch.from_numpy(T[:4096]).cuda())
+    w.close()
+
+
 def test_device_api_capacity_and_status():
     T = synth.uniform_dna(1 << 20, 0)
     P = synth.mixed_patterns(T, 100, 8, 0)
