@@ -322,7 +322,7 @@ def main():
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": recorded_traffic("ac_scan_kernel", f"est1gib_d{d}_m{args.m}_{args.mode}_n{n}"),
                 "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel": "ac_scan_kernel<uint16_t,6,1,dna,smem> + tile_offsets_kernel + expand_kernel (list mode)"}
+                "kernel": "ac_scan_kernel<uint16_t,6,1,dna,smem> + expand_kernel (list mode)"}
 
     # end to end through the public API: pinned host text in, pinned host
     # counts and occurrence list out (pm_scan_to_host), copies inside the timing
