@@ -41,14 +41,26 @@ __device__ __forceinline__ uint32_t word_of(const uint4 &v, int q)
     return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w;
 }
 
+// Entries (PRE false): (next_row << 1) | match; (PRE true, device copies of
+// ACGT tables): (next_row << 2) | match, i.e. the table index of the next
+// row's first entry, which saves a shift on every step.
+template <bool PRE>
+__device__ __forceinline__ uint32_t row_base(uint32_t e)
+{
+    return PRE ? (e & ~3u) : ((e >> 1) << 2);
+}
+
 // DFA walk over one lane's register text, ACGT-like alphabet. For every step
 // calls on_step(step, idx, e): idx the table index used, e the entry read
-// (bit 0 set when the transition entered a terminal state).
-template <int NV, class Tab, class F>
+// (bit 0 set when the transition entered a terminal state). Per byte, t is
+// 0xFFFFFFFC | class for a byte of the alphabet and just the class (row 0,
+// whose entries all lead to the root) for any other byte; the next index is
+// then (row base & t & ~3) | (t & 3).
+template <int NV, bool PRE, class Tab, class F>
 __device__ __forceinline__ void walk_dna(const uint4 (&tv)[NV], int steps, uint32_t lut,
                                          const Tab &tab, F &&on_step)
 {
-    uint32_t e = 2u;  // root (row 1)
+    uint32_t e = PRE ? 4u : 2u;  // root (row 1)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
 #pragma unroll
@@ -59,15 +71,15 @@ __device__ __forceinline__ void walk_dna(const uint4 (&tv)[NV], int steps, uint3
             const uint32_t x = w ^ __byte_perm(lut, 0u, sel);  // zero byte = in alphabet
             const uint32_t y = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
             const uint32_t vb = (y >> 7) * 0xFFu;   // 0xFF per valid byte
-            const uint32_t v2 = vb & 0xFCFCFCFCu;
+            const uint32_t a4v = a4 | (vb & 0xFCFCFCFCu);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int step = v * 16 + q * 4 + k;
                 if (step < kChunk || step < steps) {
-                    const uint32_t c = __byte_perm(a4, 0u, 0x4440 | k);
-                    const uint32_t vm = __byte_perm(
-                        v2, vb, (k) | ((4 + k) << 4) | ((4 + k) << 8) | ((4 + k) << 12));
-                    const uint32_t idx = ((e << 1) & vm) | c;  // invalid byte -> row 0
+                    const uint32_t t = __byte_perm(
+                        a4v, vb, (k) | ((4 + k) << 4) | ((4 + k) << 8) | ((4 + k) << 12));
+                    const uint32_t base = PRE ? e : (e << 1);
+                    const uint32_t idx = (base & t & ~3u) | (t & 3u);
                     e = tab(idx);
                     on_step(step, idx, e);
                 }
@@ -104,12 +116,12 @@ __device__ __forceinline__ void walk_gen(const uint4 (&tv)[NV], int steps, int l
 // Rolled re-walk of one lane's chunk straight from global memory, for the
 // rare lanes whose hit pool overflowed; same transitions as the fast walks.
 // Calls hit(step, idx) for every match.
-template <class Tab, class F>
+template <bool PRE = false, class Tab, class F>
 __device__ __forceinline__ void walk_slow(const uint8_t *text, long long n, long long g0,
                                           int steps, bool dna, uint32_t lut, int lw,
                                           const uint8_t *s_cls, const Tab &tab, F &&hit)
 {
-    uint32_t e = 2u;
+    uint32_t e = PRE ? 4u : 2u;
 #pragma unroll 1
     for (int step = 0; step < steps; ++step) {
         const long long g = g0 + step;
@@ -118,7 +130,7 @@ __device__ __forceinline__ void walk_slow(const uint8_t *text, long long n, long
         uint32_t idx;
         if (dna) {
             const uint32_t c = ((b >> 1) ^ (b >> 2)) & 3u;
-            idx = ((lut >> (8 * c)) & 0xFFu) == b ? (((e >> 1) << 2) | c) : c;
+            idx = ((lut >> (8 * c)) & 0xFFu) == b ? (row_base<PRE>(e) | c) : c;
         } else {
             const uint32_t c = s_cls[b];
             idx = c == 0xFFu ? 0u : (((e >> 1) << lw) | c);

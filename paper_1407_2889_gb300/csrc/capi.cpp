@@ -122,10 +122,17 @@ int upload_ac(pm_set *s)
     int64_t &tot = s->device_bytes;
     const int eb = t.dna ? t.entry_bytes : 4;
     int rc;
+    // the device copy of an ACGT table may hold (next_row << 2) | match, the
+    // table index of the next row's first entry (see DevAc::pre)
+    auto dev_entry = [&](uint32_t e) { return d.pre ? (((e >> 1) << 2) | (e & 1u)) : e; };
     if (eb == 2) {
         std::vector<uint16_t> t16(t.table.size());
-        for (size_t i = 0; i < t.table.size(); ++i) t16[i] = uint16_t(t.table[i]);
+        for (size_t i = 0; i < t.table.size(); ++i) t16[i] = uint16_t(dev_entry(t.table[i]));
         rc = upload(&d.table, t16.data(), t16.size() * 2, tot);
+    } else if (d.pre) {
+        std::vector<uint32_t> t32(t.table.size());
+        for (size_t i = 0; i < t.table.size(); ++i) t32[i] = dev_entry(t.table[i]);
+        rc = upload(&d.table, t32.data(), t32.size() * 4, tot);
     } else {
         rc = upload(&d.table, t.table.data(), t.table.size() * 4, tot);
     }

@@ -119,6 +119,7 @@ struct DevAc {
     int32_t ids_smem = 0;           // rank structure and canon in shared memory
     int32_t nv = 0, hv = 0;         // register text vectors (chunk + halo)
     int32_t variant = 0;            // kernel instance id
+    int32_t pre = 0;                // ACGT table stored on the device as (next_row << 2) | match
     int64_t smem_bytes = 0;
     int32_t placement = 0;
     int64_t max_warps = 0;          // warps in the largest grid a launch uses
@@ -210,7 +211,7 @@ struct BatchDesc {                 // one instance, in processing order
     const uint32_t *grp_ids;
     int smem_entries, eb, m, nwords, nterms, d;
     int ids_off, hist_off;         // byte offsets in the CTA's table region; -1 = global
-    uint32_t mid_base, lut, pad, pad2;
+    uint32_t mid_base, lut, pad, pre;  // pre: DevAc::pre of the set
 };
 
 struct BatchShape {                // launch shape and shared-memory split

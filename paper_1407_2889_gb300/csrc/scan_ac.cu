@@ -134,7 +134,7 @@ __device__ __forceinline__ void stage_issue(const AcArgs &a, long long t, uint8_
     if (bytes > 0) dev::tma_load_1d(buf, a.text + t * kWarpTile, uint32_t(bytes), bar);
 }
 
-template <typename E, int NV, int HV, bool DNA, bool HYB>
+template <typename E, int NV, int HV, bool DNA, bool HYB, bool PRE>
 __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -221,6 +221,11 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
             atomicAdd(&a.ccount[c], 1ull);
         }
     };
+    // offset of a recorded table index among the match rows' entries (in
+    // 16-bit arithmetic for u16 tables, whose match rows span < 65536 entries)
+    auto match_off = [&](E v) -> uint32_t {
+        return sizeof(E) == 2 ? uint32_t(uint16_t(v - E(a.mid_base))) : uint32_t(v) - a.mid_base;
+    };
     // multiplicity of a pattern code (1, or the size of its group)
     auto mult_of = [&](uint32_t code) -> uint32_t {
         if (!(code & kGrp)) return 1u;
@@ -290,11 +295,11 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
         // pool slot `cap` absorbs the stores of an overflowing lane
         auto rec = [&](int step, uint32_t idx, uint32_t e) {
             const uint32_t h = e & 1u;
-            pl[kslot * 32] = E(idx - a.mid_base);
+            pl[kslot * 32] = E(idx);  // the match-row base is subtracted when resolving
             kslot = min(kslot + h, cap);
-            hw[step >> 5] |= h << (step & 31);
+            hw[step >> 5] += h << (step & 31);
         };
-        if (DNA) walk_dna<NV>(tv, steps, a.lut, tab, rec);
+        if (DNA) walk_dna<NV, PRE>(tv, steps, a.lut, tab, rec);
         else walk_gen<NV>(tv, steps, a.lw, s_cls, tab, rec);
         uint32_t nh = 0;  // exact even when the pool overflowed
 #pragma unroll
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
                 uint32_t c4[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    c4[j] = ids.terminal(k0 + j < nh ? uint32_t(pl[(k0 + j) * 32]) : 0u);
+                    c4[j] = ids.terminal(k0 + j < nh ? match_off(pl[(k0 + j) * 32]) : 0u);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (k0 + j < nh) {
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
                 }
             }
         } else {
-            walk_slow(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
+            walk_slow<PRE>(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
                       [&](int, uint32_t idx) {
                           const uint32_t c = ids.terminal(idx - a.mid_base);
                           count_terminal(c);
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
             }
         } else {
             uint32_t k = 0;
-            walk_slow(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
+            walk_slow<PRE>(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
                       [&](int step, uint32_t idx) {
                           const uint32_t code = ids.code(ids.terminal(idx - a.mid_base));
                           if (k < nh) dst[k] = ((SE)(off0 + uint32_t(step)) << kOffShift) | (SE)code;
@@ -573,21 +578,29 @@ struct Variant {
     bool dna, hyb;
 };
 
-// variant ids: dna u16 smem (0-2), dna u16 hybrid (3-5), dna u32 hybrid
-// (6-8), general u32 hybrid (9-11); within each group HV = 1, 2, 4.
+// variant ids: dna u16 smem (0-2), dna u16 hybrid (3-5), dna u16 smem with
+// index entries (6-8), dna u16 hybrid with index entries (9-11), dna u32
+// hybrid with index entries (12-14), general u32 hybrid (15-17); within
+// each group HV = 1, 2, 4.
 const Variant kVariants[] = {
-    {ac_scan_kernel<uint16_t, 6, 1, true, false>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, true>, 2, 1, true, true},
-    {ac_scan_kernel<uint16_t, 7, 2, true, true>, 2, 2, true, true},
-    {ac_scan_kernel<uint16_t, 9, 4, true, true>, 2, 4, true, true},
-    {ac_scan_kernel<uint32_t, 6, 1, true, true>, 4, 1, true, true},
-    {ac_scan_kernel<uint32_t, 7, 2, true, true>, 4, 2, true, true},
-    {ac_scan_kernel<uint32_t, 9, 4, true, true>, 4, 4, true, true},
-    {ac_scan_kernel<uint32_t, 6, 1, false, true>, 4, 1, false, true},
-    {ac_scan_kernel<uint32_t, 7, 2, false, true>, 4, 2, false, true},
-    {ac_scan_kernel<uint32_t, 9, 4, false, true>, 4, 4, false, true},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, false>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, false>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, false>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, false>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, false>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, false>, 2, 4, true, true},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, true>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, true>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, true>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, true>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, true>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, true>, 2, 4, true, true},
+    {ac_scan_kernel<uint32_t, 6, 1, true, true, true>, 4, 1, true, true},
+    {ac_scan_kernel<uint32_t, 7, 2, true, true, true>, 4, 2, true, true},
+    {ac_scan_kernel<uint32_t, 9, 4, true, true, true>, 4, 4, true, true},
+    {ac_scan_kernel<uint32_t, 6, 1, false, true, false>, 4, 1, false, true},
+    {ac_scan_kernel<uint32_t, 7, 2, false, true, false>, 4, 2, false, true},
+    {ac_scan_kernel<uint32_t, 9, 4, false, true, false>, 4, 4, false, true},
 };
 
 int hv_for_m(int m)
@@ -696,10 +709,13 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     dev.stage_cap = 0;
     dev.smem_entries = best.smem_entries;
     const bool hyb = dev.smem_entries < entries || !t.dna || eb == 4;
+    // ACGT tables whose entries fit as next-row indices: u32, or u16 with
+    // fewer than 2^14 rows
+    dev.pre = t.dna && (eb == 4 || t.n_rows <= (1 << 14)) ? 1 : 0;
     int group;
-    if (!t.dna) group = 3;
-    else if (eb == 4) group = 2;
-    else group = hyb ? 1 : 0;
+    if (!t.dna) group = 5;
+    else if (eb == 4) group = 4;
+    else group = (hyb ? 1 : 0) + (dev.pre ? 2 : 0);
     dev.variant = group * 3 + hv_slot(hv);
     dev.smem_bytes = ac_smem_bytes(t, eb, best, hv, pool_cap);
     dev.max_warps = (long long)dp.sm_count * dev.ctas_per_sm * dev.warps;

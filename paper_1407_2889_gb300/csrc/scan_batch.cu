@@ -84,7 +84,7 @@ struct CtaSmem {
 };
 
 // One instance, entry type E. All threads of the CTA call it.
-template <typename E>
+template <typename E, bool PRE>
 __device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSmem &S,
                              uint32_t &phase, bool &failed)
 {
@@ -198,7 +198,7 @@ __device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSm
                     kslot = min(kslot + h, cap);
                     hw[step >> 5] |= h << (step & 31);
                 };
-                walk_dna<NV>(tv, steps, D.lut, tab, rec);
+                walk_dna<NV, PRE>(tv, steps, D.lut, tab, rec);
 #pragma unroll
                 for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
                 ovf = nh > cap;
@@ -211,7 +211,7 @@ __device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSm
                         pl[k * 32] = E(code);
                     }
                 } else {
-                    walk_slow(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
+                    walk_slow<PRE>(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
                               [&](int, uint32_t idx) {
                                   const uint32_t c = ids.terminal(idx - D.mid_base);
                                   count_terminal(c);
@@ -301,7 +301,7 @@ __device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSm
                         put_code(g0 + st - (m - 1), pl[k * 32]);
                     }
                 } else {
-                    walk_slow(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
+                    walk_slow<PRE>(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
                               [&](int step, uint32_t idx) {
                                   put_code(g0 + step - (m - 1), ids.code(ids.terminal(idx - D.mid_base)));
                               });
@@ -366,8 +366,13 @@ __global__ void __launch_bounds__(512, 1) ac_batch_kernel(const BatchArgs a)
         __syncthreads();
         if (j < 0) break;
         const BatchDesc D = a.desc[j];
-        if (D.eb == 2) run_instance<uint16_t>(a, D, S, phase, failed);
-        else run_instance<uint32_t>(a, D, S, phase, failed);
+        if (D.eb == 2) {
+            if (D.pre) run_instance<uint16_t, true>(a, D, S, phase, failed);
+            else run_instance<uint16_t, false>(a, D, S, phase, failed);
+        } else {
+            if (D.pre) run_instance<uint32_t, true>(a, D, S, phase, failed);
+            else run_instance<uint32_t, false>(a, D, S, phase, failed);
+        }
     }
 }
 
@@ -472,6 +477,7 @@ int64_t batch_fill(const BatchInst *inst, int k, const BatchShape &sh, BatchDesc
         D.d = int(t.d);
         D.mid_base = uint32_t(t.d0_row << t.lw);
         D.lut = t.lut;
+        D.pre = uint32_t(dv.pre);
         D.pad = 0;
         for (uint32_t x = 0; x < 256; ++x)  // a byte outside the alphabet
             if (t.cls[x] == 0xFF) { D.pad = x; break; }
