@@ -440,6 +440,71 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
             torch.cuda.empty_cache()
     out["ac_list_sweep"] = sweep
     out["large_sets"] = large_sets(T, d_text, stream, nocc, pm, torch, synth)
+    out["wm_list_sweep"], out["pfac_list"] = other_methods(T, d_text, stream, nocc, pm, torch, synth)
+    out["small_uniform_1mib"] = small_case(stream, nocc, pm, torch, synth)
+    return out
+
+
+def _time_scan(pm, torch, h, d_text, n, d, stream, nocc, reps=2):
+    """List-mode GB/s of set h over n device bytes (sized by a counts pass)."""
+    cnt = torch.zeros(max(d, 1), dtype=torch.int64, device="cuda")
+    ws = torch.zeros(pm.pm_scan_workspace_bytes(h, n, 0), dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        pm.pm_scan_device(h, d_text, n, pm.PM_COUNTS_ONLY, cnt, None, 0, nocc, ws, ws.numel(), stream)
+    stream.synchronize()
+    tot = int(nocc.item())
+    buf = torch.empty(max(tot, 1), dtype=torch.int64, device="cuda")
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        pm.pm_scan_device(h, d_text, n, 0, cnt, buf, buf.numel(), nocc, ws, ws.numel(), stream)
+        ev0.record(stream)
+        for _ in range(reps):
+            pm.pm_scan_device(h, d_text, n, 0, cnt, buf, buf.numel(), nocc, ws, ws.numel(), stream)
+        ev1.record(stream)
+    stream.synchronize()
+    assert pm.pm_scan_status(ws, stream) == pm.PM_OK
+    dt = ev0.elapsed_time(ev1) / reps / 1e3
+    del ws, buf
+    return n / dt / 1e9, tot, dt
+
+
+def other_methods(T, d_text, stream, nocc, pm, torch, synth):
+    """Wu-Manber (B=3) over the 9 EST sets and PFAC over two, full 1 GiB text,
+    list mode."""
+    n = T.size
+    wm = {}
+    for dd in synth.EST_D:
+        for mm in synth.EST_M:
+            _, Pq = synth.est_case(dd, mm, text=T)
+            q = pm.PatternSet.wm(Pq, 3)
+            gbs, tot, _ = _time_scan(pm, torch, q.h, d_text, n, dd, stream, nocc, reps=1)
+            wm[f"d{dd}_m{mm}"] = {"gbs": gbs, "n_occ": tot, "exact_code_tables": q.info()["dna_mode"]}
+            q.close()
+            torch.cuda.empty_cache()
+    pf = {}
+    for dd, mm in ((1000, 8), (8000, 8), (8000, 32)):
+        _, Pq = synth.est_case(dd, mm, text=T)
+        q = pm.PatternSet.pfac(Pq)
+        gbs, tot, _ = _time_scan(pm, torch, q.h, d_text, n, dd, stream, nocc)
+        pf[f"d{dd}_m{mm}"] = {"gbs": gbs, "n_occ": tot}
+        q.close()
+        torch.cuda.empty_cache()
+    return wm, pf
+
+
+def small_case(stream, nocc, pm, torch, synth):
+    """The 1 MiB uniform workload (d=100, m=8): AC, PFAC and WM B=2, list
+    mode; time per scan (launch-bound at this size)."""
+    T, P = synth.small_uniform_case()
+    d_small = torch.from_numpy(T).cuda()
+    out = {}
+    for name, mk in (("ac", lambda: pm.PatternSet.ac(P)), ("pfac", lambda: pm.PatternSet.pfac(P)),
+                     ("wm_b2", lambda: pm.PatternSet.wm(P, 2))):
+        q = mk()
+        gbs, tot, dt = _time_scan(pm, torch, q.h, d_small, T.size, P.shape[0], stream, nocc, reps=20)
+        out[name] = {"gbs": gbs, "us_per_scan": dt * 1e6, "n_occ": tot}
+        q.close()
     return out
 
 

@@ -66,6 +66,7 @@ extern "C" {
 
 #define PM_ALGO_AC 1
 #define PM_ALGO_WM 2
+#define PM_ALGO_PFAC 3
 
 /* Tuning knobs; a zero field means "pick automatically". */
 typedef struct pm_params {
@@ -86,11 +87,11 @@ typedef struct pm_params {
 typedef struct pm_set pm_set; /* compiled pattern set; owns its device tables */
 
 typedef struct pm_set_info {
-    int32_t algo;             /* PM_ALGO_AC or PM_ALGO_WM */
+    int32_t algo;             /* PM_ALGO_AC, PM_ALGO_WM or PM_ALGO_PFAC */
     int32_t m;
     int64_t d;
     int64_t n_distinct;       /* distinct patterns */
-    /* Aho-Corasick */
+    /* Aho-Corasick (and PFAC) */
     int64_t n_states;         /* trie states, including terminals */
     int64_t n_rows;           /* DFA rows kept (terminal rows elided) + reset row */
     int32_t n_classes;        /* character classes (alphabet size of P) */
@@ -136,6 +137,18 @@ int pm_ac_compile(const uint8_t *P, int64_t d, int32_t m,
  */
 int pm_wm_compile(const uint8_t *P, int64_t d, int32_t m, int32_t B,
                   const pm_params *opt, pm_set **out);
+
+/*
+ * Compile a PFAC set (failure-less Aho-Corasick, Lin et al.; the related work
+ * the paper cites next to its own kernels): the trie of Section 3.1,
+ * Algorithm 1, with no supply function. Each start position i is walked by
+ * its own thread along goto edges only; a walk that reaches depth m reports
+ * (i, r), one that finds no edge stops. Same results, scans, workspace and
+ * outputs as an AC set (pm_scan, pm_scan_device ...); the batched scan, the
+ * server, the tuner and the allocation-free scan take AC sets only.
+ */
+int pm_pfac_compile(const uint8_t *P, int64_t d, int32_t m,
+                    const pm_params *opt, pm_set **out);
 
 void pm_set_free(pm_set *s);
 int pm_set_get_info(const pm_set *s, pm_set_info *info);

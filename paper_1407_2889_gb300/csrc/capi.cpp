@@ -186,9 +186,10 @@ int finish_compile(pm_set *s, pm_set **out)
     }
     DeviceProps dp;
     int rc = device_props(dp);
-    if (!rc) rc = s->algo == PM_ALGO_AC ? ac_plan(s->ac, s->params, dp, s->dac)
-                                        : wm_plan(s->wm, s->params, dp, s->dwm);
-    if (!rc) rc = s->algo == PM_ALGO_AC ? upload_ac(s) : upload_wm(s);
+    const bool ac_like = s->algo != PM_ALGO_WM;
+    if (!rc) rc = ac_like ? ac_plan(s->ac, s->params, dp, s->dac) : wm_plan(s->wm, s->params, dp, s->dwm);
+    if (!rc && s->algo == PM_ALGO_PFAC) s->dac.pre = 0;  // PFAC walks the plain entry format
+    if (!rc) rc = ac_like ? upload_ac(s) : upload_wm(s);
     if (rc) {
         release_device(s);
         delete s;
@@ -262,7 +263,7 @@ pm_result *new_result(int64_t d, int64_t n_occ, bool list, bool pinned)
     return r;
 }
 
-int64_t set_d(const pm_set *s) { return s->algo == PM_ALGO_AC ? s->ac.d : s->wm.d; }
+int64_t set_d(const pm_set *s) { return s->algo == PM_ALGO_WM ? s->wm.d : s->ac.d; }
 
 }  // namespace
 
@@ -331,6 +332,22 @@ int pm_ac_compile(const uint8_t *P, int64_t d, int32_t m, const pm_params *opt, 
     return finish_compile(s, out);
 }
 
+int pm_pfac_compile(const uint8_t *P, int64_t d, int32_t m, const pm_params *opt, pm_set **out)
+{
+    if (!out || !P || d < 1 || m < 1 || !params_ok(opt)) return PM_EINVAL;
+    pm_set *s = new (std::nothrow) pm_set();
+    if (!s) return PM_ENOMEM;
+    s->algo = PM_ALGO_PFAC;
+    if (opt) s->params = *opt;
+    s->host_only = s->params.host_only != 0;
+    int rc = build_pfac(P, d, m, s->ac);
+    if (rc) {
+        delete s;
+        return rc;
+    }
+    return finish_compile(s, out);
+}
+
 int pm_wm_compile(const uint8_t *P, int64_t d, int32_t m, int32_t B, const pm_params *opt,
                   pm_set **out)
 {
@@ -363,7 +380,7 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
     std::memset(info, 0, sizeof(*info));
     info->algo = s->algo;
     info->device_bytes = s->device_bytes;
-    if (s->algo == PM_ALGO_AC) {
+    if (s->algo != PM_ALGO_WM) {
         const AcTables &t = s->ac;
         info->m = t.m;
         info->d = t.d;
@@ -393,7 +410,7 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
 // Wu-Manber: look-back tiles are warp tiles; no scratch
 static int64_t set_ws_bytes(const pm_set *s, int64_t n, bool list)
 {
-    if (s->algo == PM_ALGO_AC) return ac_workspace_bytes(s->ac, n, list);
+    if (s->algo != PM_ALGO_WM) return ac_workspace_bytes(s->ac, n, list);
     return workspace_bytes_for(warp_tiles(n), list, 0, 0);
 }
 
@@ -418,6 +435,9 @@ int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t f
     if (s->algo == PM_ALGO_AC)
         return ac_launch(s->ac, s->dac, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
                          d_workspace, stream);
+    if (s->algo == PM_ALGO_PFAC)
+        return pfac_launch(s->ac, s->dac, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
+                           d_workspace, stream);
     return wm_launch(s->wm, s->dwm, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
                      d_workspace, stream);
 }
@@ -694,6 +714,7 @@ int pm_selfcheck_host_walk(const pm_set *s, const uint8_t *T, int64_t n, pm_resu
         std::vector<uint64_t> occ;
         std::vector<int64_t> counts;
         if (s->algo == PM_ALGO_AC) host_walk_ac(s->ac, T, n, occ, counts);
+        else if (s->algo == PM_ALGO_PFAC) host_walk_pfac(s->ac, T, n, occ, counts);
         else host_walk_wm(s->wm, T, n, occ, counts);
         pm_result *r = new_result(int64_t(counts.size()), int64_t(occ.size()), true, false);
         if (!r) return PM_ENOMEM;

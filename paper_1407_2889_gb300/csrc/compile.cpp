@@ -292,6 +292,26 @@ static void build_wm_packed(const uint8_t *P, int64_t d, int32_t m, int32_t B, i
     t.dna = true;
 }
 
+// PFAC (failure-less Aho-Corasick): keep only the goto edges of the merged
+// table -- an edge whose target is one level deeper, or a match entry (the
+// edge into a depth-m terminal) -- and make every other entry 0, a dead end.
+int build_pfac(const uint8_t *P, int64_t d, int32_t m, AcTables &t)
+{
+    const int rc = build_ac(P, d, m, t);
+    if (rc) return rc;
+    const int64_t W = int64_t(1) << t.lw;
+    for (int64_t row = 0; row < t.n_rows; ++row) {
+        for (int64_t c = 0; c < W; ++c) {
+            uint32_t &e = t.table[size_t(row * W + c)];
+            if (row == 0) { e = 0; continue; }
+            if (e & 1u) continue;
+            const int64_t next = int64_t(e >> 1);
+            if (t.row_depth[size_t(next)] != t.row_depth[size_t(row)] + 1) e = 0;
+        }
+    }
+    return PM_OK;
+}
+
 int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTables &t)
 {
     if (!P || d < 1 || m < 1 || B < 1 || B > m || Bp < 1) return PM_EINVAL;
@@ -402,6 +422,42 @@ static void host_walk_wm_packed(const WmTables &t, const uint8_t *T, int64_t n,
         const uint32_t key = ((uint32_t(code) & bmask) << (2 * Bp)) | uint32_t(code >> (2 * (m - Bp)));
         for (uint32_t k = t.dir[key]; k < t.dir[key + 1]; ++k)
             if (t.ccode[k] == code) emit_entry(occ, counts, i - m + 1, t.cr[k]);
+    }
+}
+
+void host_walk_pfac(const AcTables &t, const uint8_t *T, int64_t n,
+                    std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
+{
+    counts.assign(size_t(t.d), 0);
+    occ.clear();
+    const uint32_t mid_base = uint32_t(t.d0_row << t.lw);
+    for (int64_t i = 0; i + t.m <= n; ++i) {
+        uint32_t e = 2u;  // root is row 1
+        for (int32_t j = 0; j < t.m; ++j) {
+            const uint32_t b = T[i + j];
+            uint32_t c;
+            if (t.dna) {
+                c = dna_code(b);
+                if (((t.lut >> (8 * c)) & 0xFFu) != b) break;
+            } else {
+                c = t.cls[b];
+                if (c == 0xFFu) break;
+            }
+            const uint32_t idx = ((e >> 1) << t.lw) | c;
+            e = t.table[idx];
+            if (e & 1u) {
+                const uint32_t v = t.mid[idx - mid_base];
+                if (v & 0x80000000u) {
+                    const uint32_t g = v & 0x7FFFFFFFu;
+                    for (uint32_t k = t.grp_off[g]; k < t.grp_off[g + 1]; ++k)
+                        emit_entry(occ, counts, i, t.grp_ids[k]);
+                } else {
+                    emit_entry(occ, counts, i, v);
+                }
+                break;
+            }
+            if (e == 0u) break;
+        }
     }
 }
 

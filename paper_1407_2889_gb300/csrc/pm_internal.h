@@ -87,12 +87,16 @@ struct WmTables {
 
 int build_ac(const uint8_t *P, int64_t d, int32_t m, AcTables &out);
 int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTables &out);
+// PFAC: build_ac, then every entry that is not a goto edge becomes 0 (dead)
+int build_pfac(const uint8_t *P, int64_t d, int32_t m, AcTables &out);
 
 // host walks used by pm_selfcheck_host_walk
 void host_walk_ac(const AcTables &t, const uint8_t *T, int64_t n,
                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
 void host_walk_wm(const WmTables &t, const uint8_t *T, int64_t n,
                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
+void host_walk_pfac(const AcTables &t, const uint8_t *T, int64_t n,
+                    std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
 
 // ---------------------------------------------------------------------------
 // Device side
@@ -170,6 +174,10 @@ int ac_launch_noalloc(const AcTables &t, const DevAc &dev, const uint8_t *d_text
                       bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
                       int64_t *d_n_occ, void *stream);
 int64_t ac_noalloc_limit_bytes();
+// PFAC scan (scan_ac.cu): same tables layout, workspace and outputs as AC
+int pfac_launch(const AcTables &t, const DevAc &dev, const uint8_t *d_text, int64_t n,
+                bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
+                int64_t *d_n_occ, void *d_ws, void *stream);
 // device workspace of an Aho-Corasick scan of n bytes
 int64_t ac_workspace_bytes(const AcTables &t, int64_t n, bool list);
 int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevWm &dev);

@@ -36,6 +36,8 @@
 #include <cstdio>
 #include <mutex>
 #include <type_traits>
+#include <utility>
+#include <vector>
 
 #include "ac_device.cuh"
 
@@ -570,6 +572,221 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
     }
 }
 
+// ---------------------------------------------------------------------------
+// PFAC scan: one walk per start position along goto edges only (Lin et al.'s
+// failure-less Aho-Corasick; the table is the merged one with every
+// non-goto entry 0). A warp takes its warp tile (staged like the DFA scan)
+// in 80 rounds of 32 consecutive positions, lane l walking position
+// 32 r + l from the root over at most m bytes; a walk that reaches depth m
+// is a match, one that meets a dead entry or a byte outside the alphabet
+// stops. A round's matches are compacted by ballot in position order into
+// the tile's slot, so the expand kernel of the DFA scan finishes the list.
+// ---------------------------------------------------------------------------
+template <typename E, bool DNA, bool HYB>
+__global__ void __launch_bounds__(512, 1) pfac_scan_kernel(const AcArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr uint32_t kGrp = sizeof(E) == 2 ? 0x8000u : 0x80000000u;
+    typedef typename std::conditional<sizeof(E) == 2, uint32_t, unsigned long long>::type SE;
+    constexpr int kOffShift = sizeof(E) == 2 ? 16 : 32;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int hv = a.m - 1 <= 16 ? 1 : a.m - 1 <= 32 ? 2 : 4;
+    const int BUF = kWarpTile + 16 * hv;
+
+    // ---- shared memory carve-up (the same as the DFA scan's) ----------------
+    unsigned char *p = smem;
+    E *s_tab = reinterpret_cast<E *>(p);
+    p += r16((long long)a.smem_entries * sizeof(E));
+    Ids<E> ids;
+    if (a.ids_smem) {
+        ids.mask = reinterpret_cast<const uint32_t *>(p);
+        p += r16((long long)a.nwords * 4);
+        ids.rank = reinterpret_cast<const E *>(p);
+        p += r16((long long)(a.nwords + 1) * sizeof(E));
+        ids.canon = reinterpret_cast<const E *>(p);
+        p += r16((long long)a.nterms * sizeof(E));
+    } else {
+        ids.mask = a.mask_g;
+        ids.rank = reinterpret_cast<const E *>(a.rank_g);
+        ids.canon = reinterpret_cast<const E *>(a.canon_g);
+    }
+    uint32_t *s_hist = a.hist_smem ? reinterpret_cast<uint32_t *>(p) : nullptr;
+    const long long hist_words = a.hist_smem == 2 ? (a.nterms + 1) / 2 : a.nterms;
+    p += a.hist_smem ? r16(hist_words * 4) : 0;
+    uint8_t *s_cls = p;
+    p += DNA ? 0 : 256;
+    p += warp * ac_warp_bytes(hv, a.pool_cap, sizeof(E));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(p);
+    uint8_t *buf = p + 16;
+
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.table_g);
+        uint4 *dst = reinterpret_cast<uint4 *>(s_tab);
+        const int nvec = int(((long long)a.smem_entries * sizeof(E) + 15) / 16);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
+    }
+    if (a.ids_smem) {
+        uint32_t *mk = const_cast<uint32_t *>(ids.mask);
+        for (int i = threadIdx.x; i < a.nwords; i += blockDim.x) mk[i] = a.mask_g[i];
+        E *rk = const_cast<E *>(ids.rank);
+        const E *rg = reinterpret_cast<const E *>(a.rank_g);
+        for (int i = threadIdx.x; i <= a.nwords; i += blockDim.x) rk[i] = rg[i];
+        E *cn = const_cast<E *>(ids.canon);
+        const E *cg = reinterpret_cast<const E *>(a.canon_g);
+        for (int i = threadIdx.x; i < a.nterms; i += blockDim.x) cn[i] = cg[i];
+    }
+    if (s_hist)
+        for (int i = threadIdx.x; i < hist_words; i += blockDim.x) s_hist[i] = 0u;
+    if (!DNA)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) s_cls[i] = a.cls_g[i];
+    if (lane == 0) dev::mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    dev::fence_proxy_async_smem();
+    __syncthreads();
+
+    const TableRef<E, HYB> tab{s_tab, reinterpret_cast<const E *>(a.table_g), uint32_t(a.smem_entries)};
+    const int m = a.m;
+    auto count_terminal = [&](uint32_t c) {
+        if (a.hist_smem == 1) {
+            atomicAdd(&s_hist[c], 1u);
+        } else if (a.hist_smem == 2) {
+            const uint32_t sh = (c & 1u) << 4;
+            const uint32_t old = atomicAdd(&s_hist[c >> 1], 1u << sh);
+            if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
+                atomicSub(&s_hist[c >> 1], 0x8000u << sh);
+                atomicAdd(&a.ccount[c], 0x8000ull);
+            }
+        } else {
+            atomicAdd(&a.ccount[c], 1ull);
+        }
+    };
+    auto mult_of = [&](uint32_t code) -> uint32_t {
+        if (!(code & kGrp)) return 1u;
+        const uint32_t g = code & ~kGrp;
+        return __ldg(a.grp_off + g + 1) - __ldg(a.grp_off + g);
+    };
+
+    const long long G = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    SE *slots = reinterpret_cast<SE *>(a.slots);
+    uint32_t phase = 0;
+    bool inflight = false;
+    bool failed = false;
+    unsigned long long my_total = 0;
+    if (gwarp < a.nsub) {
+        if (lane == 0) stage_issue(a, gwarp, buf, bar, BUF);
+        inflight = true;
+    }
+    for (long long st = gwarp; st < a.nsub && !failed; st += G) {
+        const bool got = __all_sync(kFull, dev::mbar_wait_bounded(bar, phase));
+        if (!got) {
+            if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutTma);
+            failed = true;
+            break;
+        }
+        inflight = false;
+        phase ^= 1u;
+        const long long tile0 = st * kWarpTile;
+        const int got_bytes = stage_bytes(a, st, BUF);
+        if (got_bytes < BUF) {
+            for (int b = got_bytes + lane; b < BUF; b += 32) {
+                const long long g = tile0 + b;
+                buf[b] = g < a.n ? a.text[g] : uint8_t(a.pad);
+            }
+        }
+        __syncwarp();
+        SE *dst = slots + st * kWarpTile;
+        uint32_t ent = 0, outs = 0;
+        for (int r = 0; r < kChunk; ++r) {
+            const int q = r * 32 + lane;  // start offset in the tile
+            bool hit = false;
+            uint32_t hidx = 0;
+            if (tile0 + q + m <= a.n) {
+                uint32_t e = 2u;  // root (row 1)
+                for (int j = 0; j < m; ++j) {
+                    const uint32_t b = buf[q + j];
+                    uint32_t c;
+                    if (DNA) {
+                        c = ((b >> 1) ^ (b >> 2)) & 3u;
+                        if (((a.lut >> (8 * c)) & 0xFFu) != b) break;
+                    } else {
+                        c = s_cls[b];
+                        if (c == 0xFFu) break;
+                    }
+                    const uint32_t idx = ((e >> 1) << a.lw) | c;
+                    e = tab(idx);
+                    if (e & 1u) { hit = true; hidx = idx; break; }
+                    if (e == 0u) break;
+                }
+            }
+            const uint32_t bal = __ballot_sync(kFull, hit);
+            if (hit) {
+                const uint32_t c = ids.terminal(hidx - a.mid_base);
+                const uint32_t code = ids.code(c);
+                count_terminal(c);
+                outs += mult_of(code);
+                if (a.list) dst[ent + __popc(bal & ((1u << lane) - 1u))] = ((SE)q << kOffShift) | (SE)code;
+            }
+            ent += __popc(bal);
+        }
+        // the buffer is free: stage this warp's next tile
+        dev::fence_proxy_async_smem();
+        __syncwarp();
+        if (st + G < a.nsub) {
+            if (lane == 0) stage_issue(a, st + G, buf, bar, BUF);
+            inflight = true;
+        }
+        if (!a.list) {
+            my_total += outs;
+            continue;
+        }
+        uint32_t o_tot = outs;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) o_tot += __shfl_xor_sync(kFull, o_tot, o);
+        if (lane == 31) {
+            a.tile_ent[st] = ent;
+            a.tile_out[st] = o_tot;
+            if (o_tot) atomicAdd(&a.seg_sum[st / a.seg_tiles], (unsigned long long)o_tot);
+        }
+    }
+    if (inflight) (void)dev::mbar_wait_bounded(bar, phase);
+
+    if (!a.list) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) my_total += __shfl_down_sync(kFull, my_total, o);
+        if (lane == 0 && my_total)
+            atomicAdd(reinterpret_cast<unsigned long long *>(a.n_occ), my_total);
+    }
+    __syncthreads();
+    if (s_hist) {
+        for (int c = threadIdx.x; c < a.nterms; c += blockDim.x) {
+            const uint32_t v = a.hist_smem == 2 ? (s_hist[c >> 1] >> ((c & 1) << 4)) & 0xFFFFu : s_hist[c];
+            if (v) atomicAdd(&a.ccount[c], (unsigned long long)v);
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.ws->done_ctas, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        const E *cg = reinterpret_cast<const E *>(a.canon_g);
+        for (int c = threadIdx.x; c < a.nterms; c += blockDim.x) {
+            const unsigned long long v = dev::ld_acquire(&a.ccount[c]);
+            const uint32_t code = cg[c];
+            if (code & kGrp) {
+                const uint32_t g = code & ~kGrp;
+                for (uint32_t j = a.grp_off[g]; j < a.grp_off[g + 1]; ++j)
+                    a.counts[a.grp_ids[j]] = (long long)v;
+            } else {
+                a.counts[code] = (long long)v;
+            }
+        }
+    }
+}
+
 typedef void (*AcKernel)(const AcArgs);
 
 struct Variant {
@@ -727,9 +944,18 @@ namespace {
 int slot_entry_bytes(const AcTables &t) { return (t.dna ? t.entry_bytes : 4) == 2 ? 4 : 8; }
 
 // Enqueue a whole scan on `st` with workspace `d_ws` (laid out by ac_ws_layout).
+AcKernel pfac_kernel_for(const AcTables &t, const DevAc &dv)
+{
+    const bool hyb = dv.smem_entries < ((long long)t.n_rows << t.lw);
+    const int eb = t.dna ? t.entry_bytes : 4;
+    if (!t.dna) return hyb ? pfac_scan_kernel<uint32_t, false, true> : pfac_scan_kernel<uint32_t, false, false>;
+    if (eb == 2) return hyb ? pfac_scan_kernel<uint16_t, true, true> : pfac_scan_kernel<uint16_t, true, false>;
+    return hyb ? pfac_scan_kernel<uint32_t, true, true> : pfac_scan_kernel<uint32_t, true, false>;
+}
+
 int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n, bool list,
                int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
-               cudaStream_t st)
+               cudaStream_t st, bool pfac = false)
 {
     cudaError_t e;
     const long long nsub = warp_tiles(n);
@@ -748,17 +974,22 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (n < t.m || nsub == 0) return PM_OK;
 
-    const Variant &v = kVariants[dv.variant];
+    const AcKernel fn = pfac ? pfac_kernel_for(t, dv) : kVariants[dv.variant].fn;
     {
+        // the attribute is per kernel and per device; kernels are few
         static std::mutex mu;
-        static int attr_bytes[64][sizeof(kVariants) / sizeof(kVariants[0])] = {};
+        static std::vector<std::pair<std::pair<int, const void *>, long long>> attr;
         int dev = 0;
         cudaGetDevice(&dev);
         std::lock_guard<std::mutex> lk(mu);
-        if (dev >= 0 && dev < 64 && attr_bytes[dev][dv.variant] < dv.smem_bytes) {
-            e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
+        long long *have = nullptr;
+        for (auto &x : attr)
+            if (x.first.first == dev && x.first.second == reinterpret_cast<const void *>(fn)) have = &x.second;
+        if (!have || *have < dv.smem_bytes) {
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
             if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-            attr_bytes[dev][dv.variant] = int(dv.smem_bytes);
+            if (have) *have = dv.smem_bytes;
+            else attr.push_back({{dev, reinterpret_cast<const void *>(fn)}, dv.smem_bytes});
         }
     }
     AcArgs a;
@@ -804,13 +1035,13 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
 
     const int threads = dv.warps * 32;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, threads, size_t(dv.smem_bytes));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, size_t(dv.smem_bytes));
     if (e != cudaSuccess || per_sm < 1) { set_cuda_error(int(e)); return PM_ECUDA; }
     long long grid = (long long)dp.sm_count * std::min(per_sm, dv.ctas_per_sm);
     const long long want = (nsub + dv.warps - 1) / dv.warps;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    v.fn<<<dim3(unsigned(grid)), dim3(unsigned(threads)), size_t(dv.smem_bytes), st>>>(a);
+    fn<<<dim3(unsigned(grid)), dim3(unsigned(threads)), size_t(dv.smem_bytes), st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (!list) return PM_OK;
@@ -855,6 +1086,14 @@ int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t
 {
     return ac_enqueue(t, dv, d_text, n, list, d_counts, d_occ, occ_cap, d_n_occ, d_ws,
                       static_cast<cudaStream_t>(stream));
+}
+
+int pfac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n, bool list,
+                int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
+                void *stream)
+{
+    return ac_enqueue(t, dv, d_text, n, list, d_counts, d_occ, occ_cap, d_n_occ, d_ws,
+                      static_cast<cudaStream_t>(stream), true);
 }
 
 // ---------------------------------------------------------------------------

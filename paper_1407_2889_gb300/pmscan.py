@@ -23,10 +23,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpmscan.so")
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ETOOBIG, PM_ETIMEOUT, PM_ECAPACITY, PM_ENODEV = range(8)
 PM_HOST_TEXT, PM_DEVICE_TEXT, PM_COUNTS_ONLY = 0, 1, 2
 PM_PLACE_AUTO, PM_PLACE_SMEM, PM_PLACE_HYBRID, PM_PLACE_GLOBAL = range(4)
-PM_ALGO_AC, PM_ALGO_WM = 1, 2
+PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC = 1, 2, 3
 
 EXPORTED = [
-    "pm_ac_compile", "pm_wm_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
+    "pm_ac_compile", "pm_pfac_compile", "pm_wm_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
     "pm_scan_to_host", "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device",
     "pm_scan_device_noalloc", "pm_noalloc_scratch_bytes", "pm_scan_status",
     "pm_scan_batch", "pm_batch_prepare", "pm_batch_free", "pm_batch_counts_total",
@@ -109,6 +109,8 @@ def lib():
         pp = ctypes.POINTER(vp)
         L.pm_ac_compile.restype = ctypes.c_int
         L.pm_ac_compile.argtypes = [vp, i64, i32, ctypes.POINTER(pm_params), pp]
+        L.pm_pfac_compile.restype = ctypes.c_int
+        L.pm_pfac_compile.argtypes = [vp, i64, i32, ctypes.POINTER(pm_params), pp]
         L.pm_wm_compile.restype = ctypes.c_int
         L.pm_wm_compile.argtypes = [vp, i64, i32, i32, ctypes.POINTER(pm_params), pp]
         L.pm_set_free.restype = None
@@ -238,6 +240,16 @@ def pm_ac_compile(P, params=None) -> int:
                                ctypes.byref(prm) if prm is not None else None, ctypes.byref(h)),
            "pm_ac_compile")
     return h.value
+
+
+def pm_pfac_compile(P, params=None) -> int:
+    P = _patterns(P)
+    h = ctypes.c_void_p()
+    p = _make_params(params)
+    _check(lib().pm_pfac_compile(P.ctypes.data, P.shape[0], P.shape[1],
+                                 ctypes.byref(p) if p is not None else None, ctypes.byref(h)),
+           "pm_pfac_compile")
+    return int(h.value)
 
 
 def pm_wm_compile(P, B: int, params=None) -> int:
@@ -465,6 +477,10 @@ class PatternSet:
     @classmethod
     def ac(cls, P, params=None) -> "PatternSet":
         return cls(pm_ac_compile(P, params), PM_ALGO_AC)
+
+    @classmethod
+    def pfac(cls, P, params=None) -> "PatternSet":
+        return cls(pm_pfac_compile(P, params), PM_ALGO_PFAC)
 
     @classmethod
     def wm(cls, P, B: int, params=None) -> "PatternSet":

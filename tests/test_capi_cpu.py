@@ -137,6 +137,23 @@ def test_ac_tables_match_oracle(alphabet):
         assert np.array_equal(occ, want_occ) and np.array_equal(cnt, want_cnt)
 
 
+@pytest.mark.parametrize("alphabet", [b"ACGT", b"ACGTN\n", b"AC", b"xyz", bytes(range(0, 256, 7))])
+def test_pfac_tables_match_oracle(alphabet):
+    """PFAC keeps only the goto edges of the merged table; a per-position
+    walk over them finds exactly the definition's occurrences."""
+    rng = np.random.default_rng(len(alphabet) * 53 + alphabet[0])
+    for _ in range(40):
+        T, P = _random_case(rng, alphabet)
+        want_occ, want_cnt = oracle.brute(T, P)
+        h = pm.pm_pfac_compile(P, HOST)
+        try:
+            assert pm.pm_set_get_info(h)["algo"] == pm.PM_ALGO_PFAC
+            occ, cnt = pm.pm_selfcheck_host_walk(h, T)
+        finally:
+            pm.pm_set_free(h)
+        assert np.array_equal(occ, want_occ) and np.array_equal(cnt, want_cnt)
+
+
 @pytest.mark.parametrize("B", [1, 2, 3, 4])
 def test_wm_tables_match_oracle(B):
     rng = np.random.default_rng(100 + B)

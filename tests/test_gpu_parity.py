@@ -76,6 +76,32 @@ def test_ac_random_small(alphabet):
         s.close()
 
 
+@pytest.mark.parametrize("alphabet", [b"ACGT", b"ACGTN\n", b"AC", b"xyzw#", bytes(range(1, 250, 3))])
+def test_pfac_random_small(alphabet):
+    rng = np.random.default_rng(alphabet[0] * 11 + len(alphabet))
+    for case in range(20):
+        T, P = _random_case(rng, alphabet, m_max=65 if case % 3 == 0 else 20)
+        want = oracle.brute(T, P)
+        s = pm.PatternSet.pfac(P)
+        _same(s.scan(T), want, f"PFAC case {case} n={T.size} m={P.shape[1]} d={P.shape[0]}")
+        occ, cnt = s.scan(torch.from_numpy(T).cuda(), counts_only=True)
+        assert occ.size == 0 and np.array_equal(cnt, want[1])
+        s.close()
+
+
+def test_pfac_est_sets_and_every_position_matching(est_text_full):
+    T = est_text_full[: 32 << 20]
+    for d, m in ((1000, 8), (8000, 8), (20000, 16), (8000, 32)):
+        _, P = synth.est_case(d, m, text=est_text_full)
+        s = pm.PatternSet.pfac(P)
+        _same(s.scan(T), oracle.dictionary(T, P, threads=THREADS), f"PFAC d={d} m={m}")
+        s.close()
+    A = np.full(300000, ord("A"), np.uint8)
+    s = pm.PatternSet.pfac(np.full((3, 8), ord("A"), np.uint8))
+    _same(s.scan(A), oracle.dictionary(A, np.full((3, 8), ord("A"), np.uint8)), "PFAC all hits")
+    s.close()
+
+
 @pytest.mark.parametrize("B", [1, 2, 3, 4])
 def test_wm_random_small(B):
     rng = np.random.default_rng(1000 + B)
