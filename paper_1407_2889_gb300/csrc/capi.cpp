@@ -109,6 +109,8 @@ void release_device(pm_set *s)
                     s->c_text, s->c_ws, s->c_out, s->c_counts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (s->c_pin) cudaFreeHost(s->c_pin);
+    s->c_pin = nullptr;
     s->dac = DevAc();
     s->dwm = DevWm();
     s->c_text = s->c_ws = s->c_out = s->c_counts = nullptr;
@@ -596,7 +598,7 @@ int scan_cached(pm_set *s, const uint8_t *T, int64_t n, uint32_t flags, void *st
     if (rc) return rc;
     if (!s->c_counts) {
         void *p = nullptr;
-        cudaError_t e = cudaMalloc(&p, size_t(d + 1) * 8);
+        cudaError_t e = cudaMalloc(&p, size_t(d + 2) * 8);
         if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); return PM_ENOMEM; }
         s->c_counts = p;
     }
@@ -656,6 +658,117 @@ int pm_scan(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flags, void 
     return PM_OK;
 }
 
+}  // extern "C"
+
+namespace pm {
+namespace {
+// pm_scan_to_host of a long host text with an Aho-Corasick or PFAC set, in
+// pieces split with an m-1 halo (each piece owns the windows that start in
+// it, as Section 4.3 splits the text over nodes): the copy of piece c+1 runs
+// while piece c is scanned, and the keys of each piece leave for the host as
+// soon as its running total is known. `done` false: take the plain path.
+int scan_to_host_pieces(pm_set *s, const uint8_t *T, int64_t n, uint32_t flags, int64_t *counts_out,
+                        uint64_t *occ_out, int64_t occ_capacity, int64_t *n_occ_out, void *stream,
+                        bool &done)
+{
+    done = false;
+    constexpr int64_t kMinPiece = int64_t(64) << 20;
+    if (s->algo == PM_ALGO_WM || (flags & PM_DEVICE_TEXT) || n < 2 * kMinPiece) return PM_OK;
+    const AcTables &t = s->ac;
+    const bool list = !(flags & PM_COUNTS_ONLY);
+    const int64_t d = t.d, m = t.m;
+    int64_t K = std::min<int64_t>(16, n / kMinPiece);
+    const int64_t piece = ((n + K - 1) / K + 15) & ~int64_t(15);  // 16-byte aligned starts
+    K = (n + piece - 1) / piece;
+    int rc = ensure(s->c_text, s->c_text_cap, n);
+    if (!rc) rc = ensure(s->c_ws, s->c_ws_cap, ac_workspace_bytes(t, piece + m - 1, list));
+    if (!rc && list) {
+        int64_t want = std::max<int64_t>(s->c_out_cap / 8, n / 16 + 1024);
+        rc = ensure(s->c_out, s->c_out_cap, want * 8);
+    }
+    if (rc) return rc;
+    if (!s->c_counts) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, size_t(d + 2) * 8);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); return PM_ENOMEM; }
+        s->c_counts = p;
+    }
+    if (!s->c_pin) {
+        cudaError_t e = cudaMallocHost(&s->c_pin, 16 * 8);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); s->c_pin = nullptr; return PM_ENOMEM; }
+    }
+    int64_t *d_counts = static_cast<int64_t *>(s->c_counts);
+    int64_t *d_nocc = d_counts + d;
+    unsigned long long *run = reinterpret_cast<unsigned long long *>(d_counts + d + 1);
+    int64_t *pin = static_cast<int64_t *>(s->c_pin);
+    uint8_t *text = static_cast<uint8_t *>(s->c_text);
+    uint64_t *occ = static_cast<uint64_t *>(s->c_out);
+    const int64_t cap_dev = list ? s->c_out_cap / 8 : 0;
+    cudaStream_t sc = static_cast<cudaStream_t>(stream), si = nullptr, so = nullptr;
+    std::vector<cudaEvent_t> ev(size_t(2 * K), nullptr);
+    auto cleanup = [&]() {
+        if (si) cudaStreamDestroy(si);
+        if (so) cudaStreamDestroy(so);
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&si, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&so, cudaStreamNonBlocking);
+    for (size_t i = 0; i < ev.size() && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemsetAsync(run, 0, 8, sc);
+    // the first copy must not overtake work already queued on the caller's stream
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], sc);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(si, ev[0], 0);
+    for (int64_t c = 0; c < K && e == cudaSuccess && !rc; ++c) {
+        const int64_t off = c * piece, len = std::min(piece, n - off);
+        const int64_t nc = std::min(len + m - 1, n - off);
+        e = cudaMemcpyAsync(text + off, T + off, size_t(nc), cudaMemcpyHostToDevice, si);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[size_t(2 * c)], si);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, ev[size_t(2 * c)], 0);
+        if (e != cudaSuccess) break;
+        rc = ac_launch_piece(t, s->dac, s->algo == PM_ALGO_PFAC, text + off, nc, list, d_counts, occ, cap_dev,
+                             d_nocc, s->c_ws, sc, c == 0, c == 0 ? nullptr : run, (unsigned long long)off);
+        if (rc) break;
+        if (list) e = cudaMemcpyAsync(run, d_nocc, 8, cudaMemcpyDeviceToDevice, sc);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pin + c, d_nocc, 8, cudaMemcpyDeviceToHost, sc);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[size_t(2 * c + 1)], sc);
+    }
+    int64_t prev = 0, total = 0;
+    for (int64_t c = 0; c < K && e == cudaSuccess && !rc; ++c) {
+        e = cudaEventSynchronize(ev[size_t(2 * c + 1)]);
+        if (e != cudaSuccess) break;
+        total = pin[c];
+        if (!list) continue;
+        const int64_t hi = std::min(total, std::min(occ_capacity, cap_dev));
+        if (hi > prev) {
+            e = cudaMemcpyAsync(occ_out + prev, occ + prev, size_t(hi - prev) * 8, cudaMemcpyDeviceToHost, so);
+            prev = hi;
+        }
+    }
+    if (e == cudaSuccess && !rc) e = cudaMemcpyAsync(counts_out, d_counts, size_t(d) * 8, cudaMemcpyDeviceToHost, sc);
+    if (e == cudaSuccess && !rc) e = cudaStreamSynchronize(so);
+    if (e == cudaSuccess && !rc) e = cudaStreamSynchronize(sc);
+    cleanup();
+    if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); return PM_ECUDA; }
+    if (rc) return rc;
+    rc = pm_scan_status(s->c_ws, stream);
+    if (rc) return rc;
+    if (list && total > cap_dev) {
+        // the device buffer was short: the plain path sizes it exactly
+        s->c_out_cap = 0;
+        int rc2 = ensure(s->c_out, s->c_out_cap, total * 8);
+        return rc2;  // done stays false
+    }
+    *n_occ_out = total;
+    done = true;
+    return (list && total > occ_capacity) ? PM_ECAPACITY : PM_OK;
+}
+}  // namespace
+}  // namespace pm
+
+extern "C" {
+
 int pm_scan_to_host(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flags,
                     int64_t *counts_out, uint64_t *occ_out, int64_t occ_capacity,
                     int64_t *n_occ_out, void *stream)
@@ -668,8 +781,11 @@ int pm_scan_to_host(const pm_set *cs, const uint8_t *T, int64_t n, uint32_t flag
     if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
     pm_set *s = const_cast<pm_set *>(cs);
     const int64_t d = set_d(s);
+    bool done = false;
+    int rc = scan_to_host_pieces(s, T, n, flags, counts_out, occ_out, occ_capacity, n_occ_out, stream, done);
+    if (done || rc) return rc;
     int64_t *d_counts = nullptr, n_occ = 0;
-    int rc = scan_cached(s, T, n, flags, stream, &d_counts, &n_occ);
+    rc = scan_cached(s, T, n, flags, stream, &d_counts, &n_occ);
     if (rc) return rc;
     cudaError_t e = cudaMemcpy(counts_out, d_counts, size_t(d) * 8, cudaMemcpyDeviceToHost);
     const int64_t k = list ? (n_occ < occ_capacity ? n_occ : occ_capacity) : 0;

@@ -174,6 +174,14 @@ int ac_launch_noalloc(const AcTables &t, const DevAc &dev, const uint8_t *d_text
                       bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
                       int64_t *d_n_occ, void *stream);
 int64_t ac_noalloc_limit_bytes();
+// One piece of a longer Aho-Corasick / PFAC scan (the text split with an
+// m-1 halo, as Section 4.3 splits it over nodes): the first piece zeroes the
+// results, later ones add to them; keys go after *occ_base keys with
+// positions shifted by pos_base; *d_n_occ receives the running total.
+int ac_launch_piece(const AcTables &t, const DevAc &dev, bool pfac, const uint8_t *d_text, int64_t n,
+                    bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ,
+                    void *d_ws, void *stream, bool first, const unsigned long long *occ_base,
+                    unsigned long long pos_base);
 // PFAC scan (scan_ac.cu): same tables layout, workspace and outputs as AC
 int pfac_launch(const AcTables &t, const DevAc &dev, const uint8_t *d_text, int64_t n,
                 bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
@@ -261,5 +269,6 @@ struct pm_set {
     void *c_text = nullptr;  int64_t c_text_cap = 0;
     void *c_ws = nullptr;    int64_t c_ws_cap = 0;
     void *c_out = nullptr;   int64_t c_out_cap = 0;   // uint64 entries
-    void *c_counts = nullptr;                         // int64[d] + n_occ
+    void *c_counts = nullptr;                         // int64[d] + n_occ + running total
+    void *c_pin = nullptr;                            // page-locked per-piece totals
 };

@@ -33,6 +33,7 @@
 // many resident warps copies the slots to the sorted (i, r) keys, one key per
 // pattern of a group of equal patterns (the paper's coalesced writes,
 // GPU-CW).
+#include <cstddef>
 #include <cstdio>
 #include <mutex>
 #include <type_traits>
@@ -436,7 +437,8 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
               const uint32_t *__restrict__ tile_out, const unsigned long long *__restrict__ seg_sum,
               long long nseg, long long seg_tiles, long long nsub,
               const uint32_t *__restrict__ grp_off, const uint32_t *__restrict__ grp_ids,
-              unsigned long long *__restrict__ occ, long long occ_cap, long long *n_occ)
+              unsigned long long *__restrict__ occ, long long occ_cap, long long *n_occ,
+              const unsigned long long *occ_base, unsigned long long pos_base)
 {
     extern __shared__ __align__(16) unsigned char esm[];
     unsigned long long *s_off = reinterpret_cast<unsigned long long *>(esm);  // seg_tiles + 1
@@ -456,7 +458,8 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
     if (lane == 0) s_red[warp] = part;
     __syncthreads();
-    unsigned long long seg_base = 0;
+    // a chunk of a longer scan writes after the keys of the chunks before it
+    unsigned long long seg_base = occ_base ? *occ_base : 0ull;
 #pragma unroll
     for (int w = 0; w < NW; ++w) seg_base += s_red[w];
     __syncthreads();
@@ -498,7 +501,7 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
         const uint32_t ent = s_ent[q];
         unsigned long long base = s_off[q];
         const SE *src = slots + st * kWarpTile;
-        const uint32_t tile0 = uint32_t(st * kWarpTile);
+        const uint32_t tile0 = uint32_t(pos_base + (unsigned long long)st * kWarpTile);
         for (uint32_t g0 = 0; g0 < ent; g0 += NCH * 32 * PER) {
             SE v[NCH][PER];
 #pragma unroll
@@ -953,9 +956,13 @@ AcKernel pfac_kernel_for(const AcTables &t, const DevAc &dv)
     return hyb ? pfac_scan_kernel<uint32_t, true, true> : pfac_scan_kernel<uint32_t, true, false>;
 }
 
+// first: this scan starts a result (counts, totals and per-terminal counters
+// start at zero); later chunks of a longer scan keep adding to them, write
+// their keys after occ_base keys and shift positions by pos_base.
 int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n, bool list,
                int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
-               cudaStream_t st, bool pfac = false)
+               cudaStream_t st, bool pfac = false, bool first = true,
+               const unsigned long long *occ_base = nullptr, unsigned long long pos_base = 0)
 {
     cudaError_t e;
     const long long nsub = warp_tiles(n);
@@ -968,11 +975,23 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     // every segment non-empty: at most ac_segments() of them
     const long long seg_tiles = (nsub + ac_segments(nsub, dp.sm_count) - 1) / ac_segments(nsub, dp.sm_count);
     const long long nseg = (nsub + seg_tiles - 1) / seg_tiles;
-    e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_ws, 0, size_t(L.zeroed), st);
+    if (first) {
+        e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_ws, 0, size_t(L.zeroed), st);
+    } else {
+        // keep the status word and the per-terminal counters
+        e = cudaMemsetAsync(static_cast<char *>(d_ws) + offsetof(dev::WsHeader, done_ctas), 0, 4, st);
+        if (e == cudaSuccess && L.zeroed > L.seg_sum)
+            e = cudaMemsetAsync(static_cast<char *>(d_ws) + L.seg_sum, 0, size_t(L.zeroed - L.seg_sum), st);
+    }
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-    if (n < t.m || nsub == 0) return PM_OK;
+    if (n < t.m || nsub == 0) {
+        // nothing to scan in this piece: the key total stays that of the pieces before
+        if (list && occ_base && !first) e = cudaMemcpyAsync(d_n_occ, occ_base, 8, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+        return PM_OK;
+    }
 
     const AcKernel fn = pfac ? pfac_kernel_for(t, dv) : kVariants[dv.variant].fn;
     {
@@ -1061,11 +1080,11 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     if (se == 4)
         expand_kernel<uint32_t, 16, 0x8000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
             static_cast<const uint32_t *>(a.slots), a.tile_ent, a.tile_out, a.seg_sum, nseg, seg_tiles, nsub,
-            dv.grp_off, dv.grp_ids, occ, cap, a.n_occ);
+            dv.grp_off, dv.grp_ids, occ, cap, a.n_occ, occ_base, pos_base);
     else
         expand_kernel<unsigned long long, 32, 0x80000000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
             static_cast<const unsigned long long *>(a.slots), a.tile_ent, a.tile_out, a.seg_sum, nseg,
-            seg_tiles, nsub, dv.grp_off, dv.grp_ids, occ, cap, a.n_occ);
+            seg_tiles, nsub, dv.grp_off, dv.grp_ids, occ, cap, a.n_occ, occ_base, pos_base);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     return PM_OK;
@@ -1086,6 +1105,15 @@ int ac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t
 {
     return ac_enqueue(t, dv, d_text, n, list, d_counts, d_occ, occ_cap, d_n_occ, d_ws,
                       static_cast<cudaStream_t>(stream));
+}
+
+int ac_launch_piece(const AcTables &t, const DevAc &dv, bool pfac, const uint8_t *d_text, int64_t n,
+                    bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ,
+                    void *d_ws, void *stream, bool first, const unsigned long long *occ_base,
+                    unsigned long long pos_base)
+{
+    return ac_enqueue(t, dv, d_text, n, list, d_counts, d_occ, occ_cap, d_n_occ, d_ws,
+                      static_cast<cudaStream_t>(stream), pfac, first, occ_base, pos_base);
 }
 
 int pfac_launch(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_t n, bool list,

@@ -364,6 +364,35 @@ def test_large_sets_full_text(est_text_full, d):
     w.close()
 
 
+def test_scan_to_host_in_pieces(est_text_full):
+    """Long host texts go through pm_scan_to_host in pieces (copies
+    overlapping scans, keys leaving per piece); results equal one scan of the
+    whole text, also with a short capacity, in counts-only mode and for PFAC."""
+    T = est_text_full[: (200 << 20) + 12345]
+    _, P = synth.est_case(1000, 8, text=est_text_full)
+    want_occ, want_cnt = oracle.dictionary(T, P, threads=THREADS)
+    pinned = torch.from_numpy(T).pin_memory()
+    for make in (_ac, pm.PatternSet.pfac):
+        s = make(P)
+        counts = torch.zeros(P.shape[0], dtype=torch.int64).pin_memory()
+        occ = torch.zeros(want_occ.size + 7, dtype=torch.int64).pin_memory()
+        for rep in range(2):
+            counts.zero_()
+            total = pm.pm_scan_to_host(s.h, pinned, counts, occ)
+            assert total == want_occ.size
+            assert np.array_equal(occ.numpy()[:total].view(np.uint64), want_occ)
+            assert np.array_equal(counts.numpy(), want_cnt)
+        short = torch.zeros(want_occ.size // 3, dtype=torch.int64).pin_memory()
+        with pytest.raises(pm.PmError) as e:
+            pm.pm_scan_to_host(s.h, pinned, counts, short)
+        assert e.value.code == pm.PM_ECAPACITY
+        assert np.array_equal(short.numpy().view(np.uint64), want_occ[: short.numel()])
+        counts.zero_()
+        assert pm.pm_scan_to_host(s.h, pinned, counts, None, pm.PM_COUNTS_ONLY) == want_occ.size
+        assert np.array_equal(counts.numpy(), want_cnt)
+        s.close()
+
+
 def test_scan_to_host_pinned_buffers_and_capacity():
     T = synth.est_text(1 << 21, 9)
     P = synth.mixed_patterns(T, 500, 8, 9)
