@@ -425,9 +425,11 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
 // warp tiles of segment b: its output base is the sum of the earlier
 // segments' totals (added up by the scan), each tile's offset inside the
 // segment comes from a block scan of the tiles' totals kept in shared
-// memory, and its warps then copy one tile at a time with 16-byte slot
-// loads. A chunk that names a group of equal patterns takes a running prefix
-// over the entries' multiplicities instead. The last CTA writes the total.
+// memory, and its warps then copy one tile at a time in rows of 32 entries
+// (lane l takes entry l of a row, eight rows loaded together), so slot loads
+// and key stores are both coalesced. A row that names a group of equal
+// patterns takes a warp prefix over the entries' multiplicities instead. The
+// CTA that owns the last tile writes the total.
 // ---------------------------------------------------------------------------
 constexpr int kExpandThreads = 512;
 
@@ -493,8 +495,7 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
     __syncthreads();
 
     const unsigned long long cap = (unsigned long long)occ_cap;
-    constexpr int PER = 4;   // slot entries per lane per chunk (one or two 16-byte loads)
-    constexpr int NCH = 4;   // chunks loaded together (512 entries)
+    constexpr int R = 8;  // rows of 32 entries loaded together; lane l takes entry 32 u + l of a row
     constexpr uint32_t kMask = (uint32_t)((((SE)1) << kOffShift) - 1);
     for (long long q = warp; q < nt; q += NW) {
         const long long st = t0 + q;
@@ -502,72 +503,43 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
         unsigned long long base = s_off[q];
         const SE *src = slots + st * kWarpTile;
         const uint32_t tile0 = uint32_t(pos_base + (unsigned long long)st * kWarpTile);
-        for (uint32_t g0 = 0; g0 < ent; g0 += NCH * 32 * PER) {
-            SE v[NCH][PER];
+        for (uint32_t g0 = 0; g0 < ent; g0 += R * 32) {
+            SE v[R];
 #pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) {
-                const uint32_t j = g0 + ch * 32 * PER + lane * PER;
-                if (g0 + ch * 32 * PER < ent) {
-                    if (sizeof(SE) == 4) {
-                        const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src + j));
-                        v[ch][0] = (SE)x.x; v[ch][1] = (SE)x.y; v[ch][2] = (SE)x.z; v[ch][3] = (SE)x.w;
-                    } else {
-                        const ulonglong2 x = __ldcs(reinterpret_cast<const ulonglong2 *>(src + j));
-                        const ulonglong2 y = __ldcs(reinterpret_cast<const ulonglong2 *>(src + j) + 1);
-                        v[ch][0] = (SE)x.x; v[ch][1] = (SE)x.y; v[ch][2] = (SE)y.x; v[ch][3] = (SE)y.y;
-                    }
-                } else {
-#pragma unroll
-                    for (int u = 0; u < PER; ++u) v[ch][u] = 0;
-                }
+            for (int u = 0; u < R; ++u) {
+                const uint32_t j = g0 + u * 32 + lane;
+                v[u] = j < ent ? __ldcs(src + j) : (SE)0;
             }
 #pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) {
-                const uint32_t j0 = g0 + ch * 32 * PER;
-                if (j0 >= ent) break;
-                const uint32_t j = j0 + lane * PER;
-                bool grp = false;
-#pragma unroll
-                for (int u = 0; u < PER; ++u) grp |= j + u < ent && (uint32_t(v[ch][u] & kMask) & kGrp);
+            for (int u = 0; u < R; ++u) {
+                const uint32_t row = g0 + u * 32;
+                if (row >= ent) break;
+                const uint32_t cnt = min(ent - row, 32u);
+                const bool valid = uint32_t(lane) < cnt;
+                const uint32_t code = uint32_t(v[u] & kMask);
+                const unsigned long long key_hi = (unsigned long long)(tile0 + uint32_t(v[u] >> kOffShift)) << 32;
+                const bool grp = valid && (code & kGrp);
                 if (!__any_sync(kFull, grp)) {
-#pragma unroll
-                    for (int u = 0; u < PER; ++u) {
-                        const unsigned long long gi = base + (j - j0) + u;
-                        if (j + u < ent && gi < cap)
-                            occ[gi] = ((unsigned long long)(tile0 + uint32_t(v[ch][u] >> kOffShift)) << 32) |
-                                      uint32_t(v[ch][u] & kMask);
-                    }
-                    base += min(ent - j0, uint32_t(32 * PER));
+                    // one key per entry: consecutive lanes write consecutive keys
+                    const unsigned long long gi = base + lane;
+                    if (valid && gi < cap) occ[gi] = key_hi | code;
+                    base += cnt;
                     continue;
                 }
-                // multiplicities, then the lane's keys in entry order
-                uint32_t lo[PER], mult[PER], msum = 0;
-#pragma unroll
-                for (int u = 0; u < PER; ++u) {
-                    const uint32_t code = uint32_t(v[ch][u] & kMask);
-                    lo[u] = code;
-                    mult[u] = j + u < ent ? 1u : 0u;
-                    if (j + u < ent && (code & kGrp)) {
-                        const uint32_t g = code & ~kGrp;
-                        lo[u] = __ldg(grp_off + g);
-                        mult[u] = __ldg(grp_off + g + 1) - lo[u];
-                    }
-                    msum += mult[u];
+                // a row naming a group of equal patterns: prefix over the multiplicities
+                uint32_t lo = code, mult = valid ? 1u : 0u;
+                if (grp) {
+                    const uint32_t g = code & ~kGrp;
+                    lo = __ldg(grp_off + g);
+                    mult = __ldg(grp_off + g + 1) - lo;
                 }
-                const uint32_t incl = dev::warp_incl_scan(msum, lane);
-                unsigned long long gb = base + (incl - msum);
-#pragma unroll
-                for (int u = 0; u < PER; ++u) {
-                    const uint32_t code = uint32_t(v[ch][u] & kMask);
-                    const unsigned long long key_hi =
-                        (unsigned long long)(tile0 + uint32_t(v[ch][u] >> kOffShift)) << 32;
-                    if (!(code & kGrp)) {
-                        if (mult[u] && gb < cap) occ[gb] = key_hi | code;
-                    } else {
-                        for (uint32_t k = 0; k < mult[u]; ++k)
-                            if (gb + k < cap) occ[gb + k] = key_hi | __ldg(grp_ids + lo[u] + k);
-                    }
-                    gb += mult[u];
+                const uint32_t incl = dev::warp_incl_scan(mult, lane);
+                const unsigned long long gb = base + (incl - mult);
+                if (!grp) {
+                    if (mult && gb < cap) occ[gb] = key_hi | code;
+                } else {
+                    for (uint32_t k = 0; k < mult; ++k)
+                        if (gb + k < cap) occ[gb + k] = key_hi | __ldg(grp_ids + lo + k);
                 }
                 base += __shfl_sync(kFull, incl, 31);
             }
