@@ -440,7 +440,7 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
               long long nseg, long long seg_tiles, long long nsub,
               const uint32_t *__restrict__ grp_off, const uint32_t *__restrict__ grp_ids,
               unsigned long long *__restrict__ occ, long long occ_cap, long long *n_occ,
-              const unsigned long long *occ_base, unsigned long long pos_base)
+              const unsigned long long *occ_base, unsigned long long pos_base, long long ngo, long long ngi)
 {
     extern __shared__ __align__(16) unsigned char esm[];
     unsigned long long *s_off = reinterpret_cast<unsigned long long *>(esm);  // seg_tiles + 1
@@ -492,58 +492,114 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
         run += o;
     }
     if (tid == kExpandThreads - 1 && t0 + nt == nsub) *n_occ = (long long)run;  // the last tile's CTA
+    // small group tables move to shared memory: their loads sit on a row's
+    // critical path (ngo = 0: they stay in device memory)
+    uint32_t *s_grp = s_ent + seg_tiles;
+    const uint32_t *go = grp_off, *gid = grp_ids;
+    if (ngo > 0) {
+        for (long long i = tid; i < ngo; i += kExpandThreads) s_grp[i] = grp_off[i];
+        for (long long i = tid; i < ngi; i += kExpandThreads) s_grp[ngo + i] = grp_ids[i];
+        go = s_grp;
+        gid = s_grp + ngo;
+    }
     __syncthreads();
 
     const unsigned long long cap = (unsigned long long)occ_cap;
     constexpr int R = 8;  // rows of 32 entries loaded together; lane l takes entry 32 u + l of a row
     constexpr uint32_t kMask = (uint32_t)((((SE)1) << kOffShift) - 1);
-    for (long long q = warp; q < nt; q += NW) {
-        const long long st = t0 + q;
-        const uint32_t ent = s_ent[q];
-        unsigned long long base = s_off[q];
-        const SE *src = slots + st * kWarpTile;
-        const uint32_t tile0 = uint32_t(pos_base + (unsigned long long)st * kWarpTile);
-        for (uint32_t g0 = 0; g0 < ent; g0 += R * 32) {
-            SE v[R];
+    // The warp's work items are (tile q, first entry g0) in order; the slot
+    // loads of the next item are in flight while the current one is written.
+    auto load = [&](SE (&x)[R], long long qq, uint32_t gg) {
+        const uint32_t ent = s_ent[qq];
+        const SE *src = slots + (t0 + qq) * kWarpTile;
 #pragma unroll
-            for (int u = 0; u < R; ++u) {
-                const uint32_t j = g0 + u * 32 + lane;
-                v[u] = j < ent ? __ldcs(src + j) : (SE)0;
-            }
-#pragma unroll
-            for (int u = 0; u < R; ++u) {
-                const uint32_t row = g0 + u * 32;
-                if (row >= ent) break;
-                const uint32_t cnt = min(ent - row, 32u);
-                const bool valid = uint32_t(lane) < cnt;
-                const uint32_t code = uint32_t(v[u] & kMask);
-                const unsigned long long key_hi = (unsigned long long)(tile0 + uint32_t(v[u] >> kOffShift)) << 32;
-                const bool grp = valid && (code & kGrp);
-                if (!__any_sync(kFull, grp)) {
-                    // one key per entry: consecutive lanes write consecutive keys
-                    const unsigned long long gi = base + lane;
-                    if (valid && gi < cap) occ[gi] = key_hi | code;
-                    base += cnt;
-                    continue;
-                }
-                // a row naming a group of equal patterns: prefix over the multiplicities
-                uint32_t lo = code, mult = valid ? 1u : 0u;
-                if (grp) {
-                    const uint32_t g = code & ~kGrp;
-                    lo = __ldg(grp_off + g);
-                    mult = __ldg(grp_off + g + 1) - lo;
-                }
-                const uint32_t incl = dev::warp_incl_scan(mult, lane);
-                const unsigned long long gb = base + (incl - mult);
-                if (!grp) {
-                    if (mult && gb < cap) occ[gb] = key_hi | code;
-                } else {
-                    for (uint32_t k = 0; k < mult; ++k)
-                        if (gb + k < cap) occ[gb + k] = key_hi | __ldg(grp_ids + lo + k);
-                }
-                base += __shfl_sync(kFull, incl, 31);
-            }
+        for (int u = 0; u < R; ++u) {
+            const uint32_t j = gg + u * 32 + lane;
+            x[u] = j < ent ? __ldcs(src + j) : (SE)0;
         }
+    };
+    long long q = warp;
+    while (q < nt && s_ent[q] == 0) q += NW;
+    uint32_t g0 = 0;
+    SE v[R];
+    if (q < nt) load(v, q, 0);
+    // keys of the current tile go to out[0 .. room): 32-bit offsets from the
+    // tile's base, clipped to the capacity left after it
+    unsigned long long *out = occ;
+    uint32_t room = 0, pos = 0;
+    auto enter = [&](long long qq) {
+        const unsigned long long b = s_off[qq];
+        out = occ + b;
+        room = b < cap ? uint32_t(min(cap - b, 0xFFFFFFFFull)) : 0u;
+        pos = 0;
+    };
+    if (q < nt) enter(q);
+    const uint32_t lt = (1u << lane) - 1u;
+    while (q < nt) {
+        const uint32_t ent = s_ent[q];
+        long long qn = q;
+        uint32_t gn = g0 + R * 32;
+        if (gn >= ent) {
+            gn = 0;
+            qn += NW;
+            while (qn < nt && s_ent[qn] == 0) qn += NW;
+        }
+        SE w[R];
+        if (qn < nt) {
+            load(w, qn, gn);
+        } else {
+#pragma unroll
+            for (int u = 0; u < R; ++u) w[u] = (SE)0;
+        }
+        const uint32_t tile0 = uint32_t(pos_base + (unsigned long long)(t0 + q) * kWarpTile);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const uint32_t row = g0 + u * 32;
+            if (row >= ent) break;
+            const uint32_t cnt = min(ent - row, 32u);
+            const bool valid = uint32_t(lane) < cnt;   // the valid lanes are 0 .. cnt-1
+            const uint32_t code = uint32_t(v[u] & kMask);
+            const unsigned long long key_hi = (unsigned long long)(tile0 + uint32_t(v[u] >> kOffShift)) << 32;
+            const bool grp = valid && (code & kGrp);
+            if (!__any_sync(kFull, grp)) {
+                // one key per entry: consecutive lanes write consecutive keys
+                const uint32_t o = pos + lane;
+                if (valid && o < room) out[o] = key_hi | code;
+                pos += cnt;
+                continue;
+            }
+            // a row naming a group of equal patterns: exclusive prefix over
+            // the multiplicities (from ballots while every group adds at most 3)
+            uint32_t lo = code, mult = valid ? 1u : 0u;
+            if (grp) {
+                const uint32_t g = code & ~kGrp;
+                lo = go[g];
+                mult = go[g + 1] - lo;
+            }
+            const uint32_t extra = grp ? mult - 1u : 0u;
+            uint32_t excl, tot;
+            if (__all_sync(kFull, extra < 4u)) {
+                const uint32_t e0 = __ballot_sync(kFull, extra & 1u);
+                const uint32_t e1 = __ballot_sync(kFull, extra & 2u);
+                excl = uint32_t(lane) + __popc(e0 & lt) + 2u * __popc(e1 & lt);
+                tot = cnt + __popc(e0) + 2u * __popc(e1);
+            } else {
+                const uint32_t incl = dev::warp_incl_scan(mult, lane);
+                excl = incl - mult;
+                tot = __shfl_sync(kFull, incl, 31);
+            }
+            const uint32_t o0 = pos + excl;
+            for (uint32_t k = 0; k < mult; ++k) {
+                const uint32_t id = grp ? gid[lo + k] : code;
+                if (o0 + k < room) out[o0 + k] = key_hi | id;
+            }
+            pos += tot;
+        }
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = w[u];
+        if (qn != q && qn < nt) enter(qn);
+        q = qn;
+        g0 = gn;
     }
 }
 
@@ -1041,7 +1097,11 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     // (above 48 KB only for texts of more than about 3 GB)
     unsigned long long *occ = reinterpret_cast<unsigned long long *>(d_occ);
     const long long cap = d_occ ? occ_cap : 0;
-    const size_t esmem = size_t((seg_tiles + 1) * 8 + seg_tiles * 4);
+    // group tables (offsets and ids) join it when they take at most 16 KB
+    const long long ngo_all = (long long)t.grp_off.size(), ngi_all = (long long)t.grp_ids.size();
+    const bool grp_smem = ngo_all > 0 && (ngo_all + ngi_all) * 4 <= (16 << 10);
+    const long long ngo = grp_smem ? ngo_all : 0, ngi = grp_smem ? ngi_all : 0;
+    const size_t esmem = size_t((seg_tiles + 1) * 8 + seg_tiles * 4 + (ngo + ngi) * 4);
     if (esmem > (size_t(48) << 10)) {
         e = se == 4 ? cudaFuncSetAttribute(expand_kernel<uint32_t, 16, 0x8000u>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem))
@@ -1052,11 +1112,11 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     if (se == 4)
         expand_kernel<uint32_t, 16, 0x8000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
             static_cast<const uint32_t *>(a.slots), a.tile_ent, a.tile_out, a.seg_sum, nseg, seg_tiles, nsub,
-            dv.grp_off, dv.grp_ids, occ, cap, a.n_occ, occ_base, pos_base);
+            dv.grp_off, dv.grp_ids, occ, cap, a.n_occ, occ_base, pos_base, ngo, ngi);
     else
         expand_kernel<unsigned long long, 32, 0x80000000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
             static_cast<const unsigned long long *>(a.slots), a.tile_ent, a.tile_out, a.seg_sum, nseg,
-            seg_tiles, nsub, dv.grp_off, dv.grp_ids, occ, cap, a.n_occ, occ_base, pos_base);
+            seg_tiles, nsub, dv.grp_off, dv.grp_ids, occ, cap, a.n_occ, occ_base, pos_base, ngo, ngi);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     return PM_OK;
