@@ -106,6 +106,7 @@ void release_device(pm_set *s)
                     s->dac.grp_off, s->dac.grp_ids, s->dac.cls,
                     s->dwm.shift, s->dwm.hoff, s->dwm.hids, s->dwm.hpfx, s->dwm.pats,
                     s->dwm.shift2, s->dwm.dir, s->dwm.ccode, s->dwm.cr,
+                    s->dwm.hcode, s->dwm.grp_off, s->dwm.grp_ids,
                     s->c_text, s->c_ws, s->c_out, s->c_counts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -171,6 +172,9 @@ int upload_wm(pm_set *s)
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.hids), t.hids.data(), t.hids.size() * 4, tot);
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.hpfx), t.hpfx.data(), t.hpfx.size() * 2, tot);
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.pats), t.pats.data(), t.pats.size(), tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.hcode), t.hcode.data(), t.hcode.size() * 4, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.grp_off), t.grp_off.data(), t.grp_off.size() * 4, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.grp_ids), t.grp_ids.data(), t.grp_ids.size() * 4, tot);
     if (!rc && t.dna) {
         rc = upload(reinterpret_cast<void **>(&d.shift2), t.shift2.data(), t.shift2.size(), tot);
         if (!rc) rc = upload(reinterpret_cast<void **>(&d.dir), t.dir.data(), t.dir.size() * 4, tot);
@@ -404,16 +408,16 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
         info->Bp = t.Bp;
         info->shift_entries = int64_t(t.shift.size());
         info->n_zero_shift = t.n_zero_shift;
+        info->n_distinct = t.n_distinct;
         info->dna_mode = t.dna ? 1 : 0;  // exact 2-bit-code tables in use
     }
     return PM_OK;
 }
 
-// Wu-Manber: look-back tiles are warp tiles; no scratch
 static int64_t set_ws_bytes(const pm_set *s, int64_t n, bool list)
 {
     if (s->algo != PM_ALGO_WM) return ac_workspace_bytes(s->ac, n, list);
-    return workspace_bytes_for(warp_tiles(n), list, 0, 0);
+    return wm_workspace_bytes(s->wm, n, list);
 }
 
 int64_t pm_scan_workspace_bytes(const pm_set *s, int64_t n, uint32_t flags)

@@ -231,7 +231,7 @@ static inline uint32_t wm_hash(const uint8_t *s, int len)
 // and h2. A run holds the patterns of one (block, prefix) pair sorted by
 // (packed pattern, r), so equal patterns are adjacent in ascending r.
 static void build_wm_packed(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp,
-                            WmTables &t)
+                            const std::vector<uint32_t> &code_of, WmTables &t)
 {
     t.dna = false;
     if (m > 32 || B + Bp > 6) return;
@@ -270,23 +270,23 @@ static void build_wm_packed(const uint8_t *P, int64_t d, int32_t m, int32_t B, i
         const uint32_t blk = uint32_t(c & (NB - 1));
         const uint32_t pre = uint32_t(c >> (2 * (m - Bp)));
         key[size_t(r)] = (blk << (2 * Bp)) | pre;
-        fill[key[size_t(r)] + 1]++;
+        if (code_of[size_t(r)] != 0xFFFFFFFFu) fill[key[size_t(r)] + 1]++;
     }
     for (size_t k = 0; k < NK; ++k) fill[k + 1] += fill[k];
-    std::vector<uint32_t> order(static_cast<size_t>(d));
-    for (int64_t r = 0; r < d; ++r) order[size_t(r)] = uint32_t(r);
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+    std::vector<uint32_t> order;
+    for (int64_t r = 0; r < d; ++r)
+        if (code_of[size_t(r)] != 0xFFFFFFFFu) order.push_back(uint32_t(r));
+    std::sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
         if (key[x] != key[y]) return key[x] < key[y];
-        if (code[x] != code[y]) return code[x] < code[y];
-        return x < y;
+        return code[x] < code[y];  // distinct patterns: distinct codes
     });
     t.shift2 = std::move(shift2);
     t.dir = std::move(fill);
-    t.ccode.resize(static_cast<size_t>(d));
-    t.cr.resize(static_cast<size_t>(d));
-    for (int64_t k = 0; k < d; ++k) {
-        t.ccode[size_t(k)] = code[order[size_t(k)]];
-        t.cr[size_t(k)] = order[size_t(k)];
+    t.ccode.resize(order.size());
+    t.cr.resize(order.size());
+    for (size_t k = 0; k < order.size(); ++k) {
+        t.ccode[k] = code[order[k]];
+        t.cr[k] = code_of[order[k]];
     }
     t.lut = lut;
     t.dna = true;
@@ -317,10 +317,36 @@ int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTa
     if (!P || d < 1 || m < 1 || B < 1 || B > m || Bp < 1) return PM_EINVAL;
     if (B > 4 || Bp > 3) return PM_EINVAL;
     if (Bp > m) Bp = m;
-    if (d >= (int64_t(1) << 24) || m > 255) return PM_ETOOBIG;
+    if (d >= int64_t(kWmGroup) || m > 255) return PM_ETOOBIG;
     try {
         t = WmTables();
         t.m = m; t.B = B; t.Bp = Bp; t.d = d;
+        // equal patterns: sort the ids by pattern bytes (ties by id); each
+        // run of equal patterns is one distinct pattern, entered once under
+        // its smallest id with the code r, or kWmGroup | g for a group
+        std::vector<uint32_t> code_of(static_cast<size_t>(d), 0xFFFFFFFFu);
+        {
+            std::vector<uint32_t> ids(static_cast<size_t>(d));
+            for (int64_t r = 0; r < d; ++r) ids[size_t(r)] = uint32_t(r);
+            std::stable_sort(ids.begin(), ids.end(), [&](uint32_t x, uint32_t y) {
+                return std::memcmp(P + size_t(x) * m, P + size_t(y) * m, size_t(m)) < 0;
+            });
+            t.grp_off.assign(1, 0u);
+            for (size_t a = 0; a < ids.size();) {
+                size_t b = a + 1;
+                while (b < ids.size() && std::memcmp(P + size_t(ids[a]) * m, P + size_t(ids[b]) * m, size_t(m)) == 0) ++b;
+                if (b - a == 1) {
+                    code_of[ids[a]] = ids[a];
+                } else {
+                    code_of[ids[a]] = kWmGroup | uint32_t(t.grp_off.size() - 1);
+                    for (size_t k = a; k < b; ++k) t.grp_ids.push_back(ids[k]);
+                    t.grp_off.push_back(uint32_t(t.grp_ids.size()));
+                }
+                ++t.n_distinct;
+                a = b;
+            }
+            if (t.grp_ids.empty()) t.grp_off.clear();
+        }
         const size_t H = size_t(1) << (5 * B);
         t.shift.assign(H, uint8_t(m - B + 1));
         std::vector<uint32_t> bucket_of(static_cast<size_t>(d));
@@ -335,24 +361,29 @@ int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTa
                 if (q == m) {
                     bucket_of[size_t(r)] = h;
                     prefix[size_t(r)] = uint16_t(wm_hash(p, Bp));
-                    fill[h + 1]++;
+                    if (code_of[size_t(r)] != 0xFFFFFFFFu) fill[h + 1]++;
                 }
             }
         }
         for (size_t h = 0; h < H; ++h) fill[h + 1] += fill[h];
         t.hoff = fill;
-        t.hids.assign(size_t(d), 0);
-        for (int64_t r = 0; r < d; ++r) t.hids[fill[bucket_of[size_t(r)]]++] = uint32_t(r);
+        t.hids.assign(size_t(t.n_distinct), 0);
+        for (int64_t r = 0; r < d; ++r)
+            if (code_of[size_t(r)] != 0xFFFFFFFFu) t.hids[fill[bucket_of[size_t(r)]]++] = uint32_t(r);
         for (size_t h = 0; h < H; ++h) {
             auto b = t.hids.begin() + t.hoff[h], e = t.hids.begin() + t.hoff[h + 1];
             std::stable_sort(b, e, [&](uint32_t x, uint32_t y) { return prefix[x] < prefix[y]; });
         }
-        t.hpfx.resize(size_t(d));
-        for (int64_t k = 0; k < d; ++k) t.hpfx[size_t(k)] = prefix[t.hids[size_t(k)]];
+        t.hpfx.resize(t.hids.size());
+        t.hcode.resize(t.hids.size());
+        for (size_t k = 0; k < t.hids.size(); ++k) {
+            t.hpfx[k] = prefix[t.hids[k]];
+            t.hcode[k] = code_of[t.hids[k]];
+        }
         t.pats.assign(P, P + d * int64_t(m));
         t.n_zero_shift = 0;
         for (size_t h = 0; h < H; ++h) t.n_zero_shift += t.shift[h] == 0;
-        build_wm_packed(P, d, m, B, Bp, t);
+        build_wm_packed(P, d, m, B, Bp, code_of, t);
         return PM_OK;
     } catch (const std::bad_alloc &) {
         t = WmTables();
@@ -365,6 +396,18 @@ static inline void emit_entry(std::vector<uint64_t> &occ, std::vector<int64_t> &
 {
     occ.push_back((uint64_t(i) << 32) | r);
     counts[r]++;
+}
+
+// a Wu-Manber match code: one pattern id, or every id of a group in ascending order
+static inline void emit_wm(const WmTables &t, std::vector<uint64_t> &occ, std::vector<int64_t> &counts,
+                           int64_t i, uint32_t code)
+{
+    if (code & kWmGroup) {
+        const uint32_t g = code & ~kWmGroup;
+        for (uint32_t k = t.grp_off[g]; k < t.grp_off[g + 1]; ++k) emit_entry(occ, counts, i, t.grp_ids[k]);
+    } else {
+        emit_entry(occ, counts, i, code);
+    }
 }
 
 void host_walk_ac(const AcTables &t, const uint8_t *T, int64_t n,
@@ -421,7 +464,10 @@ static void host_walk_wm_packed(const WmTables &t, const uint8_t *T, int64_t n,
         if (bad > i - m) continue;
         const uint32_t key = ((uint32_t(code) & bmask) << (2 * Bp)) | uint32_t(code >> (2 * (m - Bp)));
         for (uint32_t k = t.dir[key]; k < t.dir[key + 1]; ++k)
-            if (t.ccode[k] == code) emit_entry(occ, counts, i - m + 1, t.cr[k]);
+            if (t.ccode[k] == code) {
+                emit_wm(t, occ, counts, i - m + 1, t.cr[k]);
+                break;
+            }
     }
 }
 
@@ -485,8 +531,10 @@ void host_walk_wm(const WmTables &t, const uint8_t *T, int64_t n,
         for (uint32_t k = t.hoff[h]; k < t.hoff[h + 1]; ++k) {
             if (t.hpfx[k] != hp) continue;
             const uint32_t r = t.hids[k];
-            if (std::memcmp(t.pats.data() + size_t(r) * m, T + (i - m + 1), size_t(m)) == 0)
-                emit_entry(occ, counts, i - m + 1, r);
+            if (std::memcmp(t.pats.data() + size_t(r) * m, T + (i - m + 1), size_t(m)) == 0) {
+                emit_wm(t, occ, counts, i - m + 1, t.hcode[k]);
+                break;
+            }
         }
         i += 1;
     }

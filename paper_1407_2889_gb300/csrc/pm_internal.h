@@ -71,6 +71,15 @@ struct WmTables {
     std::vector<uint16_t> hpfx;    // PREFIX of hids[k]
     std::vector<uint8_t> pats;     // d*m pattern bytes
     int64_t n_zero_shift = 0;
+    // Equal patterns: only the smallest id of each distinct pattern enters
+    // HASH (and the exact-code runs); what a match there reports is a code,
+    // the pattern id r, or kWmGroup | g for a group g of equal patterns whose
+    // ids are grp_ids[grp_off[g] .. grp_off[g+1]) in ascending order. A
+    // window then matches at most one distinct pattern.
+    std::vector<uint32_t> hcode;   // code of hids[k]
+    std::vector<uint32_t> grp_off;
+    std::vector<uint32_t> grp_ids;
+    int64_t n_distinct = 0;
     // ACGT-like sets with m <= 32 (and B + B' <= 6) also get tables over the
     // exact 2-bit codes of the blocks (an injective h1 / h2): SHIFT over the
     // 4^B blocks, a directory of the candidate runs of each (block, prefix)
@@ -81,9 +90,10 @@ struct WmTables {
     uint32_t lut = 0;              // byte of code c in byte c
     std::vector<uint8_t> shift2;   // 4^B
     std::vector<uint32_t> dir;     // 4^(B+B') + 1 run offsets, key = block << 2B' | prefix
-    std::vector<uint64_t> ccode;   // d packed patterns, run order (code, then r)
-    std::vector<uint32_t> cr;      // their pattern ids
+    std::vector<uint64_t> ccode;   // distinct packed patterns, run order (ascending code)
+    std::vector<uint32_t> cr;      // their codes (pattern id or kWmGroup | g)
 };
+constexpr uint32_t kWmGroup = 0x800000u;  // codes fit 24 bits: d < 2^23
 
 int build_ac(const uint8_t *P, int64_t d, int32_t m, AcTables &out);
 int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTables &out);
@@ -139,6 +149,9 @@ struct DevWm {
     uint32_t *dir = nullptr;
     uint64_t *ccode = nullptr;
     uint32_t *cr = nullptr;
+    uint32_t *hcode = nullptr;      // code of each HASH entry
+    uint32_t *grp_off = nullptr;    // groups of equal patterns
+    uint32_t *grp_ids = nullptr;
     int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0, stage_cap = 0;
     int32_t shift_smem = 0, hist_smem = 0, dna = 0;
     int64_t smem_bytes = 0;
@@ -188,6 +201,31 @@ int pfac_launch(const AcTables &t, const DevAc &dev, const uint8_t *d_text, int6
                 int64_t *d_n_occ, void *d_ws, void *stream);
 // device workspace of an Aho-Corasick scan of n bytes
 int64_t ac_workspace_bytes(const AcTables &t, int64_t n, bool list);
+
+// List mode shared by the Aho-Corasick and Wu-Manber scans (scan_ac.cu):
+// the scan kernel writes each warp tile's entries ((start offset in the
+// tile << shift) | code, in text order) into the tile's slot, the tile's
+// entry and key counts, and adds the key count to its segment's sum; the
+// expand kernel turns the slots into sorted keys. Workspace:
+//   [header][per-terminal counters u64 x nterms][segment sums] -- zeroed
+//   [tile entries u32][tile keys u32][slots: kWarpTile entries per tile]
+struct ListParts {
+    int64_t zeroed_bytes = 0;
+    unsigned long long *seg_sum = nullptr;
+    uint32_t *tile_ent = nullptr, *tile_out = nullptr;
+    void *slots = nullptr;
+    int64_t seg_tiles = 0;
+};
+int64_t list_workspace_bytes(int64_t nsub, bool list, int64_t nterms, int slot_entry_bytes);
+void list_workspace_parts(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes, ListParts &out);
+// slots of 4-byte entries hold (offset << 16) | 16-bit code (group flag
+// 0x8000), 8-byte entries (offset << 32) | 32-bit code (group flag 2^31)
+int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes, const uint32_t *grp_off,
+                  const uint32_t *grp_ids, int64_t n_grp_off, int64_t n_grp_ids, uint64_t *d_occ,
+                  int64_t occ_cap, int64_t *d_n_occ, const unsigned long long *occ_base,
+                  unsigned long long pos_base, void *stream);
+// device workspace of a Wu-Manber scan of n bytes (scan_wm.cu)
+int64_t wm_workspace_bytes(const WmTables &t, int64_t n, bool list);
 int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevWm &dev);
 int wm_launch(const WmTables &t, const DevWm &dev, const uint8_t *d_text, int64_t n,
               bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,

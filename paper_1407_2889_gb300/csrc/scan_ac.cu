@@ -1002,7 +1002,6 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     const AcWsLayout L = ac_ws_layout(nsub, list, nterms, se, dp.sm_count);
     // every segment non-empty: at most ac_segments() of them
     const long long seg_tiles = (nsub + ac_segments(nsub, dp.sm_count) - 1) / ac_segments(nsub, dp.sm_count);
-    const long long nseg = (nsub + seg_tiles - 1) / seg_tiles;
     if (first) {
         e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
@@ -1093,36 +1092,74 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (!list) return PM_OK;
 
+    return expand_launch(d_ws, nsub, nterms, se, dv.grp_off, dv.grp_ids, (int64_t)t.grp_off.size(),
+                         (int64_t)t.grp_ids.size(), d_occ, occ_cap, d_n_occ, occ_base, pos_base, st);
+}
+
+}  // namespace
+
+int64_t list_workspace_bytes(int64_t nsub, bool list, int64_t nterms, int slot_entry_bytes)
+{
+    DeviceProps dp;
+    if (device_props(dp)) dp.sm_count = 1024;  // an upper bound on the segments
+    return ac_ws_layout(nsub, list, nterms, slot_entry_bytes, dp.sm_count).total;
+}
+
+void list_workspace_parts(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes, ListParts &out)
+{
+    DeviceProps dp;
+    if (device_props(dp)) dp.sm_count = 1;
+    const AcWsLayout L = ac_ws_layout(nsub, true, nterms, slot_entry_bytes, dp.sm_count);
+    char *w = static_cast<char *>(d_ws);
+    out.zeroed_bytes = L.zeroed;
+    out.seg_sum = reinterpret_cast<unsigned long long *>(w + L.seg_sum);
+    out.tile_ent = reinterpret_cast<uint32_t *>(w + L.tile_ent);
+    out.tile_out = reinterpret_cast<uint32_t *>(w + L.tile_out);
+    out.slots = w + L.slots;
+    const long long segs = ac_segments(nsub, dp.sm_count);
+    out.seg_tiles = (nsub + segs - 1) / segs;
+}
+
+int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes, const uint32_t *grp_off,
+                  const uint32_t *grp_ids, int64_t n_grp_off, int64_t n_grp_ids, uint64_t *d_occ,
+                  int64_t occ_cap, int64_t *d_n_occ, const unsigned long long *occ_base,
+                  unsigned long long pos_base, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ListParts P;
+    list_workspace_parts(d_ws, nsub, nterms, slot_entry_bytes, P);
+    const long long seg_tiles = P.seg_tiles;
+    const long long nseg = (nsub + seg_tiles - 1) / seg_tiles;
     // shared memory of the expand kernel: 12 bytes per tile of a segment
     // (above 48 KB only for texts of more than about 3 GB)
     unsigned long long *occ = reinterpret_cast<unsigned long long *>(d_occ);
     const long long cap = d_occ ? occ_cap : 0;
     // group tables (offsets and ids) join it when they take at most 16 KB
-    const long long ngo_all = (long long)t.grp_off.size(), ngi_all = (long long)t.grp_ids.size();
-    const bool grp_smem = ngo_all > 0 && (ngo_all + ngi_all) * 4 <= (16 << 10);
-    const long long ngo = grp_smem ? ngo_all : 0, ngi = grp_smem ? ngi_all : 0;
+    const bool grp_smem = n_grp_off > 0 && (n_grp_off + n_grp_ids) * 4 <= (16 << 10);
+    const long long ngo = grp_smem ? n_grp_off : 0, ngi = grp_smem ? n_grp_ids : 0;
     const size_t esmem = size_t((seg_tiles + 1) * 8 + seg_tiles * 4 + (ngo + ngi) * 4);
+    cudaError_t e = cudaSuccess;
+    const bool se4 = slot_entry_bytes == 4;
     if (esmem > (size_t(48) << 10)) {
-        e = se == 4 ? cudaFuncSetAttribute(expand_kernel<uint32_t, 16, 0x8000u>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem))
-                    : cudaFuncSetAttribute(expand_kernel<unsigned long long, 32, 0x80000000u>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem));
+        e = se4 ? cudaFuncSetAttribute(expand_kernel<uint32_t, 16, 0x8000u>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem))
+                : cudaFuncSetAttribute(expand_kernel<unsigned long long, 32, 0x80000000u>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem));
         if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     }
-    if (se == 4)
+    long long *n_occ = reinterpret_cast<long long *>(d_n_occ);
+    if (se4)
         expand_kernel<uint32_t, 16, 0x8000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
-            static_cast<const uint32_t *>(a.slots), a.tile_ent, a.tile_out, a.seg_sum, nseg, seg_tiles, nsub,
-            dv.grp_off, dv.grp_ids, occ, cap, a.n_occ, occ_base, pos_base, ngo, ngi);
+            static_cast<const uint32_t *>(P.slots), P.tile_ent, P.tile_out, P.seg_sum, nseg, seg_tiles, nsub,
+            grp_off, grp_ids, occ, cap, n_occ, occ_base, pos_base, ngo, ngi);
     else
         expand_kernel<unsigned long long, 32, 0x80000000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
-            static_cast<const unsigned long long *>(a.slots), a.tile_ent, a.tile_out, a.seg_sum, nseg,
-            seg_tiles, nsub, dv.grp_off, dv.grp_ids, occ, cap, a.n_occ, occ_base, pos_base, ngo, ngi);
+            static_cast<const unsigned long long *>(P.slots), P.tile_ent, P.tile_out, P.seg_sum, nseg,
+            seg_tiles, nsub, grp_off, grp_ids, occ, cap, n_occ, occ_base, pos_base, ngo, ngi);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     return PM_OK;
 }
-
-}  // namespace
 
 int64_t ac_workspace_bytes(const AcTables &t, int64_t n, bool list)
 {

@@ -6,11 +6,13 @@
 // from its chunk start + m - 1 on, and runs Algorithm 5 over them: hash the
 // B-byte block ending at the window end, jump by SHIFT when it is non-zero,
 // else hash the B'-byte window prefix, take the run of HASH[h] whose PREFIX
-// equals it (buckets are sorted by PREFIX, so a binary search finds it) and
-// verify each candidate byte by byte. SHIFT lives in shared memory when it
-// has at most 2^15 entries (B <= 3); HASH, PREFIX and the patterns are read
-// through L1/L2. Matches go through the same pool / warp scan / look-back /
-// staged-store path as the Aho-Corasick kernel.
+// equals it and verify its candidates. Equal patterns enter the tables once
+// (a group code), so a window matches at most one candidate and the walk
+// stops at the first. ACGT-like sets with m <= 32 walk the lane's text from
+// registers with the exact 2-bit codes as h1 / h2 (the next tile's copy is
+// in flight meanwhile); other sets read the staged tile byte by byte. Matches
+// go through the lane's pool into the tile's slot, and the expand kernel of
+// the Aho-Corasick scan writes the sorted keys (list mode).
 #include "scan_common.cuh"
 
 namespace pm {
@@ -26,18 +28,23 @@ struct WmArgs {
     int hbits;
     const uint32_t *hoff;
     const uint32_t *hids;
+    const uint32_t *hcode;
     const uint16_t *hpfx;
     const uint8_t *pats;
     int m, B, Bp;
     long long ntiles;
-    int pool_cap, stage_cap, buf;
+    int pool_cap, buf;
     int list, hist_smem, d;
     long long *counts;
-    unsigned long long *occ;
-    long long occ_cap;
     long long *n_occ;
     dev::WsHeader *ws;
-    dev::LookbackRefs lb;
+    const uint32_t *grp_off;      // groups of equal patterns (kWmGroup codes)
+    const uint32_t *grp_ids;
+    uint32_t *tile_ent;           // list: entries per warp tile
+    uint32_t *tile_out;           // list: keys per warp tile (groups expanded)
+    unsigned long long *seg_sum;  // list: keys per segment of seg_tiles warp tiles
+    long long seg_tiles;
+    unsigned long long *slots;    // list: kWarpTile entries per warp tile
     // exact-code tables (ACGT-like sets, m <= 32)
     uint32_t lut;
     const uint8_t *shift2_g;
@@ -51,9 +58,20 @@ __host__ __device__ constexpr int r16w(long long x) { return int((x + 15) & ~15L
 
 __host__ __device__ inline int wm_buf_bytes(int m) { return kWarpTile + r16w(m - 1 > 0 ? m - 1 : 0); }
 
-__host__ __device__ inline int wm_warp_bytes(int m, int pool_cap, int stage_cap)
+// register text of the exact-code walk: chunk + halo in 16-byte vectors
+__host__ __device__ inline int wm_nv(int m) { return m - 1 <= 16 ? 6 : 7; }
+
+// staged bytes per warp tile: the windows' bytes, and for the exact-code
+// walk every byte the last lane loads into registers
+__host__ __device__ inline int wm_tile_buf(int m, bool dna)
 {
-    return 16 + r16w(wm_buf_bytes(m)) + r16w((long long)pool_cap * 32 * 4) + stage_cap * 8;
+    const int b = wm_buf_bytes(m), r = (kLane - 1) * kChunk + 16 * wm_nv(m);
+    return dna && r > b ? r : b;
+}
+
+__host__ __device__ inline int wm_warp_bytes(int m, int pool_cap, bool dna)
+{
+    return 16 + r16w(wm_tile_buf(m, dna)) + r16w((long long)pool_cap * 32 * 4);
 }
 
 __device__ __forceinline__ uint32_t block_hash(const uint8_t *s, int len)
@@ -79,8 +97,8 @@ __device__ __forceinline__ void wm_stage_issue(const WmArgs &a, long long t, uin
     if (bytes > 0) dev::tma_load_1d(buf, a.text + t * kWarpTile, uint32_t(bytes), bar);
 }
 
-// Algorithm 5 over one lane's windows; hit(start_offset, r) per match, in
-// ascending (start, r).
+// Algorithm 5 over one lane's windows; hit(start_offset, code) per match,
+// in ascending start (at most one distinct pattern matches a window).
 template <bool SHIFT_SMEM, class F>
 __device__ __forceinline__ void wm_walk(const WmArgs &a, const uint8_t *s_shift,
                                         const uint8_t *w, int lim, F &&hit)
@@ -105,59 +123,97 @@ __device__ __forceinline__ void wm_walk(const WmArgs &a, const uint8_t *s_shift,
             else hi = md;
         }
         for (uint32_t k = lo; k < end && __ldg(a.hpfx + k) == hp; ++k) {
-            const uint32_t r = __ldg(a.hids + k);
-            const uint8_t *pp = a.pats + (size_t)r * m;
+            const uint8_t *pp = a.pats + (size_t)__ldg(a.hids + k) * m;
             int j = 0;
             while (j < m && __ldg(pp + j) == win[j]) ++j;
-            if (j == m) hit(i - (m - 1), r);
+            if (j == m) {
+                hit(i - (m - 1), __ldg(a.hcode + k));
+                break;
+            }
         }
         ++i;
     }
 }
 
 // Algorithm 5 over one lane's windows on an ACGT-like set, with h1 and h2
-// the exact 2-bit codes of the block and the prefix. The lane keeps the
-// packed code of its last m characters (first character in the high bits)
-// and the offset of its last byte outside the alphabet; the window ends
-// Algorithm 5 visits are the same as with the byte hash (a block holding a
-// byte outside the alphabet occurs in no pattern: SHIFT m-B+1), and each
-// candidate of the (block, prefix) run is verified by one comparison of
-// packed codes (equal patterns are adjacent in the run, in ascending r).
-template <class F>
+// the exact 2-bit codes of the block and the prefix, over the lane's bytes
+// held in registers (NV vectors: chunk + halo). The lane keeps the packed
+// code of its last m characters (first character in the high bits), the
+// offset of its last byte outside the alphabet and the next window end
+// Algorithm 5 examines; the window ends visited are the same as with the
+// byte hash (a block holding a byte outside the alphabet occurs in no
+// pattern: SHIFT m-B+1). A run of candidates is sorted by packed code, so
+// its scan stops at the first code not below the window's. Bytes past the
+// text are 0, outside every ACGT-like alphabet.
+template <int NV, class F>
 __device__ __forceinline__ void wm_walk_dna(const WmArgs &a, const uint8_t *s_shift2,
-                                            const uint32_t *s_dir, const uint8_t *w, int lim, F &&hit)
+                                            const uint32_t *s_dir, const uint4 (&tv)[NV], F &&hit)
 {
     const int m = a.m, B = a.B, Bp = a.Bp;
     const unsigned long long mask = m >= 32 ? ~0ull : ((1ull << (2 * m)) - 1ull);
     const uint32_t bmask = (1u << (2 * B)) - 1u;
     const int pshift = 2 * (m - Bp);
+    const int lim = kChunk + m - 1;   // window ends at offsets < lim
     unsigned long long code = 0;
-    int bad = -1;   // last offset holding a byte outside the alphabet
-    int skip = 0;   // window ends still to pass over after a SHIFT > 1
-    for (int i = 0; i < lim; ++i) {
-        const uint32_t b = w[i];
-        const uint32_t c = ((b >> 1) ^ (b >> 2)) & 3u;
-        if (((a.lut >> (8 * c)) & 0xFFu) != b) bad = i;
-        code = ((code << 2) | c) & mask;
-        if (i < m - 1) continue;
-        if (skip > 0) { --skip; continue; }
-        const uint32_t sh = bad > i - B ? uint32_t(m - B + 1) : uint32_t(s_shift2[uint32_t(code) & bmask]);
-        if (sh > 0) { skip = int(sh) - 1; continue; }
-        if (bad > i - m) continue;  // the window holds a byte no pattern has
-        const uint32_t key = ((uint32_t(code) & bmask) << (2 * Bp)) | uint32_t(code >> pshift);
-        const uint32_t lo = s_dir[key], hi = s_dir[key + 1];
-        for (uint32_t k0 = lo; k0 < hi; k0 += 4) {
-            unsigned long long cc[4];
+    int bad = -1;                     // last offset holding a byte outside the alphabet
+    int next = m - 1;                 // next window end to examine
+    // one 16-byte vector per iteration (a rolled loop keeps the code small;
+    // the vector is picked from the registers by predicated moves)
+#pragma unroll 1
+    for (int v = 0; v < NV && v * 16 < lim; ++v) {
+        uint4 tx = tv[0];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) cc[u] = k0 + u < hi ? __ldg(a.ccode + k0 + u) : ~code;
+        for (int u = 1; u < NV; ++u)
+            if (v == u) tx = tv[u];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (cc[u] == code) hit(i - (m - 1), __ldg(a.cr + k0 + u));
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t w = q == 0 ? tx.x : q == 1 ? tx.y : q == 2 ? tx.z : tx.w;
+            const uint32_t a4 = ((w >> 1) ^ (w >> 2)) & 0x03030303u;
+            const uint32_t sel = __byte_perm(a4 | (a4 >> 4), 0u, 0x4420);
+            const uint32_t x = w ^ __byte_perm(a.lut, 0u, sel);  // zero byte = in the alphabet
+            const uint32_t y = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = v * 16 + q * 4 + k;
+                if (i < lim) {
+                    code = ((code << 2) | ((a4 >> (8 * k)) & 3u)) & mask;
+                    if (!((y >> (8 * k + 7)) & 1u)) bad = i;
+                    if (i >= next) {
+                        const uint32_t blk = uint32_t(code) & bmask;
+                        const uint32_t sh = bad > i - B ? uint32_t(m - B + 1) : uint32_t(s_shift2[blk]);
+                        if (sh > 0) {
+                            next = i + int(sh);
+                        } else {
+                            next = i + 1;
+                            if (bad <= i - m) {
+                                const uint32_t key = (blk << (2 * Bp)) | uint32_t(code >> pshift);
+                                const uint32_t lo = s_dir[key], hi = s_dir[key + 1];
+                                for (uint32_t k0 = lo; k0 < hi; k0 += 4) {
+                                    unsigned long long cc[4];
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) cc[u] = k0 + u < hi ? __ldg(a.ccode + k0 + u) : ~0ull;
+                                    // the run is sorted: stop at the first code not below the window's
+                                    bool stop = false;
+                                    int hu = -1;
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) {
+                                        const bool ok = k0 + u < hi;
+                                        stop |= ok && cc[u] >= code;
+                                        if (ok && cc[u] == code) hu = u;
+                                    }
+                                    if (hu >= 0) hit(i - (m - 1), __ldg(a.cr + k0 + hu));
+                                    if (stop) break;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
         }
     }
 }
 
-template <bool SHIFT_SMEM, bool DNA>
+template <bool SHIFT_SMEM, bool DNA, int NV>
 __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -172,12 +228,10 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
     p += DNA ? r16w((long long)(a.nkey + 1) * 4) : 0;
     uint32_t *s_hist = a.hist_smem ? reinterpret_cast<uint32_t *>(p) : nullptr;
     p += a.hist_smem ? r16w((long long)a.d * 4) : 0;
-    p += warp * wm_warp_bytes(a.m, a.pool_cap, a.stage_cap);
+    p += warp * wm_warp_bytes(a.m, a.pool_cap, DNA);
     uint64_t *bar = reinterpret_cast<uint64_t *>(p);
     uint8_t *buf = p + 16;
     uint32_t *pool = reinterpret_cast<uint32_t *>(buf + r16w(a.buf));
-    unsigned long long *stage = reinterpret_cast<unsigned long long *>(
-        reinterpret_cast<unsigned char *>(pool) + r16w((long long)a.pool_cap * 32 * 4));
 
     if (DNA) {
         for (int i = threadIdx.x; i < (1 << (2 * a.B)); i += blockDim.x) s_shift2[i] = a.shift2_g[i];
@@ -198,18 +252,36 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
     uint32_t *pl = pool + lane;
     const uint32_t cap = uint32_t(a.pool_cap);
     const int m = a.m;
-    dev::TileSchedule sch;
-    sch.init(a.ntiles);
+    const long long G = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     uint32_t phase = 0;
+    bool inflight = false;
     unsigned long long my_total = 0;
-    if (sch.cur >= 0 && lane == 0) wm_stage_issue(a, sch.cur, buf, bar);
+    if (gwarp < a.ntiles) {
+        if (lane == 0) wm_stage_issue(a, gwarp, buf, bar);
+        inflight = true;
+    }
 
-    for (long long t = sch.cur; t >= 0; t = sch.next_of(t)) {
+    // a match code counts every id it stands for; returns how many
+    auto count_code = [&](uint32_t code) -> uint32_t {
+        if (!(code & kWmGroup)) {
+            dev::count_pattern(code, s_hist, a.counts);
+            return 1u;
+        }
+        const uint32_t g = code & ~kWmGroup;
+        const uint32_t j1 = __ldg(a.grp_off + g + 1);
+        uint32_t c = 0;
+        for (uint32_t j = __ldg(a.grp_off + g); j < j1; ++j, ++c) dev::count_pattern(__ldg(a.grp_ids + j), s_hist, a.counts);
+        return c;
+    };
+
+    for (long long t = gwarp; t < a.ntiles; t += G) {
         const bool got = __all_sync(kFull, dev::mbar_wait_bounded(bar, phase));
         if (!got) {
             if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutTma);
-            break;
+            break;  // the copy stays in flight: waited for below
         }
+        inflight = false;
         phase ^= 1u;
         const long long tile0 = t * kWarpTile;
         const int got_bytes = wm_stage_bytes(a, t);
@@ -222,91 +294,100 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
         __syncwarp();
 
         const int cs = lane * kChunk;
-        const long long g0 = tile0 + cs;
-        int lim = kChunk + m - 1;          // window ends at offsets < lim
+        int lim = kChunk + m - 1;  // window ends at offsets < lim
         {
-            const long long left = a.n - g0;
+            const long long left = a.n - (tile0 + cs);
             if (left < lim) lim = left <= 0 ? 0 : int(left);
         }
-        const uint8_t *w = buf + cs;
         uint32_t nh = 0;
-        auto rec = [&](int off, uint32_t r) {
-            if (nh < cap) pl[nh * 32] = (uint32_t(off) << 24) | r;
+        auto rec = [&](int off, uint32_t code) {
+            if (nh < cap) pl[nh * 32] = (uint32_t(off) << 24) | code;
             ++nh;
         };
-        if (DNA) wm_walk_dna(a, s_shift2, s_dir, w, lim, rec);
-        else wm_walk<SHIFT_SMEM>(a, s_shift, w, lim, rec);
-        const bool ovf = nh > cap;
-        const uint32_t cnt = nh;
-
-        if (!a.list) {
-            if (!ovf) {
-                for (uint32_t k = 0; k < nh; ++k)
-                    dev::count_pattern(pl[k * 32] & 0xFFFFFFu, s_hist, a.counts);
-            } else {
-                auto cnt_hit = [&](int, uint32_t r) { dev::count_pattern(r, s_hist, a.counts); };
-                if (DNA) wm_walk_dna(a, s_shift2, s_dir, w, lim, cnt_hit);
-                else wm_walk<SHIFT_SMEM>(a, s_shift, w, lim, cnt_hit);
+        uint4 tv[DNA ? NV : 1];
+        if (DNA) {
+            const uint4 *bv = reinterpret_cast<const uint4 *>(buf + cs);
+#pragma unroll
+            for (int v = 0; v < (DNA ? NV : 1); ++v) tv[v] = bv[v];
+            // the buffer is free: stage the next tile while this one is walked
+            dev::fence_proxy_async_smem();
+            __syncwarp();
+            if (t + G < a.ntiles) {
+                if (lane == 0) wm_stage_issue(a, t + G, buf, bar);
+                inflight = true;
             }
+            wm_walk_dna<(DNA ? NV : 1)>(a, s_shift2, s_dir, tv, rec);
+        } else {
+            wm_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, rec);
+        }
+        const bool ovf = nh > cap;
+
+        // slot of this tile (list mode): the lane's entries follow the
+        // entries of the lanes before it
+        unsigned long long *dst = nullptr;
+        uint32_t e_incl = 0;
+        if (a.list) {
+            e_incl = dev::warp_incl_scan(nh, lane);
+            dst = a.slots + t * kWarpTile + (e_incl - nh);
+        }
+        // slot entry: (start offset in the tile << 32) | code, group flag 2^31
+        auto put = [&](uint32_t k, int off, uint32_t code) {
+            const uint32_t c32 = (code & kWmGroup) ? (0x80000000u | (code & ~kWmGroup)) : code;
+            dst[k] = ((unsigned long long)(cs + off) << 32) | c32;
+        };
+        uint32_t cnt = 0;  // keys of this lane (groups expanded)
+        if (!ovf) {
+            for (uint32_t k = 0; k < nh; ++k) {
+                const uint32_t v = pl[k * 32];
+                cnt += count_code(v & 0xFFFFFFu);
+                if (a.list) put(k, int(v >> 24), v & 0xFFFFFFu);
+            }
+        } else {
+            // the pool overflowed: walk again and take the matches as they come
+            uint32_t k = 0;
+            auto again = [&](int off, uint32_t code) {
+                cnt += count_code(code);
+                if (a.list && k < nh) put(k, off, code);
+                ++k;
+            };
+            if (DNA) {
+                // the staged copy may already hold the next tile: text from global memory
+                uint4 tw[DNA ? NV : 1];
+                uint8_t *tb = reinterpret_cast<uint8_t *>(tw);
+                const long long g0 = tile0 + cs;
+                for (int b = 0; b < 16 * (DNA ? NV : 1); ++b) tb[b] = g0 + b < a.n ? a.text[g0 + b] : uint8_t(0);
+                wm_walk_dna<(DNA ? NV : 1)>(a, s_shift2, s_dir, tw, again);
+            } else {
+                wm_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, again);
+            }
+        }
+        if (!a.list) {
             my_total += cnt;
         } else {
-            const uint32_t incl = dev::warp_incl_scan(cnt, lane);
-            const uint32_t excl = incl - cnt;
-            const uint32_t wtot = __shfl_sync(kFull, incl, 31);
-            bool ok;
-            const unsigned long long base = dev::lookback(a.lb, t, wtot, lane, ok);
-            if (!ok) {
-                if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutLookback);
-                break;
-            }
-            if (lane == 0 && t == a.ntiles - 1) *a.n_occ = (long long)(base + wtot);
-            if (!__any_sync(kFull, ovf)) {
-                uint32_t k = 0, my = excl;
-                const uint32_t S = uint32_t(a.stage_cap);
-                for (uint32_t w0 = 0; w0 < wtot; w0 += S) {
-                    const uint32_t wend = min(w0 + S, wtot);
-                    const uint32_t lim = min(wend, incl);  // this lane's entries in the window
-                    while (my < lim) {
-                        const uint32_t v = pl[k * 32];
-                        ++k;
-                        const uint32_t r = v & 0xFFFFFFu;
-                        stage[my - w0] = ((unsigned long long)(g0 + (v >> 24)) << 32) | r;
-                        dev::count_pattern(r, s_hist, a.counts);
-                        ++my;
-                    }
-                    __syncwarp();
-                    for (uint32_t q = w0 + lane; q < wend; q += 32) {
-                        const unsigned long long gi = base + q;
-                        if (gi < (unsigned long long)a.occ_cap) a.occ[gi] = stage[q - w0];
-                    }
-                    __syncwarp();
-                }
-            } else {
-                unsigned long long gi = base + excl;
-                auto put = [&](long long pos, uint32_t r) {
-                    if (gi < (unsigned long long)a.occ_cap)
-                        a.occ[gi] = ((unsigned long long)pos << 32) | r;
-                    ++gi;
-                    dev::count_pattern(r, s_hist, a.counts);
-                };
-                if (!ovf) {
-                    for (uint32_t k = 0; k < nh; ++k) {
-                        const uint32_t v = pl[k * 32];
-                        put(g0 + (v >> 24), v & 0xFFFFFFu);
-                    }
-                } else {
-                    auto put_hit = [&](int off, uint32_t r) { put(g0 + off, r); };
-                    if (DNA) wm_walk_dna(a, s_shift2, s_dir, w, lim, put_hit);
-                    else wm_walk<SHIFT_SMEM>(a, s_shift, w, lim, put_hit);
-                }
+            uint32_t o_tot = cnt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) o_tot += __shfl_xor_sync(kFull, o_tot, o);
+            if (lane == 31) {
+                a.tile_ent[t] = e_incl;
+                a.tile_out[t] = o_tot;
+                if (o_tot) atomicAdd(&a.seg_sum[t / a.seg_tiles], (unsigned long long)o_tot);
             }
         }
 
-        // the buffer is free: stage the next tile
-        dev::fence_proxy_async_smem();
-        __syncwarp();
-        if (sch.next_of(t) >= 0 && lane == 0) wm_stage_issue(a, sch.next_of(t), buf, bar);
+        if (!DNA) {
+            // the buffer is free: stage the next tile
+            dev::fence_proxy_async_smem();
+            __syncwarp();
+            if (t + G < a.ntiles) {
+                if (lane == 0) wm_stage_issue(a, t + G, buf, bar);
+                inflight = true;
+            }
+        }
     }
+
+    // a copy still in flight after an error exit: wait for it (bounded) so
+    // it is not still writing this CTA's shared memory when the CTA exits
+    if (inflight) (void)dev::mbar_wait_bounded(bar, phase);
 
     if (!a.list) {
 #pragma unroll
@@ -324,11 +405,11 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
 }
 
 long long wm_smem_bytes(int hbits, bool shift_smem, int hist, int d, int warps, int m,
-                        int pool_cap, int stage_cap, bool dna, int B, int nkey)
+                        int pool_cap, bool dna, int B, int nkey)
 {
     const long long tables = dna ? r16w(1LL << (2 * B)) + r16w((long long)(nkey + 1) * 4)
                                  : (shift_smem ? r16w(1LL << hbits) : 0);
-    return tables + (hist ? r16w((long long)d * 4) : 0) + (long long)warps * wm_warp_bytes(m, pool_cap, stage_cap);
+    return tables + (hist ? r16w((long long)d * 4) : 0) + (long long)warps * wm_warp_bytes(m, pool_cap, dna);
 }
 
 }  // namespace
@@ -338,7 +419,7 @@ int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevW
     const long long budget = (long long)dp.smem_optin - 1024;
     const int hbits = 5 * t.B;
     dev.pool_cap = 40;
-    dev.stage_cap = 128;
+    dev.stage_cap = 0;
     dev.ctas_per_sm = opt.ctas_per_sm > 0 ? opt.ctas_per_sm : 1;
     const int forced = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, 16) : 0;
     const bool shift_smem = hbits <= 15;
@@ -348,7 +429,7 @@ int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevW
             const int w = forced ? forced : choices[wi];
             const int hist = pass == 0 ? 1 : 0;
             const long long need = wm_smem_bytes(hbits, shift_smem, hist, int(t.d), w, t.m, dev.pool_cap,
-                                                 dev.stage_cap, t.dna, t.B, 1 << (2 * (t.B + t.Bp)));
+                                                 t.dna, t.B, 1 << (2 * (t.B + t.Bp)));
             if (need <= budget) {
                 dev.warps = w;
                 dev.hist_smem = hist;
@@ -363,6 +444,11 @@ int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevW
     return PM_ETOOBIG;
 }
 
+int64_t wm_workspace_bytes(const WmTables &, int64_t n, bool list)
+{
+    return list_workspace_bytes(warp_tiles(n), list, 0, 8);
+}
+
 int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t n, bool list,
               int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
               void *stream)
@@ -370,18 +456,21 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     const long long ntiles = warp_tiles(n);
+    ListParts L;
+    list_workspace_parts(d_ws, ntiles, 0, 8, L);
+    const int64_t zeroed = list ? L.zeroed_bytes : kWsHeader;
     e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(d_ws, 0, size_t(zeroed_workspace_bytes(ntiles, list, 0)), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_ws, 0, size_t(zeroed), st);
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (n < t.m || ntiles == 0) return PM_OK;
 
     typedef void (*K)(const WmArgs);
-    K fn = dv.dna ? wm_scan_kernel<false, true>
-                  : (dv.shift_smem ? wm_scan_kernel<true, false> : wm_scan_kernel<false, false>);
-    static int attr_bytes[3] = {0, 0, 0};
-    const int slot = dv.dna ? 2 : (dv.shift_smem ? 1 : 0);
+    const int nv = wm_nv(t.m);
+    K fn = dv.dna ? (nv == 6 ? wm_scan_kernel<false, true, 6> : wm_scan_kernel<false, true, 7>)
+                  : (dv.shift_smem ? wm_scan_kernel<true, false, 1> : wm_scan_kernel<false, false, 1>);
+    static int attr_bytes[4] = {0, 0, 0, 0};
+    const int slot = dv.dna ? (nv == 6 ? 2 : 3) : (dv.shift_smem ? 1 : 0);
     if (attr_bytes[slot] < dv.smem_bytes) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
         if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
@@ -399,6 +488,7 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     a.hbits = 5 * t.B;
     a.hoff = dv.hoff;
     a.hids = dv.hids;
+    a.hcode = dv.hcode;
     a.hpfx = dv.hpfx;
     a.pats = dv.pats;
     a.m = t.m;
@@ -406,21 +496,20 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     a.Bp = t.Bp;
     a.ntiles = ntiles;
     a.pool_cap = dv.pool_cap;
-    a.stage_cap = dv.stage_cap;
-    a.buf = wm_buf_bytes(t.m);
+    a.buf = wm_tile_buf(t.m, dv.dna != 0);
     a.list = list ? 1 : 0;
     a.hist_smem = dv.hist_smem;
     a.d = int(t.d);
     a.counts = reinterpret_cast<long long *>(d_counts);
-    a.occ = reinterpret_cast<unsigned long long *>(d_occ);
-    a.occ_cap = list ? occ_cap : 0;
     a.n_occ = reinterpret_cast<long long *>(d_n_occ);
-    char *w = static_cast<char *>(d_ws);
-    a.ws = reinterpret_cast<dev::WsHeader *>(w);
-    a.lb.tile_st = reinterpret_cast<unsigned long long *>(w + kWsHeader);
-    a.lb.super_acc = reinterpret_cast<unsigned long long *>(w + kWsHeader + ntiles * 8);
-    a.lb.super_pre = reinterpret_cast<unsigned long long *>(w + kWsHeader + ntiles * 16);
-    a.lb.ntiles = ntiles;
+    a.ws = reinterpret_cast<dev::WsHeader *>(d_ws);
+    a.grp_off = dv.grp_off;
+    a.grp_ids = dv.grp_ids;
+    a.tile_ent = L.tile_ent;
+    a.tile_out = L.tile_out;
+    a.seg_sum = L.seg_sum;
+    a.seg_tiles = L.seg_tiles;
+    a.slots = static_cast<unsigned long long *>(L.slots);
     a.lut = t.lut;
     a.shift2_g = dv.shift2;
     a.dir_g = dv.dir;
@@ -428,7 +517,6 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     a.cr = dv.cr;
     a.nkey = t.dna ? (1 << (2 * (t.B + t.Bp))) : 0;
 
-    // the static tile schedule needs every CTA of the grid resident at once
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, dv.warps * 32, size_t(dv.smem_bytes));
     if (e != cudaSuccess || per_sm < 1) { set_cuda_error(int(e)); return PM_ECUDA; }
@@ -436,11 +524,12 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     const long long want = (ntiles + dv.warps - 1) / dv.warps;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    a.lb.super_tiles = dev::super_size_for(grid * dv.warps);
     fn<<<dim3(unsigned(grid)), dim3(unsigned(dv.warps * 32)), size_t(dv.smem_bytes), st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-    return PM_OK;
+    if (!list) return PM_OK;
+    return expand_launch(d_ws, ntiles, 0, 8, dv.grp_off, dv.grp_ids, (int64_t)t.grp_off.size(),
+                         (int64_t)t.grp_ids.size(), d_occ, occ_cap, d_n_occ, nullptr, 0, stream);
 }
 
 }  // namespace pm
