@@ -17,19 +17,6 @@ void set_cuda_error(int e) { g_last_cuda = e; }
 
 int64_t warp_tiles(int64_t n) { return n <= 0 ? 0 : (n + kWarpTile - 1) / kWarpTile; }
 
-static int64_t round16(int64_t x) { return (x + 15) & ~int64_t(15); }
-
-int64_t zeroed_workspace_bytes(int64_t tiles, bool list, int64_t n_terms)
-{
-    int64_t b = kWsHeader + round16(n_terms * 8);
-    if (list) b += round16(tiles * 24);   // tile status, super sums, super prefixes
-    return b;
-}
-
-int64_t workspace_bytes_for(int64_t tiles, bool list, int64_t n_terms, int64_t scratch_bytes)
-{
-    return zeroed_workspace_bytes(tiles, list, n_terms) + (list ? round16(scratch_bytes) : 0);
-}
 
 int device_props(DeviceProps &p)
 {

@@ -157,17 +157,10 @@ struct DevWm {
     int64_t smem_bytes = 0;
 };
 
-// Workspace (device scratch), zeroed by the launcher before each scan:
-//   [header 256 B] [per-terminal counts u64 x n_terms]
-//   list mode only: [tile status u64 x tiles] [super-tile sums u64 x tiles]
-//                   [super-tile prefixes u64 x tiles]  (super-tiles <= tiles)
-//                   [Aho-Corasick: per-warp scratch slots, not zeroed]
+// Workspace (device scratch) of a plain scan: a 256-byte header (status
+// word, finished-CTA count) first; the list-mode layout is ListParts below.
 constexpr int64_t kWsHeader = 256;
 int64_t warp_tiles(int64_t n);
-// scratch_per_warp: bytes of list-mode scratch per warp of the largest grid
-// (tiles = look-back tiles; scratch_bytes = list-mode scratch of the largest grid)
-int64_t workspace_bytes_for(int64_t tiles, bool list, int64_t n_terms, int64_t scratch_bytes);
-int64_t zeroed_workspace_bytes(int64_t tiles, bool list, int64_t n_terms);
 
 struct DeviceProps {
     int sm_count = 0;

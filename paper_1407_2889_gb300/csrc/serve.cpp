@@ -41,7 +41,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int64_t kAlign = 256;
 // Requests at least this long run as their own whole-GPU scan (the plain
-// kernel, decoupled look-back over all SMs); shorter ones share a batched
+// scan and expand kernels over all SMs); shorter ones share a batched
 // launch, where one CTA takes a whole request.
 constexpr int64_t kPlainMin = int64_t(256) << 10;
 
