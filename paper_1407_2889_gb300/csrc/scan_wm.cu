@@ -13,6 +13,8 @@
 // in flight meanwhile); other sets read the staged tile byte by byte. Matches
 // go through the lane's pool into the tile's slot, and the expand kernel of
 // the Aho-Corasick scan writes the sorted keys (list mode).
+#include <type_traits>
+
 #include "scan_common.cuh"
 
 namespace pm {
@@ -145,16 +147,18 @@ __device__ __forceinline__ void wm_walk(const WmArgs &a, const uint8_t *s_shift,
 // pattern: SHIFT m-B+1). A run of candidates is sorted by packed code, so
 // its scan stops at the first code not below the window's. Bytes past the
 // text are 0, outside every ACGT-like alphabet.
-template <int NV, class F>
+template <int NV, bool WIDE, class F>
 __device__ __forceinline__ void wm_walk_dna(const WmArgs &a, const uint8_t *s_shift2,
-                                            const uint32_t *s_dir, const uint4 (&tv)[NV], F &&hit)
+                                            const uint2 *s_run, const uint4 (&tv)[NV], F &&hit)
 {
+    // packed codes: 32 bits for m <= 16, else 64
+    typedef typename std::conditional<WIDE, unsigned long long, uint32_t>::type CT;
     const int m = a.m, B = a.B, Bp = a.Bp;
-    const unsigned long long mask = m >= 32 ? ~0ull : ((1ull << (2 * m)) - 1ull);
+    const CT mask = m >= int(4 * sizeof(CT)) ? ~CT(0) : CT((CT(1) << (2 * m)) - 1);
     const uint32_t bmask = (1u << (2 * B)) - 1u;
     const int pshift = 2 * (m - Bp);
     const int lim = kChunk + m - 1;   // window ends at offsets < lim
-    unsigned long long code = 0;
+    CT code = 0;
     int bad = -1;                     // last offset holding a byte outside the alphabet
     int next = m - 1;                 // next window end to examine
     // one 16-byte vector per iteration (a rolled loop keeps the code small;
@@ -176,28 +180,29 @@ __device__ __forceinline__ void wm_walk_dna(const WmArgs &a, const uint8_t *s_sh
             for (int k = 0; k < 4; ++k) {
                 const int i = v * 16 + q * 4 + k;
                 if (i < lim) {
-                    code = ((code << 2) | ((a4 >> (8 * k)) & 3u)) & mask;
+                    code = ((code << 2) | CT((a4 >> (8 * k)) & 3u)) & mask;
                     if (!((y >> (8 * k + 7)) & 1u)) bad = i;
                     if (i >= next) {
                         const uint32_t blk = uint32_t(code) & bmask;
-                        const uint32_t sh = bad > i - B ? uint32_t(m - B + 1) : uint32_t(s_shift2[blk]);
+                        uint32_t sh = s_shift2[blk];
+                        if (bad > i - B) sh = uint32_t(m - B + 1);
                         if (sh > 0) {
                             next = i + int(sh);
                         } else {
                             next = i + 1;
                             if (bad <= i - m) {
-                                const uint32_t key = (blk << (2 * Bp)) | uint32_t(code >> pshift);
-                                const uint32_t lo = s_dir[key], hi = s_dir[key + 1];
-                                for (uint32_t k0 = lo; k0 < hi; k0 += 4) {
-                                    unsigned long long cc[4];
+                                // the run of (block, prefix), sorted by packed code:
+                                // stop at the first code not below the window's
+                                const uint2 run = s_run[(blk << (2 * Bp)) | uint32_t(code >> pshift)];
+                                for (uint32_t k0 = run.x; k0 < run.y; k0 += 4) {
+                                    CT cc[4];
 #pragma unroll
-                                    for (int u = 0; u < 4; ++u) cc[u] = k0 + u < hi ? __ldg(a.ccode + k0 + u) : ~0ull;
-                                    // the run is sorted: stop at the first code not below the window's
+                                    for (int u = 0; u < 4; ++u) cc[u] = k0 + u < run.y ? CT(__ldg(a.ccode + k0 + u)) : CT(0);
                                     bool stop = false;
                                     int hu = -1;
 #pragma unroll
                                     for (int u = 0; u < 4; ++u) {
-                                        const bool ok = k0 + u < hi;
+                                        const bool ok = k0 + u < run.y;
                                         stop |= ok && cc[u] >= code;
                                         if (ok && cc[u] == code) hu = u;
                                     }
@@ -213,7 +218,7 @@ __device__ __forceinline__ void wm_walk_dna(const WmArgs &a, const uint8_t *s_sh
     }
 }
 
-template <bool SHIFT_SMEM, bool DNA, int NV>
+template <bool SHIFT_SMEM, bool DNA, int NV, bool WIDE>
 __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -224,8 +229,8 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
     p += (SHIFT_SMEM && !DNA) ? r16w(1LL << a.hbits) : 0;
     uint8_t *s_shift2 = p;
     p += DNA ? r16w(1LL << (2 * a.B)) : 0;
-    uint32_t *s_dir = reinterpret_cast<uint32_t *>(p);
-    p += DNA ? r16w((long long)(a.nkey + 1) * 4) : 0;
+    uint2 *s_run = reinterpret_cast<uint2 *>(p);   // (first, end) of each run
+    p += DNA ? r16w((long long)a.nkey * 8) : 0;
     uint32_t *s_hist = a.hist_smem ? reinterpret_cast<uint32_t *>(p) : nullptr;
     p += a.hist_smem ? r16w((long long)a.d * 4) : 0;
     p += warp * wm_warp_bytes(a.m, a.pool_cap, DNA);
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
 
     if (DNA) {
         for (int i = threadIdx.x; i < (1 << (2 * a.B)); i += blockDim.x) s_shift2[i] = a.shift2_g[i];
-        for (int i = threadIdx.x; i <= a.nkey; i += blockDim.x) s_dir[i] = a.dir_g[i];
+        for (int i = threadIdx.x; i < a.nkey; i += blockDim.x) s_run[i] = make_uint2(a.dir_g[i], a.dir_g[i + 1]);
     } else if (SHIFT_SMEM) {
         const uint4 *src = reinterpret_cast<const uint4 *>(a.shift_g);
         uint4 *dst = reinterpret_cast<uint4 *>(s_shift);
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
                 if (lane == 0) wm_stage_issue(a, t + G, buf, bar);
                 inflight = true;
             }
-            wm_walk_dna<(DNA ? NV : 1)>(a, s_shift2, s_dir, tv, rec);
+            wm_walk_dna<(DNA ? NV : 1), WIDE>(a, s_shift2, s_run, tv, rec);
         } else {
             wm_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, rec);
         }
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
                 uint8_t *tb = reinterpret_cast<uint8_t *>(tw);
                 const long long g0 = tile0 + cs;
                 for (int b = 0; b < 16 * (DNA ? NV : 1); ++b) tb[b] = g0 + b < a.n ? a.text[g0 + b] : uint8_t(0);
-                wm_walk_dna<(DNA ? NV : 1)>(a, s_shift2, s_dir, tw, again);
+                wm_walk_dna<(DNA ? NV : 1), WIDE>(a, s_shift2, s_run, tw, again);
             } else {
                 wm_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, again);
             }
@@ -407,7 +412,7 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
 long long wm_smem_bytes(int hbits, bool shift_smem, int hist, int d, int warps, int m,
                         int pool_cap, bool dna, int B, int nkey)
 {
-    const long long tables = dna ? r16w(1LL << (2 * B)) + r16w((long long)(nkey + 1) * 4)
+    const long long tables = dna ? r16w(1LL << (2 * B)) + r16w((long long)nkey * 8)
                                  : (shift_smem ? r16w(1LL << hbits) : 0);
     return tables + (hist ? r16w((long long)d * 4) : 0) + (long long)warps * wm_warp_bytes(m, pool_cap, dna);
 }
@@ -467,10 +472,12 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
 
     typedef void (*K)(const WmArgs);
     const int nv = wm_nv(t.m);
-    K fn = dv.dna ? (nv == 6 ? wm_scan_kernel<false, true, 6> : wm_scan_kernel<false, true, 7>)
-                  : (dv.shift_smem ? wm_scan_kernel<true, false, 1> : wm_scan_kernel<false, false, 1>);
-    static int attr_bytes[4] = {0, 0, 0, 0};
-    const int slot = dv.dna ? (nv == 6 ? 2 : 3) : (dv.shift_smem ? 1 : 0);
+    const bool wide = t.m > 16;
+    K fn = dv.dna ? (nv == 6 ? (wide ? wm_scan_kernel<false, true, 6, true> : wm_scan_kernel<false, true, 6, false>)
+                             : wm_scan_kernel<false, true, 7, true>)
+                  : (dv.shift_smem ? wm_scan_kernel<true, false, 1, false> : wm_scan_kernel<false, false, 1, false>);
+    static int attr_bytes[5] = {0, 0, 0, 0, 0};
+    const int slot = dv.dna ? (nv == 6 ? (wide ? 3 : 2) : 4) : (dv.shift_smem ? 1 : 0);
     if (attr_bytes[slot] < dv.smem_bytes) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
         if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
