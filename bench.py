@@ -403,8 +403,7 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
     out["ac_counts_only_gbs"] = n / t / 1e9
     try:
         w = pm.PatternSet.wm(P, 3)
-        t = timeit(w.h, occ, occ.numel(), 0, reps=2)
-        out["wm_b3_list_gbs"] = n / t / 1e9
+        out["wm_b3_list_gbs"] = _time_scan(pm, torch, w.h, d_text, n, P.shape[0], stream, nocc)[0]
         w.close()
     except Exception as e:  # report, never hide
         out["wm_b3_list_error"] = str(e)

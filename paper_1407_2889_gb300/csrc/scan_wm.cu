@@ -46,7 +46,8 @@ struct WmArgs {
     uint32_t *tile_out;           // list: keys per warp tile (groups expanded)
     unsigned long long *seg_sum;  // list: keys per segment of seg_tiles warp tiles
     long long seg_tiles;
-    unsigned long long *slots;    // list: kWarpTile entries per warp tile
+    void *slots;                  // list: kWarpTile entries per warp tile
+    int se4;                      // 4-byte entries (codes fit 15 bits), else 8
     // exact-code tables (ACGT-like sets, m <= 32)
     uint32_t lut;
     const uint8_t *shift2_g;
@@ -329,16 +330,22 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
 
         // slot of this tile (list mode): the lane's entries follow the
         // entries of the lanes before it
-        unsigned long long *dst = nullptr;
+        long long first = 0;
         uint32_t e_incl = 0;
         if (a.list) {
             e_incl = dev::warp_incl_scan(nh, lane);
-            dst = a.slots + t * kWarpTile + (e_incl - nh);
+            first = t * kWarpTile + (e_incl - nh);
         }
-        // slot entry: (start offset in the tile << 32) | code, group flag 2^31
+        // slot entry: (start offset in the tile << 16) | code with group flag
+        // 2^15 (4-byte entries), or << 32 with group flag 2^31
         auto put = [&](uint32_t k, int off, uint32_t code) {
-            const uint32_t c32 = (code & kWmGroup) ? (0x80000000u | (code & ~kWmGroup)) : code;
-            dst[k] = ((unsigned long long)(cs + off) << 32) | c32;
+            const bool grp = (code & kWmGroup) != 0;
+            const uint32_t c = code & ~kWmGroup;
+            if (a.se4)
+                static_cast<uint32_t *>(a.slots)[first + k] = (uint32_t(cs + off) << 16) | (grp ? 0x8000u : 0u) | c;
+            else
+                static_cast<unsigned long long *>(a.slots)[first + k] =
+                    ((unsigned long long)(cs + off) << 32) | (grp ? 0x80000000u : 0u) | c;
         };
         uint32_t cnt = 0;  // keys of this lane (groups expanded)
         if (!ovf) {
@@ -449,9 +456,16 @@ int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevW
     return PM_ETOOBIG;
 }
 
-int64_t wm_workspace_bytes(const WmTables &, int64_t n, bool list)
+// slot entry bytes: 4 when every code (pattern id, or group | 2^15) fits 16 bits
+int wm_slot_bytes(const WmTables &t)
 {
-    return list_workspace_bytes(warp_tiles(n), list, 0, 8);
+    const int64_t groups = t.grp_off.empty() ? 0 : int64_t(t.grp_off.size()) - 1;
+    return t.d < 32768 && groups < 32768 ? 4 : 8;
+}
+
+int64_t wm_workspace_bytes(const WmTables &t, int64_t n, bool list)
+{
+    return list_workspace_bytes(warp_tiles(n), list, 0, wm_slot_bytes(t));
 }
 
 int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t n, bool list,
@@ -461,8 +475,9 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     const long long ntiles = warp_tiles(n);
+    const int se = wm_slot_bytes(t);
     ListParts L;
-    list_workspace_parts(d_ws, ntiles, 0, 8, L);
+    list_workspace_parts(d_ws, ntiles, 0, se, L);
     const int64_t zeroed = list ? L.zeroed_bytes : kWsHeader;
     e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
@@ -516,7 +531,8 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     a.tile_out = L.tile_out;
     a.seg_sum = L.seg_sum;
     a.seg_tiles = L.seg_tiles;
-    a.slots = static_cast<unsigned long long *>(L.slots);
+    a.slots = L.slots;
+    a.se4 = se == 4 ? 1 : 0;
     a.lut = t.lut;
     a.shift2_g = dv.shift2;
     a.dir_g = dv.dir;
@@ -535,7 +551,7 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (!list) return PM_OK;
-    return expand_launch(d_ws, ntiles, 0, 8, dv.grp_off, dv.grp_ids, (int64_t)t.grp_off.size(),
+    return expand_launch(d_ws, ntiles, 0, se, dv.grp_off, dv.grp_ids, (int64_t)t.grp_off.size(),
                          (int64_t)t.grp_ids.size(), d_occ, occ_cap, d_n_occ, nullptr, 0, stream);
 }
 

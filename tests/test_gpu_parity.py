@@ -117,6 +117,37 @@ def test_wm_random_small(B):
         s.close()
 
 
+def test_wm_byte_path_groups_and_overflow():
+    """Sets outside the ACGT-like form take the byte-hash walk; equal
+    patterns enter HASH once under a group code (every id reported, in
+    ascending order), and a lane whose pool overflows walks its staged bytes
+    again."""
+    rng = np.random.default_rng(77)
+    A = np.frombuffer(b"ACGTN", np.uint8)
+    T = A[rng.integers(0, 5, 300000)]
+    P = A[rng.integers(0, 5, (300, 6))]
+    for r in range(0, 300, 3):  # a third copied from the text
+        s0 = int(rng.integers(0, T.size - 6))
+        P[r] = T[s0:s0 + 6]
+    P[1] = P[0]
+    P[2] = P[0]
+    P[5] = P[4]
+    want = oracle.dictionary(T, P, threads=THREADS)
+    for B in (2, 3):
+        s = _wm(P, B)
+        info = s.info()
+        assert info["dna_mode"] == 0 and info["n_distinct"] < P.shape[0]
+        _same(s.scan(T), want, f"byte path B={B}")
+        occ, cnt = s.scan(T, counts_only=True)
+        assert np.array_equal(cnt, want[1])
+        s.close()
+    Tn = np.full(40000, ord("N"), np.uint8)
+    Pn = np.array([list(b"NNNNNNNN"), list(b"NNNNNNNN"), list(b"ANNNNNNN")], np.uint8)
+    s = _wm(Pn, 2)
+    _same(s.scan(Tn), oracle.brute(Tn, Pn), "all-N, every window a match")
+    s.close()
+
+
 def test_edge_cases():
     P = np.frombuffer(b"ACGTACGT", np.uint8).reshape(1, 8)
     for n in [0, 1, 7, 8, 9, 15, 16, 17, 2559, 2560, 2561, 2567, 5120 + 3]:
