@@ -145,6 +145,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="ac", choices=["ac", "wm"],
+                    help="method of the timed steps: Aho-Corasick (the headline) or Wu-Manber")
+    ap.add_argument("--wm-b", type=int, default=3, help="Wu-Manber block length B (with --algo wm)")
     ap.add_argument("--d", type=int, default=8000)
     ap.add_argument("--m", type=int, default=8)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
@@ -158,6 +161,8 @@ def parse():
     ap.add_argument("--only-serve", action="store_true",
                     help="run only the serving measurement and print it")
     ap.add_argument("--no-tune", action="store_true", help="keep the planner's default launch plan")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end pm_scan_to_host timing (ncu launch lists of the timed steps)")
     ap.add_argument("--mode", default="list", choices=["list", "counts"],
                     help="timed step: list mode (default) or counts only")
     ap.add_argument("--text-mib", type=int, default=0,
@@ -167,7 +172,8 @@ def parse():
 
 def workload_name(args) -> str:
     mib = args.text_mib or 1024
-    return (f"EST-shaped {mib} MiB text (seed 1), Aho-Corasick DFA, {args.mode} mode, "
+    method = "Aho-Corasick DFA" if args.algo == "ac" else f"Wu-Manber B={args.wm_b}"
+    return (f"EST-shaped {mib} MiB text (seed 1), {method}, {args.mode} mode, "
             f"d={args.d}, m={args.m} (half copied from the text, half random)")
 
 
@@ -256,11 +262,11 @@ def main():
         T = T[: args.text_mib << 20]
     n = T.size
     d = P.shape[0]
-    s = pm.PatternSet.ac(P)
+    s = pm.PatternSet.ac(P) if args.algo == "ac" else pm.PatternSet.wm(P, args.wm_b)
     stream = torch.cuda.Stream()
     d_text = torch.from_numpy(T).cuda()
     tuned = None
-    if not args.no_tune:  # the autotuner picks the launch plan (not timed)
+    if not args.no_tune and args.algo == "ac":  # the autotuner picks the launch plan (not timed)
         params, tms = s.tune(d_text, counts_only=args.mode == "counts", reps=3)
         tuned = {"ms_per_scan": tms, **{k: params[k] for k in ("placement", "warps_per_cta", "counters", "ids_place")}}
     info = s.info()
@@ -320,14 +326,14 @@ def main():
     achieved = alg_bytes / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": recorded_traffic("ac_scan_kernel", f"est1gib_d{d}_m{args.m}_{args.mode}_n{n}"),
+                "traffic": recorded_traffic(f"{args.algo}_scan_kernel", f"est1gib_d{d}_m{args.m}_{args.mode}_n{n}"),
                 "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel": "ac_scan_kernel<uint16_t,6,1,dna,smem> + expand_kernel (list mode)"}
+                "kernel": (f"{args.algo}_scan_kernel" + (" + expand_kernel (list mode)" if args.mode == "list" else ""))}
 
     # end to end through the public API: pinned host text in, pinned host
     # counts and occurrence list out (pm_scan_to_host), copies inside the timing
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         pinned = torch.from_numpy(T).pin_memory()
         h_counts = torch.empty(d, dtype=torch.int64).pin_memory()
         h_occ = torch.empty(max(n_occ, 1), dtype=torch.int64).pin_memory()
@@ -346,7 +352,7 @@ def main():
                "ms_per_call": [round(x * 1e3, 3) for x in reps], "statistic": "median of 7 calls"}
 
     extras = {}
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and not args.no_extras and args.algo == "ac":
         extras = secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, torch, synth)
         torch.cuda.empty_cache()
         if args.batch_k > 0:
@@ -354,7 +360,7 @@ def main():
             extras["batched"] = batched_comparison(args, T, d_text, pm, torch, synth)
             torch.cuda.empty_cache()
 
-    if rank == 0 and not args.no_extras and args.serve_seconds > 0:
+    if rank == 0 and not args.no_extras and args.algo == "ac" and args.serve_seconds > 0:
         extras["serving"] = serving_run(args, pinned, pm, torch, synth)
 
     cpu = None
@@ -369,10 +375,11 @@ def main():
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": workload_name(args),
-                       "text_bytes": n, "d": d, "m": args.m, "algo": "AC", "mode": args.mode,
+                       "text_bytes": n, "d": d, "m": args.m, "algo": args.algo.upper(), "mode": args.mode,
                        "n_occ": n_occ, "l2": "inputs larger than L2 (1 GiB text), no flush",
                        "parallelism": f"replicas x{world}",
-                       "table": {k: info[k] for k in ("n_rows", "entry_bytes", "placement", "smem_rows", "table_bytes")},
+                       "table": {k: info[k] for k in ("n_rows", "entry_bytes", "placement", "smem_rows", "table_bytes",
+                                                      "B", "Bp", "dna_mode") if info.get(k)},
                        "plan": tuned or "planner default"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * (3 if args.mode == "list" else 1), "clocks": clk, "extras": extras,
