@@ -12,7 +12,9 @@ per-pattern counts. Four independent routes are offered (see ``pm_oracle.c``):
 * :func:`dictionary` -- membership of each window in a sorted dictionary,
   multithreaded (large inputs);
 * :func:`ac_search` -- sequential Aho-Corasick, Algorithms 1-3;
-* :func:`wm_search` -- sequential Wu-Manber, Algorithms 4-5, paper's hash.
+* :func:`wm_search` -- sequential Wu-Manber, Algorithms 4-5, paper's hash;
+* :func:`brute_var` / :func:`dictionary_var` -- the definition for sets whose
+  patterns have their own lengths (each pattern's length in place of m).
 
 Occurrences come back as ``uint64`` keys ``(i << 32) | r`` sorted ascending.
 """
@@ -90,6 +92,11 @@ def _bind(lib):
     lib.orc_wm_hash_next.argtypes = [vp, i64]
     lib.orc_wm_search.restype = i64
     lib.orc_wm_search.argtypes = [vp, _u8p, i64, _u64p, i64, _i64p]
+    if hasattr(lib, "orc_brute_var"):
+        lib.orc_brute_var.restype = i64
+        lib.orc_brute_var.argtypes = [_u8p, i64, _u8p, _i64p, i64, _u64p, i64, _i64p]
+        lib.orc_dict_var.restype = i64
+        lib.orc_dict_var.argtypes = [_u8p, i64, _u8p, _i64p, i64, i32, _u64p, i64, _i64p]
     return lib
 
 
@@ -187,6 +194,49 @@ def dictionary(T, P, threads: int | None = None, lib=None):
     def fn(occ, cap, counts):
         return lib.orc_dict(_ptr(T, _u8p), T.size, _ptr(P, _u8p), d, m, int(threads),
                             _ptr(occ, _u64p), cap, _ptr(counts, _i64p))
+
+    return _run_two_pass(fn, max(1024, T.size // 4), d)
+
+
+def _as_var_patterns(P):
+    """A variable-length set as (concatenated bytes, offsets int64[d+1]) from
+    a list of byte strings / str / uint8 arrays."""
+    rows = [np.frombuffer(p.encode() if isinstance(p, str) else bytes(p), dtype=np.uint8)
+            if not isinstance(p, np.ndarray) else np.ascontiguousarray(p, dtype=np.uint8) for p in P]
+    if not rows:
+        raise ValueError("empty pattern set")
+    off = np.zeros(len(rows) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([r.size for r in rows])
+    cat = np.ascontiguousarray(np.concatenate(rows)) if off[-1] else np.zeros(1, np.uint8)
+    return cat, off
+
+
+def brute_var(T, P, lib=None):
+    """The definition for patterns of their own lengths, as loops. Returns (occ, counts)."""
+    lib = lib or _load()
+    T = _as_text(T)
+    cat, off = _as_var_patterns(P)
+    d = off.size - 1
+
+    def fn(occ, cap, counts):
+        return lib.orc_brute_var(_ptr(T, _u8p), T.size, _ptr(cat, _u8p), _ptr(off, _i64p), d,
+                                 _ptr(occ, _u64p), cap, _ptr(counts, _i64p))
+
+    return _run_two_pass(fn, max(1024, T.size // 8), d)
+
+
+def dictionary_var(T, P, threads: int | None = None, lib=None):
+    """Same set as :func:`brute_var`, by dictionary membership per length; multithreaded."""
+    lib = lib or _load()
+    T = _as_text(T)
+    cat, off = _as_var_patterns(P)
+    d = off.size - 1
+    if threads is None:
+        threads = os.cpu_count() or 1
+
+    def fn(occ, cap, counts):
+        return lib.orc_dict_var(_ptr(T, _u8p), T.size, _ptr(cat, _u8p), _ptr(off, _i64p), d, int(threads),
+                                _ptr(occ, _u64p), cap, _ptr(counts, _i64p))
 
     return _run_two_pass(fn, max(1024, T.size // 4), d)
 

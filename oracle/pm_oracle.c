@@ -28,6 +28,11 @@
  *                  breadth-first order, search that follows supply links.
  *   orc_wm_*    -- sequential Wu-Manber, Algorithms 4 and 5 (Section 3.2)
  *                  with the paper's shift-and-add hash (bitshift 2).
+ *   orc_brute_var, orc_dict_var -- the same definition for a set whose
+ *                  patterns have their own lengths len_r: every (i, r) with
+ *                  i + len_r <= n and t_{i+k} = p^r_k for all k < len_r
+ *                  (the paper's sets have one length m; this is the
+ *                  definition with m replaced by len_r).
  *
  * Readings of the paper taken here (each is also listed in the design notes):
  *   - Algorithm 1 adds pattern i to Output() of the state its path ends in.
@@ -437,4 +442,174 @@ int64_t orc_wm_search(const orc_wm *w, const uint8_t *T, int64_t n,
         }
     }
     return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Variable-length sets: the Section 1 definition with |p^r| = len_r.       */
+/* Pattern r is the bytes P[off[r] .. off[r+1]), off[0] = 0.                */
+/* ------------------------------------------------------------------------ */
+
+/* The definition as loops over start positions and patterns (ascending),   */
+/* so the output is sorted by (i, r) as it is produced.                     */
+int64_t orc_brute_var(const uint8_t *T, int64_t n, const uint8_t *P, const int64_t *off,
+                      int64_t d, uint64_t *occ, int64_t cap, int64_t *counts)
+{
+    int64_t total = 0;
+    for (int64_t r = 0; r < d; r++) counts[r] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t r = 0; r < d; r++) {
+            const int64_t len = off[r + 1] - off[r];
+            if (len < 1 || i + len > n) continue;
+            const uint8_t *q = P + off[r];
+            int64_t k = 0;
+            while (k < len && q[k] == T[i + k]) k++;
+            if (k < len) continue;
+            if (total < cap) occ[total] = ORC_OCC(i, r);
+            total++;
+            counts[r]++;
+        }
+    }
+    return total;
+}
+
+/* By dictionary membership: the patterns sorted by (length, bytes, r); for  */
+/* each start i and each distinct length L, the window T[i..i+L) is located  */
+/* by binary search among the length-L patterns; the ids found at i (over    */
+/* all lengths) are put in ascending order before they are reported.        */
+typedef struct {
+    const uint8_t *P;
+    const int64_t *off;
+} orc_var_ctx;
+
+static orc_var_ctx g_var_ctx;
+
+static int orc_cmp_var(const void *a, const void *b)
+{
+    const int64_t ra = *(const int64_t *)a, rb = *(const int64_t *)b;
+    const int64_t la = g_var_ctx.off[ra + 1] - g_var_ctx.off[ra];
+    const int64_t lb = g_var_ctx.off[rb + 1] - g_var_ctx.off[rb];
+    if (la != lb) return (la > lb) - (la < lb);
+    const int c = memcmp(g_var_ctx.P + g_var_ctx.off[ra], g_var_ctx.P + g_var_ctx.off[rb], (size_t)la);
+    if (c) return c;
+    return (ra > rb) - (ra < rb);
+}
+
+typedef struct {
+    const uint8_t *T;
+    int64_t n;
+    const uint8_t *P;
+    const int64_t *off;
+    const int64_t *sorted;   /* ids by (length, bytes, r) */
+    const int64_t *gfirst;   /* length groups: sorted[gfirst[g] .. gfirst[g+1]) */
+    const int64_t *glen;
+    int64_t ngroups, d;
+    int64_t i0, i1;
+    uint64_t *buf;
+    int64_t len, cap;
+    int64_t *counts;
+    int64_t *found;          /* ids found at one start, up to d */
+    int failed;
+} orc_var_job;
+
+static void *orc_dict_var_worker(void *arg)
+{
+    orc_var_job *jb = (orc_var_job *)arg;
+    for (int64_t i = jb->i0; i < jb->i1; i++) {
+        int64_t nf = 0;
+        for (int64_t g = 0; g < jb->ngroups; g++) {
+            const int64_t L = jb->glen[g];
+            if (i + L > jb->n) continue;
+            const uint8_t *win = jb->T + i;
+            int64_t a = jb->gfirst[g], b = jb->gfirst[g + 1];
+            while (a < b) {  /* first pattern of the group not below the window */
+                const int64_t h = a + (b - a) / 2;
+                if (memcmp(jb->P + jb->off[jb->sorted[h]], win, (size_t)L) >= 0) b = h;
+                else a = h + 1;
+            }
+            for (int64_t k = a; k < jb->gfirst[g + 1]; k++) {
+                const int64_t r = jb->sorted[k];
+                if (memcmp(jb->P + jb->off[r], win, (size_t)L) != 0) break;
+                jb->found[nf++] = r;
+            }
+        }
+        /* ids of different lengths interleave: order them (insertion sort) */
+        for (int64_t x = 1; x < nf; x++) {
+            const int64_t v = jb->found[x];
+            int64_t y = x;
+            while (y > 0 && jb->found[y - 1] > v) { jb->found[y] = jb->found[y - 1]; y--; }
+            jb->found[y] = v;
+        }
+        for (int64_t x = 0; x < nf; x++) {
+            if (jb->len == jb->cap) {
+                const int64_t nc = jb->cap ? 2 * jb->cap : 4096;
+                uint64_t *nb = (uint64_t *)realloc(jb->buf, (size_t)nc * sizeof(uint64_t));
+                if (!nb) { jb->failed = 1; return NULL; }
+                jb->buf = nb;
+                jb->cap = nc;
+            }
+            jb->buf[jb->len++] = ORC_OCC(i, jb->found[x]);
+            jb->counts[jb->found[x]]++;
+        }
+    }
+    return NULL;
+}
+
+/* Returns the total, or -1 if memory ran out. */
+int64_t orc_dict_var(const uint8_t *T, int64_t n, const uint8_t *P, const int64_t *off,
+                     int64_t d, int32_t nthreads, uint64_t *occ, int64_t cap, int64_t *counts)
+{
+    for (int64_t r = 0; r < d; r++) counts[r] = 0;
+    if (d < 1 || n < 1) return 0;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > n) nthreads = (int32_t)n;
+    int64_t *sorted = (int64_t *)malloc((size_t)d * sizeof(int64_t));
+    int64_t *gfirst = (int64_t *)malloc((size_t)(d + 1) * sizeof(int64_t));
+    int64_t *glen = (int64_t *)malloc((size_t)d * sizeof(int64_t));
+    orc_var_job *jobs = (orc_var_job *)calloc((size_t)nthreads, sizeof(orc_var_job));
+    pthread_t *tids = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!sorted || !gfirst || !glen || !jobs || !tids) {
+        free(sorted); free(gfirst); free(glen); free(jobs); free(tids);
+        return -1;
+    }
+    int64_t nz = 0;  /* empty patterns match nowhere: left out */
+    for (int64_t r = 0; r < d; r++)
+        if (off[r + 1] > off[r]) sorted[nz++] = r;
+    g_var_ctx.P = P;
+    g_var_ctx.off = off;
+    qsort(sorted, (size_t)nz, sizeof(int64_t), orc_cmp_var);
+    int64_t ng = 0;
+    for (int64_t k = 0; k < nz; k++) {
+        const int64_t L = off[sorted[k] + 1] - off[sorted[k]];
+        if (ng == 0 || glen[ng - 1] != L) { gfirst[ng] = k; glen[ng] = L; ng++; }
+    }
+    gfirst[ng] = nz;
+
+    int64_t total = 0;
+    int failed = 0;
+    for (int32_t t = 0; t < nthreads; t++) {
+        orc_var_job *jb = &jobs[t];
+        jb->T = T; jb->n = n; jb->P = P; jb->off = off; jb->sorted = sorted;
+        jb->gfirst = gfirst; jb->glen = glen; jb->ngroups = ng; jb->d = d;
+        jb->i0 = n * t / nthreads;
+        jb->i1 = n * (t + 1) / nthreads;
+        jb->counts = (int64_t *)calloc((size_t)d, sizeof(int64_t));
+        jb->found = (int64_t *)malloc((size_t)d * sizeof(int64_t));
+        if (!jb->counts || !jb->found) failed = 1;
+    }
+    if (!failed) {
+        for (int32_t t = 0; t < nthreads; t++) pthread_create(&tids[t], NULL, orc_dict_var_worker, &jobs[t]);
+        for (int32_t t = 0; t < nthreads; t++) pthread_join(tids[t], NULL);
+        /* workers cover consecutive start ranges: concatenation is sorted */
+        for (int32_t t = 0; t < nthreads; t++) {
+            if (jobs[t].failed) failed = 1;
+            for (int64_t k = 0; k < jobs[t].len; k++) {
+                if (total < cap) occ[total] = jobs[t].buf[k];
+                total++;
+            }
+            for (int64_t r = 0; r < d; r++) counts[r] += jobs[t].counts[r];
+        }
+    }
+    for (int32_t t = 0; t < nthreads; t++) { free(jobs[t].buf); free(jobs[t].counts); free(jobs[t].found); }
+    free(sorted); free(gfirst); free(glen); free(jobs); free(tids);
+    return failed ? -1 : total;
 }

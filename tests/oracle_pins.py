@@ -8,7 +8,10 @@ planted mistake) and raises ``AssertionError`` if the oracle disagrees with:
 * the Wu-Manber tables of Algorithm 4 worked by hand (Section 3.2 hash);
 * closed forms: a single run of one letter, de Bruijn texts, m = 1, n < m;
 * Python's ``re`` engine (overlapping lookahead search), a library routine
-  that enumerates occurrences independently of every route here.
+  that enumerates occurrences independently of every route here;
+* for sets whose patterns have their own lengths: a hand-worked example,
+  runs of one letter, a de Bruijn text, the regex engine, and agreement with
+  the fixed-length routes when all lengths are equal.
 
 ``tests/test_oracle_pins.py`` runs them on the oracle; ``tests/test_oracle_mutants.py``
 plants mistakes in a copy of the oracle and checks that some pin fails.
@@ -200,8 +203,100 @@ def pin_periodic(lib):
     _check_against(_regex_matches(T, P), T, P, lib)
 
 
+# ---------------------------------------------------------------------------
+# Sets whose patterns have their own lengths (the definition with len_r for m)
+def _var_routes(T, P, lib):
+    yield ("brute_var",) + tuple(oracle.brute_var(T, P, lib=lib))
+    yield ("dictionary_var",) + tuple(oracle.dictionary_var(T, P, threads=3, lib=lib))
+
+
+def _check_var(expected_pairs, T, P, lib):
+    exp_counts = np.zeros(len(P), dtype=np.int64)
+    for _, r in expected_pairs:
+        exp_counts[r] += 1
+    for name, occ, counts in _var_routes(T, P, lib):
+        got = _pairs(occ)
+        assert got == expected_pairs, f"{name}: occurrences differ ({len(got)} vs {len(expected_pairs)})"
+        assert np.array_equal(counts, exp_counts), f"{name}: per-pattern counts differ"
+
+
+def pin_var_hand_example(lib):
+    # AAAAAC against A, AA, AAC, C, AC, worked by hand from the definition:
+    # A at 0-4, AA at 0-3, AAC at 3, C at 5, AC at 4
+    exp = [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (3, 1), (3, 2),
+           (4, 0), (4, 4), (5, 3)]
+    _check_var(exp, b"AAAAAC", [b"A", b"AA", b"AAC", b"C", b"AC"], lib)
+
+
+def pin_var_letter_runs(lib):
+    # A^L occurs n-L+1 times in A^n (none when L > n); runs of C never
+    for n in (1, 5, 17, 64):
+        P = [b"A" * L for L in (1, 2, 3, 5, 8, 13)] + [b"CC", b"AAA"]
+        exp = sorted((i, r) for r, p in enumerate(P) if p[:1] == b"A" for i in range(n - len(p) + 1))
+        _check_var(exp, b"A" * n, P, lib)
+
+
+def pin_var_de_bruijn(lib):
+    # linearised de Bruijn text of order k (length 4^k + k - 1): every k-mer
+    # once; every L-mer 4^(k-L) times cyclically, plus at most k-L of the
+    # wrapped windows; the L-mers together fill all n - L + 1 windows
+    k = 4
+    s = _de_bruijn(4, k)
+    T = bytes(b"ACGT"[c] for c in s + s[: k - 1])
+    n = len(T)
+    mers = {L: [bytes(b"ACGT"[(x >> (2 * (L - 1 - j))) & 3] for j in range(L)) for x in range(4 ** L)]
+            for L in (1, 2, k)}
+    P = mers[k] + mers[1] + mers[2]
+    for name, occ, counts in _var_routes(T, P, lib):
+        off = 0
+        for L in (k, 1, 2):
+            c = counts[off:off + 4 ** L]
+            assert int(c.sum()) == n - L + 1, f"{name}: the {L}-mers fill every window"
+            assert np.all(c >= 4 ** (k - L)) and np.all(c <= 4 ** (k - L) + (k - L)), f"{name}: {L}-mer counts"
+            off += 4 ** L
+        i, r = oracle.unpack(occ)
+        for ii, rr in zip(i.tolist(), r.tolist()):
+            assert T[ii:ii + len(P[rr])] == P[rr], f"{name}: wrong pattern at {ii}"
+
+
+def pin_var_regex_random(lib, cases: int = 60, seed: int = 11):
+    # mixed lengths, prefixes of one another, duplicates: Python's regex engine
+    rng = np.random.default_rng(seed)
+    for case in range(cases):
+        alphabet = b"ACGTN"[: int(rng.integers(2, 6))]
+        n = int(rng.integers(0, 300))
+        T = bytes(alphabet[j] for j in rng.integers(0, len(alphabet), n))
+        P = []
+        for _ in range(int(rng.integers(1, 14))):
+            L = int(rng.integers(1, 10))
+            if n >= L and rng.random() < 0.5:
+                s0 = int(rng.integers(0, n - L + 1))
+                P.append(T[s0:s0 + L])
+            else:
+                P.append(bytes(alphabet[j] for j in rng.integers(0, len(alphabet), L)))
+        if len(P) > 1 and rng.random() < 0.5:
+            P.append(P[0][: max(1, len(P[0]) - 1)])  # a prefix of another pattern
+        if rng.random() < 0.3:
+            P.append(P[-1])  # a duplicate
+        _check_var(_regex_matches(T, P), T, P, lib)
+
+
+def pin_var_equal_lengths(lib):
+    # with one length for all patterns the set is that of the fixed-length routes
+    rng = np.random.default_rng(5)
+    for case in range(20):
+        m = int(rng.integers(1, 9))
+        T = bytes(b"ACG"[j] for j in rng.integers(0, 3, int(rng.integers(0, 500))))
+        P = [bytes(b"ACG"[j] for j in rng.integers(0, 3, m)) for _ in range(int(rng.integers(1, 10)))]
+        want = oracle.brute(T, P, lib=lib)
+        for name, occ, counts in _var_routes(T, P, lib):
+            assert np.array_equal(occ, want[0]) and np.array_equal(counts, want[1]), name
+
+
 ALL_PINS = [pin_ac_worked_example, pin_wm_tables_example, pin_single_letter_run,
-            pin_de_bruijn, pin_degenerate_sizes, pin_regex_random, pin_periodic]
+            pin_de_bruijn, pin_degenerate_sizes, pin_regex_random, pin_periodic,
+            pin_var_hand_example, pin_var_letter_runs, pin_var_de_bruijn, pin_var_regex_random,
+            pin_var_equal_lengths]
 
 
 def run_all(lib) -> list[str]:

@@ -13,6 +13,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 # (name, exact text in pm_oracle.c, replacement)
 MUTANTS = [
+    ("brute_var_drops_last_window", "if (len < 1 || i + len > n) continue;", "if (len < 1 || i + len >= n) continue;"),
+    ("brute_var_index_i_not_i_plus_k", "while (k < len && q[k] == T[i + k]) k++;", "while (k < len && q[k] == T[i]) k++;"),
+    ("dict_var_lower_bound_skips_equal", "(size_t)L) >= 0) b = h;", "(size_t)L) > 0) b = h;"),
+    ("dict_var_ids_descending", "while (y > 0 && jb->found[y - 1] > v)", "while (y > 0 && jb->found[y - 1] < v)"),
+    ("dict_var_one_length_group", "if (ng == 0 || glen[ng - 1] != L) {", "if (ng == 0) {"),
     ("brute_drops_last_window", "for (int64_t i = 0; i < n - m + 1; i++) {\n        for (int64_t r = 0; r < d; r++) {",
      "for (int64_t i = 0; i < n - m; i++) {\n        for (int64_t r = 0; r < d; r++) {"),
     ("brute_reversed_pattern", "if (T[i + j] != p[j])", "if (T[i + j] != p[m - 1 - j])"),
