@@ -67,6 +67,7 @@ extern "C" {
 #define PM_ALGO_AC 1
 #define PM_ALGO_WM 2
 #define PM_ALGO_PFAC 3
+#define PM_ALGO_ACV 4   /* Aho-Corasick over patterns of mixed lengths */
 
 /* Tuning knobs; a zero field means "pick automatically". */
 typedef struct pm_params {
@@ -87,7 +88,7 @@ typedef struct pm_params {
 typedef struct pm_set pm_set; /* compiled pattern set; owns its device tables */
 
 typedef struct pm_set_info {
-    int32_t algo;             /* PM_ALGO_AC, PM_ALGO_WM or PM_ALGO_PFAC */
+    int32_t algo;             /* PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC or PM_ALGO_ACV */
     int32_t m;
     int64_t d;
     int64_t n_distinct;       /* distinct patterns */
@@ -108,6 +109,9 @@ typedef struct pm_set_info {
     int64_t n_zero_shift;     /* SHIFT entries equal to 0 */
     /* both */
     int64_t device_bytes;     /* device memory owned by the set */
+    /* mixed lengths (PM_ALGO_ACV; m is then the longest length) */
+    int32_t m_min;            /* shortest pattern length (= m for one length) */
+    int32_t max_starts;       /* most patterns that can start at one position */
 } pm_set_info;
 
 typedef struct pm_result {    /* library-owned; release with pm_result_free */
@@ -149,6 +153,24 @@ int pm_wm_compile(const uint8_t *P, int64_t d, int32_t m, int32_t B,
  */
 int pm_pfac_compile(const uint8_t *P, int64_t d, int32_t m,
                     const pm_params *opt, pm_set **out);
+
+/*
+ * Compile an Aho-Corasick set whose patterns have their own lengths (the
+ * Section 1 definition with each pattern's length in place of m; the
+ * paper's sets have one length). Pattern r is P[offsets[r] .. offsets[r+1]),
+ * offsets[0] = 0, each length 1..65; P and offsets are copied. Algorithm 1's
+ * trie, Algorithm 2's supply links and output propagation (Output(s) takes
+ * Output(Supply(s))), merged into one DFA with a row per state; a position
+ * reports every pattern ending there, each at its own start. pm_scan,
+ * pm_scan_to_host (single launch) and pm_scan_device take such sets; the
+ * occurrence list is sorted by (i, r) as for the other sets. The slot part
+ * of the list-mode workspace grows with pm_set_info.max_starts. The batched
+ * scan, the server, the tuner and the allocation-free scan take AC sets only.
+ * Errors: PM_EINVAL (bad offsets, a length 0), PM_ETOOBIG (a length above
+ * 65, d >= 2^25).
+ */
+int pm_acv_compile(const uint8_t *P, const int64_t *offsets, int64_t d,
+                   const pm_params *opt, pm_set **out);
 
 void pm_set_free(pm_set *s);
 int pm_set_get_info(const pm_set *s, pm_set_info *info);

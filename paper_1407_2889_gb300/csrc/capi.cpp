@@ -94,6 +94,7 @@ void release_device(pm_set *s)
                     s->dwm.shift, s->dwm.hoff, s->dwm.hids, s->dwm.hpfx, s->dwm.pats,
                     s->dwm.shift2, s->dwm.dir, s->dwm.ccode, s->dwm.cr,
                     s->dwm.hcode, s->dwm.grp_off, s->dwm.grp_ids,
+                    s->dacv.table, s->dacv.cls, s->dacv.omask, s->dacv.orank, s->dacv.out_off, s->dacv.out_ent,
                     s->c_text, s->c_ws, s->c_out, s->c_counts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -101,6 +102,7 @@ void release_device(pm_set *s)
     s->c_pin = nullptr;
     s->dac = DevAc();
     s->dwm = DevWm();
+    s->dacv = DevAcv();
     s->c_text = s->c_ws = s->c_out = s->c_counts = nullptr;
     s->c_text_cap = s->c_ws_cap = s->c_out_cap = 0;
 }
@@ -149,6 +151,32 @@ int upload_ac(pm_set *s)
     return rc;
 }
 
+int upload_acv(pm_set *s)
+{
+    const AcvTables &v = s->acv;
+    const AcTables &t = v.ac;
+    DevAcv &d = s->dacv;
+    int64_t &tot = s->device_bytes;
+    int rc;
+    // index entries (next_row << 2) | flag for ACGT sets (see DevAc::pre)
+    auto dev_entry = [&](uint32_t e) { return d.pre ? (((e >> 1) << 2) | (e & 1u)) : e; };
+    if (d.entry_bytes == 2) {
+        std::vector<uint16_t> t16(t.table.size());
+        for (size_t i = 0; i < t.table.size(); ++i) t16[i] = uint16_t(dev_entry(t.table[i]));
+        rc = upload(&d.table, t16.data(), t16.size() * 2, tot);
+    } else {
+        std::vector<uint32_t> t32(t.table.size());
+        for (size_t i = 0; i < t.table.size(); ++i) t32[i] = dev_entry(t.table[i]);
+        rc = upload(&d.table, t32.data(), t32.size() * 4, tot);
+    }
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.cls), t.cls, 256, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.omask), v.omask.data(), v.omask.size() * 4, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.orank), v.orank.data(), v.orank.size() * 4, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.out_off), v.out_off.data(), v.out_off.size() * 4, tot);
+    if (!rc) rc = upload(reinterpret_cast<void **>(&d.out_ent), v.out_ent.data(), v.out_ent.size() * 4, tot);
+    return rc;
+}
+
 int upload_wm(pm_set *s)
 {
     const WmTables &t = s->wm;
@@ -179,10 +207,13 @@ int finish_compile(pm_set *s, pm_set **out)
     }
     DeviceProps dp;
     int rc = device_props(dp);
-    const bool ac_like = s->algo != PM_ALGO_WM;
-    if (!rc) rc = ac_like ? ac_plan(s->ac, s->params, dp, s->dac) : wm_plan(s->wm, s->params, dp, s->dwm);
+    const bool ac_like = s->algo == PM_ALGO_AC || s->algo == PM_ALGO_PFAC;
+    if (!rc) {
+        if (s->algo == PM_ALGO_ACV) rc = acv_plan(s->acv, s->params, dp, s->dacv);
+        else rc = ac_like ? ac_plan(s->ac, s->params, dp, s->dac) : wm_plan(s->wm, s->params, dp, s->dwm);
+    }
     if (!rc && s->algo == PM_ALGO_PFAC) s->dac.pre = 0;  // PFAC walks the plain entry format
-    if (!rc) rc = ac_like ? upload_ac(s) : upload_wm(s);
+    if (!rc) rc = s->algo == PM_ALGO_ACV ? upload_acv(s) : ac_like ? upload_ac(s) : upload_wm(s);
     if (rc) {
         release_device(s);
         delete s;
@@ -256,7 +287,10 @@ pm_result *new_result(int64_t d, int64_t n_occ, bool list, bool pinned)
     return r;
 }
 
-int64_t set_d(const pm_set *s) { return s->algo == PM_ALGO_WM ? s->wm.d : s->ac.d; }
+int64_t set_d(const pm_set *s)
+{
+    return s->algo == PM_ALGO_WM ? s->wm.d : s->algo == PM_ALGO_ACV ? s->acv.ac.d : s->ac.d;
+}
 
 }  // namespace
 
@@ -341,6 +375,22 @@ int pm_pfac_compile(const uint8_t *P, int64_t d, int32_t m, const pm_params *opt
     return finish_compile(s, out);
 }
 
+int pm_acv_compile(const uint8_t *P, const int64_t *offsets, int64_t d, const pm_params *opt, pm_set **out)
+{
+    if (!out || !P || !offsets || d < 1 || !params_ok(opt)) return PM_EINVAL;
+    pm_set *s = new (std::nothrow) pm_set();
+    if (!s) return PM_ENOMEM;
+    s->algo = PM_ALGO_ACV;
+    if (opt) s->params = *opt;
+    s->host_only = s->params.host_only != 0;
+    int rc = build_acv(P, offsets, d, s->acv);
+    if (rc) {
+        delete s;
+        return rc;
+    }
+    return finish_compile(s, out);
+}
+
 int pm_wm_compile(const uint8_t *P, int64_t d, int32_t m, int32_t B, const pm_params *opt,
                   pm_set **out)
 {
@@ -373,9 +423,29 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
     std::memset(info, 0, sizeof(*info));
     info->algo = s->algo;
     info->device_bytes = s->device_bytes;
+    if (s->algo == PM_ALGO_ACV) {
+        const AcTables &t = s->acv.ac;
+        info->m = t.m;
+        info->m_min = s->acv.m_min;
+        info->max_starts = s->acv.K;
+        info->d = t.d;
+        info->n_distinct = t.n_distinct;
+        info->n_states = t.n_states;
+        info->n_rows = t.n_rows;
+        info->n_classes = t.n_classes;
+        info->row_width = 1 << t.lw;
+        info->entry_bytes = s->host_only ? (t.dna && t.n_rows <= (1 << 14) ? 2 : 4) : s->dacv.entry_bytes;
+        info->dna_mode = t.dna ? 1 : 0;
+        info->placement = s->dacv.placement;
+        info->smem_rows = s->dacv.smem_entries >> t.lw;
+        info->table_bytes = (t.n_rows << t.lw) * info->entry_bytes;
+        return PM_OK;
+    }
+    info->max_starts = 1;
     if (s->algo != PM_ALGO_WM) {
         const AcTables &t = s->ac;
         info->m = t.m;
+        info->m_min = t.m;
         info->d = t.d;
         info->n_distinct = t.n_distinct;
         info->n_states = t.n_states;
@@ -396,6 +466,7 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
         info->shift_entries = int64_t(t.shift.size());
         info->n_zero_shift = t.n_zero_shift;
         info->n_distinct = t.n_distinct;
+        info->m_min = t.m;
         info->dna_mode = t.dna ? 1 : 0;  // exact 2-bit-code tables in use
     }
     return PM_OK;
@@ -403,6 +474,7 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
 
 static int64_t set_ws_bytes(const pm_set *s, int64_t n, bool list)
 {
+    if (s->algo == PM_ALGO_ACV) return acv_workspace_bytes(s->acv, n, list);
     if (s->algo != PM_ALGO_WM) return ac_workspace_bytes(s->ac, n, list);
     return wm_workspace_bytes(s->wm, n, list);
 }
@@ -431,6 +503,9 @@ int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t f
     if (s->algo == PM_ALGO_PFAC)
         return pfac_launch(s->ac, s->dac, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
                            d_workspace, stream);
+    if (s->algo == PM_ALGO_ACV)
+        return acv_launch(s->acv, s->dacv, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
+                          d_workspace, stream);
     return wm_launch(s->wm, s->dwm, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
                      d_workspace, stream);
 }
@@ -664,7 +739,8 @@ int scan_to_host_pieces(pm_set *s, const uint8_t *T, int64_t n, uint32_t flags, 
 {
     done = false;
     constexpr int64_t kMinPiece = int64_t(64) << 20;
-    if (s->algo == PM_ALGO_WM || (flags & PM_DEVICE_TEXT) || n < 2 * kMinPiece) return PM_OK;
+    if ((s->algo != PM_ALGO_AC && s->algo != PM_ALGO_PFAC) || (flags & PM_DEVICE_TEXT) || n < 2 * kMinPiece)
+        return PM_OK;
     const AcTables &t = s->ac;
     const bool list = !(flags & PM_COUNTS_ONLY);
     const int64_t d = t.d, m = t.m;
@@ -822,6 +898,7 @@ int pm_selfcheck_host_walk(const pm_set *s, const uint8_t *T, int64_t n, pm_resu
         std::vector<int64_t> counts;
         if (s->algo == PM_ALGO_AC) host_walk_ac(s->ac, T, n, occ, counts);
         else if (s->algo == PM_ALGO_PFAC) host_walk_pfac(s->ac, T, n, occ, counts);
+        else if (s->algo == PM_ALGO_ACV) host_walk_acv(s->acv, T, n, occ, counts);
         else host_walk_wm(s->wm, T, n, occ, counts);
         pm_result *r = new_result(int64_t(counts.size()), int64_t(occ.size()), true, false);
         if (!r) return PM_ENOMEM;

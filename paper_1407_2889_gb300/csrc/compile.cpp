@@ -24,6 +24,52 @@ namespace pm {
 
 static inline uint32_t dna_code(uint32_t b) { return ((b >> 1) ^ (b >> 2)) & 3u; }
 
+// Character classes of a pattern alphabet: an ACGT-like alphabet (at most
+// four bytes with distinct codes ((b >> 1) ^ (b >> 2)) & 3) is decoded
+// arithmetically (dna, 4 columns, lut holds the byte of each code); any other
+// alphabet gets dense class numbers and 2^lw columns.
+static void set_classes(const bool present[256], AcTables &t)
+{
+    int nbytes = 0;
+    for (int b = 0; b < 256; ++b) nbytes += present[b];
+    bool dna = nbytes <= 4;
+    int byte_of_code[4] = {-1, -1, -1, -1};
+    for (int b = 0; b < 256 && dna; ++b) {
+        if (!present[b]) continue;
+        int c = int(dna_code(uint32_t(b)));
+        if (byte_of_code[c] >= 0) dna = false;
+        byte_of_code[c] = b;
+    }
+    std::memset(t.cls, 0xFF, sizeof(t.cls));
+    if (dna) {
+        t.dna = true;
+        t.lw = 2;
+        t.n_classes = 4;
+        uint32_t lut = 0;
+        for (int c = 0; c < 4; ++c) {
+            int b = byte_of_code[c];
+            if (b < 0) {
+                // a byte whose own code differs from c can never pass the
+                // check T == lut[code(T)] for code c
+                for (b = 0; b < 256; ++b)
+                    if (int(dna_code(uint32_t(b))) != c) break;
+            }
+            lut |= uint32_t(b) << (8 * c);
+        }
+        t.lut = lut;
+        for (int b = 0; b < 256; ++b)
+            if (present[b]) t.cls[b] = uint8_t(dna_code(uint32_t(b)));
+    } else {
+        int k = 0;
+        for (int b = 0; b < 256; ++b)
+            if (present[b]) t.cls[b] = uint8_t(k++);
+        t.n_classes = k;
+        int lw = 0;
+        while ((1 << lw) < k) ++lw;
+        t.lw = lw;
+    }
+}
+
 int build_ac(const uint8_t *P, int64_t d, int32_t m, AcTables &t)
 {
     if (!P || d < 1 || m < 1) return PM_EINVAL;
@@ -38,44 +84,7 @@ int build_ac(const uint8_t *P, int64_t d, int32_t m, AcTables &t)
         // ---- character classes -------------------------------------------
         bool present[256] = {};
         for (int64_t k = 0; k < d * int64_t(m); ++k) present[P[k]] = true;
-        int nbytes = 0;
-        for (int b = 0; b < 256; ++b) nbytes += present[b];
-        bool dna = nbytes <= 4;
-        int byte_of_code[4] = {-1, -1, -1, -1};
-        for (int b = 0; b < 256 && dna; ++b) {
-            if (!present[b]) continue;
-            int c = int(dna_code(uint32_t(b)));
-            if (byte_of_code[c] >= 0) dna = false;
-            byte_of_code[c] = b;
-        }
-        std::memset(t.cls, 0xFF, sizeof(t.cls));
-        if (dna) {
-            t.dna = true;
-            t.lw = 2;
-            t.n_classes = 4;
-            uint32_t lut = 0;
-            for (int c = 0; c < 4; ++c) {
-                int b = byte_of_code[c];
-                if (b < 0) {
-                    // a byte whose own code differs from c can never pass the
-                    // check T == lut[code(T)] for code c
-                    for (b = 0; b < 256; ++b)
-                        if (int(dna_code(uint32_t(b))) != c) break;
-                }
-                lut |= uint32_t(b) << (8 * c);
-            }
-            t.lut = lut;
-            for (int b = 0; b < 256; ++b)
-                if (present[b]) t.cls[b] = uint8_t(dna_code(uint32_t(b)));
-        } else {
-            int k = 0;
-            for (int b = 0; b < 256; ++b)
-                if (present[b]) t.cls[b] = uint8_t(k++);
-            t.n_classes = k;
-            int lw = 0;
-            while ((1 << lw) < k) ++lw;
-            t.lw = lw;
-        }
+        set_classes(present, t);
         const int W = 1 << t.lw;
 
         // ---- goto function: the trie, states in creation order -----------
@@ -538,6 +547,201 @@ void host_walk_wm(const WmTables &t, const uint8_t *T, int64_t n,
         }
         i += 1;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-length sets: Algorithms 1-2 over patterns of their own lengths. The
+// trie and the supply links are built as for one length; Output(s) takes
+// the patterns ending at s (ascending r) followed by Output(Supply(s))
+// (breadth-first, so the supply's set is complete first). No row is elided.
+// ---------------------------------------------------------------------------
+int build_acv(const uint8_t *P, const int64_t *off, int64_t d, AcvTables &out)
+{
+    if (!P || !off || d < 1 || off[0] != 0) return PM_EINVAL;
+    for (int64_t r = 0; r < d; ++r) {
+        const int64_t len = off[r + 1] - off[r];
+        if (len < 1) return PM_EINVAL;
+        if (len > kAcvMaxLen) return PM_ETOOBIG;
+    }
+    if (d >= (int64_t(1) << 25)) return PM_ETOOBIG;
+    const int64_t total = off[d];
+    if (total + 1 >= (int64_t(1) << 30)) return PM_ETOOBIG;
+    try {
+        out = AcvTables();
+        AcTables &t = out.ac;
+        t.d = d;
+        bool present[256] = {};
+        for (int64_t k = 0; k < total; ++k) present[P[k]] = true;
+        set_classes(present, t);
+        const int W = 1 << t.lw;
+        out.lens.resize(size_t(d));
+        int32_t mmin = kAcvMaxLen, mmax = 0;
+        for (int64_t r = 0; r < d; ++r) {
+            const int32_t len = int32_t(off[r + 1] - off[r]);
+            out.lens[size_t(r)] = len;
+            mmin = std::min(mmin, len);
+            mmax = std::max(mmax, len);
+        }
+        t.m = mmax;
+        out.m_min = mmin;
+
+        // ---- goto trie (Algorithm 1), patterns in input order ------------
+        std::vector<int32_t> go, depth, parent, own_first, own_last;
+        std::vector<int32_t> own_next(size_t(d), -1);
+        auto new_state = [&](int32_t dep, int32_t par) {
+            const int32_t st = int32_t(depth.size());
+            go.insert(go.end(), size_t(W), -1);
+            depth.push_back(dep);
+            parent.push_back(par);
+            own_first.push_back(-1);
+            own_last.push_back(-1);
+            return st;
+        };
+        new_state(0, 0);
+        for (int64_t r = 0; r < d; ++r) {
+            int32_t st = 0;
+            for (int64_t j = off[r]; j < off[r + 1]; ++j) {
+                const int c = t.cls[P[j]];
+                int32_t nx = go[size_t(st) * W + c];
+                if (nx < 0) {
+                    nx = new_state(depth[st] + 1, st);
+                    go[size_t(st) * W + c] = nx;
+                }
+                st = nx;
+            }
+            if (own_last[st] < 0) own_first[st] = int32_t(r);
+            else own_next[own_last[st]] = int32_t(r);
+            own_last[st] = int32_t(r);
+        }
+        const int64_t S = int64_t(depth.size());
+        t.n_states = S;
+
+        // ---- breadth-first order, supply links, full transitions (Alg. 2)
+        std::vector<int32_t> order;
+        order.reserve(size_t(S));
+        order.push_back(0);
+        for (size_t h = 0; h < order.size(); ++h)
+            for (int c = 0; c < W; ++c) {
+                const int32_t nx = go[size_t(order[h]) * W + c];
+                if (nx >= 0) order.push_back(nx);
+            }
+        std::vector<int32_t> supply(size_t(S), 0);
+        for (int c = 0; c < W; ++c)
+            if (go[size_t(c)] < 0) go[size_t(c)] = 0;
+        for (size_t h = 1; h < order.size(); ++h) {
+            const int32_t st = order[h], f = supply[st];
+            for (int c = 0; c < W; ++c) {
+                const int32_t nx = go[size_t(st) * W + c];
+                const int32_t via = go[size_t(f) * W + c];
+                if (nx >= 0) supply[nx] = via;
+                else go[size_t(st) * W + c] = via;
+            }
+        }
+        // the patterns on a state's root path (prefixes of its string): the
+        // most patterns that can start at one text position is their maximum
+        std::vector<int32_t> chain(size_t(S), 0);
+        int32_t K = 1;
+        for (size_t h = 1; h < order.size(); ++h) {
+            const int32_t st = order[h];
+            int32_t own = 0;
+            for (int32_t r = own_first[st]; r >= 0; r = own_next[r]) ++own;
+            chain[size_t(st)] = chain[size_t(parent[st])] + own;
+            K = std::max(K, chain[size_t(st)]);
+        }
+        out.K = K;
+
+        // ---- Output(s) = own(s) + Output(Supply(s)), breadth-first -------
+        std::vector<std::vector<uint32_t>> outs(static_cast<size_t>(S));
+        for (size_t h = 0; h < order.size(); ++h) {
+            const int32_t st = order[h];
+            std::vector<uint32_t> &o = outs[size_t(st)];
+            for (int32_t r = own_first[st]; r >= 0; r = own_next[r])
+                o.push_back((uint32_t(r) << 7) | uint32_t(out.lens[size_t(r)]));
+            if (h > 0) {
+                const std::vector<uint32_t> &f = outs[size_t(supply[st])];
+                o.insert(o.end(), f.begin(), f.end());
+            }
+            std::sort(o.begin(), o.end(), [](uint32_t x, uint32_t y) {
+                const uint32_t lx = x & 127u, ly = y & 127u;
+                if (lx != ly) return lx > ly;  // longer first (earlier start)
+                return (x >> 7) < (y >> 7);
+            });
+            out.max_out = std::max(out.max_out, int32_t(o.size()));
+        }
+
+        // ---- rows: reset row 0, every state breadth-first -------------------
+        std::vector<int32_t> row_of(size_t(S), -1);
+        for (size_t h = 0; h < order.size(); ++h) row_of[order[h]] = int32_t(h + 1);
+        const int64_t rows = S + 1;
+        t.n_rows = rows;
+        t.d0_row = 1;
+        t.table.assign(size_t(rows) << t.lw, 0u);
+        t.row_depth.assign(size_t(rows), 0);
+        for (int c = 0; c < W; ++c) t.table[size_t(c)] = uint32_t(row_of[0]) << 1;  // reset row -> root
+        for (size_t h = 0; h < order.size(); ++h) {
+            const int32_t st = order[h];
+            const int64_t row = row_of[st];
+            t.row_depth[size_t(row)] = depth[st];
+            for (int c = 0; c < W; ++c) {
+                const int32_t nx = go[size_t(st) * W + c];
+                t.table[size_t(row << t.lw) + size_t(c)] =
+                    (uint32_t(row_of[nx]) << 1) | (outs[size_t(nx)].empty() ? 0u : 1u);
+            }
+        }
+        const size_t nwords = size_t((rows + 31) / 32);
+        out.omask.assign(nwords, 0u);
+        out.orank.assign(nwords + 1, 0u);
+        out.out_off.assign(1, 0u);
+        for (int64_t row = 1; row < rows; ++row) {
+            const std::vector<uint32_t> &o = outs[size_t(order[size_t(row - 1)])];
+            if (o.empty()) continue;
+            out.omask[size_t(row) >> 5] |= 1u << (row & 31);
+            out.out_ent.insert(out.out_ent.end(), o.begin(), o.end());
+            out.out_off.push_back(uint32_t(out.out_ent.size()));
+        }
+        for (size_t w = 0; w < nwords; ++w)
+            out.orank[w + 1] = out.orank[w] + uint32_t(__builtin_popcount(out.omask[w]));
+        int64_t distinct = 0;
+        for (int64_t st = 0; st < S; ++st) distinct += own_first[st] >= 0;
+        t.n_distinct = distinct;
+        t.entry_bytes = rows <= 32768 ? 2 : 4;
+        return PM_OK;
+    } catch (const std::bad_alloc &) {
+        out = AcvTables();
+        return PM_ENOMEM;
+    }
+}
+
+// One sequential pass over the DFA; every position reports its output set
+// (each pattern at its own start), then the pairs are put in (i, r) order.
+void host_walk_acv(const AcvTables &v, const uint8_t *T, int64_t n,
+                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
+{
+    const AcTables &t = v.ac;
+    counts.assign(size_t(t.d), 0);
+    occ.clear();
+    uint32_t e = 2u;  // root is row 1
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t b = T[i];
+        uint32_t idx;
+        if (t.dna) {
+            const uint32_t c = dna_code(b);
+            idx = ((t.lut >> (8 * c)) & 0xFFu) == b ? (((e >> 1) << 2) | c) : c;
+        } else {
+            const uint32_t c = t.cls[b];
+            idx = c == 0xFFu ? 0u : (((e >> 1) << t.lw) | c);
+        }
+        e = t.table[idx];
+        if (!(e & 1u)) continue;
+        const uint32_t row = e >> 1;
+        const uint32_t w = row >> 5;
+        const uint32_t rank = v.orank[w] + uint32_t(__builtin_popcount(v.omask[w] & ((1u << (row & 31)) - 1u)));
+        for (uint32_t k = v.out_off[rank]; k < v.out_off[rank + 1]; ++k) {
+            const uint32_t r = v.out_ent[k] >> 7, len = v.out_ent[k] & 127u;
+            emit_entry(occ, counts, i - int64_t(len) + 1, r);
+        }
+    }
+    std::sort(occ.begin(), occ.end());
 }
 
 }  // namespace pm

@@ -95,7 +95,35 @@ struct WmTables {
 };
 constexpr uint32_t kWmGroup = 0x800000u;  // codes fit 24 bits: d < 2^23
 
+// ---------------------------------------------------------------------------
+// Aho-Corasick over a set whose patterns have their own lengths (the
+// Section 1 definition with each pattern's length for m). The DFA keeps a
+// row for every trie state (no terminal elision: a terminal may have
+// children); an entry is (next_row << 1) | flag, the flag set when the
+// next state's output set is not empty. Output(s) = the patterns ending at
+// s plus Output(Supply(s)) (Algorithm 2's output propagation), so a
+// position reports every pattern that ends there. Rows with an output set
+// are numbered by a bitmap with per-word prefix counts; their outputs are a
+// CSR list of (r << 7) | len, longer patterns first, then ascending r.
+// ---------------------------------------------------------------------------
+struct AcvTables {
+    AcTables ac;                   // classes, table, n_rows, entry_bytes (m = longest length)
+    int32_t m_min = 0;
+    std::vector<int32_t> lens;     // per pattern
+    std::vector<uint32_t> omask;   // one bit per row: Output not empty
+    std::vector<uint32_t> orank;   // set bits before each word
+    std::vector<uint32_t> out_off; // CSR over the output rows, in rank order
+    std::vector<uint32_t> out_ent; // (r << 7) | len
+    int32_t K = 1;                 // most patterns that can start at one position
+    int32_t max_out = 1;           // largest output set
+};
+constexpr int32_t kAcvMaxLen = 65; // the halo of the scan kernels (64 bytes)
+
 int build_ac(const uint8_t *P, int64_t d, int32_t m, AcTables &out);
+// pattern r is P[off[r] .. off[r+1]); lengths 1..kAcvMaxLen
+int build_acv(const uint8_t *P, const int64_t *off, int64_t d, AcvTables &out);
+void host_walk_acv(const AcvTables &t, const uint8_t *T, int64_t n,
+                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
 int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTables &out);
 // PFAC: build_ac, then every entry that is not a goto edge becomes 0 (dead)
 int build_pfac(const uint8_t *P, int64_t d, int32_t m, AcTables &out);
@@ -137,6 +165,16 @@ struct DevAc {
     int64_t smem_bytes = 0;
     int32_t placement = 0;
     int64_t max_warps = 0;          // warps in the largest grid a launch uses
+};
+
+struct DevAcv {
+    void *table = nullptr;          // entry_bytes * (n_rows << lw), index entries for ACGT sets
+    uint8_t *cls = nullptr;
+    uint32_t *omask = nullptr, *orank = nullptr, *out_off = nullptr, *out_ent = nullptr;
+    int64_t smem_entries = 0;
+    int32_t warps = 0, pool_cap = 0, hist_smem = 0, hv = 0, entry_bytes = 0, pre = 0, variant = 0;
+    int32_t placement = 0, omask_smem = 0;
+    int64_t smem_bytes = 0;
 };
 
 struct DevWm {
@@ -217,6 +255,12 @@ int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes
                   const uint32_t *grp_ids, int64_t n_grp_off, int64_t n_grp_ids, uint64_t *d_occ,
                   int64_t occ_cap, int64_t *d_n_occ, const unsigned long long *occ_base,
                   unsigned long long pos_base, void *stream);
+// mixed-length Aho-Corasick (scan_acv.cu)
+int acv_plan(const AcvTables &v, const pm_params &opt, const DeviceProps &dp, DevAcv &dev);
+int64_t acv_workspace_bytes(const AcvTables &v, int64_t n, bool list);
+int acv_launch(const AcvTables &v, const DevAcv &dv, const uint8_t *d_text, int64_t n, bool list,
+               int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
+               void *stream);
 // device workspace of a Wu-Manber scan of n bytes (scan_wm.cu)
 int64_t wm_workspace_bytes(const WmTables &t, int64_t n, bool list);
 int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevWm &dev);
@@ -293,8 +337,10 @@ struct pm_set {
     bool host_only = false;
     pm::AcTables ac;
     pm::WmTables wm;
+    pm::AcvTables acv;               // PM_ALGO_ACV
     pm::DevAc dac;
     pm::DevWm dwm;
+    pm::DevAcv dacv;
     int64_t device_bytes = 0;
     // caches for pm_scan (host-pointer convenience path)
     void *c_text = nullptr;  int64_t c_text_cap = 0;

@@ -23,10 +23,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpmscan.so")
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ETOOBIG, PM_ETIMEOUT, PM_ECAPACITY, PM_ENODEV = range(8)
 PM_HOST_TEXT, PM_DEVICE_TEXT, PM_COUNTS_ONLY = 0, 1, 2
 PM_PLACE_AUTO, PM_PLACE_SMEM, PM_PLACE_HYBRID, PM_PLACE_GLOBAL = range(4)
-PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC = 1, 2, 3
+PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC, PM_ALGO_ACV = 1, 2, 3, 4
 
 EXPORTED = [
-    "pm_ac_compile", "pm_pfac_compile", "pm_wm_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
+    "pm_ac_compile", "pm_pfac_compile", "pm_acv_compile", "pm_wm_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
     "pm_scan_to_host", "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device",
     "pm_scan_device_noalloc", "pm_noalloc_scratch_bytes", "pm_scan_status",
     "pm_scan_batch", "pm_batch_prepare", "pm_batch_free", "pm_batch_counts_total",
@@ -54,7 +54,8 @@ class pm_set_info(ctypes.Structure):
                 ("smem_rows", ctypes.c_int64), ("table_bytes", ctypes.c_int64),
                 ("B", ctypes.c_int32), ("Bp", ctypes.c_int32),
                 ("shift_entries", ctypes.c_int64), ("n_zero_shift", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("m_min", ctypes.c_int32),
+                ("max_starts", ctypes.c_int32)]
 
 
 class pm_result(ctypes.Structure):
@@ -111,6 +112,8 @@ def lib():
         L.pm_ac_compile.argtypes = [vp, i64, i32, ctypes.POINTER(pm_params), pp]
         L.pm_pfac_compile.restype = ctypes.c_int
         L.pm_pfac_compile.argtypes = [vp, i64, i32, ctypes.POINTER(pm_params), pp]
+        L.pm_acv_compile.restype = ctypes.c_int
+        L.pm_acv_compile.argtypes = [vp, vp, i64, ctypes.POINTER(pm_params), pp]
         L.pm_wm_compile.restype = ctypes.c_int
         L.pm_wm_compile.argtypes = [vp, i64, i32, i32, ctypes.POINTER(pm_params), pp]
         L.pm_set_free.restype = None
@@ -249,6 +252,32 @@ def pm_pfac_compile(P, params=None) -> int:
     _check(lib().pm_pfac_compile(P.ctypes.data, P.shape[0], P.shape[1],
                                  ctypes.byref(p) if p is not None else None, ctypes.byref(h)),
            "pm_pfac_compile")
+    return int(h.value)
+
+
+def var_patterns(P):
+    """A mixed-length set as (concatenated uint8 bytes, int64 offsets[d+1])
+    from a list of byte strings, str or uint8 arrays, or such a pair."""
+    if isinstance(P, tuple) and len(P) == 2 and isinstance(P[1], np.ndarray):
+        cat = np.ascontiguousarray(P[0], dtype=np.uint8)
+        off = np.ascontiguousarray(P[1], dtype=np.int64)
+        return cat, off
+    rows = [np.frombuffer(p.encode() if isinstance(p, str) else bytes(p), dtype=np.uint8)
+            if not isinstance(p, np.ndarray) else np.ascontiguousarray(p, dtype=np.uint8).ravel() for p in P]
+    off = np.zeros(len(rows) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([r.size for r in rows])
+    cat = np.ascontiguousarray(np.concatenate(rows)) if rows and off[-1] else np.zeros(1, np.uint8)
+    return cat, off
+
+
+def pm_acv_compile(P, params=None) -> int:
+    """Compile a set of patterns of mixed lengths (a list, or (bytes, offsets))."""
+    cat, off = var_patterns(P)
+    h = ctypes.c_void_p()
+    p = _make_params(params)
+    _check(lib().pm_acv_compile(cat.ctypes.data, off.ctypes.data, off.size - 1,
+                                ctypes.byref(p) if p is not None else None, ctypes.byref(h)),
+           "pm_acv_compile")
     return int(h.value)
 
 
@@ -485,6 +514,11 @@ class PatternSet:
     @classmethod
     def wm(cls, P, B: int, params=None) -> "PatternSet":
         return cls(pm_wm_compile(P, B, params), PM_ALGO_WM)
+
+    @classmethod
+    def acv(cls, P, params=None) -> "PatternSet":
+        """Aho-Corasick over patterns of mixed lengths (list of byte strings)."""
+        return cls(pm_acv_compile(P, params), PM_ALGO_ACV)
 
     def info(self) -> dict:
         return pm_set_get_info(self.h)

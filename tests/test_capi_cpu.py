@@ -216,3 +216,69 @@ def test_table_sizes_of_est_sets():
         assert info["n_distinct"] <= 8000
     finally:
         pm.pm_set_free(h)
+
+
+def _var_case(rng, alphabet, n_hi=3000, max_len=20):
+    A = np.frombuffer(alphabet, np.uint8)
+    n = int(rng.integers(0, n_hi))
+    T = A[rng.integers(0, A.size, n)]
+    if n and rng.random() < 0.5:
+        T[rng.integers(0, n, max(1, n // 200))] = ord("\n")
+    P = []
+    for _ in range(int(rng.integers(1, 60))):
+        L = int(rng.integers(1, max_len + 1))
+        if n >= L and rng.random() < 0.6:
+            s0 = int(rng.integers(0, n - L + 1))
+            P.append(bytes(T[s0:s0 + L]))
+        else:
+            P.append(bytes(A[rng.integers(0, A.size, L)]))
+    P.append(P[0][: max(1, len(P[0]) // 2)])   # a prefix of another pattern
+    P.append(P[1 % len(P)][-max(1, len(P[1 % len(P)]) // 2):])  # a suffix
+    P.append(P[0])                              # a duplicate
+    return T, P
+
+
+def _max_starts(P):
+    return max(sum(1 for q in P if p[:len(q)] == q) for p in P)
+
+
+@pytest.mark.parametrize("alphabet", [b"ACGT", b"ACGTN", b"xyz"])
+def test_acv_host_walk_matches_oracle(alphabet):
+    """Mixed-length sets: the host walk of the compiled DFA (output sets
+    through supply links, every pattern at its own start) equals the
+    oracle's definition; info reports the shortest length and the most
+    patterns that can start at one position."""
+    rng = np.random.default_rng(400 + len(alphabet))
+    for case in range(30):
+        T, P = _var_case(rng, alphabet)
+        want_occ, want_cnt = oracle.dictionary_var(T, P, threads=4)
+        h = pm.pm_acv_compile(P, HOST)
+        try:
+            info = pm.pm_set_get_info(h)
+            assert info["algo"] == pm.PM_ALGO_ACV
+            assert info["m"] == max(len(p) for p in P) and info["m_min"] == min(len(p) for p in P)
+            assert info["max_starts"] == _max_starts(P)
+            acgt = set(b"".join(P)) <= set(b"ACGT")
+            assert info["dna_mode"] == (1 if acgt else 0)
+            occ, cnt = pm.pm_selfcheck_host_walk(h, T)
+        finally:
+            pm.pm_set_free(h)
+        assert np.array_equal(occ, want_occ), f"case {case}"
+        assert np.array_equal(cnt, want_cnt), f"case {case}"
+
+
+def test_acv_long_patterns_and_rejects():
+    rng = np.random.default_rng(9)
+    T = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, 5000)]
+    P = [bytes(T[100:165]), bytes(T[100:101]), bytes(T[200:233]), bytes(T[4000:4017])]
+    h = pm.pm_acv_compile(P, HOST)
+    try:
+        occ, cnt = pm.pm_selfcheck_host_walk(h, T)
+    finally:
+        pm.pm_set_free(h)
+    want = oracle.brute_var(T, P)
+    assert np.array_equal(occ, want[0]) and np.array_equal(cnt, want[1])
+    for bad, code in (([b"ACGT" * 17], pm.PM_ETOOBIG), ((np.zeros(4, np.uint8), np.array([0, 2, 2, 4])), pm.PM_EINVAL)):
+        with pytest.raises(pm.PmError) as e:
+            pm.pm_acv_compile(bad, HOST)
+        assert e.value.code == code
