@@ -449,6 +449,7 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
     out["ac_list_sweep"] = sweep
     out["large_sets"] = large_sets(T, d_text, stream, nocc, pm, torch, synth)
     out["wm_list_sweep"], out["pfac_list"] = other_methods(T, d_text, stream, nocc, pm, torch, synth)
+    out["mixed_lengths_list"] = mixed_lengths(T, d_text, stream, nocc, pm, torch, synth)
     out["small_uniform_1mib"] = small_case(stream, nocc, pm, torch, synth)
     return out
 
@@ -475,6 +476,23 @@ def _time_scan(pm, torch, h, d_text, n, d, stream, nocc, reps=2):
     dt = ev0.elapsed_time(ev1) / reps / 1e3
     del ws, buf
     return n / dt / 1e9, tot, dt
+
+
+def mixed_lengths(T, d_text, stream, nocc, pm, torch, synth):
+    """Aho-Corasick over mixed-length sets (lengths uniform in [8, 16] and
+    [8, 32], half copied from the text), full 1 GiB text, list mode."""
+    n = T.size
+    out = {}
+    for d, lo, hi, seed in ((1000, 8, 16, 301), (8000, 8, 16, 302), (8000, 8, 32, 303)):
+        P = synth.mixed_length_patterns(T, d, lo, hi, seed)
+        s = pm.PatternSet.acv(P)
+        gbs, tot, _ = _time_scan(pm, torch, s.h, d_text, n, d, stream, nocc)
+        inf = s.info()
+        out[f"d{d}_len{lo}-{hi}"] = {"gbs": gbs, "n_occ": tot, "rows": inf["n_rows"],
+                                     "placement": inf["placement"], "max_starts": inf["max_starts"]}
+        s.close()
+        torch.cuda.empty_cache()
+    return out
 
 
 def other_methods(T, d_text, stream, nocc, pm, torch, synth):

@@ -186,6 +186,22 @@ def mixed_patterns(text: np.ndarray, d: int, m: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(np.concatenate([a, b]), dtype=np.uint8)
 
 
+def mixed_length_patterns(text: np.ndarray, d: int, lmin: int, lmax: int, seed: int) -> list[bytes]:
+    """d patterns whose lengths are uniform in [lmin, lmax]; patterns
+    0..d//2-1 are ACGT-only windows copied from the text, the rest i.i.d.
+    ACGT (each length drawn from its own streams, seed * 1000 + length)."""
+    lens = uniform_int(seed, SID_MISC, d, lmin, lmax)
+    out: list[bytes] = [b""] * d
+    for L in range(lmin, lmax + 1):
+        idx = np.nonzero(lens == L)[0]
+        k = int((idx < d // 2).sum())
+        a = sampled_patterns(text, k, L, seed * 1000 + L)
+        b = random_patterns(idx.size - k, L, seed * 1000 + L)
+        for j, r in enumerate(idx):
+            out[int(r)] = bytes(a[j] if j < k else b[j - k])
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Named workloads
 # ---------------------------------------------------------------------------
