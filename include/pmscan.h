@@ -68,6 +68,7 @@ extern "C" {
 #define PM_ALGO_WM 2
 #define PM_ALGO_PFAC 3
 #define PM_ALGO_ACV 4   /* Aho-Corasick over patterns of mixed lengths */
+#define PM_ALGO_WMV 5   /* Wu-Manber over patterns of mixed lengths */
 
 /* Tuning knobs; a zero field means "pick automatically". */
 typedef struct pm_params {
@@ -88,7 +89,7 @@ typedef struct pm_params {
 typedef struct pm_set pm_set; /* compiled pattern set; owns its device tables */
 
 typedef struct pm_set_info {
-    int32_t algo;             /* PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC or PM_ALGO_ACV */
+    int32_t algo;             /* PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC, PM_ALGO_ACV or PM_ALGO_WMV */
     int32_t m;
     int64_t d;
     int64_t n_distinct;       /* distinct patterns */
@@ -109,7 +110,7 @@ typedef struct pm_set_info {
     int64_t n_zero_shift;     /* SHIFT entries equal to 0 */
     /* both */
     int64_t device_bytes;     /* device memory owned by the set */
-    /* mixed lengths (PM_ALGO_ACV; m is then the longest length) */
+    /* mixed lengths (PM_ALGO_ACV, PM_ALGO_WMV; m is then the longest length) */
     int32_t m_min;            /* shortest pattern length (= m for one length) */
     int32_t max_starts;       /* most patterns that can start at one position */
 } pm_set_info;
@@ -170,6 +171,19 @@ int pm_pfac_compile(const uint8_t *P, int64_t d, int32_t m,
  * 65, d >= 2^25).
  */
 int pm_acv_compile(const uint8_t *P, const int64_t *offsets, int64_t d,
+                   const pm_params *opt, pm_set **out);
+
+/*
+ * Compile Wu-Manber tables for a set of mixed lengths (same layout of P and
+ * offsets as pm_acv_compile), with m = the shortest length: Algorithm 4 over
+ * every pattern's first m characters (1 <= B <= min(shortest length, 4)),
+ * HASH holding every id in (PREFIX, r) order, and each candidate verified
+ * over its own length. Algorithm 5 visits the windows of length m; the
+ * matches at one start come out in ascending r. Byte-hash tables only (no
+ * exact-code path). Same scan entry points and restrictions as
+ * pm_acv_compile.
+ */
+int pm_wmv_compile(const uint8_t *P, const int64_t *offsets, int64_t d, int32_t B,
                    const pm_params *opt, pm_set **out);
 
 void pm_set_free(pm_set *s);

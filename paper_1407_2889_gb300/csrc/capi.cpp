@@ -93,7 +93,7 @@ void release_device(pm_set *s)
                     s->dac.grp_off, s->dac.grp_ids, s->dac.cls,
                     s->dwm.shift, s->dwm.hoff, s->dwm.hids, s->dwm.hpfx, s->dwm.pats,
                     s->dwm.shift2, s->dwm.dir, s->dwm.ccode, s->dwm.cr,
-                    s->dwm.hcode, s->dwm.grp_off, s->dwm.grp_ids,
+                    s->dwm.hcode, s->dwm.grp_off, s->dwm.grp_ids, s->dwm.poff,
                     s->dacv.table, s->dacv.cls, s->dacv.omask, s->dacv.orank, s->dacv.out_off, s->dacv.out_ent,
                     s->c_text, s->c_ws, s->c_out, s->c_counts};
     for (void *p : ptrs)
@@ -190,6 +190,7 @@ int upload_wm(pm_set *s)
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.hcode), t.hcode.data(), t.hcode.size() * 4, tot);
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.grp_off), t.grp_off.data(), t.grp_off.size() * 4, tot);
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.grp_ids), t.grp_ids.data(), t.grp_ids.size() * 4, tot);
+    if (!rc && t.var) rc = upload(reinterpret_cast<void **>(&d.poff), t.poff.data(), t.poff.size() * 8, tot);
     if (!rc && t.dna) {
         rc = upload(reinterpret_cast<void **>(&d.shift2), t.shift2.data(), t.shift2.size(), tot);
         if (!rc) rc = upload(reinterpret_cast<void **>(&d.dir), t.dir.data(), t.dir.size() * 4, tot);
@@ -289,7 +290,8 @@ pm_result *new_result(int64_t d, int64_t n_occ, bool list, bool pinned)
 
 int64_t set_d(const pm_set *s)
 {
-    return s->algo == PM_ALGO_WM ? s->wm.d : s->algo == PM_ALGO_ACV ? s->acv.ac.d : s->ac.d;
+    if (s->algo == PM_ALGO_WM || s->algo == PM_ALGO_WMV) return s->wm.d;
+    return s->algo == PM_ALGO_ACV ? s->acv.ac.d : s->ac.d;
 }
 
 }  // namespace
@@ -391,6 +393,24 @@ int pm_acv_compile(const uint8_t *P, const int64_t *offsets, int64_t d, const pm
     return finish_compile(s, out);
 }
 
+int pm_wmv_compile(const uint8_t *P, const int64_t *offsets, int64_t d, int32_t B, const pm_params *opt,
+                   pm_set **out)
+{
+    if (!out || !P || !offsets || d < 1 || B < 1 || !params_ok(opt)) return PM_EINVAL;
+    pm_set *s = new (std::nothrow) pm_set();
+    if (!s) return PM_ENOMEM;
+    s->algo = PM_ALGO_WMV;
+    if (opt) s->params = *opt;
+    s->host_only = s->params.host_only != 0;
+    const int bp = s->params.wm_prefix_len > 0 ? s->params.wm_prefix_len : 2;
+    int rc = build_wmv(P, offsets, d, B, bp, s->wm);
+    if (rc) {
+        delete s;
+        return rc;
+    }
+    return finish_compile(s, out);
+}
+
 int pm_wm_compile(const uint8_t *P, int64_t d, int32_t m, int32_t B, const pm_params *opt,
                   pm_set **out)
 {
@@ -442,7 +462,7 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
         return PM_OK;
     }
     info->max_starts = 1;
-    if (s->algo != PM_ALGO_WM) {
+    if (s->algo == PM_ALGO_AC || s->algo == PM_ALGO_PFAC) {
         const AcTables &t = s->ac;
         info->m = t.m;
         info->m_min = t.m;
@@ -467,6 +487,10 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
         info->n_zero_shift = t.n_zero_shift;
         info->n_distinct = t.n_distinct;
         info->m_min = t.m;
+        if (t.var) {
+            info->m = t.m_max;
+            info->max_starts = t.K;
+        }
         info->dna_mode = t.dna ? 1 : 0;  // exact 2-bit-code tables in use
     }
     return PM_OK;
@@ -475,7 +499,7 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
 static int64_t set_ws_bytes(const pm_set *s, int64_t n, bool list)
 {
     if (s->algo == PM_ALGO_ACV) return acv_workspace_bytes(s->acv, n, list);
-    if (s->algo != PM_ALGO_WM) return ac_workspace_bytes(s->ac, n, list);
+    if (s->algo == PM_ALGO_AC || s->algo == PM_ALGO_PFAC) return ac_workspace_bytes(s->ac, n, list);
     return wm_workspace_bytes(s->wm, n, list);
 }
 
@@ -899,6 +923,7 @@ int pm_selfcheck_host_walk(const pm_set *s, const uint8_t *T, int64_t n, pm_resu
         if (s->algo == PM_ALGO_AC) host_walk_ac(s->ac, T, n, occ, counts);
         else if (s->algo == PM_ALGO_PFAC) host_walk_pfac(s->ac, T, n, occ, counts);
         else if (s->algo == PM_ALGO_ACV) host_walk_acv(s->acv, T, n, occ, counts);
+        else if (s->algo == PM_ALGO_WMV) host_walk_wmv(s->wm, T, n, occ, counts);
         else host_walk_wm(s->wm, T, n, occ, counts);
         pm_result *r = new_result(int64_t(counts.size()), int64_t(occ.size()), true, false);
         if (!r) return PM_ENOMEM;

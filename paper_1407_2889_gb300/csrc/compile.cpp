@@ -744,4 +744,128 @@ void host_walk_acv(const AcvTables &v, const uint8_t *T, int64_t n,
     std::sort(occ.begin(), occ.end());
 }
 
+// ---------------------------------------------------------------------------
+// Wu-Manber over mixed lengths (m = the shortest length): Algorithm 4 over
+// every pattern's first m characters, HASH sorted by (PREFIX, r) with every
+// id, the patterns kept whole for verification over their own lengths.
+// ---------------------------------------------------------------------------
+int build_wmv(const uint8_t *P, const int64_t *off, int64_t d, int32_t B, int32_t Bp, WmTables &t)
+{
+    if (!P || !off || d < 1 || off[0] != 0 || B < 1 || Bp < 1) return PM_EINVAL;
+    int32_t mmin = kAcvMaxLen + 1, mmax = 0;
+    for (int64_t r = 0; r < d; ++r) {
+        const int64_t len = off[r + 1] - off[r];
+        if (len < 1) return PM_EINVAL;
+        if (len > kAcvMaxLen) return PM_ETOOBIG;
+        mmin = std::min<int32_t>(mmin, int32_t(len));
+        mmax = std::max<int32_t>(mmax, int32_t(len));
+    }
+    if (B > mmin || B > 4 || Bp > 3) return PM_EINVAL;
+    if (Bp > mmin) Bp = mmin;
+    if (d >= int64_t(kWmGroup)) return PM_ETOOBIG;
+    try {
+        t = WmTables();
+        t.var = true;
+        t.m = mmin;
+        t.m_max = mmax;
+        t.B = B;
+        t.Bp = Bp;
+        t.d = d;
+        const int32_t m = mmin;
+        const size_t H = size_t(1) << (5 * B);
+        t.shift.assign(H, uint8_t(m - B + 1));
+        std::vector<uint32_t> bucket_of(static_cast<size_t>(d));
+        std::vector<uint16_t> prefix(static_cast<size_t>(d));
+        std::vector<uint32_t> fill(H + 1, 0);
+        for (int64_t r = 0; r < d; ++r) {
+            const uint8_t *p = P + off[r];
+            for (int32_t q = m; q >= B; --q) {
+                const uint32_t h = wm_hash(p + (q - B), B);
+                const uint8_t sh = uint8_t(m - q);
+                if (sh < t.shift[h]) t.shift[h] = sh;
+                if (q == m) {
+                    bucket_of[size_t(r)] = h;
+                    prefix[size_t(r)] = uint16_t(wm_hash(p, Bp));
+                    fill[h + 1]++;
+                }
+            }
+        }
+        for (size_t h = 0; h < H; ++h) fill[h + 1] += fill[h];
+        t.hoff = fill;
+        t.hids.assign(size_t(d), 0);
+        for (int64_t r = 0; r < d; ++r) t.hids[fill[bucket_of[size_t(r)]]++] = uint32_t(r);
+        for (size_t h = 0; h < H; ++h) {
+            auto b = t.hids.begin() + t.hoff[h], e = t.hids.begin() + t.hoff[h + 1];
+            std::stable_sort(b, e, [&](uint32_t x, uint32_t y) { return prefix[x] < prefix[y]; });
+        }
+        t.hpfx.resize(size_t(d));
+        t.hcode.resize(size_t(d));
+        for (int64_t k = 0; k < d; ++k) {
+            t.hpfx[size_t(k)] = prefix[t.hids[size_t(k)]];
+            t.hcode[size_t(k)] = t.hids[size_t(k)];
+        }
+        t.pats.assign(P, P + off[d]);
+        t.poff.assign(off, off + d + 1);
+        t.n_distinct = d;
+        t.n_zero_shift = 0;
+        for (size_t h = 0; h < H; ++h) t.n_zero_shift += t.shift[h] == 0;
+        // most patterns that are prefixes of one of them (with multiplicity)
+        std::vector<int64_t> ids(static_cast<size_t>(d));
+        for (int64_t r = 0; r < d; ++r) ids[size_t(r)] = r;
+        std::sort(ids.begin(), ids.end(), [&](int64_t x, int64_t y) {
+            const int64_t lx = off[x + 1] - off[x], ly = off[y + 1] - off[y];
+            const int c = std::memcmp(P + off[x], P + off[y], size_t(std::min(lx, ly)));
+            if (c) return c < 0;
+            return lx < ly;
+        });
+        int32_t K = 1;
+        std::vector<int64_t> stack;  // the chain of patterns that are prefixes of the current one
+        for (int64_t r : ids) {
+            const int64_t len = off[r + 1] - off[r];
+            while (!stack.empty()) {
+                const int64_t q = stack.back(), lq = off[q + 1] - off[q];
+                if (lq <= len && std::memcmp(P + off[q], P + off[r], size_t(lq)) == 0) break;
+                stack.pop_back();
+            }
+            stack.push_back(r);
+            K = std::max<int32_t>(K, int32_t(stack.size()));
+        }
+        t.K = K;
+        return PM_OK;
+    } catch (const std::bad_alloc &) {
+        t = WmTables();
+        return PM_ENOMEM;
+    }
+}
+
+// Algorithm 5 over the shortest length's windows; every candidate whose
+// whole pattern fits and equals the text is reported at the window start.
+void host_walk_wmv(const WmTables &t, const uint8_t *T, int64_t n,
+                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
+{
+    counts.assign(size_t(t.d), 0);
+    occ.clear();
+    const int32_t m = t.m, B = t.B, Bp = t.Bp;
+    int64_t i = m - 1;
+    while (i < n) {
+        const uint32_t h = wm_hash(T + (i - B + 1), B);
+        const uint32_t sh = t.shift[h];
+        if (sh > 0) {
+            i += sh;
+            continue;
+        }
+        const int64_t start = i - m + 1;
+        const uint16_t hp = uint16_t(wm_hash(T + start, Bp));
+        for (uint32_t k = t.hoff[h]; k < t.hoff[h + 1]; ++k) {
+            if (t.hpfx[k] != hp) continue;
+            const uint32_t r = t.hids[k];
+            const int64_t len = t.poff[r + 1] - t.poff[r];
+            if (start + len > n) continue;
+            if (std::memcmp(t.pats.data() + t.poff[r], T + start, size_t(len)) == 0)
+                emit_entry(occ, counts, start, r);
+        }
+        i += 1;
+    }
+}
+
 }  // namespace pm

@@ -92,6 +92,14 @@ struct WmTables {
     std::vector<uint32_t> dir;     // 4^(B+B') + 1 run offsets, key = block << 2B' | prefix
     std::vector<uint64_t> ccode;   // distinct packed patterns, run order (ascending code)
     std::vector<uint32_t> cr;      // their codes (pattern id or kWmGroup | g)
+    // Mixed lengths (pm_wmv_compile): m is the shortest length; SHIFT, HASH
+    // and PREFIX are those of every pattern's first m characters, HASH holds
+    // every id (no group codes: the matches at one start are reported in
+    // ascending r), and a candidate is verified over its own length.
+    bool var = false;
+    int32_t m_max = 0;
+    std::vector<int64_t> poff;     // pattern r is pats[poff[r] .. poff[r+1])
+    int32_t K = 1;                 // most patterns that can start at one position
 };
 constexpr uint32_t kWmGroup = 0x800000u;  // codes fit 24 bits: d < 2^23
 
@@ -125,6 +133,8 @@ int build_acv(const uint8_t *P, const int64_t *off, int64_t d, AcvTables &out);
 void host_walk_acv(const AcvTables &t, const uint8_t *T, int64_t n,
                    std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
 int build_wm(const uint8_t *P, int64_t d, int32_t m, int32_t B, int32_t Bp, WmTables &out);
+// pattern r is P[off[r] .. off[r+1]); 1 <= B <= shortest length, lengths <= kAcvMaxLen
+int build_wmv(const uint8_t *P, const int64_t *off, int64_t d, int32_t B, int32_t Bp, WmTables &out);
 // PFAC: build_ac, then every entry that is not a goto edge becomes 0 (dead)
 int build_pfac(const uint8_t *P, int64_t d, int32_t m, AcTables &out);
 
@@ -133,6 +143,8 @@ void host_walk_ac(const AcTables &t, const uint8_t *T, int64_t n,
                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
 void host_walk_wm(const WmTables &t, const uint8_t *T, int64_t n,
                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
+void host_walk_wmv(const WmTables &t, const uint8_t *T, int64_t n,
+                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
 void host_walk_pfac(const AcTables &t, const uint8_t *T, int64_t n,
                     std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
 
@@ -188,6 +200,7 @@ struct DevWm {
     uint64_t *ccode = nullptr;
     uint32_t *cr = nullptr;
     uint32_t *hcode = nullptr;      // code of each HASH entry
+    int64_t *poff = nullptr;        // mixed lengths: pattern offsets
     uint32_t *grp_off = nullptr;    // groups of equal patterns
     uint32_t *grp_ids = nullptr;
     int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0, stage_cap = 0;
@@ -261,6 +274,11 @@ int64_t acv_workspace_bytes(const AcvTables &v, int64_t n, bool list);
 int acv_launch(const AcvTables &v, const DevAcv &dv, const uint8_t *d_text, int64_t n, bool list,
                int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
                void *stream);
+// list mode of the mixed-length scans: slots of kWarpTile * per_pos entries
+// per tile, (start << 20) | r (4 bytes) or (start << 32) | r (8 bytes), each
+// lane's run sorted by (start, r) while the keys are written
+int sorted_expand_launch(void *d_ws, int64_t nsub, int slot_bytes, int per_pos, uint64_t *d_occ,
+                         int64_t occ_cap, int64_t *d_n_occ, void *stream);
 // device workspace of a Wu-Manber scan of n bytes (scan_wm.cu)
 int64_t wm_workspace_bytes(const WmTables &t, int64_t n, bool list);
 int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevWm &dev);

@@ -576,24 +576,35 @@ int acv_launch(const AcvTables &v, const DevAcv &dv, const uint8_t *d_text, int6
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (!list) return PM_OK;
 
+    return sorted_expand_launch(d_ws, nsub, se, v.K, d_occ, occ_cap, d_n_occ, stream);
+}
+
+int sorted_expand_launch(void *d_ws, int64_t nsub, int slot_bytes, int per_pos, uint64_t *d_occ,
+                         int64_t occ_cap, int64_t *d_n_occ, void *stream)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ListParts L;
+    list_workspace_parts(d_ws, nsub, 0, slot_bytes * per_pos, L);
+    const long long stride = (long long)kWarpTile * per_pos;
     const long long seg_tiles = L.seg_tiles;
     const long long nseg = (nsub + seg_tiles - 1) / seg_tiles;
-    const size_t esmem = size_t((kSortThreads / 32) * kSortCap * se + seg_tiles * 8);
+    const size_t esmem = size_t((kSortThreads / 32) * kSortCap * slot_bytes + seg_tiles * 8);
     unsigned long long *occ = reinterpret_cast<unsigned long long *>(d_occ);
+    long long *n_occ = reinterpret_cast<long long *>(d_n_occ);
     const long long cap = d_occ ? occ_cap : 0;
-    if (se == 4) {
+    cudaError_t e;
+    if (slot_bytes == 4) {
         e = cudaFuncSetAttribute(acv_expand_kernel<uint32_t, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem));
         if (e == cudaSuccess)
             acv_expand_kernel<uint32_t, 20><<<unsigned(nseg), kSortThreads, esmem, st>>>(
-                static_cast<uint32_t *>(L.slots), a.slot_stride, L.tile_ent, L.seg_sum, seg_tiles, nsub, occ, cap,
-                a.n_occ);
+                static_cast<uint32_t *>(L.slots), stride, L.tile_ent, L.seg_sum, seg_tiles, nsub, occ, cap, n_occ);
     } else {
         e = cudaFuncSetAttribute(acv_expand_kernel<unsigned long long, 32>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem));
         if (e == cudaSuccess)
             acv_expand_kernel<unsigned long long, 32><<<unsigned(nseg), kSortThreads, esmem, st>>>(
-                static_cast<unsigned long long *>(L.slots), a.slot_stride, L.tile_ent, L.seg_sum, seg_tiles, nsub,
-                occ, cap, a.n_occ);
+                static_cast<unsigned long long *>(L.slots), stride, L.tile_ent, L.seg_sum, seg_tiles, nsub, occ,
+                cap, n_occ);
     }
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }

@@ -33,7 +33,9 @@ struct WmArgs {
     const uint32_t *hcode;
     const uint16_t *hpfx;
     const uint8_t *pats;
-    int m, B, Bp;
+    const long long *poff;        // mixed lengths: pattern r is pats[poff[r] .. poff[r+1])
+    int m, B, Bp;                 // mixed lengths: m is the shortest length
+    int mbuf;                     // length that sizes the staged halo (the longest)
     long long ntiles;
     int pool_cap, buf;
     int list, hist_smem, d;
@@ -46,8 +48,9 @@ struct WmArgs {
     uint32_t *tile_out;           // list: keys per warp tile (groups expanded)
     unsigned long long *seg_sum;  // list: keys per segment of seg_tiles warp tiles
     long long seg_tiles;
-    void *slots;                  // list: kWarpTile entries per warp tile
-    int se4;                      // 4-byte entries (codes fit 15 bits), else 8
+    void *slots;                  // list: slot_stride entries per warp tile
+    long long slot_stride;
+    int se4;                      // 4-byte entries, else 8
     // exact-code tables (ACGT-like sets, m <= 32)
     uint32_t lut;
     const uint8_t *shift2_g;
@@ -138,6 +141,49 @@ __device__ __forceinline__ void wm_walk(const WmArgs &a, const uint8_t *s_shift,
     }
 }
 
+// Algorithm 5 over the windows of the shortest length m of a mixed-length
+// set; a candidate (the HASH run with the window's PREFIX, in ascending r)
+// matches when its whole pattern, of its own length, equals the text from
+// the window start (avail bytes of text from the lane's chunk start).
+// hit(start_offset, r) in ascending (start, r).
+template <bool SHIFT_SMEM, class F>
+__device__ __forceinline__ void wmv_walk(const WmArgs &a, const uint8_t *s_shift, const uint8_t *w,
+                                         int lim, long long avail, F &&hit)
+{
+    const int m = a.m, B = a.B, Bp = a.Bp;
+    int i = m - 1;
+    while (i < lim) {
+        const uint32_t h = block_hash(w + i - B + 1, B);
+        const uint32_t sh = SHIFT_SMEM ? uint32_t(s_shift[h]) : uint32_t(__ldg(a.shift_g + h));
+        if (sh > 0) {
+            i += int(sh);
+            continue;
+        }
+        const int start = i - (m - 1);
+        const uint8_t *win = w + start;
+        const uint16_t hp = uint16_t(block_hash(win, Bp));
+        uint32_t lo = __ldg(a.hoff + h);
+        const uint32_t end = __ldg(a.hoff + h + 1);
+        uint32_t hi = end;
+        while (lo < hi) {  // first entry with PREFIX >= h'
+            const uint32_t md = (lo + hi) >> 1;
+            if (__ldg(a.hpfx + md) < hp) lo = md + 1;
+            else hi = md;
+        }
+        for (uint32_t k = lo; k < end && __ldg(a.hpfx + k) == hp; ++k) {
+            const uint32_t r = __ldg(a.hids + k);
+            const long long p0 = __ldg(a.poff + r);
+            const int len = int(__ldg(a.poff + r + 1) - p0);
+            if (start + len > avail) continue;
+            const uint8_t *pp = a.pats + p0;
+            int j = 0;
+            while (j < len && __ldg(pp + j) == win[j]) ++j;
+            if (j == len) hit(start, r);
+        }
+        ++i;
+    }
+}
+
 // Algorithm 5 over one lane's windows on an ACGT-like set, with h1 and h2
 // the exact 2-bit codes of the block and the prefix, over the lane's bytes
 // held in registers (NV vectors: chunk + halo). The lane keeps the packed
@@ -219,7 +265,7 @@ __device__ __forceinline__ void wm_walk_dna(const WmArgs &a, const uint8_t *s_sh
     }
 }
 
-template <bool SHIFT_SMEM, bool DNA, int NV, bool WIDE>
+template <bool SHIFT_SMEM, bool DNA, int NV, bool WIDE, bool VAR>
 __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -234,7 +280,7 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
     p += DNA ? r16w((long long)a.nkey * 8) : 0;
     uint32_t *s_hist = a.hist_smem ? reinterpret_cast<uint32_t *>(p) : nullptr;
     p += a.hist_smem ? r16w((long long)a.d * 4) : 0;
-    p += warp * wm_warp_bytes(a.m, a.pool_cap, DNA);
+    p += warp * wm_warp_bytes(a.mbuf, a.pool_cap, DNA);
     uint64_t *bar = reinterpret_cast<uint64_t *>(p);
     uint8_t *buf = p + 16;
     uint32_t *pool = reinterpret_cast<uint32_t *>(buf + r16w(a.buf));
@@ -323,6 +369,8 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
                 inflight = true;
             }
             wm_walk_dna<(DNA ? NV : 1), WIDE>(a, s_shift2, s_run, tv, rec);
+        } else if (VAR) {
+            wmv_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, a.n - (tile0 + cs), rec);
         } else {
             wm_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, rec);
         }
@@ -334,11 +382,19 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
         uint32_t e_incl = 0;
         if (a.list) {
             e_incl = dev::warp_incl_scan(nh, lane);
-            first = t * kWarpTile + (e_incl - nh);
+            first = t * a.slot_stride + (e_incl - nh);
         }
         // slot entry: (start offset in the tile << 16) | code with group flag
         // 2^15 (4-byte entries), or << 32 with group flag 2^31
         auto put = [&](uint32_t k, int off, uint32_t code) {
+            if (VAR) {  // (start << 20) | r or (start << 32) | r: no groups
+                if (a.se4)
+                    static_cast<uint32_t *>(a.slots)[first + k] = (uint32_t(cs + off) << 20) | code;
+                else
+                    static_cast<unsigned long long *>(a.slots)[first + k] =
+                        ((unsigned long long)(cs + off) << 32) | code;
+                return;
+            }
             const bool grp = (code & kWmGroup) != 0;
             const uint32_t c = code & ~kWmGroup;
             if (a.se4)
@@ -369,6 +425,8 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
                 const long long g0 = tile0 + cs;
                 for (int b = 0; b < 16 * (DNA ? NV : 1); ++b) tb[b] = g0 + b < a.n ? a.text[g0 + b] : uint8_t(0);
                 wm_walk_dna<(DNA ? NV : 1), WIDE>(a, s_shift2, s_run, tw, again);
+            } else if (VAR) {
+                wmv_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, a.n - (tile0 + cs), again);
             } else {
                 wm_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, again);
             }
@@ -440,8 +498,8 @@ int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevW
         for (int wi = 0; wi < 3; ++wi) {
             const int w = forced ? forced : choices[wi];
             const int hist = pass == 0 ? 1 : 0;
-            const long long need = wm_smem_bytes(hbits, shift_smem, hist, int(t.d), w, t.m, dev.pool_cap,
-                                                 t.dna, t.B, 1 << (2 * (t.B + t.Bp)));
+            const long long need = wm_smem_bytes(hbits, shift_smem, hist, int(t.d), w, t.var ? t.m_max : t.m,
+                                                 dev.pool_cap, t.dna, t.B, 1 << (2 * (t.B + t.Bp)));
             if (need <= budget) {
                 dev.warps = w;
                 dev.hist_smem = hist;
@@ -463,8 +521,12 @@ int wm_slot_bytes(const WmTables &t)
     return t.d < 32768 && groups < 32768 ? 4 : 8;
 }
 
+// mixed lengths: 4-byte (start << 20) | r entries for d <= 2^20, K per position
+static int wmv_slot_bytes(const WmTables &t) { return t.d <= (1 << 20) ? 4 : 8; }
+
 int64_t wm_workspace_bytes(const WmTables &t, int64_t n, bool list)
 {
+    if (t.var) return list_workspace_bytes(warp_tiles(n), list, 0, wmv_slot_bytes(t) * t.K);
     return list_workspace_bytes(warp_tiles(n), list, 0, wm_slot_bytes(t));
 }
 
@@ -475,9 +537,10 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     const long long ntiles = warp_tiles(n);
-    const int se = wm_slot_bytes(t);
+    const int se = t.var ? wmv_slot_bytes(t) : wm_slot_bytes(t);
+    const int per_pos = t.var ? t.K : 1;
     ListParts L;
-    list_workspace_parts(d_ws, ntiles, 0, se, L);
+    list_workspace_parts(d_ws, ntiles, 0, se * per_pos, L);
     const int64_t zeroed = list ? L.zeroed_bytes : kWsHeader;
     e = cudaMemsetAsync(d_counts, 0, size_t(t.d) * sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_n_occ, 0, sizeof(int64_t), st);
@@ -488,11 +551,20 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     typedef void (*K)(const WmArgs);
     const int nv = wm_nv(t.m);
     const bool wide = t.m > 16;
-    K fn = dv.dna ? (nv == 6 ? (wide ? wm_scan_kernel<false, true, 6, true> : wm_scan_kernel<false, true, 6, false>)
-                             : wm_scan_kernel<false, true, 7, true>)
-                  : (dv.shift_smem ? wm_scan_kernel<true, false, 1, false> : wm_scan_kernel<false, false, 1, false>);
-    static int attr_bytes[5] = {0, 0, 0, 0, 0};
-    const int slot = dv.dna ? (nv == 6 ? (wide ? 3 : 2) : 4) : (dv.shift_smem ? 1 : 0);
+    K fn;
+    int slot;
+    if (t.var) {
+        fn = dv.shift_smem ? wm_scan_kernel<true, false, 1, false, true> : wm_scan_kernel<false, false, 1, false, true>;
+        slot = dv.shift_smem ? 6 : 5;
+    } else if (dv.dna) {
+        fn = nv == 6 ? (wide ? wm_scan_kernel<false, true, 6, true, false> : wm_scan_kernel<false, true, 6, false, false>)
+                     : wm_scan_kernel<false, true, 7, true, false>;
+        slot = nv == 6 ? (wide ? 3 : 2) : 4;
+    } else {
+        fn = dv.shift_smem ? wm_scan_kernel<true, false, 1, false, false> : wm_scan_kernel<false, false, 1, false, false>;
+        slot = dv.shift_smem ? 1 : 0;
+    }
+    static int attr_bytes[7] = {0, 0, 0, 0, 0, 0, 0};
     if (attr_bytes[slot] < dv.smem_bytes) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
         if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
@@ -513,12 +585,14 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     a.hcode = dv.hcode;
     a.hpfx = dv.hpfx;
     a.pats = dv.pats;
+    a.poff = reinterpret_cast<const long long *>(dv.poff);
     a.m = t.m;
+    a.mbuf = t.var ? t.m_max : t.m;
     a.B = t.B;
     a.Bp = t.Bp;
     a.ntiles = ntiles;
     a.pool_cap = dv.pool_cap;
-    a.buf = wm_tile_buf(t.m, dv.dna != 0);
+    a.buf = wm_tile_buf(a.mbuf, dv.dna != 0);
     a.list = list ? 1 : 0;
     a.hist_smem = dv.hist_smem;
     a.d = int(t.d);
@@ -532,6 +606,7 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     a.seg_sum = L.seg_sum;
     a.seg_tiles = L.seg_tiles;
     a.slots = L.slots;
+    a.slot_stride = (long long)kWarpTile * per_pos;
     a.se4 = se == 4 ? 1 : 0;
     a.lut = t.lut;
     a.shift2_g = dv.shift2;
@@ -551,6 +626,7 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (!list) return PM_OK;
+    if (t.var) return sorted_expand_launch(d_ws, ntiles, se, per_pos, d_occ, occ_cap, d_n_occ, stream);
     return expand_launch(d_ws, ntiles, 0, se, dv.grp_off, dv.grp_ids, (int64_t)t.grp_off.size(),
                          (int64_t)t.grp_ids.size(), d_occ, occ_cap, d_n_occ, nullptr, 0, stream);
 }

@@ -23,10 +23,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpmscan.so")
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_ETOOBIG, PM_ETIMEOUT, PM_ECAPACITY, PM_ENODEV = range(8)
 PM_HOST_TEXT, PM_DEVICE_TEXT, PM_COUNTS_ONLY = 0, 1, 2
 PM_PLACE_AUTO, PM_PLACE_SMEM, PM_PLACE_HYBRID, PM_PLACE_GLOBAL = range(4)
-PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC, PM_ALGO_ACV = 1, 2, 3, 4
+PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC, PM_ALGO_ACV, PM_ALGO_WMV = 1, 2, 3, 4, 5
 
 EXPORTED = [
-    "pm_ac_compile", "pm_pfac_compile", "pm_acv_compile", "pm_wm_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
+    "pm_ac_compile", "pm_pfac_compile", "pm_acv_compile", "pm_wm_compile", "pm_wmv_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
     "pm_scan_to_host", "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device",
     "pm_scan_device_noalloc", "pm_noalloc_scratch_bytes", "pm_scan_status",
     "pm_scan_batch", "pm_batch_prepare", "pm_batch_free", "pm_batch_counts_total",
@@ -114,6 +114,8 @@ def lib():
         L.pm_pfac_compile.argtypes = [vp, i64, i32, ctypes.POINTER(pm_params), pp]
         L.pm_acv_compile.restype = ctypes.c_int
         L.pm_acv_compile.argtypes = [vp, vp, i64, ctypes.POINTER(pm_params), pp]
+        L.pm_wmv_compile.restype = ctypes.c_int
+        L.pm_wmv_compile.argtypes = [vp, vp, i64, i32, ctypes.POINTER(pm_params), pp]
         L.pm_wm_compile.restype = ctypes.c_int
         L.pm_wm_compile.argtypes = [vp, i64, i32, i32, ctypes.POINTER(pm_params), pp]
         L.pm_set_free.restype = None
@@ -278,6 +280,17 @@ def pm_acv_compile(P, params=None) -> int:
     _check(lib().pm_acv_compile(cat.ctypes.data, off.ctypes.data, off.size - 1,
                                 ctypes.byref(p) if p is not None else None, ctypes.byref(h)),
            "pm_acv_compile")
+    return int(h.value)
+
+
+def pm_wmv_compile(P, B: int, params=None) -> int:
+    """Wu-Manber tables for patterns of mixed lengths (a list, or (bytes, offsets))."""
+    cat, off = var_patterns(P)
+    h = ctypes.c_void_p()
+    p = _make_params(params)
+    _check(lib().pm_wmv_compile(cat.ctypes.data, off.ctypes.data, off.size - 1, int(B),
+                                ctypes.byref(p) if p is not None else None, ctypes.byref(h)),
+           "pm_wmv_compile")
     return int(h.value)
 
 
@@ -519,6 +532,11 @@ class PatternSet:
     def acv(cls, P, params=None) -> "PatternSet":
         """Aho-Corasick over patterns of mixed lengths (list of byte strings)."""
         return cls(pm_acv_compile(P, params), PM_ALGO_ACV)
+
+    @classmethod
+    def wmv(cls, P, B: int, params=None) -> "PatternSet":
+        """Wu-Manber over patterns of mixed lengths (m = the shortest)."""
+        return cls(pm_wmv_compile(P, B, params), PM_ALGO_WMV)
 
     def info(self) -> dict:
         return pm_set_get_info(self.h)

@@ -282,3 +282,28 @@ def test_acv_long_patterns_and_rejects():
         with pytest.raises(pm.PmError) as e:
             pm.pm_acv_compile(bad, HOST)
         assert e.value.code == code
+
+
+@pytest.mark.parametrize("alphabet", [b"ACGT", b"ACGTN", b"xyz"])
+def test_wmv_host_walk_matches_oracle(alphabet):
+    """Wu-Manber over mixed lengths (m = the shortest length, every candidate
+    verified over its own length): the host walk equals the oracle."""
+    rng = np.random.default_rng(700 + len(alphabet))
+    for case in range(30):
+        T, P = _var_case(rng, alphabet)
+        mmin = min(len(p) for p in P)
+        want_occ, want_cnt = oracle.dictionary_var(T, P, threads=4)
+        for B in sorted({1, min(2, mmin), min(3, mmin)}):
+            h = pm.pm_wmv_compile(P, B, HOST)
+            try:
+                info = pm.pm_set_get_info(h)
+                assert info["algo"] == pm.PM_ALGO_WMV and info["m_min"] == mmin
+                assert info["m"] == max(len(p) for p in P) and info["max_starts"] == _max_starts(P)
+                occ, cnt = pm.pm_selfcheck_host_walk(h, T)
+            finally:
+                pm.pm_set_free(h)
+            assert np.array_equal(occ, want_occ), f"case {case} B={B}"
+            assert np.array_equal(cnt, want_cnt), f"case {case} B={B}"
+    with pytest.raises(pm.PmError) as e:  # B above the shortest length
+        pm.pm_wmv_compile([b"ACGT", b"AC"], 3, HOST)
+    assert e.value.code == pm.PM_EINVAL

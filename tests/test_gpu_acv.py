@@ -1,4 +1,5 @@
-"""GPU parity of the mixed-length Aho-Corasick scan (pm_acv_compile).
+"""GPU parity of the mixed-length scans: Aho-Corasick (pm_acv_compile) and
+Wu-Manber with m = the shortest length (pm_wmv_compile).
 
 Every result must equal, bit for bit, the oracle's definition with each
 pattern's own length: random sets over several alphabets (prefixes,
@@ -152,4 +153,46 @@ def test_acv_more_than_2_20_patterns():
     want = oracle.dictionary_var(T, P, threads=THREADS)
     s = pm.PatternSet.acv(P)
     _same(s.scan(T), want, "d > 2^20")
+    s.close()
+
+
+@pytest.mark.parametrize("alphabet,lo,hi,B", [(b"ACGT", 4, 16, 3), (b"ACGT", 8, 40, 3), (b"ACGTN", 3, 12, 2),
+                                              (b"ab", 2, 20, 1)])
+def test_wmv_random_sets(alphabet, lo, hi, B):
+    rng = np.random.default_rng(800 + hi + B)
+    A = np.frombuffer(alphabet, np.uint8)
+    for case in range(10):
+        n = int(rng.integers(0, 200000))
+        T = A[rng.integers(0, A.size, n)]
+        P = []
+        for _ in range(int(rng.integers(1, 120))):
+            L = int(rng.integers(lo, hi + 1))
+            if n >= L and rng.random() < 0.6:
+                s0 = int(rng.integers(0, n - L + 1))
+                P.append(bytes(T[s0:s0 + L]))
+            else:
+                P.append(bytes(A[rng.integers(0, A.size, L)]))
+        P.append(P[0][: max(lo, len(P[0]) - 2)])
+        P.append(P[0])
+        want = oracle.dictionary_var(T, P, threads=THREADS)
+        s = pm.PatternSet.wmv(P, B)
+        _same(s.scan(T), want, f"case {case}")
+        _, cnt = s.scan(T, counts_only=True)
+        assert np.array_equal(cnt, want[1])
+        s.close()
+
+
+def test_wmv_est_text_and_overflow():
+    T = synth.est_text(16 << 20, 1)
+    P = synth.mixed_length_patterns(T, 2000, 8, 24, 311)
+    want = oracle.dictionary_var(T, P, threads=THREADS)
+    s = pm.PatternSet.wmv(P, 3)
+    _same(s.scan(torch.from_numpy(T).cuda()), want, "EST 16 MiB")
+    s.close()
+    A = np.full(60000, ord("A"), np.uint8)
+    A[4242] = ord("C")
+    Pa = [b"A" * L for L in range(2, 13)] + [b"AAAA", b"CAAA"]
+    s = pm.PatternSet.wmv(Pa, 2)
+    assert s.info()["max_starts"] == 12
+    _same(s.scan(A), oracle.dictionary_var(A, Pa, threads=THREADS), "all-A")
     s.close()
