@@ -479,8 +479,9 @@ def _time_scan(pm, torch, h, d_text, n, d, stream, nocc, reps=2):
 
 
 def mixed_lengths(T, d_text, stream, nocc, pm, torch, synth):
-    """Aho-Corasick over mixed-length sets (lengths uniform in [8, 16] and
-    [8, 32], half copied from the text), full 1 GiB text, list mode."""
+    """Aho-Corasick and Wu-Manber (B=3, m = the shortest length) over
+    mixed-length sets (lengths uniform in [8, 16] and [8, 32], half copied
+    from the text), full 1 GiB text, list mode."""
     n = T.size
     out = {}
     for d, lo, hi, seed in ((1000, 8, 16, 301), (8000, 8, 16, 302), (8000, 8, 32, 303)):
@@ -488,9 +489,13 @@ def mixed_lengths(T, d_text, stream, nocc, pm, torch, synth):
         s = pm.PatternSet.acv(P)
         gbs, tot, _ = _time_scan(pm, torch, s.h, d_text, n, d, stream, nocc)
         inf = s.info()
-        out[f"d{d}_len{lo}-{hi}"] = {"gbs": gbs, "n_occ": tot, "rows": inf["n_rows"],
-                                     "placement": inf["placement"], "max_starts": inf["max_starts"]}
         s.close()
+        w = pm.PatternSet.wmv(P, 3)
+        wgbs, wtot, _ = _time_scan(pm, torch, w.h, d_text, n, d, stream, nocc)
+        w.close()
+        assert wtot == tot
+        out[f"d{d}_len{lo}-{hi}"] = {"ac_gbs": gbs, "wm_b3_gbs": wgbs, "n_occ": tot, "rows": inf["n_rows"],
+                                     "placement": inf["placement"], "max_starts": inf["max_starts"]}
         torch.cuda.empty_cache()
     return out
 
