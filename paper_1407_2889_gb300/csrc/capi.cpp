@@ -93,7 +93,7 @@ void release_device(pm_set *s)
                     s->dac.grp_off, s->dac.grp_ids, s->dac.cls,
                     s->dwm.shift, s->dwm.hoff, s->dwm.hids, s->dwm.hpfx, s->dwm.pats,
                     s->dwm.shift2, s->dwm.dir, s->dwm.ccode, s->dwm.cr,
-                    s->dwm.hcode, s->dwm.grp_off, s->dwm.grp_ids, s->dwm.poff,
+                    s->dwm.hcode, s->dwm.grp_off, s->dwm.grp_ids, s->dwm.poff, s->dwm.fcode, s->dwm.flen,
                     s->dacv.table, s->dacv.cls, s->dacv.omask, s->dacv.orank, s->dacv.out_off, s->dacv.out_ent,
                     s->c_text, s->c_ws, s->c_out, s->c_counts};
     for (void *p : ptrs)
@@ -191,6 +191,10 @@ int upload_wm(pm_set *s)
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.grp_off), t.grp_off.data(), t.grp_off.size() * 4, tot);
     if (!rc) rc = upload(reinterpret_cast<void **>(&d.grp_ids), t.grp_ids.data(), t.grp_ids.size() * 4, tot);
     if (!rc && t.var) rc = upload(reinterpret_cast<void **>(&d.poff), t.poff.data(), t.poff.size() * 8, tot);
+    if (!rc && t.var && t.dna) {
+        rc = upload(reinterpret_cast<void **>(&d.fcode), t.fcode.data(), t.fcode.size() * 8, tot);
+        if (!rc) rc = upload(reinterpret_cast<void **>(&d.flen), t.flen.data(), t.flen.size(), tot);
+    }
     if (!rc && t.dna) {
         rc = upload(reinterpret_cast<void **>(&d.shift2), t.shift2.data(), t.shift2.size(), tot);
         if (!rc) rc = upload(reinterpret_cast<void **>(&d.dir), t.dir.data(), t.dir.size() * 4, tot);

@@ -744,6 +744,80 @@ void host_walk_acv(const AcvTables &v, const uint8_t *T, int64_t n,
     std::sort(occ.begin(), occ.end());
 }
 
+// Exact-code tables of a mixed-length ACGT-like set (longest length <= 32,
+// B + B' <= 6): those of build_wm_packed over every pattern's first m
+// characters, every id kept (runs sorted by (code of the m characters, r)),
+// plus each candidate's whole packed pattern and its length.
+static void build_wmv_packed(const uint8_t *P, const int64_t *off, int64_t d, int32_t m, int32_t mmax,
+                             int32_t B, int32_t Bp, WmTables &t)
+{
+    t.dna = false;
+    if (mmax > 32 || B + Bp > 6) return;
+    bool present[256] = {};
+    for (int64_t k = 0; k < off[d]; ++k) present[P[k]] = true;
+    int byte_of_code[4] = {-1, -1, -1, -1};
+    for (int b = 0; b < 256; ++b) {
+        if (!present[b]) continue;
+        const int c = int(dna_code(uint32_t(b)));
+        if (byte_of_code[c] >= 0) return;  // not ACGT-like
+        byte_of_code[c] = b;
+    }
+    uint32_t lut = 0;
+    for (int c = 0; c < 4; ++c) {
+        int b = byte_of_code[c];
+        if (b < 0)
+            for (b = 0; b < 256; ++b)
+                if (int(dna_code(uint32_t(b))) != c) break;
+        lut |= uint32_t(b) << (8 * c);
+    }
+    const size_t NB = size_t(1) << (2 * B), NK = size_t(1) << (2 * (B + Bp));
+    std::vector<uint8_t> shift2(NB, uint8_t(m - B + 1));
+    std::vector<uint64_t> pre(static_cast<size_t>(d)), full(static_cast<size_t>(d));
+    std::vector<uint32_t> key(static_cast<size_t>(d));
+    std::vector<uint32_t> fill(NK + 1, 0);
+    for (int64_t r = 0; r < d; ++r) {
+        const uint8_t *p = P + off[r];
+        const int32_t len = int32_t(off[r + 1] - off[r]);
+        uint64_t c = 0;
+        for (int32_t j = 0; j < len; ++j) {
+            c = (c << 2) | dna_code(p[j]);
+            if (j == m - 1) pre[size_t(r)] = c;
+        }
+        full[size_t(r)] = c;
+        for (int32_t q = m; q >= B; --q) {
+            uint32_t h = 0;
+            for (int32_t j = q - B; j < q; ++j) h = (h << 2) | dna_code(p[j]);
+            if (uint8_t(m - q) < shift2[h]) shift2[h] = uint8_t(m - q);
+        }
+        const uint64_t pc = pre[size_t(r)];
+        key[size_t(r)] = (uint32_t(pc & (NB - 1)) << (2 * Bp)) | uint32_t(pc >> (2 * (m - Bp)));
+        fill[key[size_t(r)] + 1]++;
+    }
+    for (size_t k = 0; k < NK; ++k) fill[k + 1] += fill[k];
+    std::vector<uint32_t> order(static_cast<size_t>(d));
+    for (int64_t r = 0; r < d; ++r) order[size_t(r)] = uint32_t(r);
+    std::sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        if (key[x] != key[y]) return key[x] < key[y];
+        if (pre[x] != pre[y]) return pre[x] < pre[y];
+        return x < y;
+    });
+    t.shift2 = std::move(shift2);
+    t.dir = std::move(fill);
+    t.ccode.resize(size_t(d));
+    t.cr.resize(size_t(d));
+    t.fcode.resize(size_t(d));
+    t.flen.resize(size_t(d));
+    for (int64_t k = 0; k < d; ++k) {
+        const uint32_t r = order[size_t(k)];
+        t.ccode[size_t(k)] = pre[r];
+        t.cr[size_t(k)] = r;
+        t.fcode[size_t(k)] = full[r];
+        t.flen[size_t(k)] = uint8_t(off[r + 1] - off[r]);
+    }
+    t.lut = lut;
+    t.dna = true;
+}
+
 // ---------------------------------------------------------------------------
 // Wu-Manber over mixed lengths (m = the shortest length): Algorithm 4 over
 // every pattern's first m characters, HASH sorted by (PREFIX, r) with every
@@ -831,10 +905,51 @@ int build_wmv(const uint8_t *P, const int64_t *off, int64_t d, int32_t B, int32_
             K = std::max<int32_t>(K, int32_t(stack.size()));
         }
         t.K = K;
+        build_wmv_packed(P, off, d, mmin, mmax, B, Bp, t);
         return PM_OK;
     } catch (const std::bad_alloc &) {
         t = WmTables();
         return PM_ENOMEM;
+    }
+}
+
+// Algorithm 5 over the shortest length's windows with the exact-code
+// tables: the run of the window's (block, prefix) entries whose code of the
+// first m characters equals the window's, in ascending r; a longer
+// candidate also needs the text's next len - m bytes to extend the window's
+// code to its whole packed pattern.
+static void host_walk_wmv_packed(const WmTables &t, const uint8_t *T, int64_t n,
+                                 std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
+{
+    const int32_t m = t.m, B = t.B, Bp = t.Bp;
+    const uint64_t mask = m >= 32 ? ~uint64_t(0) : ((uint64_t(1) << (2 * m)) - 1);
+    const uint32_t bmask = (1u << (2 * B)) - 1u;
+    auto ok = [&](uint32_t b) { return ((t.lut >> (8 * dna_code(b))) & 0xFFu) == b; };
+    uint64_t code = 0;
+    int64_t bad = -1, skip = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t b = T[i];
+        if (!ok(b)) bad = i;
+        code = ((code << 2) | dna_code(b)) & mask;
+        if (i < m - 1) continue;
+        if (skip > 0) { --skip; continue; }
+        const uint32_t sh = bad > i - B ? uint32_t(m - B + 1) : t.shift2[uint32_t(code) & bmask];
+        if (sh > 0) { skip = int64_t(sh) - 1; continue; }
+        if (bad > i - m) continue;
+        const uint32_t key = ((uint32_t(code) & bmask) << (2 * Bp)) | uint32_t(code >> (2 * (m - Bp)));
+        for (uint32_t k = t.dir[key]; k < t.dir[key + 1]; ++k) {
+            if (t.ccode[k] < code) continue;
+            if (t.ccode[k] > code) break;
+            const int64_t len = t.flen[k], start = i - m + 1;
+            if (start + len > n) continue;
+            uint64_t ext = code;
+            bool good = true;
+            for (int64_t j = i + 1; j < start + len && good; ++j) {
+                good = ok(T[j]);
+                ext = (ext << 2) | dna_code(T[j]);
+            }
+            if (good && ext == t.fcode[k]) emit_entry(occ, counts, start, t.cr[k]);
+        }
     }
 }
 
@@ -845,6 +960,10 @@ void host_walk_wmv(const WmTables &t, const uint8_t *T, int64_t n,
 {
     counts.assign(size_t(t.d), 0);
     occ.clear();
+    if (t.dna) {
+        host_walk_wmv_packed(t, T, n, occ, counts);
+        return;
+    }
     const int32_t m = t.m, B = t.B, Bp = t.Bp;
     int64_t i = m - 1;
     while (i < n) {

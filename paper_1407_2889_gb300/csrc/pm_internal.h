@@ -100,6 +100,12 @@ struct WmTables {
     int32_t m_max = 0;
     std::vector<int64_t> poff;     // pattern r is pats[poff[r] .. poff[r+1])
     int32_t K = 1;                 // most patterns that can start at one position
+    // mixed lengths on an ACGT-like set (longest length <= 32): the exact-code
+    // tables keyed by the first m characters (dir, shift2, ccode = the code
+    // of those m characters, cr = r, runs sorted by (code, r)), plus each
+    // candidate's whole packed pattern and its length
+    std::vector<uint64_t> fcode;
+    std::vector<uint8_t> flen;
 };
 constexpr uint32_t kWmGroup = 0x800000u;  // codes fit 24 bits: d < 2^23
 
@@ -201,6 +207,8 @@ struct DevWm {
     uint32_t *cr = nullptr;
     uint32_t *hcode = nullptr;      // code of each HASH entry
     int64_t *poff = nullptr;        // mixed lengths: pattern offsets
+    uint64_t *fcode = nullptr;      // mixed lengths, exact codes: whole packed patterns
+    uint8_t *flen = nullptr;
     uint32_t *grp_off = nullptr;    // groups of equal patterns
     uint32_t *grp_ids = nullptr;
     int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0, stage_cap = 0;

@@ -57,6 +57,8 @@ struct WmArgs {
     const uint32_t *dir_g;
     const unsigned long long *ccode;
     const uint32_t *cr;
+    const unsigned long long *fcode;  // mixed lengths: whole packed pattern of each candidate
+    const uint8_t *flen;              // and its length
     int nkey;                     // 4^(B + B')
 };
 
@@ -181,6 +183,71 @@ __device__ __forceinline__ void wmv_walk(const WmArgs &a, const uint8_t *s_shift
             if (j == len) hit(start, r);
         }
         ++i;
+    }
+}
+
+// Algorithm 5 over the windows of the shortest length m of a mixed-length
+// ACGT-like set, with the exact-code tables, over the staged bytes: the
+// rolling code of the window's m characters picks the candidates of its
+// (block, prefix) run with the same code (the run is sorted by (code, r));
+// a longer candidate extends that code with the next len - m bytes and
+// compares it with its whole packed pattern. hit(start_offset, r) in
+// ascending (start, r).
+template <class F>
+__device__ __forceinline__ void wmv_walk_dna(const WmArgs &a, const uint8_t *s_shift2, const uint2 *s_run,
+                                             const uint8_t *w, int lim, long long avail, F &&hit)
+{
+    const int m = a.m, B = a.B, Bp = a.Bp;
+    const unsigned long long mask = m >= 32 ? ~0ull : ((1ull << (2 * m)) - 1ull);
+    const uint32_t bmask = (1u << (2 * B)) - 1u;
+    const int pshift = 2 * (m - Bp);
+    auto cls = [](uint32_t b) { return ((b >> 1) ^ (b >> 2)) & 3u; };
+    auto ok = [&](uint32_t b) { return ((a.lut >> (8 * cls(b))) & 0xFFu) == b; };
+    unsigned long long code = 0;
+    int bad = -1;       // last offset holding a byte outside the alphabet
+    int next = m - 1;   // next window end to examine
+    for (int i = 0; i < lim; ++i) {
+        const uint32_t b = w[i];
+        if (!ok(b)) bad = i;
+        code = ((code << 2) | cls(b)) & mask;
+        if (i < next) continue;
+        const uint32_t blk = uint32_t(code) & bmask;
+        uint32_t sh = s_shift2[blk];
+        if (bad > i - B) sh = uint32_t(m - B + 1);
+        if (sh > 0) {
+            next = i + int(sh);
+            continue;
+        }
+        next = i + 1;
+        if (bad > i - m) continue;
+        const uint2 run = s_run[(blk << (2 * Bp)) | uint32_t(code >> pshift)];
+        const int start = i - (m - 1);
+        // four candidates per step; the run is sorted, so it stops at the
+        // first code above the window's
+        for (uint32_t k0 = run.x; k0 < run.y; k0 += 4) {
+            unsigned long long cc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cc[u] = k0 + u < run.y ? __ldg(a.ccode + k0 + u) : 0ull;
+            bool stop = false;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t k = k0 + u;
+                const bool in = k < run.y;
+                stop |= in && cc[u] > code;
+                if (!in || cc[u] != code) continue;
+                const int len = __ldg(a.flen + k);
+                if (start + len > avail) continue;
+                unsigned long long ext = code;
+                bool good = true;
+                for (int j = i + 1; j < start + len && good; ++j) {
+                    const uint32_t bj = w[j];
+                    good = ok(bj);
+                    ext = (ext << 2) | cls(bj);
+                }
+                if (good && ext == __ldg(a.fcode + k)) hit(start, __ldg(a.cr + k));
+            }
+            if (stop) break;
+        }
     }
 }
 
@@ -357,7 +424,7 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
             ++nh;
         };
         uint4 tv[DNA ? NV : 1];
-        if (DNA) {
+        if (DNA && !VAR) {
             const uint4 *bv = reinterpret_cast<const uint4 *>(buf + cs);
 #pragma unroll
             for (int v = 0; v < (DNA ? NV : 1); ++v) tv[v] = bv[v];
@@ -369,6 +436,8 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
                 inflight = true;
             }
             wm_walk_dna<(DNA ? NV : 1), WIDE>(a, s_shift2, s_run, tv, rec);
+        } else if (VAR && DNA) {
+            wmv_walk_dna(a, s_shift2, s_run, buf + cs, lim, a.n - (tile0 + cs), rec);
         } else if (VAR) {
             wmv_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, a.n - (tile0 + cs), rec);
         } else {
@@ -418,13 +487,15 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
                 if (a.list && k < nh) put(k, off, code);
                 ++k;
             };
-            if (DNA) {
+            if (DNA && !VAR) {
                 // the staged copy may already hold the next tile: text from global memory
                 uint4 tw[DNA ? NV : 1];
                 uint8_t *tb = reinterpret_cast<uint8_t *>(tw);
                 const long long g0 = tile0 + cs;
                 for (int b = 0; b < 16 * (DNA ? NV : 1); ++b) tb[b] = g0 + b < a.n ? a.text[g0 + b] : uint8_t(0);
                 wm_walk_dna<(DNA ? NV : 1), WIDE>(a, s_shift2, s_run, tw, again);
+            } else if (VAR && DNA) {
+                wmv_walk_dna(a, s_shift2, s_run, buf + cs, lim, a.n - (tile0 + cs), again);
             } else if (VAR) {
                 wmv_walk<SHIFT_SMEM>(a, s_shift, buf + cs, lim, a.n - (tile0 + cs), again);
             } else {
@@ -444,7 +515,7 @@ __global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
             }
         }
 
-        if (!DNA) {
+        if (!DNA || VAR) {
             // the buffer is free: stage the next tile
             dev::fence_proxy_async_smem();
             __syncwarp();
@@ -553,7 +624,10 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     const bool wide = t.m > 16;
     K fn;
     int slot;
-    if (t.var) {
+    if (t.var && dv.dna) {
+        fn = wm_scan_kernel<false, true, 1, false, true>;
+        slot = 7;
+    } else if (t.var) {
         fn = dv.shift_smem ? wm_scan_kernel<true, false, 1, false, true> : wm_scan_kernel<false, false, 1, false, true>;
         slot = dv.shift_smem ? 6 : 5;
     } else if (dv.dna) {
@@ -564,7 +638,7 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
         fn = dv.shift_smem ? wm_scan_kernel<true, false, 1, false, false> : wm_scan_kernel<false, false, 1, false, false>;
         slot = dv.shift_smem ? 1 : 0;
     }
-    static int attr_bytes[7] = {0, 0, 0, 0, 0, 0, 0};
+    static int attr_bytes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (attr_bytes[slot] < dv.smem_bytes) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
         if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
@@ -613,6 +687,8 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     a.dir_g = dv.dir;
     a.ccode = reinterpret_cast<const unsigned long long *>(dv.ccode);
     a.cr = dv.cr;
+    a.fcode = reinterpret_cast<const unsigned long long *>(dv.fcode);
+    a.flen = dv.flen;
     a.nkey = t.dna ? (1 << (2 * (t.B + t.Bp))) : 0;
 
     int per_sm = 0;
