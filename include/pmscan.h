@@ -15,7 +15,10 @@
  *   - Wu-Manber (Section 3.2, Algorithms 4-5): SHIFT / HASH / PREFIX tables
  *     over blocks of B characters, candidates verified against the text.
  * The data-parallel split of the text into chunks that overlap by m-1
- * characters follows Section 4.2.1 (Algorithms 6-9).
+ * characters follows Section 4.2.1 (Algorithms 6-9). pm_pfac_compile adds
+ * the failure-less Aho-Corasick variant; pm_acv_compile and pm_wmv_compile
+ * take sets whose patterns have their own lengths (the definition with each
+ * pattern's length in place of m).
  *
  * Conventions shared by every call:
  *   - P is d*m contiguous bytes, row r = p^r. Any byte values are allowed.
@@ -26,7 +29,8 @@
  *   - Occurrences are uint64 keys ((uint64_t)i << 32) | r, sorted ascending,
  *     i.e. by position, then by pattern id.
  *   - counts[r] is the number of occurrences of pattern r (int64).
- *   - n must be < 2^32 and d < 2^24; otherwise PM_ETOOBIG.
+ *   - n must be < 2^32 and d < 2^24 (2^23 for Wu-Manber sets); otherwise
+ *     PM_ETOOBIG.
  *   - n < m is not an error: the result is empty.
  *   - Every call returns PM_OK (0) or one of the error codes below; no C++
  *     exception crosses this boundary. On error, output pointers are left

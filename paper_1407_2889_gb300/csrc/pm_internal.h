@@ -174,7 +174,7 @@ struct DevAc {
     void *flag_rank = nullptr;      // u16 or u32 per mask word (entry_bytes)
     void *canon = nullptr;          // u16 or u32 per terminal (entry_bytes)
     int64_t smem_entries = 0;       // table entries copied to shared memory
-    int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0, stage_cap = 0;
+    int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0;
     int32_t hist_smem = 0;          // per-terminal counters in shared memory
     int32_t ids_smem = 0;           // rank structure and canon in shared memory
     int32_t nv = 0, hv = 0;         // register text vectors (chunk + halo)
@@ -211,7 +211,7 @@ struct DevWm {
     uint8_t *flen = nullptr;
     uint32_t *grp_off = nullptr;    // groups of equal patterns
     uint32_t *grp_ids = nullptr;
-    int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0, stage_cap = 0;
+    int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0;
     int32_t shift_smem = 0, hist_smem = 0, dna = 0;
     int64_t smem_bytes = 0;
 };

@@ -954,7 +954,6 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     dev.warps = best.warps;
     dev.hist_smem = best.hist;
     dev.ids_smem = best.ids;
-    dev.stage_cap = 0;
     dev.smem_entries = best.smem_entries;
     const bool hyb = dev.smem_entries < entries || !t.dna || eb == 4;
     // ACGT tables whose entries fit as next-row indices: u32, or u16 with

@@ -560,7 +560,6 @@ int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevW
     const long long budget = (long long)dp.smem_optin - 1024;
     const int hbits = 5 * t.B;
     dev.pool_cap = 40;
-    dev.stage_cap = 0;
     dev.ctas_per_sm = opt.ctas_per_sm > 0 ? opt.ctas_per_sm : 1;
     const int forced = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, 16) : 0;
     const bool shift_smem = hbits <= 15;
