@@ -382,7 +382,8 @@ def main():
                                                       "B", "Bp", "dna_mode") if info.get(k)},
                        "plan": tuned or "planner default"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * (3 if args.mode == "list" else 1), "clocks": clk, "extras": extras,
+            # scan + expand kernels per list-mode step (the workspace zeroing is a memset call)
+            "gpu_launches": args.steps * (2 if args.mode == "list" else 1), "clocks": clk, "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if dist:

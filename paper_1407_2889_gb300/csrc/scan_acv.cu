@@ -80,7 +80,7 @@ __device__ __forceinline__ void acv_stage_issue(const AcvArgs &a, long long t, u
     if (bytes > 0) dev::tma_load_1d(buf, a.text + t * kWarpTile, uint32_t(bytes), bar);
 }
 
-template <typename E, int NV, int HV, bool DNA, bool PRE>
+template <typename E, int NV, int HV, bool DNA, bool PRE, bool HYB>
 __global__ void __launch_bounds__(512, 1) acv_scan_kernel(const AcvArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(512, 1) acv_scan_kernel(const AcvArgs a)
     dev::fence_proxy_async_smem();
     __syncthreads();
 
-    const TableRef<E, true> tab{s_tab, reinterpret_cast<const E *>(a.table_g), uint32_t(a.smem_entries)};
+    const TableRef<E, HYB> tab{s_tab, reinterpret_cast<const E *>(a.table_g), uint32_t(a.smem_entries)};
     E *pl = pool + lane;
     const uint32_t cap = uint32_t(a.pool_cap);
     const int m = a.m;
@@ -418,18 +418,23 @@ struct AcvVariant {
     bool dna, pre;
 };
 
-// dna u16 index entries (0-2), dna u32 index entries (3-5), general u32 (6-8);
-// within each group HV = 1, 2, 4
+// dna u16 index entries (0-2), dna u32 index entries (3-5), general u32
+// (6-8), all with a table prefix in shared memory and the rest in device
+// memory; dna u16 index entries with the whole table in shared memory
+// (9-11); within each group HV = 1, 2, 4
 const AcvVariant kAcvVariants[] = {
-    {acv_scan_kernel<uint16_t, 6, 1, true, true>, 2, 1, true, true},
-    {acv_scan_kernel<uint16_t, 7, 2, true, true>, 2, 2, true, true},
-    {acv_scan_kernel<uint16_t, 9, 4, true, true>, 2, 4, true, true},
-    {acv_scan_kernel<uint32_t, 6, 1, true, true>, 4, 1, true, true},
-    {acv_scan_kernel<uint32_t, 7, 2, true, true>, 4, 2, true, true},
-    {acv_scan_kernel<uint32_t, 9, 4, true, true>, 4, 4, true, true},
-    {acv_scan_kernel<uint32_t, 6, 1, false, false>, 4, 1, false, false},
-    {acv_scan_kernel<uint32_t, 7, 2, false, false>, 4, 2, false, false},
-    {acv_scan_kernel<uint32_t, 9, 4, false, false>, 4, 4, false, false},
+    {acv_scan_kernel<uint16_t, 6, 1, true, true, true>, 2, 1, true, true},
+    {acv_scan_kernel<uint16_t, 7, 2, true, true, true>, 2, 2, true, true},
+    {acv_scan_kernel<uint16_t, 9, 4, true, true, true>, 2, 4, true, true},
+    {acv_scan_kernel<uint32_t, 6, 1, true, true, true>, 4, 1, true, true},
+    {acv_scan_kernel<uint32_t, 7, 2, true, true, true>, 4, 2, true, true},
+    {acv_scan_kernel<uint32_t, 9, 4, true, true, true>, 4, 4, true, true},
+    {acv_scan_kernel<uint32_t, 6, 1, false, false, true>, 4, 1, false, false},
+    {acv_scan_kernel<uint32_t, 7, 2, false, false, true>, 4, 2, false, false},
+    {acv_scan_kernel<uint32_t, 9, 4, false, false, true>, 4, 4, false, false},
+    {acv_scan_kernel<uint16_t, 6, 1, true, true, false>, 2, 1, true, true},
+    {acv_scan_kernel<uint16_t, 7, 2, true, true, false>, 2, 2, true, true},
+    {acv_scan_kernel<uint16_t, 9, 4, true, true, false>, 2, 4, true, true},
 };
 
 int acv_hv(int m) { return m - 1 <= 16 ? 1 : m - 1 <= 32 ? 2 : m - 1 <= 64 ? 4 : -1; }
@@ -487,7 +492,8 @@ int acv_plan(const AcvTables &v, const pm_params &opt, const DeviceProps &dp, De
     dev.hv = hv;
     dev.entry_bytes = eb;
     dev.pre = v.ac.dna ? 1 : 0;
-    dev.variant = (v.ac.dna ? (eb == 2 ? 0 : 3) : 6) + (hv == 1 ? 0 : hv == 2 ? 1 : 2);
+    const bool whole_u16 = v.ac.dna && eb == 2 && dev.placement == PM_PLACE_SMEM;
+    dev.variant = (whole_u16 ? 9 : v.ac.dna ? (eb == 2 ? 0 : 3) : 6) + (hv == 1 ? 0 : hv == 2 ? 1 : 2);
     return PM_OK;
 }
 
@@ -516,7 +522,7 @@ int acv_launch(const AcvTables &v, const DevAcv &dv, const uint8_t *d_text, int6
 
     const AcvKernel fn = kAcvVariants[dv.variant].fn;
     {
-        static int attr[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        static int attr[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
         if (attr[dv.variant] < dv.smem_bytes) {
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
             if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
