@@ -88,6 +88,10 @@ typedef struct pm_params {
                                  3 64-bit in device memory */
     int32_t ids_place;        /* AC terminal-id structure: 0 auto, 1 shared
                                  memory, 2 device memory (through L1/L2) */
+    int32_t stride;           /* AC characters per table lookup: 0 or 1 one; 2 two
+                                 (a 16-entry row per state and character pair,
+                                 for ACGT sets of at most 4096 rows and m <= 33;
+                                 PM_ETOOBIG otherwise); pm_tune tries both */
 } pm_params;
 
 typedef struct pm_set pm_set; /* compiled pattern set; owns its device tables */
@@ -117,6 +121,7 @@ typedef struct pm_set_info {
     /* mixed lengths (PM_ALGO_ACV, PM_ALGO_WMV; m is then the longest length) */
     int32_t m_min;            /* shortest pattern length (= m for one length) */
     int32_t max_starts;       /* most patterns that can start at one position */
+    int32_t stride;           /* AC characters per table lookup in use (1 or 2) */
 } pm_set_info;
 
 typedef struct pm_result {    /* library-owned; release with pm_result_free */

@@ -95,6 +95,7 @@ void release_device(pm_set *s)
                     s->dwm.shift2, s->dwm.dir, s->dwm.ccode, s->dwm.cr,
                     s->dwm.hcode, s->dwm.grp_off, s->dwm.grp_ids, s->dwm.poff, s->dwm.fcode, s->dwm.flen,
                     s->dacv.table, s->dacv.cls, s->dacv.omask, s->dacv.orank, s->dacv.out_off, s->dacv.out_ent,
+                    s->dac2.table2,
                     s->c_text, s->c_ws, s->c_out, s->c_counts};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -103,6 +104,7 @@ void release_device(pm_set *s)
     s->dac = DevAc();
     s->dwm = DevWm();
     s->dacv = DevAcv();
+    s->dac2 = DevAc2();
     s->c_text = s->c_ws = s->c_out = s->c_counts = nullptr;
     s->c_text_cap = s->c_ws_cap = s->c_out_cap = 0;
 }
@@ -219,6 +221,15 @@ int finish_compile(pm_set *s, pm_set **out)
     }
     if (!rc && s->algo == PM_ALGO_PFAC) s->dac.pre = 0;  // PFAC walks the plain entry format
     if (!rc) rc = s->algo == PM_ALGO_ACV ? upload_acv(s) : ac_like ? upload_ac(s) : upload_wm(s);
+    if (!rc && s->algo == PM_ALGO_AC && !s->ac.table2.empty()) {
+        // two characters per lookup: uploaded whenever the set is eligible
+        // (the tuner may pick it); used when pm_params.stride is 2
+        rc = upload(&s->dac2.table2, s->ac.table2.data(), s->ac.table2.size() * 2, s->device_bytes);
+        if (!rc && s->params.stride == 2) {
+            rc = ac2_plan(s->ac, s->params, dp, s->dac2);
+            s->dac2.use = rc == PM_OK;
+        }
+    }
     if (rc) {
         release_device(s);
         delete s;
@@ -346,7 +357,8 @@ static bool params_ok(const pm_params *p)
     return p->placement >= 0 && p->placement <= PM_PLACE_GLOBAL && p->smem_table_bytes >= 0 &&
            p->warps_per_cta >= 0 && p->warps_per_cta <= 32 && p->ctas_per_sm >= 0 &&
            p->ctas_per_sm <= 8 && p->wm_prefix_len >= 0 && p->wm_prefix_len <= 3 &&
-           p->counters >= 0 && p->counters <= 3 && p->ids_place >= 0 && p->ids_place <= 2;
+           p->counters >= 0 && p->counters <= 3 && p->ids_place >= 0 && p->ids_place <= 2 &&
+           p->stride >= 0 && p->stride <= 2;
 }
 
 int pm_ac_compile(const uint8_t *P, int64_t d, int32_t m, const pm_params *opt, pm_set **out)
@@ -358,6 +370,10 @@ int pm_ac_compile(const uint8_t *P, int64_t d, int32_t m, const pm_params *opt, 
     if (opt) s->params = *opt;
     s->host_only = s->params.host_only != 0;
     int rc = build_ac(P, d, m, s->ac);
+    if (!rc) {
+        build_ac2(s->ac);  // the two-character table of an eligible set
+        if (s->params.stride == 2 && s->ac.table2.empty()) rc = PM_ETOOBIG;
+    }
     if (rc) {
         delete s;
         return rc;
@@ -466,6 +482,7 @@ int pm_set_get_info(const pm_set *s, pm_set_info *info)
         return PM_OK;
     }
     info->max_starts = 1;
+    info->stride = (s->algo == PM_ALGO_AC && s->dac2.use) ? 2 : 1;
     if (s->algo == PM_ALGO_AC || s->algo == PM_ALGO_PFAC) {
         const AcTables &t = s->ac;
         info->m = t.m;
@@ -525,6 +542,9 @@ int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t f
     if (list && occ_capacity > 0 && !d_occ) return PM_EINVAL;
     if (occ_capacity < 0) return PM_EINVAL;
     if (workspace_bytes < set_ws_bytes(s, n, list)) return PM_EINVAL;
+    if (s->algo == PM_ALGO_AC && s->dac2.use)
+        return ac2_launch(s->ac, s->dac, s->dac2, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
+                          d_workspace, stream);
     if (s->algo == PM_ALGO_AC)
         return ac_launch(s->ac, s->dac, d_text, n, list, d_counts, d_occ, occ_capacity, d_n_occ,
                          d_workspace, stream);
@@ -599,11 +619,13 @@ int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t
     // candidate plans: the current one, then placement x warps x counters x ids
     std::vector<pm_params> cand;
     cand.push_back(s->params);
+    cand.back().stride = 1;
     for (int place : {PM_PLACE_AUTO, PM_PLACE_HYBRID})
         for (int w : {0, 16, 12, 8})
             for (int c : {0, 1, 2, 3})
                 for (int idp : {0, 1, 2}) {
                     pm_params p = s->params;
+                    p.stride = 1;
                     p.placement = place;
                     p.warps_per_cta = w;
                     p.counters = c;
@@ -639,15 +661,48 @@ int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t
         if (rc) break;
         tried.push_back(Tried{plan, p, ms / float(reps)});
     }
+    // two characters per lookup, when the set is eligible
+    float ms2 = -1.0f;
+    DevAc2 plan2 = s->dac2;
+    pm_params p2 = s->params;
+    p2.stride = 2;
+    p2.warps_per_cta = 0;
+    if (!rc && plan2.table2 && ac2_plan(t, p2, dp, plan2) == PM_OK) {
+        auto run2 = [&]() {
+            return ac2_launch(t, saved, plan2, d_text, n, list, static_cast<int64_t *>(counts),
+                              static_cast<uint64_t *>(occ), n_occ, static_cast<int64_t *>(nocc), ws, st);
+        };
+        rc = run2();
+        if (!rc) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && !rc && e == cudaSuccess; ++r) rc = run2();
+        if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); rc = PM_ECUDA; }
+        if (!rc && pm_scan_status(ws, stream) != PM_OK) rc = PM_ETIMEOUT;
+        if (!rc) ms2 = ms / float(reps);
+    }
     cleanup();
     if (rc) return rc;
-    if (tried.empty()) return PM_ETOOBIG;
+    if (tried.empty() && ms2 < 0.0f) return PM_ETOOBIG;
     size_t bi = 0;
     for (size_t i = 1; i < tried.size(); ++i)
         if (tried[i].ms < tried[bi].ms) bi = i;
+    if (ms2 >= 0.0f && (tried.empty() || ms2 < tried[bi].ms)) {
+        s->dac = saved;
+        plan2.use = true;
+        s->dac2 = plan2;
+        s->params = p2;
+        if (best_out) *best_out = p2;
+        if (best_ms) *best_ms = ms2;
+        return PM_OK;
+    }
     s->dac = tried[bi].plan;  // same device tables, new launch plan
+    s->dac2.use = false;
     s->params = tried[bi].params;
-    if (best_out) *best_out = tried[bi].params;
+    s->params.stride = 1;
+    if (best_out) *best_out = s->params;
     if (best_ms) *best_ms = tried[bi].ms;
     return PM_OK;
 }
@@ -924,7 +979,8 @@ int pm_selfcheck_host_walk(const pm_set *s, const uint8_t *T, int64_t n, pm_resu
     try {
         std::vector<uint64_t> occ;
         std::vector<int64_t> counts;
-        if (s->algo == PM_ALGO_AC) host_walk_ac(s->ac, T, n, occ, counts);
+        if (s->algo == PM_ALGO_AC && s->params.stride == 2) host_walk_ac2(s->ac, T, n, occ, counts);
+        else if (s->algo == PM_ALGO_AC) host_walk_ac(s->ac, T, n, occ, counts);
         else if (s->algo == PM_ALGO_PFAC) host_walk_pfac(s->ac, T, n, occ, counts);
         else if (s->algo == PM_ALGO_ACV) host_walk_acv(s->acv, T, n, occ, counts);
         else if (s->algo == PM_ALGO_WMV) host_walk_wmv(s->wm, T, n, occ, counts);

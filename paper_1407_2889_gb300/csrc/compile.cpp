@@ -987,4 +987,69 @@ void host_walk_wmv(const WmTables &t, const uint8_t *T, int64_t n,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Two characters per lookup (the multi-character table of the DFA form of
+// Section 3.1): the one-character table composed with itself.
+// ---------------------------------------------------------------------------
+bool ac2_eligible(const AcTables &t)
+{
+    return t.dna && t.entry_bytes == 2 && t.n_rows <= 4096 && t.m >= 1 && t.m - 1 <= 32 && !t.table.empty();
+}
+
+void build_ac2(AcTables &t)
+{
+    t.table2.clear();
+    if (!ac2_eligible(t)) return;
+    t.table2.assign(size_t(t.n_rows) * 16, 0);
+    for (int64_t r = 0; r < t.n_rows; ++r)
+        for (uint32_t c1 = 0; c1 < 4; ++c1) {
+            const uint32_t e1 = t.table[size_t(r) * 4 + c1];
+            const uint32_t r1 = e1 >> 1, m1 = e1 & 1u;
+            for (uint32_t c2 = 0; c2 < 4; ++c2) {
+                const uint32_t e2 = t.table[size_t(r1) * 4 + c2];
+                t.table2[size_t(r) * 16 + c1 * 4 + c2] = uint16_t(((e2 >> 1) << 4) | ((e2 & 1u) << 1) | m1);
+            }
+        }
+}
+
+// Every byte is walked under its class ((b >> 1) ^ (b >> 2)) & 3, so a byte
+// outside the alphabet does not reset the walk; a match whose window of m
+// bytes holds such a byte is dropped. A match depends only on its window,
+// so the others are exactly those of the one-character walk.
+void host_walk_ac2(const AcTables &t, const uint8_t *T, int64_t n,
+                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
+{
+    counts.assign(size_t(t.d), 0);
+    occ.clear();
+    const int64_t m = t.m;
+    const uint32_t mid_base = uint32_t(t.d0_row << t.lw);
+    auto bad = [&](uint32_t b) { return ((t.lut >> (8 * dna_code(b))) & 0xFFu) != b; };
+    auto report = [&](int64_t j, uint32_t idx1) {
+        const uint32_t v = t.mid[idx1 - mid_base];
+        const int64_t pos = j - m + 1;
+        if (v & 0x80000000u) {
+            const uint32_t g = v & 0x7FFFFFFFu;
+            for (uint32_t k = t.grp_off[g]; k < t.grp_off[g + 1]; ++k) emit_entry(occ, counts, pos, t.grp_ids[k]);
+        } else {
+            emit_entry(occ, counts, pos, v);
+        }
+    };
+    uint32_t E = 1u << 4;   // root (row 1)
+    int64_t last_bad = -1;
+    for (int64_t i = 0; i < n; i += 2) {
+        const uint32_t b1 = T[i], b2 = i + 1 < n ? T[i + 1] : 0u;
+        const uint32_t c1 = dna_code(b1), c2 = dna_code(b2);
+        const uint32_t idx2 = (E & ~15u) | (c1 << 2) | c2;
+        E = t.table2[idx2];
+        if (bad(b1)) last_bad = i;
+        if ((E & 1u) && last_bad < i - m + 1) report(i, idx2 >> 2);
+        if (i + 1 >= n) break;
+        if (bad(b2)) last_bad = i + 1;
+        if ((E & 2u) && last_bad < i + 1 - m + 1) {
+            const uint32_t e1 = t.table[idx2 >> 2];
+            report(i + 1, ((e1 >> 1) << 2) | c2);
+        }
+    }
+}
+
 }  // namespace pm

@@ -54,6 +54,11 @@ struct AcTables {
     std::vector<uint32_t> flag_mask;
     std::vector<uint32_t> flag_rank;
     std::vector<uint32_t> canon;
+    // Two characters per lookup (ACGT sets of at most 4096 rows, m <= 33):
+    // row r, classes (c1, c2) -> (r2 << 4) | (m2 << 1) | m1, where r1 and m1
+    // are the state and flag after c1 and r2, m2 those after c2 (the
+    // one-character table applied twice). Empty when not eligible.
+    std::vector<uint16_t> table2;
 };
 
 // ---------------------------------------------------------------------------
@@ -145,6 +150,13 @@ int build_wmv(const uint8_t *P, const int64_t *off, int64_t d, int32_t B, int32_
 int build_pfac(const uint8_t *P, int64_t d, int32_t m, AcTables &out);
 
 // host walks used by pm_selfcheck_host_walk
+// the two-character table of an eligible set (fills t.table2)
+bool ac2_eligible(const AcTables &t);
+void build_ac2(AcTables &t);
+// the two-character walk as the device runs it (bytes outside the alphabet
+// walked under their class, matches whose window holds one dropped)
+void host_walk_ac2(const AcTables &t, const uint8_t *T, int64_t n,
+                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
 void host_walk_ac(const AcTables &t, const uint8_t *T, int64_t n,
                   std::vector<uint64_t> &occ, std::vector<int64_t> &counts);
 void host_walk_wm(const WmTables &t, const uint8_t *T, int64_t n,
@@ -183,6 +195,14 @@ struct DevAc {
     int64_t smem_bytes = 0;
     int32_t placement = 0;
     int64_t max_warps = 0;          // warps in the largest grid a launch uses
+};
+
+// Plan and table of the two-character AC scan (scan_ac2.cu).
+struct DevAc2 {
+    void *table2 = nullptr;         // u16, n_rows * 16
+    bool use = false;               // pm_params.stride == 2
+    int32_t warps = 0, pool_cap = 0, hist_smem = 0, hv = 0, nv = 0;
+    int64_t smem_bytes = 0;
 };
 
 struct DevAcv {
@@ -276,6 +296,12 @@ int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes
                   const uint32_t *grp_ids, int64_t n_grp_off, int64_t n_grp_ids, uint64_t *d_occ,
                   int64_t occ_cap, int64_t *d_n_occ, const unsigned long long *occ_base,
                   unsigned long long pos_base, void *stream);
+// two characters per lookup (scan_ac2.cu): plan (PM_ETOOBIG if the set is
+// not eligible or the tables do not fit) and scan on the AC workspace
+int ac2_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevAc2 &dev);
+int ac2_launch(const AcTables &t, const DevAc &dv, const DevAc2 &d2, const uint8_t *d_text, int64_t n,
+               bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap, int64_t *d_n_occ, void *d_ws,
+               void *stream);
 // mixed-length Aho-Corasick (scan_acv.cu)
 int acv_plan(const AcvTables &v, const pm_params &opt, const DeviceProps &dp, DevAcv &dev);
 int64_t acv_workspace_bytes(const AcvTables &v, int64_t n, bool list);
@@ -367,6 +393,7 @@ struct pm_set {
     pm::DevAc dac;
     pm::DevWm dwm;
     pm::DevAcv dacv;
+    pm::DevAc2 dac2;
     int64_t device_bytes = 0;
     // caches for pm_scan (host-pointer convenience path)
     void *c_text = nullptr;  int64_t c_text_cap = 0;

@@ -42,7 +42,8 @@ class pm_params(ctypes.Structure):
     _fields_ = [("placement", ctypes.c_int32), ("smem_table_bytes", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("wm_prefix_len", ctypes.c_int32), ("host_only", ctypes.c_int32),
-                ("counters", ctypes.c_int32), ("ids_place", ctypes.c_int32)]
+                ("counters", ctypes.c_int32), ("ids_place", ctypes.c_int32),
+                ("stride", ctypes.c_int32)]
 
 
 class pm_set_info(ctypes.Structure):
@@ -55,7 +56,7 @@ class pm_set_info(ctypes.Structure):
                 ("B", ctypes.c_int32), ("Bp", ctypes.c_int32),
                 ("shift_entries", ctypes.c_int64), ("n_zero_shift", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("m_min", ctypes.c_int32),
-                ("max_starts", ctypes.c_int32)]
+                ("max_starts", ctypes.c_int32), ("stride", ctypes.c_int32)]
 
 
 class pm_result(ctypes.Structure):

@@ -307,3 +307,42 @@ def test_wmv_host_walk_matches_oracle(alphabet):
     with pytest.raises(pm.PmError) as e:  # B above the shortest length
         pm.pm_wmv_compile([b"ACGT", b"AC"], 3, HOST)
     assert e.value.code == pm.PM_EINVAL
+
+
+def test_stride2_host_walk_matches_oracle():
+    """Two characters per lookup (ACGT sets of at most 4096 rows, m <= 33):
+    bytes outside the alphabet are walked under their class and the matches
+    whose window holds one are dropped; the result is the definition's."""
+    rng = np.random.default_rng(900)
+    A = np.frombuffer(b"ACGT", np.uint8)
+    checked = 0
+    for case in range(60):
+        m = int(rng.choice([1, 2, 3, 5, 8, 9, 16, 17, 24, 33]))
+        d = int(rng.integers(1, 120))
+        n = int(rng.integers(0, 5000))
+        T = np.frombuffer(b"ACGTN\n", np.uint8)[rng.choice(6, n, p=[.235, .235, .235, .235, .04, .02])]
+        P = A[rng.integers(0, 4, (d, m))]
+        for r in range(d):
+            if n >= m and rng.random() < 0.6:
+                s0 = int(rng.integers(0, n - m + 1))
+                if all(x in b"ACGT" for x in T[s0:s0 + m].tobytes()):
+                    P[r] = T[s0:s0 + m]
+        if d > 2:
+            P[-1] = P[0]
+        P = np.ascontiguousarray(P)
+        want = oracle.brute(T, P)
+        try:
+            h = pm.pm_ac_compile(P, {"host_only": 1, "stride": 2})
+        except pm.PmError as e:
+            assert e.code == pm.PM_ETOOBIG  # more than 4096 rows
+            continue
+        try:
+            occ, cnt = pm.pm_selfcheck_host_walk(h, T)
+        finally:
+            pm.pm_set_free(h)
+        assert np.array_equal(occ, want[0]) and np.array_equal(cnt, want[1]), f"case {case} m={m} n={n}"
+        checked += 1
+    assert checked >= 40
+    with pytest.raises(pm.PmError) as e:  # not an ACGT-like set
+        pm.pm_ac_compile([b"ACGN"], {"host_only": 1, "stride": 2})
+    assert e.value.code == pm.PM_ETOOBIG

@@ -442,3 +442,61 @@ def test_scan_to_host_pinned_buffers_and_capacity():
     assert e.value.code == pm.PM_ECAPACITY
     assert np.array_equal(small.numpy().view(np.uint64), want_occ[:10])
     s.close()
+
+
+def test_stride2_scan_matches_oracle():
+    """Two characters per lookup: random ACGT sets over texts with N and
+    newline bytes (matches whose window holds one are dropped), odd and even
+    m up to 33, duplicates, list and counts modes, unaligned device text, a
+    text where every position matches (pool overflow), and the tuner."""
+    rng = np.random.default_rng(1200)
+    A = np.frombuffer(b"ACGT", np.uint8)
+    for case in range(24):
+        m = int(rng.choice([1, 2, 3, 7, 8, 9, 16, 17, 33]))
+        d = int(rng.integers(1, 200))
+        n = int(rng.integers(0, 300000))
+        T = np.frombuffer(b"ACGTN\n", np.uint8)[rng.choice(6, n, p=[.2425, .2425, .2425, .2425, .02, .01])]
+        P = A[rng.integers(0, 4, (d, m))]
+        for r in range(d):
+            if n >= m and rng.random() < 0.6:
+                s0 = int(rng.integers(0, n - m + 1))
+                if all(x in b"ACGT" for x in T[s0:s0 + m].tobytes()):
+                    P[r] = T[s0:s0 + m]
+        if d > 2:
+            P[-1] = P[0]
+        P = np.ascontiguousarray(P)
+        try:
+            s = _ac(P, stride=2)
+        except pm.PmError as e:
+            assert e.code == pm.PM_ETOOBIG
+            continue
+        assert s.info()["stride"] == 2
+        want = oracle.dictionary(T, P, threads=THREADS)
+        _same(s.scan(T), want, f"stride 2, case {case}, m={m}, n={n}")
+        _, cnt = s.scan(T, counts_only=True)
+        assert np.array_equal(cnt, want[1])
+        if n > 5:
+            d_T = torch.from_numpy(T).cuda()
+            _same(s.scan(d_T[3:]), oracle.dictionary(T[3:], P, threads=THREADS), f"stride 2 unaligned {case}")
+        s.close()
+    T = np.full(60000, ord("A"), np.uint8)
+    T[999] = ord("N")
+    P = np.array([list(b"AAAAAAAA"), list(b"AAAAAAAA"), list(b"CAAAAAAA")], np.uint8)
+    s = _ac(P, stride=2)
+    _same(s.scan(T), oracle.brute(T, P), "stride 2, every position")
+    s.close()
+
+
+def test_stride2_est_and_tuner(est_text_full):
+    T = est_text_full[: 64 << 20]
+    _, P = synth.est_case(1000, 8, text=est_text_full)
+    want = oracle.dictionary(T, P, threads=THREADS)
+    d_T = torch.from_numpy(T).cuda()
+    for kw in ({"stride": 2}, {"stride": 1}, {}):
+        s = _ac(P, **kw)
+        _same(s.scan(d_T), want, f"EST 64 MiB {kw}")
+        if not kw:
+            params, ms = s.tune(d_T, reps=1)
+            assert params["stride"] in (1, 2) and s.info()["stride"] == params["stride"]
+            _same(s.scan(d_T), want, "after tuning")
+        s.close()
