@@ -18,6 +18,28 @@ void set_cuda_error(int e) { g_last_cuda = e; }
 int64_t warp_tiles(int64_t n) { return n <= 0 ? 0 : (n + kWarpTile - 1) / kWarpTile; }
 
 
+// The dynamic shared memory a kernel may use is a per-device attribute of
+// the kernel: raise it once per (device, kernel) to the largest launch seen,
+// under a lock (launchers run on several host threads).
+int kernel_smem_attr(const void *fn, int64_t bytes)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<int, const void *>, int64_t>> seen;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    std::lock_guard<std::mutex> lk(mu);
+    int64_t *have = nullptr;
+    for (auto &x : seen)
+        if (x.first.first == dev && x.first.second == fn) have = &x.second;
+    if (have && *have >= bytes) return PM_OK;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); return PM_ECUDA; }
+    if (have) *have = bytes;
+    else seen.push_back({{dev, fn}, bytes});
+    return PM_OK;
+}
+
 int device_props(DeviceProps &p)
 {
     static std::mutex mu;

@@ -248,6 +248,9 @@ struct DeviceProps {
     int l2_bytes = 0;
 };
 int device_props(DeviceProps &p);
+// raise a kernel's dynamic shared memory limit on the current device (once
+// per device, kernel and size; thread-safe)
+int kernel_smem_attr(const void *fn, int64_t bytes);
 
 // Plan and launch. Return PM_* codes; PM_ECUDA records the CUDA error.
 int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevAc &dev);

@@ -396,17 +396,10 @@ int ac2_launch(const AcTables &t, const DevAc &dv, const DevAc2 &d2, const uint8
 
     typedef void (*K)(const Ac2Args);
     const K fn = d2.hv == 1 ? ac2_scan_kernel<6, 1> : ac2_scan_kernel<7, 2>;
-    {
-        static int attr[2] = {0, 0};
-        int &have = attr[d2.hv == 1 ? 0 : 1];
-        if (have < d2.smem_bytes) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(d2.smem_bytes));
-            if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-            have = int(d2.smem_bytes);
-        }
-    }
+    int rc = kernel_smem_attr(reinterpret_cast<const void *>(fn), d2.smem_bytes);
+    if (rc) return rc;
     DeviceProps dp;
-    int rc = device_props(dp);
+    rc = device_props(dp);
     if (rc) return rc;
     Ac2Args a;
     a.text = d_text;

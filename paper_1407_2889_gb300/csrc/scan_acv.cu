@@ -521,16 +521,10 @@ int acv_launch(const AcvTables &v, const DevAcv &dv, const uint8_t *d_text, int6
     if (n < v.m_min || nsub == 0) return PM_OK;
 
     const AcvKernel fn = kAcvVariants[dv.variant].fn;
-    {
-        static int attr[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-        if (attr[dv.variant] < dv.smem_bytes) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
-            if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-            attr[dv.variant] = int(dv.smem_bytes);
-        }
-    }
+    int rc = kernel_smem_attr(reinterpret_cast<const void *>(fn), dv.smem_bytes);
+    if (rc) return rc;
     DeviceProps dp;
-    int rc = device_props(dp);
+    rc = device_props(dp);
     if (rc) return rc;
     AcvArgs a;
     a.text = d_text;
@@ -598,21 +592,18 @@ int sorted_expand_launch(void *d_ws, int64_t nsub, int slot_bytes, int per_pos, 
     unsigned long long *occ = reinterpret_cast<unsigned long long *>(d_occ);
     long long *n_occ = reinterpret_cast<long long *>(d_n_occ);
     const long long cap = d_occ ? occ_cap : 0;
-    cudaError_t e;
-    if (slot_bytes == 4) {
-        e = cudaFuncSetAttribute(acv_expand_kernel<uint32_t, 20>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem));
-        if (e == cudaSuccess)
-            acv_expand_kernel<uint32_t, 20><<<unsigned(nseg), kSortThreads, esmem, st>>>(
-                static_cast<uint32_t *>(L.slots), stride, L.tile_ent, L.seg_sum, seg_tiles, nsub, occ, cap, n_occ);
-    } else {
-        e = cudaFuncSetAttribute(acv_expand_kernel<unsigned long long, 32>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem));
-        if (e == cudaSuccess)
-            acv_expand_kernel<unsigned long long, 32><<<unsigned(nseg), kSortThreads, esmem, st>>>(
-                static_cast<unsigned long long *>(L.slots), stride, L.tile_ent, L.seg_sum, seg_tiles, nsub, occ,
-                cap, n_occ);
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
+    const void *fn = slot_bytes == 4 ? reinterpret_cast<const void *>(acv_expand_kernel<uint32_t, 20>)
+                                     : reinterpret_cast<const void *>(acv_expand_kernel<unsigned long long, 32>);
+    const int rc = kernel_smem_attr(fn, int64_t(esmem));
+    if (rc) return rc;
+    if (slot_bytes == 4)
+        acv_expand_kernel<uint32_t, 20><<<unsigned(nseg), kSortThreads, esmem, st>>>(
+            static_cast<uint32_t *>(L.slots), stride, L.tile_ent, L.seg_sum, seg_tiles, nsub, occ, cap, n_occ);
+    else
+        acv_expand_kernel<unsigned long long, 32><<<unsigned(nseg), kSortThreads, esmem, st>>>(
+            static_cast<unsigned long long *>(L.slots), stride, L.tile_ent, L.seg_sum, seg_tiles, nsub, occ, cap,
+            n_occ);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     return PM_OK;
 }

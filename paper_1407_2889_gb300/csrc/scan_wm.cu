@@ -622,29 +622,20 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     const int nv = wm_nv(t.m);
     const bool wide = t.m > 16;
     K fn;
-    int slot;
     if (t.var && dv.dna) {
         fn = wm_scan_kernel<false, true, 1, false, true>;
-        slot = 7;
     } else if (t.var) {
         fn = dv.shift_smem ? wm_scan_kernel<true, false, 1, false, true> : wm_scan_kernel<false, false, 1, false, true>;
-        slot = dv.shift_smem ? 6 : 5;
     } else if (dv.dna) {
         fn = nv == 6 ? (wide ? wm_scan_kernel<false, true, 6, true, false> : wm_scan_kernel<false, true, 6, false, false>)
                      : wm_scan_kernel<false, true, 7, true, false>;
-        slot = nv == 6 ? (wide ? 3 : 2) : 4;
     } else {
         fn = dv.shift_smem ? wm_scan_kernel<true, false, 1, false, false> : wm_scan_kernel<false, false, 1, false, false>;
-        slot = dv.shift_smem ? 1 : 0;
     }
-    static int attr_bytes[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (attr_bytes[slot] < dv.smem_bytes) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
-        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-        attr_bytes[slot] = int(dv.smem_bytes);
-    }
+    int rc = kernel_smem_attr(reinterpret_cast<const void *>(fn), dv.smem_bytes);
+    if (rc) return rc;
     DeviceProps dp;
-    int rc = device_props(dp);
+    rc = device_props(dp);
     if (rc) return rc;
 
     WmArgs a;
