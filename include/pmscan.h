@@ -275,10 +275,12 @@ int64_t pm_noalloc_scratch_bytes(void);
  * the planner accepts over table placement (shared memory / hybrid prefix),
  * warps per CTA (auto, 16, 12, 8), per-terminal counters (32-bit or 16-bit
  * in shared memory, or device memory) and the terminal-id structure (shared
- * or device memory), and keeps the fastest for the set: later scans use it.
+ * or device memory), plus the two-character scan (stride 2) when the set
+ * qualifies, and keeps the fastest for the set: later scans use it.
  * Results never depend on the plan. Allocates its own scratch, synchronises
  * `stream`. *best_out / *best_ms (may be NULL) receive the chosen pm_params
- * and its time per scan. PM_EINVAL for Wu-Manber and host-only sets.
+ * and its time per scan. PM_EINVAL for sets other than Aho-Corasick (PFAC,
+ * Wu-Manber, mixed lengths) and for host-only sets.
  */
 int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t reps,
             void *stream, pm_params *best_out, float *best_ms);
