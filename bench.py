@@ -268,7 +268,8 @@ def main():
     tuned = None
     if not args.no_tune and args.algo == "ac":  # the autotuner picks the launch plan (not timed)
         params, tms = s.tune(d_text, counts_only=args.mode == "counts", reps=3)
-        tuned = {"ms_per_scan": tms, **{k: params[k] for k in ("placement", "warps_per_cta", "counters", "ids_place")}}
+        tuned = {"ms_per_scan": tms,
+                 **{k: params[k] for k in ("placement", "warps_per_cta", "counters", "ids_place", "stride")}}
     info = s.info()
     ws = torch.zeros(s.workspace_bytes(n), dtype=torch.uint8, device="cuda")
     counts = torch.zeros(d, dtype=torch.int64, device="cuda")
