@@ -44,3 +44,13 @@ def test_sampled_patterns_come_from_acgt_windows():
 def test_small_uniform_case_shape():
     T, P = synth.small_uniform_case()
     assert T.size == 1 << 20 and P.shape == (100, 8)
+
+
+def test_mixed_length_patterns():
+    T = synth.est_text(1 << 22, 1)
+    P = synth.mixed_length_patterns(T, 500, 8, 16, 301)
+    assert P == synth.mixed_length_patterns(T, 500, 8, 16, 301)  # seeded
+    assert len(P) == 500 and {len(p) for p in P} <= set(range(8, 17)) and len({len(p) for p in P}) > 5
+    assert all(set(p) <= set(b"ACGT") for p in P)
+    text = T.tobytes()
+    assert all(text.find(p) >= 0 for p in P[:250])  # the first half are windows of the text
