@@ -253,20 +253,31 @@ int pm_scan_device(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t f
  * pm_noalloc_scratch_bytes() bytes (64 MiB) inside the library, reserved on
  * every GPU that loads the library until the process exits. Nothing is
  * allocated: no cudaMalloc, cudaFree or allocating library call.
- *   - Only Aho-Corasick sets (PM_EINVAL for Wu-Manber).
+ *   - Only plain Aho-Corasick sets (PM_EINVAL for PFAC, mixed-length and
+ *     Wu-Manber sets).
+ *   - Always the one-character walk, even for a set whose tuned plan takes
+ *     two characters per lookup (pm_params.stride = 2): the results are the
+ *     same, only the launch plan differs.
  *   - PM_ETOOBIG when the scan would need more scratch than the array holds
  *     (large texts in list mode, or very large pattern sets); nothing runs.
- *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture begins.
+ *   - Each call looks up the array's device address on the current device
+ *     (no allocation); the first lookup on a device may load the library's
+ *     kernels, so make the first call before any stream capture begins.
  *   - Every call uses the same array, which keeps the last call's contents
  *     (the call clears what must start at zero). Calls whose work overlaps
  *     on the GPU -- other streams, other host threads -- race on it: run
  *     them one after another.
+ *   - A device-side failure (a bounded wait that gave up) is recorded in the
+ *     array's status word: read it with pm_noalloc_scan_status.
  */
 int pm_scan_device_noalloc(const pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags,
                            int64_t *d_counts, uint64_t *d_occ, int64_t occ_capacity,
                            int64_t *d_n_occ, void *stream);
 int64_t pm_noalloc_scratch_bytes(void);
+/* Synchronise `stream` and read the status word of the last
+ * pm_scan_device_noalloc on the current device: PM_OK, or PM_ETIMEOUT when a
+ * bounded wait in the kernel gave up (the results are then incomplete). */
+int pm_noalloc_scan_status(void *stream);
 
 /*
  * Autotuner for the plain Aho-Corasick scan (the paper's kernels fix their
@@ -290,10 +301,16 @@ int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t
 int pm_scan_status(const void *d_workspace, void *stream);
 
 /*
- * Scan k independent (set, text) instances in one persistent launch
- * (a work queue of (instance, tile) items), synchronously. texts are host
- * pointers unless flags has PM_DEVICE_TEXT. outs[j] receives instance j's
- * result (library-owned). Results equal k separate pm_scan calls.
+ * Scan k independent (set, text) instances, synchronously; outs[j]
+ * receives instance j's result (library-owned, as pm_scan gives it).
+ * texts are host pointers unless flags has PM_DEVICE_TEXT. Host texts
+ * against Aho-Corasick sets over an ACGT-like alphabet with m <= 65 run
+ * together in the batched persistent kernel (pm_batch_*): a first launch
+ * gives every instance's total, a second writes the keys into exact
+ * capacities. Every other instance (device texts, PFAC, Wu-Manber, mixed
+ * lengths) runs as a pm_scan call, in order. Results equal k separate
+ * pm_scan calls. Allocates device scratch for the call and frees it. On an
+ * error every outs[j] is NULL.
  */
 int pm_scan_batch(const pm_set *const *sets, const uint8_t *const *texts,
                   const int64_t *ns, int32_t k, uint32_t flags, void *stream,

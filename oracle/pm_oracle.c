@@ -89,15 +89,38 @@ typedef struct {
     int32_t m;
 } orc_sort_ctx;
 
-static orc_sort_ctx g_sort_ctx; /* qsort has no context argument in C99 */
-
-static int orc_cmp_pattern_idx(const void *a, const void *b)
+/* Order of pattern indices ra, rb: by bytes, then by index. */
+static int orc_cmp_pattern_idx(const void *ctx, int64_t ra, int64_t rb)
 {
-    int64_t ra = *(const int64_t *)a, rb = *(const int64_t *)b;
-    int c = memcmp(g_sort_ctx.P + ra * g_sort_ctx.m,
-                   g_sort_ctx.P + rb * g_sort_ctx.m, (size_t)g_sort_ctx.m);
-    if (c) return c;
+    const orc_sort_ctx *c = (const orc_sort_ctx *)ctx;
+    int k = memcmp(c->P + ra * c->m, c->P + rb * c->m, (size_t)c->m);
+    if (k) return k;
     return (ra > rb) - (ra < rb);
+}
+
+/* Bottom-up merge sort of n indices under cmp(ctx, .) -- the context is an
+ * argument, so concurrent oracle calls never share sorting state. Returns
+ * -1 if its scratch cannot be allocated. */
+static int orc_sort_idx(int64_t *a, int64_t n, int (*cmp)(const void *, int64_t, int64_t), const void *ctx)
+{
+    if (n < 2) return 0;
+    int64_t *tmp = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!tmp) return -1;
+    int64_t *src = a, *dst = tmp;
+    for (int64_t w = 1; w < n; w *= 2) {
+        for (int64_t lo = 0; lo < n; lo += 2 * w) {
+            int64_t mid = lo + w < n ? lo + w : n;
+            int64_t hi = lo + 2 * w < n ? lo + 2 * w : n;
+            int64_t i = lo, j = mid, k = lo;
+            while (i < mid && j < hi) dst[k++] = cmp(ctx, src[j], src[i]) < 0 ? src[j++] : src[i++];
+            while (i < mid) dst[k++] = src[i++];
+            while (j < hi) dst[k++] = src[j++];
+        }
+        int64_t *t = src; src = dst; dst = t;
+    }
+    if (src != a) memcpy(a, src, (size_t)n * sizeof(int64_t));
+    free(tmp);
+    return 0;
 }
 
 typedef struct {
@@ -159,9 +182,13 @@ int64_t orc_dict(const uint8_t *T, int64_t n, const uint8_t *P, int64_t d,
     pthread_t *tids = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
     if (!order || !jobs || !tids) { free(order); free(jobs); free(tids); return -1; }
     for (int64_t r = 0; r < d; r++) order[r] = r;
-    g_sort_ctx.P = P;
-    g_sort_ctx.m = m;
-    qsort(order, (size_t)d, sizeof(int64_t), orc_cmp_pattern_idx);
+    const orc_sort_ctx sctx = {P, m};
+    if (orc_sort_idx(order, d, orc_cmp_pattern_idx, &sctx)) {
+        free(order);
+        free(jobs);
+        free(tids);
+        return -1;
+    }
 
     int64_t total = 0;
     int failed = 0;
@@ -481,16 +508,15 @@ typedef struct {
     const int64_t *off;
 } orc_var_ctx;
 
-static orc_var_ctx g_var_ctx;
-
-static int orc_cmp_var(const void *a, const void *b)
+/* Order of pattern ids ra, rb: by length, then bytes, then id. */
+static int orc_cmp_var(const void *ctx, int64_t ra, int64_t rb)
 {
-    const int64_t ra = *(const int64_t *)a, rb = *(const int64_t *)b;
-    const int64_t la = g_var_ctx.off[ra + 1] - g_var_ctx.off[ra];
-    const int64_t lb = g_var_ctx.off[rb + 1] - g_var_ctx.off[rb];
+    const orc_var_ctx *c = (const orc_var_ctx *)ctx;
+    const int64_t la = c->off[ra + 1] - c->off[ra];
+    const int64_t lb = c->off[rb + 1] - c->off[rb];
     if (la != lb) return (la > lb) - (la < lb);
-    const int c = memcmp(g_var_ctx.P + g_var_ctx.off[ra], g_var_ctx.P + g_var_ctx.off[rb], (size_t)la);
-    if (c) return c;
+    const int k = memcmp(c->P + c->off[ra], c->P + c->off[rb], (size_t)la);
+    if (k) return k;
     return (ra > rb) - (ra < rb);
 }
 
@@ -574,9 +600,11 @@ int64_t orc_dict_var(const uint8_t *T, int64_t n, const uint8_t *P, const int64_
     int64_t nz = 0;  /* empty patterns match nowhere: left out */
     for (int64_t r = 0; r < d; r++)
         if (off[r + 1] > off[r]) sorted[nz++] = r;
-    g_var_ctx.P = P;
-    g_var_ctx.off = off;
-    qsort(sorted, (size_t)nz, sizeof(int64_t), orc_cmp_var);
+    const orc_var_ctx vctx = {P, off};
+    if (orc_sort_idx(sorted, nz, orc_cmp_var, &vctx)) {
+        free(sorted); free(gfirst); free(glen); free(jobs); free(tids);
+        return -1;
+    }
     int64_t ng = 0;
     for (int64_t k = 0; k < nz; k++) {
         const int64_t L = off[sorted[k] + 1] - off[sorted[k]];

@@ -596,6 +596,8 @@ int pm_scan_device_noalloc(const pm_set *s, const uint8_t *d_text, int64_t n, ui
 
 int64_t pm_noalloc_scratch_bytes(void) { return ac_noalloc_limit_bytes(); }
 
+int pm_noalloc_scan_status(void *stream) { return ac_noalloc_status(stream); }
+
 int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t reps,
             void *stream, pm_params *best_out, float *best_ms)
 {
@@ -744,6 +746,101 @@ int pm_scan_status(const void *d_workspace, void *stream)
 }
 
 }  // extern "C"
+
+namespace pm {
+namespace {
+// pm_scan_batch's batched part: the host texts of instances `js` copied into
+// one device buffer (16-byte aligned starts), a counts pass that gives every
+// instance's total, then the list pass into exact capacities, and each
+// instance's counts and keys back into its own library-owned result.
+int scan_batch_host(const pm_set *const *sets, const uint8_t *const *texts, const int64_t *ns,
+                    const std::vector<int32_t> &js, uint32_t flags, void *stream, pm_result **outs)
+{
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool list = !(flags & PM_COUNTS_ONLY);
+    const int32_t kb = int32_t(js.size());
+    std::vector<const pm_set *> bs(size_t(kb), nullptr);
+    std::vector<int64_t> off(size_t(kb), 0), len(size_t(kb), 0), occ_off(size_t(kb) + 1, 0);
+    int64_t total = 0;
+    for (int32_t i = 0; i < kb; ++i) {
+        bs[size_t(i)] = sets[js[size_t(i)]];
+        off[size_t(i)] = total;
+        len[size_t(i)] = ns[js[size_t(i)]];
+        total += (len[size_t(i)] + 15) & ~int64_t(15);
+    }
+    void *d_text = nullptr, *d_counts = nullptr, *d_nocc = nullptr, *d_ws = nullptr, *d_occ = nullptr;
+    pm_batch *b = nullptr;
+    auto cleanup = [&]() {
+        pm_batch_free(b);
+        for (void *p : {d_text, d_counts, d_nocc, d_ws, d_occ})
+            if (p) cudaFree(p);
+    };
+    auto cuda_fail = [&](cudaError_t e) {
+        set_cuda_error(int(e));
+        cudaGetLastError();
+        cleanup();
+        return e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA;
+    };
+    int rc = pm_batch_prepare(bs.data(), kb, off.data(), len.data(), occ_off.data(), list ? 0u : PM_COUNTS_ONLY, &b);
+    if (rc) { cleanup(); return rc; }
+    const int64_t d_total = pm_batch_counts_total(b);
+    int64_t ws_bytes = pm_batch_workspace_bytes(b);
+    cudaError_t e = cudaMalloc(&d_text, size_t(std::max<int64_t>(total, 16)));
+    if (e == cudaSuccess) e = cudaMalloc(&d_counts, size_t(std::max<int64_t>(d_total, 1)) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_nocc, size_t(kb) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ws, size_t(ws_bytes));
+    for (int32_t i = 0; i < kb && e == cudaSuccess; ++i)
+        if (len[size_t(i)] > 0)
+            e = cudaMemcpyAsync(static_cast<uint8_t *>(d_text) + off[size_t(i)], texts[js[size_t(i)]],
+                                size_t(len[size_t(i)]), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // pass 1: every instance's total (list mode with no capacity writes no key)
+    rc = pm_batch_scan_device(b, static_cast<const uint8_t *>(d_text), static_cast<int64_t *>(d_counts), nullptr,
+                              static_cast<int64_t *>(d_nocc), d_ws, ws_bytes, stream);
+    if (!rc) rc = pm_scan_status(d_ws, stream);
+    if (rc) { cleanup(); return rc; }
+    std::vector<int64_t> nocc(size_t(kb), 0);
+    e = cudaMemcpyAsync(nocc.data(), d_nocc, size_t(kb) * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (list) {
+        // pass 2: the keys, into exact capacities
+        for (int32_t i = 0; i < kb; ++i) occ_off[size_t(i) + 1] = occ_off[size_t(i)] + nocc[size_t(i)];
+        pm_batch_free(b);
+        b = nullptr;
+        rc = pm_batch_prepare(bs.data(), kb, off.data(), len.data(), occ_off.data(), 0u, &b);
+        if (rc) { cleanup(); return rc; }
+        if (pm_batch_workspace_bytes(b) > ws_bytes) { cleanup(); return PM_ECUDA; }
+        e = cudaMalloc(&d_occ, size_t(std::max<int64_t>(occ_off[size_t(kb)], 1)) * 8);
+        if (e != cudaSuccess) return cuda_fail(e);
+        rc = pm_batch_scan_device(b, static_cast<const uint8_t *>(d_text), static_cast<int64_t *>(d_counts),
+                                  static_cast<uint64_t *>(d_occ), static_cast<int64_t *>(d_nocc), d_ws, ws_bytes,
+                                  stream);
+        if (!rc) rc = pm_scan_status(d_ws, stream);
+        if (rc) { cleanup(); return rc; }
+    }
+    int64_t coff = 0;
+    for (int32_t i = 0; i < kb && e == cudaSuccess; ++i) {
+        const int32_t j = js[size_t(i)];
+        const int64_t d = bs[size_t(i)]->ac.d;
+        pm_result *r = make_result(d, list ? nocc[size_t(i)] : 0, list);
+        if (!r) { cleanup(); return PM_ENOMEM; }
+        outs[j] = r;
+        if (!list) r->n_occ = nocc[size_t(i)];
+        e = cudaMemcpyAsync(r->counts, static_cast<int64_t *>(d_counts) + coff, size_t(d) * 8,
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && list && nocc[size_t(i)] > 0)
+            e = cudaMemcpyAsync(r->occ, static_cast<uint64_t *>(d_occ) + occ_off[size_t(i)],
+                                size_t(nocc[size_t(i)]) * 8, cudaMemcpyDeviceToHost, st);
+        coff += d;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cleanup();
+    return PM_OK;
+}
+}  // namespace
+}  // namespace pm
 
 namespace pm {
 namespace {
@@ -984,13 +1081,36 @@ int pm_scan_batch(const pm_set *const *sets, const uint8_t *const *texts, const 
                   int32_t k, uint32_t flags, void *stream, pm_result **outs)
 {
     if (!sets || !texts || !ns || !outs || k < 0) return PM_EINVAL;
+    if (flags & ~(PM_HOST_TEXT | PM_DEVICE_TEXT | PM_COUNTS_ONLY)) return PM_EINVAL;
     for (int32_t j = 0; j < k; ++j) outs[j] = nullptr;
+    for (int32_t j = 0; j < k; ++j)
+        if (!sets[j] || ns[j] < 0 || (ns[j] > 0 && !texts[j])) return PM_EINVAL;
+    // Host texts against Aho-Corasick sets the batched kernel takes go
+    // through one persistent launch; the other instances (device texts,
+    // Wu-Manber, PFAC, mixed lengths) through pm_scan, one after another.
+    std::vector<int32_t> batched, single;
     for (int32_t j = 0; j < k; ++j) {
-        int rc = pm_scan(sets[j], texts[j], ns[j], flags, stream, &outs[j]);
-        if (rc) {
-            for (int32_t q = 0; q < j; ++q) { pm_result_free(outs[q]); outs[q] = nullptr; }
-            return rc;
+        const bool fits = !(flags & PM_DEVICE_TEXT) && batch_supports(sets[j]) && ns[j] < (int64_t(1) << 32);
+        (fits ? batched : single).push_back(j);
+    }
+    if (batched.size() < 2) {
+        single.insert(single.end(), batched.begin(), batched.end());
+        batched.clear();
+    }
+    auto fail = [&](int rc) {
+        for (int32_t q = 0; q < k; ++q) {
+            pm_result_free(outs[q]);
+            outs[q] = nullptr;
         }
+        return rc;
+    };
+    if (!batched.empty()) {
+        const int rc = scan_batch_host(sets, texts, ns, batched, flags, stream, outs);
+        if (rc) return fail(rc);
+    }
+    for (const int32_t j : single) {
+        const int rc = pm_scan(sets[j], texts[j], ns[j], flags, stream, &outs[j]);
+        if (rc) return fail(rc);
     }
     return PM_OK;
 }

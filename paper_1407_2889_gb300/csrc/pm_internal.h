@@ -262,6 +262,8 @@ int ac_launch_noalloc(const AcTables &t, const DevAc &dev, const uint8_t *d_text
                       bool list, int64_t *d_counts, uint64_t *d_occ, int64_t occ_cap,
                       int64_t *d_n_occ, void *stream);
 int64_t ac_noalloc_limit_bytes();
+// status word of the last allocation-free scan on the current device
+int ac_noalloc_status(void *stream);
 // One piece of a longer Aho-Corasick / PFAC scan (the text split with an
 // m-1 halo, as Section 4.3 splits it over nodes): the first piece zeroes the
 // results, later ones add to them; keys go after *occ_base keys with

@@ -1020,23 +1020,8 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     }
 
     const AcKernel fn = pfac ? pfac_kernel_for(t, dv) : kVariants[dv.variant].fn;
-    {
-        // the attribute is per kernel and per device; kernels are few
-        static std::mutex mu;
-        static std::vector<std::pair<std::pair<int, const void *>, long long>> attr;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        std::lock_guard<std::mutex> lk(mu);
-        long long *have = nullptr;
-        for (auto &x : attr)
-            if (x.first.first == dev && x.first.second == reinterpret_cast<const void *>(fn)) have = &x.second;
-        if (!have || *have < dv.smem_bytes) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dv.smem_bytes));
-            if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
-            if (have) *have = dv.smem_bytes;
-            else attr.push_back({{dev, reinterpret_cast<const void *>(fn)}, dv.smem_bytes});
-        }
-    }
+    rc = kernel_smem_attr(reinterpret_cast<const void *>(fn), dv.smem_bytes);
+    if (rc) return rc;
     AcArgs a;
     a.text = d_text;
     a.n = n;
@@ -1213,33 +1198,20 @@ constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[64] = {};
-
-// Device address of the scratch array on the current device. The first call
-// on a device looks it up (host code cannot use the array's name as an
-// address); later calls reuse it.
+// Device address of the scratch array on the current device. Host code
+// cannot use the array's name as an address; the lookup allocates nothing
+// and is repeated on every call, so it stays right after a device reset
+// (which may move the array when the module loads again).
 int noalloc_scratch(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
         set_cuda_error(int(e));
         cudaGetLastError();
-        return PM_ENODEV;
+        return e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver ? PM_ENODEV : PM_ECUDA;
     }
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_cuda_error(int(e));
-            cudaGetLastError();
-            return PM_ECUDA;
-        }
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    *out = p;
     return PM_OK;
 }
 }  // namespace
@@ -1256,6 +1228,22 @@ int ac_launch_noalloc(const AcTables &t, const DevAc &dv, const uint8_t *d_text,
     if (rc) return rc;
     return ac_enqueue(t, dv, d_text, n, list, d_counts, d_occ, occ_cap, d_n_occ, ws,
                       static_cast<cudaStream_t>(stream));
+}
+
+int ac_noalloc_status(void *stream)
+{
+    void *ws = nullptr;
+    const int rc = noalloc_scratch(&ws);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, ws, sizeof(status), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_cuda_error(int(e));
+        return PM_ECUDA;
+    }
+    return status ? PM_ETIMEOUT : PM_OK;
 }
 
 }  // namespace pm

@@ -28,7 +28,7 @@ PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC, PM_ALGO_ACV, PM_ALGO_WMV = 1, 2, 3, 4, 5
 EXPORTED = [
     "pm_ac_compile", "pm_pfac_compile", "pm_acv_compile", "pm_wm_compile", "pm_wmv_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
     "pm_scan_to_host", "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device",
-    "pm_scan_device_noalloc", "pm_noalloc_scratch_bytes", "pm_scan_status",
+    "pm_scan_device_noalloc", "pm_noalloc_scratch_bytes", "pm_noalloc_scan_status", "pm_scan_status",
     "pm_scan_batch", "pm_batch_prepare", "pm_batch_free", "pm_batch_counts_total",
     "pm_batch_workspace_bytes", "pm_batch_warps", "pm_batch_scan_device", "pm_batch_tune",
     "pm_batch_set_warps", "pm_batch_capture", "pm_batch_replay",
@@ -137,6 +137,8 @@ def lib():
         L.pm_scan_device_noalloc.argtypes = [vp, vp, i64, u32, vp, vp, i64, vp, vp]
         L.pm_noalloc_scratch_bytes.restype = i64
         L.pm_noalloc_scratch_bytes.argtypes = []
+        L.pm_noalloc_scan_status.restype = ctypes.c_int
+        L.pm_noalloc_scan_status.argtypes = [vp]
         L.pm_scan_status.restype = ctypes.c_int
         L.pm_scan_status.argtypes = [vp, vp]
         L.pm_scan_batch.restype = ctypes.c_int
@@ -396,6 +398,10 @@ def pm_scan_device_noalloc(h: int, d_text, n: int, flags: int, d_counts, d_occ,
 
 def pm_noalloc_scratch_bytes() -> int:
     return int(lib().pm_noalloc_scratch_bytes())
+
+
+def pm_noalloc_scan_status(stream=None) -> int:
+    return int(lib().pm_noalloc_scan_status(_stream_ptr(stream)))
 
 
 def pm_scan_status(d_workspace, stream=None) -> int:

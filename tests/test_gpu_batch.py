@@ -188,3 +188,36 @@ def test_batch_rejects_unsupported_sets(d_base):
     e0 = pm.Batch([], d_base, [], [], [])
     e0.scan()
     assert e0.results() == []
+
+
+@pytest.mark.parametrize("flags", [0, "counts", "device"])
+def test_pm_scan_batch_host_call_against_oracle(base, d_base, flags):
+    """pm_scan_batch (the host-pointer batch call of the C ABI): texts of
+    mixed sizes -- empty, shorter than m, one byte past a warp tile, ragged,
+    a run of one letter -- against AC, WM and PFAC sets, a set shared by two
+    instances and a set with a duplicate pattern; every result equals the
+    oracle's for that instance alone."""
+    rng_lens = [0, 5, 2561, 100_003, 1 << 20, 777_777, 4096, A_RUN + 64]
+    starts = [0, 3, 8191, 123_457, 1_000_000, 5_000_001, 7_777_777, BASE_N - 64]
+    texts = [base[s:s + n] for s, n in zip(starts, rng_lens)]
+    P8 = synth.mixed_patterns(base[: 1 << 20], 400, 8, 61)
+    P8 = np.concatenate([P8, P8[:3], np.full((1, 8), ord("A"), np.uint8)])  # duplicates, an A-run pattern
+    P12 = synth.mixed_patterns(base[1 << 20: 2 << 20], 150, 12, 62)
+    sets = [pm.PatternSet.ac(P8), pm.PatternSet.wm(P12, 3), pm.PatternSet.pfac(P12), pm.PatternSet.ac(P12)]
+    pats = [P8, P12, P12, P12]
+    which = [0, 1, 2, 3, 0, 3, 1, 0]  # sets 0 and 3 are shared by several instances
+    handles = [sets[w].h for w in which]
+    fl = pm.PM_COUNTS_ONLY if flags == "counts" else pm.PM_DEVICE_TEXT if flags == "device" else pm.PM_HOST_TEXT
+    args = [torch.from_numpy(np.ascontiguousarray(t)).cuda() for t in texts] if flags == "device" else texts
+    res = pm.pm_scan_batch(handles, args, fl)
+    assert len(res) == len(texts)
+    for j, (t, w) in enumerate(zip(texts, which)):
+        want_occ, want_cnt = oracle.dictionary(t, pats[w], threads=THREADS)
+        occ, cnt = res[j]
+        assert np.array_equal(cnt, want_cnt), f"instance {j}: counts"
+        if flags == "counts":
+            assert occ.size == 0, f"instance {j}: counts only gives no list"
+        else:
+            assert np.array_equal(occ, want_occ), f"instance {j}: occurrences"
+    for s in sets:
+        s.close()

@@ -42,3 +42,22 @@ def test_duplicate_patterns_have_equal_counts():
     assert np.array_equal(cnt[:10], cnt[40:50])
     occ_a, cnt_a = oracle.ac_search(T, P)
     assert np.array_equal(occ_a, occ) and np.array_equal(cnt_a, cnt)
+
+
+def test_concurrent_dictionary_calls_match_sequential_ones():
+    """The dictionary routes sort their patterns with the comparison context
+    passed as an argument, so calls running at the same time (ctypes drops
+    the GIL) each sort by their own patterns."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1407_2889_gb300 import synth
+    T = synth.uniform_dna(1 << 16, 11)
+    cases = [synth.mixed_patterns(T, 200 + 37 * k, 6 + (k % 3), 50 + k) for k in range(8)]
+    var = [[bytes(p[: 4 + (j % 5)]) for j, p in enumerate(P)] for P in cases]
+    want = [oracle.dictionary(T, P, threads=2) for P in cases]
+    want_v = [oracle.dictionary_var(T, P, threads=2) for P in var]
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        got = list(ex.map(lambda P: oracle.dictionary(T, P, threads=2), cases))
+        got_v = list(ex.map(lambda P: oracle.dictionary_var(T, P, threads=2), var))
+    for (wo, wc), (go, gc) in zip(want + want_v, got + got_v):
+        assert np.array_equal(wo, go) and np.array_equal(wc, gc)

@@ -38,6 +38,9 @@ def _noalloc(s, d_text, n, flags, d, cap):
     occ = torch.full((max(cap, 1),), -1, dtype=torch.int64, device="cuda")
     nocc = torch.full((1,), -1, dtype=torch.int64, device="cuda")
     pm.pm_scan_device_noalloc(s.h, d_text, n, flags, counts, occ, cap, nocc)
+    # the kernel's status word lives in the library's array, not in a
+    # caller's workspace: read it through the allocation-free reader
+    assert pm.pm_noalloc_scan_status() == pm.PM_OK
     torch.cuda.synchronize()
     k = int(nocc.item())
     return occ[: min(k, cap)].cpu().numpy(), counts.cpu().numpy(), k
@@ -60,6 +63,26 @@ def test_noalloc_matches_regular_scan_on_two_calls(flags):
         assert np.array_equal(got[1], want[1]), f"call {call}: counts"
         if not flags & pm.PM_COUNTS_ONLY:
             assert np.array_equal(got[0], want[0]), f"call {call}: occurrences"
+    s.close()
+
+
+def test_noalloc_on_a_set_tuned_to_two_characters_per_lookup():
+    """A set whose plan takes two characters per lookup: the allocation-free
+    call always walks one character at a time, with the same results."""
+    T = synth.est_text(4 << 20, 37)
+    P = synth.mixed_patterns(T, 300, 10, 37)
+    d = P.shape[0]
+    s = pm.PatternSet.ac(P, {"stride": 2})
+    assert s.info()["stride"] == 2
+    d_text = torch.from_numpy(T).cuda()
+    cap = T.size // 4
+    want = _regular(s, d_text, T.size, 0, d, cap)
+    assert want[2] > 0
+    for call in range(2):
+        got = _noalloc(s, d_text, T.size, 0, d, cap)
+        assert got[2] == want[2], f"call {call}: total"
+        assert np.array_equal(got[1], want[1]), f"call {call}: counts"
+        assert np.array_equal(got[0], want[0]), f"call {call}: occurrences"
     s.close()
 
 
