@@ -123,20 +123,40 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(T: np.ndarray, P: np.ndarray, target_s: float = 12.0):
-    """Time the oracle's dictionary route (all host cores) on a prefix sized
-    for about target_s seconds of work. Returns (GB/s, cores, sample text)."""
+def cpu_baselines(T: np.ndarray, P: np.ndarray, target_s: float = 4.0):
+    """Time two CPU routes on the host cores, each on all cores and on one
+    core, every measurement on a prefix of the text sized for about target_s
+    seconds: the oracle's sorted-dictionary route, and the multithreaded CPU
+    Aho-Corasick DFA scan (the oracle's automaton merged into a full DFA over
+    byte classes, threads over contiguous ranges with the m-1 overlap).
+    Returns the cpu_baseline object: value = the fastest all-core route."""
     import oracle
     cores = os.cpu_count() or 1
-    probe = min(T.size, 4 << 20)
-    t0 = time.perf_counter()
-    oracle.dictionary(T[:probe], P, threads=cores)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    size = int(min(T.size, max(probe, probe * target_s / dt)))
-    t0 = time.perf_counter()
-    occ, _ = oracle.dictionary(T[:size], P, threads=cores)
-    dt = time.perf_counter() - t0
-    return size / dt / 1e9, cores, f"first {size} bytes of the text ({size / 2**20:.0f} MiB), d={P.shape[0]}, m={P.shape[1]}, {occ.size} occurrences, {dt:.1f} s"
+    A = oracle.ACAutomaton(P)
+    routes = {
+        "dictionary": lambda t, th: oracle.dictionary(t, P, threads=th),
+        "ac_dfa": lambda t, th: oracle.ac_dfa_scan(t, P, threads=th, automaton=A),
+    }
+    out = {}
+    for name, fn in routes.items():
+        for th in (cores, 1):
+            probe = min(T.size, 1 << 20)
+            t0 = time.perf_counter()
+            fn(T[:probe], th)
+            dt = max(time.perf_counter() - t0, 1e-3)
+            size = int(min(T.size, max(probe, probe * target_s / dt)))
+            t0 = time.perf_counter()
+            occ, _ = fn(T[:size], th)
+            dt = time.perf_counter() - t0
+            out[f"{name}_{'all' if th == cores else '1'}_cores"] = {
+                "gbs": size / dt / 1e9, "threads": th, "bytes": size, "seconds": round(dt, 2), "n_occ": int(occ.size)}
+    best = max(("dictionary", "ac_dfa"), key=lambda k: out[f"{k}_all_cores"]["gbs"])
+    b = out[f"{best}_all_cores"]
+    return {"value": b["gbs"], "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "route": best,
+            "sample": (f"prefixes of the 1 GiB EST text sized for about {target_s:.0f} s each "
+                       f"(best all-core route: {best}, {b['bytes'] >> 20} MiB), d={P.shape[0]}, m={P.shape[1]}"),
+            "routes": out, "nproc": cores}
 
 
 def parse():
@@ -156,7 +176,7 @@ def parse():
                     help="instances of the batched-vs-plain comparison (0 skips it)")
     ap.add_argument("--only-batch", action="store_true",
                     help="run only the batched-vs-plain comparison and print it")
-    ap.add_argument("--serve-seconds", type=float, default=6.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the Poisson request stream of the serving run (0 skips it)")
     ap.add_argument("--only-serve", action="store_true",
                     help="run only the serving measurement and print it")
@@ -366,8 +386,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, cores, sample = cpu_oracle_rate(T, P)
-        cpu = {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = cpu_baselines(T, P)
 
     if rank == 0:
         line = {
@@ -425,26 +444,31 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
                 q.tune(d_text, reps=2)
             cnt_q = torch.zeros(dd, dtype=torch.int64, device="cuda")
             ws = torch.zeros(q.workspace_bytes(n), dtype=torch.uint8, device="cuda")
-            with torch.cuda.stream(stream):
-                pm.pm_scan_device(q.h, d_text, n, pm.PM_COUNTS_ONLY, cnt_q, None, 0, nocc, ws, ws.numel(), stream)
-            stream.synchronize()
+
+            def timed(flags, buf, cap, reps=3):
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    pm.pm_scan_device(q.h, d_text, n, flags, cnt_q, buf, cap, nocc, ws, ws.numel(), stream)
+                    ev0.record(stream)
+                    for _ in range(reps):
+                        pm.pm_scan_device(q.h, d_text, n, flags, cnt_q, buf, cap, nocc, ws, ws.numel(), stream)
+                    ev1.record(stream)
+                stream.synchronize()
+                assert pm.pm_scan_status(ws, stream) == pm.PM_OK
+                return ev0.elapsed_time(ev1) / reps / 1e3
+
+            dt_c = timed(pm.PM_COUNTS_ONLY, None, 0)
             tot = int(nocc.item())
             buf = occ if tot <= occ.numel() else torch.empty(tot, dtype=torch.int64, device="cuda")
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(stream):
-                pm.pm_scan_device(q.h, d_text, n, 0, cnt_q, buf, buf.numel(), nocc, ws, ws.numel(), stream)
-                ev0.record(stream)
-                for _ in range(3):
-                    pm.pm_scan_device(q.h, d_text, n, 0, cnt_q, buf, buf.numel(), nocc, ws, ws.numel(), stream)
-                ev1.record(stream)
-            stream.synchronize()
-            dt = ev0.elapsed_time(ev1) / 3 / 1e3
+            dt = timed(0, buf, buf.numel())
             inf = q.info()
+            peak = measured_peaks()[0]
             sweep[f"d{dd}_m{mm}"] = {"gbs": n / dt / 1e9, "n_occ": tot,
-                                      "alg_frac": (n + 8 * tot + 8 * dd) / dt / 1e9 / measured_peaks()[0],
+                                      "alg_frac": (n + 8 * tot + 8 * dd) / dt / 1e9 / peak,
+                                      "counts_gbs": n / dt_c / 1e9, "counts_alg_frac": (n + 8 * dd) / dt_c / 1e9 / peak,
                                       "placement": inf["placement"], "rows": inf["n_rows"],
-                                      "entry_bytes": inf["entry_bytes"]}
+                                      "entry_bytes": inf["entry_bytes"], "stride": inf["stride"]}
             q.close()
             del buf, ws
             torch.cuda.empty_cache()

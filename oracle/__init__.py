@@ -92,6 +92,8 @@ def _bind(lib):
     lib.orc_wm_hash_next.argtypes = [vp, i64]
     lib.orc_wm_search.restype = i64
     lib.orc_wm_search.argtypes = [vp, _u8p, i64, _u64p, i64, _i64p]
+    lib.orc_ac_dfa_scan.restype = i64
+    lib.orc_ac_dfa_scan.argtypes = [vp, _u8p, i64, i32, _u64p, i64, _i64p]
     if hasattr(lib, "orc_brute_var"):
         lib.orc_brute_var.restype = i64
         lib.orc_brute_var.argtypes = [_u8p, i64, _u8p, _i64p, i64, _u64p, i64, _i64p]
@@ -341,6 +343,22 @@ class WMTables:
 def ac_search(T, P, lib=None):
     """Sequential Aho-Corasick (Algorithms 1-3). Returns (occ, counts)."""
     return ACAutomaton(P, lib=lib).search(T)
+
+
+def ac_dfa_scan(T, P, threads: int | None = None, automaton=None, lib=None, n_hint: int | None = None):
+    """The CPU baseline: Algorithms 1-2's automaton as a full DFA over byte
+    classes, walked by ``threads`` host threads over contiguous ranges with
+    the m-1 overlap. Returns (occ, counts). Pass ``automaton`` (an
+    ACAutomaton of P) to time the scan without the build."""
+    T = _as_text(T)
+    A = automaton or ACAutomaton(P, lib=lib)
+    nt = int(threads or os.cpu_count() or 1)
+
+    def fn(occ, cap, counts):
+        return A._lib.orc_ac_dfa_scan(A._h, _ptr(T, _u8p), T.size, nt, _ptr(occ, _u64p), cap,
+                                      _ptr(counts, _i64p))
+
+    return _run_two_pass(fn, n_hint if n_hint is not None else max(1024, T.size // 8), A.d)
 
 
 def wm_search(T, P, B: int, Bp: int = 2, lib=None):

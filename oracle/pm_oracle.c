@@ -28,6 +28,9 @@
  *                  breadth-first order, search that follows supply links.
  *   orc_wm_*    -- sequential Wu-Manber, Algorithms 4 and 5 (Section 3.2)
  *                  with the paper's shift-and-add hash (bitshift 2).
+ *   orc_ac_dfa_scan -- the CPU baseline: the same automaton as a full DFA
+ *                  over byte classes, walked by host threads over contiguous
+ *                  ranges with the m-1 overlap (timed, not a parity route).
  *   orc_brute_var, orc_dict_var -- the same definition for a set whose
  *                  patterns have their own lengths len_r: every (i, r) with
  *                  i + len_r <= n and t_{i+k} = p^r_k for all k < len_r
@@ -361,6 +364,127 @@ int64_t orc_ac_search(const orc_ac *a, const uint8_t *T, int64_t n,
         }
     }
     return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* CPU baseline: the same automaton as a full DFA (goto and supply merged,   */
+/* the "array of size |Sigma|" form of Section 3.1) over byte classes, walked */
+/* by nthreads threads, each over a contiguous range of start positions plus */
+/* the m-1 characters after it (Section 4.2.1's chunk-with-overlap split,    */
+/* here over host threads). Not a parity route: it exists to be timed.       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const int32_t *dfa;     /* nstates x ncls */
+    const uint8_t *cls;     /* byte -> class (0 = a byte in no pattern) */
+    const orc_ac *a;
+    int32_t ncls;
+    const uint8_t *T;
+    int64_t n, i0, i1;      /* start positions [i0, i1) */
+    uint64_t *buf;
+    int64_t len, cap;
+    int64_t *counts;
+    int failed;
+} orc_dfa_job;
+
+static void *orc_dfa_worker(void *arg)
+{
+    orc_dfa_job *jb = (orc_dfa_job *)arg;
+    const int32_t m = jb->a->m;
+    int64_t end = jb->i1 + m - 1;
+    if (end > jb->n) end = jb->n;
+    int32_t q = 0;
+    for (int64_t e = jb->i0; e < end; e++) {
+        q = jb->dfa[(int64_t)q * jb->ncls + jb->cls[jb->T[e]]];
+        for (int64_t r = jb->a->out_head[q]; r >= 0; r = jb->a->out_next[r]) {
+            if (jb->len == jb->cap) {
+                int64_t nc = jb->cap ? 2 * jb->cap : 4096;
+                uint64_t *nb = (uint64_t *)realloc(jb->buf, (size_t)nc * sizeof(uint64_t));
+                if (!nb) { jb->failed = 1; return NULL; }
+                jb->buf = nb;
+                jb->cap = nc;
+            }
+            jb->buf[jb->len++] = ORC_OCC(e - m + 1, r);
+            jb->counts[r]++;
+        }
+    }
+    return NULL;
+}
+
+int64_t orc_ac_dfa_scan(const orc_ac *a, const uint8_t *T, int64_t n, int32_t nthreads,
+                        uint64_t *occ, int64_t cap, int64_t *counts)
+{
+    for (int64_t r = 0; r < a->d; r++) counts[r] = 0;
+    const int32_t m = a->m;
+    if (n < m) return 0;
+    /* byte classes: each byte that leaves the root or any state, in byte order */
+    uint8_t cls[ORC_SIGMA];
+    int32_t ncls = 1;
+    for (int c = 0; c < ORC_SIGMA; c++) {
+        int used = 0;
+        for (int64_t q = 0; q < a->nstates && !used; q++) {
+            int32_t t = a->g[q * ORC_SIGMA + c];
+            used = t != ORC_FAIL && t != 0;
+        }
+        cls[c] = used ? (uint8_t)ncls++ : 0;
+    }
+    /* breadth-first order from the depths, then delta(q, c) = g(q, c) if
+     * defined, else delta(Supply(q), c) (Supply(q) is shallower) */
+    int64_t ns = a->nstates;
+    int32_t *dfa = (int32_t *)malloc((size_t)ns * (size_t)ncls * sizeof(int32_t));
+    int64_t *order = (int64_t *)malloc((size_t)ns * sizeof(int64_t));
+    int64_t *first = (int64_t *)calloc((size_t)m + 2, sizeof(int64_t));
+    if (!dfa || !order || !first) { free(dfa); free(order); free(first); return -1; }
+    for (int64_t q = 0; q < ns; q++) first[a->depth[q] + 1]++;
+    for (int32_t k = 1; k <= m + 1; k++) first[k] += first[k - 1];
+    for (int64_t q = 0; q < ns; q++) order[first[a->depth[q]]++] = q;
+    int32_t rep[ORC_SIGMA];   /* a byte of each class */
+    for (int c = ORC_SIGMA - 1; c >= 0; c--) rep[cls[c]] = c;
+    for (int64_t k = 0; k < ns; k++) {
+        const int64_t q = order[k];
+        for (int32_t c = 0; c < ncls; c++) {
+            int32_t t = c == 0 ? ORC_FAIL : a->g[q * ORC_SIGMA + rep[c]];
+            if (q == 0) dfa[c] = (t == ORC_FAIL) ? 0 : t;
+            else dfa[q * ncls + c] = (t == ORC_FAIL) ? dfa[(int64_t)a->supply[q] * ncls + c] : t;
+        }
+    }
+    free(order);
+    free(first);
+
+    if (nthreads < 1) nthreads = 1;
+    int64_t nwin = n - m + 1;
+    if (nthreads > nwin) nthreads = (int32_t)nwin;
+    orc_dfa_job *jobs = (orc_dfa_job *)calloc((size_t)nthreads, sizeof(orc_dfa_job));
+    pthread_t *tids = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !tids) { free(dfa); free(jobs); free(tids); return -1; }
+    int failed = 0;
+    for (int32_t t = 0; t < nthreads; t++) {
+        jobs[t].dfa = dfa; jobs[t].cls = cls; jobs[t].a = a; jobs[t].ncls = ncls;
+        jobs[t].T = T; jobs[t].n = n;
+        jobs[t].i0 = nwin * t / nthreads;
+        jobs[t].i1 = nwin * (t + 1) / nthreads;
+        jobs[t].counts = (int64_t *)calloc((size_t)a->d, sizeof(int64_t));
+        if (!jobs[t].counts) failed = 1;
+    }
+    if (!failed) {
+        for (int32_t t = 0; t < nthreads; t++) pthread_create(&tids[t], NULL, orc_dfa_worker, &jobs[t]);
+        for (int32_t t = 0; t < nthreads; t++) pthread_join(tids[t], NULL);
+    }
+    int64_t total = 0;
+    for (int32_t t = 0; t < nthreads; t++) {
+        failed |= jobs[t].failed;
+        for (int64_t k = 0; k < jobs[t].len; k++) {
+            if (total < cap) occ[total] = jobs[t].buf[k];
+            total++;
+        }
+        if (jobs[t].counts)
+            for (int64_t r = 0; r < a->d; r++) counts[r] += jobs[t].counts[r];
+        free(jobs[t].buf);
+        free(jobs[t].counts);
+    }
+    free(jobs);
+    free(tids);
+    free(dfa);
+    return failed ? -1 : total;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -61,3 +61,20 @@ def test_concurrent_dictionary_calls_match_sequential_ones():
         got_v = list(ex.map(lambda P: oracle.dictionary_var(T, P, threads=2), var))
     for (wo, wc), (go, gc) in zip(want + want_v, got + got_v):
         assert np.array_equal(wo, go) and np.array_equal(wc, gc)
+
+
+@pytest.mark.parametrize("threads", [1, 3, 7])
+def test_cpu_dfa_baseline_equals_the_definition(threads):
+    """The multithreaded CPU DFA scan (the timed baseline) reports exactly the
+    definition's set, whatever the split: ranges cut mid-match, texts with
+    bytes in no pattern, duplicate patterns, and runs of one letter."""
+    from paper_1407_2889_gb300 import synth
+    T = synth.est_text(1 << 16, 13)
+    T = np.concatenate([T, np.full(500, ord("A"), np.uint8), T[:333]])
+    P = synth.mixed_patterns(T, 150, 7, 13)
+    P = np.concatenate([P, P[:5], np.full((1, 7), ord("A"), np.uint8)])
+    want = oracle.brute(T, P)
+    got = oracle.ac_dfa_scan(T, P, threads=threads)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+    short = T[:5]
+    assert oracle.ac_dfa_scan(short, P, threads=threads)[0].size == 0
