@@ -460,8 +460,8 @@ int64_t orc_ac_dfa_scan(const orc_ac *a, const uint8_t *T, int64_t n, int32_t nt
     for (int32_t t = 0; t < nthreads; t++) {
         jobs[t].dfa = dfa; jobs[t].cls = cls; jobs[t].a = a; jobs[t].ncls = ncls;
         jobs[t].T = T; jobs[t].n = n;
-        jobs[t].i0 = nwin * t / nthreads;
-        jobs[t].i1 = nwin * (t + 1) / nthreads;
+        jobs[t].i0 = (nwin * t) / nthreads;        /* thread t's start positions */
+        jobs[t].i1 = (nwin * (t + 1)) / nthreads;
         jobs[t].counts = (int64_t *)calloc((size_t)a->d, sizeof(int64_t));
         if (!jobs[t].counts) failed = 1;
     }
