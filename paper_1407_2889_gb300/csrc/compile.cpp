@@ -1012,10 +1012,11 @@ void build_ac2(AcTables &t)
         }
 }
 
-// Every byte is walked under its class ((b >> 1) ^ (b >> 2)) & 3, so a byte
-// outside the alphabet does not reset the walk; a match whose window of m
-// bytes holds such a byte is dropped. A match depends only on its window,
-// so the others are exactly those of the one-character walk.
+// The two-character walk as the device runs it: a pair (b1, b2) moves the
+// state to table2[row * 16 + c1 * 4 + c2]. A byte outside the alphabet
+// resets the walk: as b1 it selects row 0 (after a reset byte: the entry of
+// (c1, c2) is the root's transition on c2, whatever c1), as b2 it sends the
+// state to the root after the pair and drops the pair's second flag.
 void host_walk_ac2(const AcTables &t, const uint8_t *T, int64_t n,
                    std::vector<uint64_t> &occ, std::vector<int64_t> &counts)
 {
@@ -1034,18 +1035,18 @@ void host_walk_ac2(const AcTables &t, const uint8_t *T, int64_t n,
             emit_entry(occ, counts, pos, v);
         }
     };
-    uint32_t E = 1u << 4;   // root (row 1)
-    int64_t last_bad = -1;
+    uint32_t E = 16u;  // the root: row 1, as an index of its first entry
     for (int64_t i = 0; i < n; i += 2) {
-        const uint32_t b1 = T[i], b2 = i + 1 < n ? T[i + 1] : 0u;
+        const uint32_t b1 = T[i];
+        const bool last = i + 1 >= n;          // the text ends inside this pair
+        const uint32_t b2 = last ? 0u : T[i + 1];
         const uint32_t c1 = dna_code(b1), c2 = dna_code(b2);
-        const uint32_t idx2 = (E & ~15u) | (c1 << 2) | c2;
+        const uint32_t row = bad(b1) ? 0u : (E & ~15u);
+        const uint32_t idx2 = row | (c1 << 2) | c2;
         E = t.table2[idx2];
-        if (bad(b1)) last_bad = i;
-        if ((E & 1u) && last_bad < i - m + 1) report(i, idx2 >> 2);
-        if (i + 1 >= n) break;
-        if (bad(b2)) last_bad = i + 1;
-        if ((E & 2u) && last_bad < i + 1 - m + 1) {
+        if (last || bad(b2)) E = (E & 1u) | 16u;
+        if (E & 1u) report(i, idx2 >> 2);
+        if (E & 2u) {
             const uint32_t e1 = t.table[idx2 >> 2];
             report(i + 1, ((e1 >> 1) << 2) | c2);
         }

@@ -4,16 +4,17 @@
 //
 // A row has 16 entries, one per pair of character classes, holding the
 // state after both characters and a match flag for each: the one-character
-// table applied twice (the same rows, terminal rows elided). A lane walks its
-// chunk + halo a pair at a time with every byte under its class
-// ((b >> 1) ^ (b >> 2)) & 3, so a byte outside the alphabet does not reset
-// the walk; instead the lane records where such bytes are and drops every
-// match whose window of m bytes holds one. A match depends only on its
-// window, so the others are exactly those of the one-character walk. A pool
-// entry keeps the pair's two-character index, its two flags and the pair's
-// number, so the resolution writes the tile's slot in text order directly.
-// The workspace, slots and expand kernel are those of the one-character
-// scan.
+// table applied twice (the same rows, terminal rows elided). A lane walks
+// its chunk + halo a pair at a time. A byte outside the alphabet resets the
+// walk inside the lookup chain: as the pair's first byte it selects row 0
+// (the one-character reset row applied first, so its entry for (c1, c2) is
+// the root's transition on c2), as the second it sends the state to the
+// root after the pair and drops the pair's second flag. The walk keeps a
+// step bitmask of matches in registers and stores each 16-byte vector's
+// eight pair indices with one shared-memory store; the matches are resolved
+// afterwards from those records (a second-character match through one more
+// lookup of the one-character table). The workspace, slots and expand
+// kernel are those of the one-character scan.
 #include "ac_device.cuh"
 
 namespace pm {
@@ -53,10 +54,22 @@ struct Ac2Args {
 
 __host__ __device__ constexpr long long r16a(long long x) { return (x + 15) & ~15LL; }
 
-__host__ __device__ inline long long ac2_warp_bytes(int hv, int pool_cap)
+constexpr int kAc2MaxWarps = 20;  // one CTA per SM
+
+// prmt.b32 in its generic mode: a selector nibble with bit 3 set fills its
+// result byte with the sign (bit 7) of the selected byte (the __byte_perm
+// intrinsic ignores that bit)
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t sel)
 {
-    // barrier | text buffer | pool of 32-bit entries (pool_cap + 1 slots per lane)
-    return 16 + r16a(kWarpTile + 16 * hv) + r16a((long long)(pool_cap + 1) * 32 * 4);
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(0u), "r"(sel));
+    return d;
+}
+
+__host__ __device__ inline long long ac2_warp_bytes(int hv, int)
+{
+    // barrier | text buffer | pair records (16 bytes per lane per text vector)
+    return 16 + r16a(kWarpTile + 16 * hv) + (long long)(5 + hv) * 32 * 16;
 }
 
 __device__ __forceinline__ int ac2_stage_bytes(const Ac2Args &a, long long t, int buf)
@@ -75,18 +88,8 @@ __device__ __forceinline__ void ac2_stage_issue(const Ac2Args &a, long long t, u
     if (bytes > 0) dev::tma_load_1d(buf, a.text + t * kWarpTile, uint32_t(bytes), bar);
 }
 
-template <int HW>
-__device__ __forceinline__ uint32_t pick_word(const uint32_t (&w)[HW], uint32_t i)
-{
-    uint32_t v = w[0];
-#pragma unroll
-    for (int k = 1; k < HW; ++k)
-        if (i == uint32_t(k)) v = w[k];
-    return v;
-}
-
 template <int NV, int HV>
-__global__ void __launch_bounds__(512, 1) ac2_scan_kernel(const Ac2Args a)
+__global__ void __launch_bounds__(kAc2MaxWarps * 32, 1) ac2_scan_kernel(const Ac2Args a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr uint32_t kGrp = 0x8000u;
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(512, 1) ac2_scan_kernel(const Ac2Args a)
     p += warp * ac2_warp_bytes(HV, a.pool_cap);
     uint64_t *bar = reinterpret_cast<uint64_t *>(p);
     uint8_t *buf = p + 16;
-    uint32_t *pool = reinterpret_cast<uint32_t *>(buf + r16a(BUF));
+    unsigned char *rec = buf + r16a(BUF);  // lane l, vector v: 16 bytes at (v * 32 + l) * 16
 
     {
         const int n1 = int(((long long)a.n_rows * 8 + 15) / 16), n2 = int(((long long)a.n_rows * 32 + 15) / 16);
@@ -131,9 +134,6 @@ __global__ void __launch_bounds__(512, 1) ac2_scan_kernel(const Ac2Args a)
     dev::fence_proxy_async_smem();
     __syncthreads();
 
-    const acdev::TableRef<uint16_t, false> tab1{s_t1, a.tab1_g, uint32_t(a.n_rows) * 4};
-    uint32_t *pl = pool + lane;
-    const uint32_t cap = uint32_t(a.pool_cap);
     const int m = a.m;
     const long long G = (long long)gridDim.x * (blockDim.x >> 5);
     const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -205,95 +205,86 @@ __global__ void __launch_bounds__(512, 1) ac2_scan_kernel(const Ac2Args a)
 
         // ---- walk, a pair of characters per lookup ------------------------
         const int steps = kChunk + m - 1;
-        uint32_t hw[HW], xw[HW];
+        uint32_t hw[HW];
 #pragma unroll
-        for (int j = 0; j < HW; ++j) hw[j] = xw[j] = 0u;
+        for (int j = 0; j < HW; ++j) hw[j] = 0u;
         uint32_t e2 = 16u;  // root: row 1
-        uint32_t kslot = 0;
+        const uint32_t rec0 = dev::smem_addr(rec) + uint32_t(lane) * 16u;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
+            uint32_t pk[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint32_t w = acdev::word_of(tv[v], q);
                 const int s0 = v * 16 + q * 4;
+                if (!(s0 < kChunk || s0 < steps)) continue;
                 const uint32_t a4 = ((w >> 1) ^ (w >> 2)) & 0x03030303u;
                 const uint32_t sel = __byte_perm(a4 | (a4 >> 4), 0u, 0x4420);
                 const uint32_t x = w ^ __byte_perm(a.lut, 0u, sel);  // zero byte = in the alphabet
-                const uint32_t y = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
-                const uint32_t inv = ~y & 0x80808080u;             // 0x80 per byte outside it
-                xw[s0 >> 5] |= ((((inv >> 7) * 0x00204081u) >> 21) & 15u) << (s0 & 31);
-                const uint32_t u = (a4 << 2) | (a4 >> 8);           // pair codes in bytes 0 and 2
+                // bit 7 of each byte of y: the byte is outside the alphabet
+                const uint32_t y = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
+                const uint32_t u = (a4 << 2) | (a4 >> 8);            // pair codes in bytes 0 and 2
+                // per pair (16-bit halves): t2 = 0xFFF0 | code, or the code
+                // alone (row 0) when the first byte is outside; mx = 0xFFFF,
+                // or 0x0001 when the second byte is outside
+                const uint32_t inv1 = prmt_sign(y, 0xAA88u);
+                const uint32_t t2w = (~inv1 & 0xFFF0FFF0u) | (u & 0x000F000Fu);
+                const uint32_t mxw = ~prmt_sign(y, 0xBB99u) | 0x00010001u;
 #pragma unroll
                 for (int pp = 0; pp < 2; ++pp) {
-                    const int j0 = s0 + 2 * pp;                      // first character's step
+                    const int j0 = s0 + 2 * pp;  // first character's step
                     if (j0 < kChunk || j0 < steps) {
-                        const uint32_t idx2 = (e2 & ~15u) | ((u >> (16 * pp)) & 15u);
+                        const uint32_t t2 = pp ? (t2w >> 16) : t2w;
+                        const uint32_t mx = pp ? (mxw >> 16) : mxw;
+                        const uint32_t idx2 = (e2 & t2 & ~15u) | (t2 & 15u);
                         e2 = s_t2[idx2];
-                        uint32_t h2 = e2 & 3u;
-                        if (!(j0 + 1 < kChunk || j0 + 1 < steps)) h2 &= 1u;  // past the lane's last step
-                        pl[kslot * 32] = idx2 | (h2 << 16) | (uint32_t(j0 >> 1) << 18);
-                        kslot = min(kslot + min(h2, 1u), cap);
-                        hw[j0 >> 5] |= h2 << (j0 & 31);
+                        e2 = (e2 & mx) | (16u & ~mx);
+                        hw[j0 >> 5] |= (e2 & 3u) << (j0 & 31);
+                        pk[q] = pp ? (pk[q] | (idx2 << 16)) : idx2;
                     }
                 }
             }
+            if (v * 16 < steps)
+                asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(rec0 + uint32_t(v) * 512u),
+                             "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3])
+                             : "memory");
         }
-        // windows holding a byte outside the alphabet: step j is dropped when
-        // a marked byte lies in [j - m + 1, j] (the marks spread m - 1 up)
-        uint32_t bw[HW];
-#pragma unroll
-        for (int j = 0; j < HW; ++j) bw[j] = xw[j];
-        for (int len = 1; len < m;) {
-            const int k = min(len, m - len);  // < 32 for m <= 33
-#pragma unroll
-            for (int j = HW - 1; j >= 0; --j) bw[j] |= j > 0 ? __funnelshift_l(bw[j - 1], bw[j], k) : (bw[j] << k);
-            len += k;
-        }
-        uint32_t vh[HW], npe = 0, nh = 0;
+        // a match at a step past the lane's last (the second byte of a last
+        // pair that straddles it) is not this lane's
 #pragma unroll
         for (int j = 0; j < HW; ++j) {
-            npe += __popc((hw[j] | (hw[j] >> 1)) & 0x55555555u);
-            vh[j] = hw[j] & ~bw[j];
-            nh += __popc(vh[j]);
+            const int lo = j * 32;
+            if (lo + 32 > steps) hw[j] &= lo >= steps ? 0u : ((1u << (steps - lo)) - 1u);
         }
-        const bool ovf = npe > cap;
+        uint32_t nh = 0;
+#pragma unroll
+        for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
+        __syncwarp();
 
         // ---- matches -> counters, and the tile's slot in text order -------
-        const long long g0 = tile0 + (long long)lane * kChunk;
         const uint32_t e_incl = a.list ? dev::warp_incl_scan(nh, lane) : 0u;
         uint32_t *dst = a.slots + st * kWarpTile + (e_incl - nh);
         const uint32_t off0 = uint32_t(lane * kChunk - (m - 1));
         uint32_t cnt = 0, kout = 0;
-        auto take = [&](int step, uint32_t idx1) {
-            const uint32_t c = terminal(idx1);
-            const uint32_t code = s_canon[c];
-            count_terminal(c);
-            cnt += mult_of(code);
-            if (a.list && kout < nh) dst[kout] = ((off0 + uint32_t(step)) << 16) | code;
-            ++kout;
-        };
-        if (!ovf) {
-            for (uint32_t k0 = 0; k0 < npe; k0 += 4) {
-                uint32_t pv[4];
+        const uint16_t *rec16 = reinterpret_cast<const uint16_t *>(rec);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) pv[j] = k0 + j < npe ? pl[(k0 + j) * 32] : 0u;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (k0 + j >= npe) break;
-                    const uint32_t idx2 = pv[j] & 0xFFFFu;
-                    const int j0 = int(pv[j] >> 18) * 2;
-                    const uint32_t bits = (pick_word<HW>(vh, uint32_t(j0) >> 5) >> (j0 & 31)) & 3u;
-                    if (bits & 1u) take(j0, idx2 >> 2);
-                    if (bits & 2u) {
-                        const uint32_t e1 = s_t1[idx2 >> 2];
-                        take(j0 + 1, (e1 & ~3u) | (idx2 & 3u));
-                    }
-                }
+        for (int j = 0; j < HW; ++j) {
+            uint32_t wj = hw[j];
+            while (wj) {
+                const int b = __ffs(int(wj)) - 1;
+                wj &= wj - 1u;
+                const int step = j * 32 + b;
+                const int p = step >> 1;
+                const uint32_t idx2 = rec16[((p >> 3) * 32 + lane) * 8 + (p & 7)];
+                uint32_t idx1 = idx2 >> 2;
+                if (step & 1) idx1 = (uint32_t(s_t1[idx1]) & ~3u) | (idx2 & 3u);
+                const uint32_t c = terminal(idx1);
+                const uint32_t code = s_canon[c];
+                count_terminal(c);
+                cnt += mult_of(code);
+                if (a.list) dst[kout] = ((off0 + uint32_t(step)) << 16) | code;
+                ++kout;
             }
-        } else {
-            // the pool overflowed: the one-character walk from device memory
-            acdev::walk_slow<true>(a.text, a.n, g0, steps, true, a.lut, 2, nullptr, tab1,
-                                   [&](int step, uint32_t idx) { take(step, idx); });
         }
 
         if (!a.list) {
@@ -360,21 +351,19 @@ int ac2_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, Dev
     if (!ac2_eligible(t) || t.table2.empty()) return PM_ETOOBIG;
     const int hv = t.m - 1 <= 16 ? 1 : 2;
     const long long budget = (long long)dp.smem_optin - 1024;
-    const int forced = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, 16) : 0;
-    for (int hist : {1, 2})
-        for (int w : {16, 12, 8}) {
-            if (forced && w != forced) continue;
-            for (int cap : {40, 32, 24}) {
-                const long long need = ac2_smem_bytes(t, hist, w, hv, cap);
-                if (need > budget) continue;
-                dev.warps = w;
-                dev.pool_cap = cap;
-                dev.hist_smem = hist;
-                dev.hv = hv;
-                dev.nv = 5 + hv;
-                dev.smem_bytes = need;
-                return PM_OK;
-            }
+    const int forced = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, kAc2MaxWarps) : 0;
+    // the most warps that fit, 32-bit counters before 16-bit ones
+    for (int w = forced ? forced : kAc2MaxWarps; w >= (forced ? forced : 4); --w)
+        for (int hist : {1, 2}) {
+            const long long need = ac2_smem_bytes(t, hist, w, hv, 0);
+            if (need > budget) continue;
+            dev.warps = w;
+            dev.pool_cap = 0;
+            dev.hist_smem = hist;
+            dev.hv = hv;
+            dev.nv = 5 + hv;
+            dev.smem_bytes = need;
+            return PM_OK;
         }
     return PM_ETOOBIG;
 }
