@@ -1007,13 +1007,14 @@ void build_ac2(AcTables &t)
             const uint32_t r1 = e1 >> 1, m1 = e1 & 1u;
             for (uint32_t c2 = 0; c2 < 4; ++c2) {
                 const uint32_t e2 = t.table[size_t(r1) * 4 + c2];
-                t.table2[size_t(r) * 16 + c1 * 4 + c2] = uint16_t(((e2 >> 1) << 4) | ((e2 & 1u) << 1) | m1);
+                t.table2[size_t(r) * 16 + c1 * 4 + c2] = uint16_t(((e2 >> 1) << 4) | (m1 << 1) | (e2 & 1u));
             }
         }
 }
 
 // The two-character walk as the device runs it: a pair (b1, b2) moves the
-// state to table2[row * 16 + c1 * 4 + c2]. A byte outside the alphabet
+// state to table2[row * 16 + c1 * 4 + c2] (flags: bit 1 after c1, bit 0
+// after c2). A byte outside the alphabet
 // resets the walk: as b1 it selects row 0 (after a reset byte: the entry of
 // (c1, c2) is the root's transition on c2, whatever c1), as b2 it sends the
 // state to the root after the pair and drops the pair's second flag.
@@ -1044,9 +1045,9 @@ void host_walk_ac2(const AcTables &t, const uint8_t *T, int64_t n,
         const uint32_t row = bad(b1) ? 0u : (E & ~15u);
         const uint32_t idx2 = row | (c1 << 2) | c2;
         E = t.table2[idx2];
-        if (last || bad(b2)) E = (E & 1u) | 16u;
-        if (E & 1u) report(i, idx2 >> 2);
-        if (E & 2u) {
+        if (last || bad(b2)) E = (E & 2u) | 16u;   // keep the first character's flag
+        if (E & 2u) report(i, idx2 >> 2);
+        if (E & 1u) {
             const uint32_t e1 = t.table[idx2 >> 2];
             report(i + 1, ((e1 >> 1) << 2) | c2);
         }

@@ -55,7 +55,7 @@ struct AcTables {
     std::vector<uint32_t> flag_rank;
     std::vector<uint32_t> canon;
     // Two characters per lookup (ACGT sets of at most 4096 rows, m <= 33):
-    // row r, classes (c1, c2) -> (r2 << 4) | (m2 << 1) | m1, where r1 and m1
+    // row r, classes (c1, c2) -> (r2 << 4) | (m1 << 1) | m2, where r1 and m1
     // are the state and flag after c1 and r2, m2 those after c2 (the
     // one-character table applied twice). Empty when not eligible.
     std::vector<uint16_t> table2;

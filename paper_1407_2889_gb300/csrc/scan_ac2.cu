@@ -3,8 +3,8 @@
 // 3) on sm_103a, for ACGT-like sets of at most 4096 rows and m <= 33.
 //
 // A row has 16 entries, one per pair of character classes, holding the
-// state after both characters and a match flag for each: the one-character
-// table applied twice (the same rows, terminal rows elided). A lane walks
+// state after both characters and a match flag for each, (r2 << 4) |
+// (m1 << 1) | m2: the one-character table applied twice (the same rows, terminal rows elided). A lane walks
 // its chunk + halo a pair at a time. A byte outside the alphabet resets the
 // walk inside the lookup chain: as the pair's first byte it selects row 0
 // (the one-character reset row applied first, so its entry for (c1, c2) is
@@ -50,6 +50,11 @@ struct Ac2Args {
     unsigned long long *seg_sum;
     long long seg_tiles;
     uint32_t *slots;              // (start offset in the tile << 16) | code
+    // Multipliers of the walk's shifts and adds, passed as arguments so the
+    // compiler issues them as integer multiply-adds (the fused multiply-add
+    // pipe, idle in this walk) instead of folding them into shifts on the
+    // integer logic pipe, which the byte decoding keeps busy.
+    uint32_t k_sh1, k_sh2, k_sh4, k_sh8, k_sh16, k_x2, k_x4, k_x65536, k_one;
 };
 
 __host__ __device__ constexpr long long r16a(long long x) { return (x + 15) & ~15LL; }
@@ -210,37 +215,53 @@ __global__ void __launch_bounds__(kAc2MaxWarps * 32, 1) ac2_scan_kernel(const Ac
         for (int j = 0; j < HW; ++j) hw[j] = 0u;
         uint32_t e2 = 16u;  // root: row 1
         const uint32_t rec0 = dev::smem_addr(rec) + uint32_t(lane) * 16u;
+        const uint32_t t2_base = dev::smem_addr(s_t2);
+        // x >> k as the high word of x * 2^(32-k), x << k and x + c as x * 2^k
+        // + c: integer multiply-adds with multipliers the compiler cannot see
+        const uint32_t K1 = a.k_sh1, K2 = a.k_sh2, K4 = a.k_sh4, K8 = a.k_sh8, K16 = a.k_sh16;
+        const uint32_t X2 = a.k_x2, X4 = a.k_x4, X64K = a.k_x65536, ONE = a.k_one;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             uint32_t pk[4] = {0u, 0u, 0u, 0u};
+            uint32_t hv = 0u;  // this vector's match bits, two per pair, first pair highest
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint32_t w = acdev::word_of(tv[v], q);
                 const int s0 = v * 16 + q * 4;
-                if (!(s0 < kChunk || s0 < steps)) continue;
-                const uint32_t a4 = ((w >> 1) ^ (w >> 2)) & 0x03030303u;
-                const uint32_t sel = __byte_perm(a4 | (a4 >> 4), 0u, 0x4420);
-                const uint32_t x = w ^ __byte_perm(a.lut, 0u, sel);  // zero byte = in the alphabet
+                if (!(s0 < kChunk || s0 < steps)) {
+                    hv <<= 4;  // two pairs past the lane's walk
+                    continue;
+                }
+                // class of each byte: ((b >> 1) ^ (b >> 2)) & 3
+                const uint32_t a4 = (__umulhi(w, K1) ^ __umulhi(w, K2)) & 0x03030303u;
+                // selector of the alphabet's byte for each class (nibbles)
+                const uint32_t sel = __byte_perm(__umulhi(a4, K4) + a4, 0u, 0x4420);
+                const uint32_t lutb = __byte_perm(a.lut, 0u, sel);
                 // bit 7 of each byte of y: the byte is outside the alphabet
-                const uint32_t y = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;
-                const uint32_t u = (a4 << 2) | (a4 >> 8);            // pair codes in bytes 0 and 2
+                const uint32_t t7 = (w ^ lutb) & 0x7F7F7F7Fu;
+                const uint32_t y = (t7 * ONE + 0x7F7F7F7Fu) | (w ^ lutb);
+                // pair codes (c1 << 2) | c2 in bytes 0 and 2
+                const uint32_t u = __umulhi(a4, K8) + a4 * X4;
                 // per pair (16-bit halves): t2 = 0xFFF0 | code, or the code
                 // alone (row 0) when the first byte is outside; mx = 0xFFFF,
-                // or 0x0001 when the second byte is outside
-                const uint32_t inv1 = prmt_sign(y, 0xAA88u);
-                const uint32_t t2w = (~inv1 & 0xFFF0FFF0u) | (u & 0x000F000Fu);
-                const uint32_t mxw = ~prmt_sign(y, 0xBB99u) | 0x00010001u;
+                // or 0x0002 (keep the first character's flag) when the second
+                // byte is outside
+                const uint32_t t2w = (~prmt_sign(y, 0xAA88u) & 0xFFF0FFF0u) | (u & 0x000F000Fu);
+                const uint32_t mxw = ~prmt_sign(y, 0xBB99u) | 0x00020002u;
 #pragma unroll
                 for (int pp = 0; pp < 2; ++pp) {
                     const int j0 = s0 + 2 * pp;  // first character's step
                     if (j0 < kChunk || j0 < steps) {
-                        const uint32_t t2 = pp ? (t2w >> 16) : t2w;
-                        const uint32_t mx = pp ? (mxw >> 16) : mxw;
+                        const uint32_t t2 = pp ? __umulhi(t2w, K16) : t2w;
+                        const uint32_t mx = pp ? __umulhi(mxw, K16) : mxw;
                         const uint32_t idx2 = (e2 & t2 & ~15u) | (t2 & 15u);
-                        e2 = s_t2[idx2];
-                        e2 = (e2 & mx) | (16u & ~mx);
-                        hw[j0 >> 5] |= (e2 & 3u) << (j0 & 31);
-                        pk[q] = pp ? (pk[q] | (idx2 << 16)) : idx2;
+                        uint16_t ev;
+                        asm("ld.shared.u16 %0, [%1];" : "=h"(ev) : "r"(idx2 * X2 + t2_base));
+                        e2 = (uint32_t(ev) & mx) | (16u & ~mx);
+                        hv = hv * X4 + (e2 & 3u);
+                        pk[q] = pp ? idx2 * X64K + pk[q] : idx2;
+                    } else {
+                        hv = hv * X4;
                     }
                 }
             }
@@ -248,6 +269,10 @@ __global__ void __launch_bounds__(kAc2MaxWarps * 32, 1) ac2_scan_kernel(const Ac
                 asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(rec0 + uint32_t(v) * 512u),
                              "r"(pk[0]), "r"(pk[1]), "r"(pk[2]), "r"(pk[3])
                              : "memory");
+            // an entry's flags are (first character << 1) | second, so pair k
+            // of the vector sits at bits 15 - 2k (first) and 14 - 2k: the
+            // reversed word, shifted down, has step 16 v + i at bit i
+            hw[v >> 1] |= (__brev(hv) >> 16) << (16 * (v & 1));
         }
         // a match at a step past the lane's last (the second byte of a last
         // pair that straddles it) is not this lane's
@@ -424,6 +449,15 @@ int ac2_launch(const AcTables &t, const DevAc &dv, const DevAc2 &d2, const uint8
     a.seg_sum = L.seg_sum;
     a.seg_tiles = L.seg_tiles;
     a.slots = static_cast<uint32_t *>(L.slots);
+    a.k_sh1 = 1u << 31;
+    a.k_sh2 = 1u << 30;
+    a.k_sh4 = 1u << 28;
+    a.k_sh8 = 1u << 24;
+    a.k_sh16 = 1u << 16;
+    a.k_x2 = 2u;
+    a.k_x4 = 4u;
+    a.k_x65536 = 65536u;
+    a.k_one = 1u;
 
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, d2.warps * 32, size_t(d2.smem_bytes));
