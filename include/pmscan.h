@@ -346,7 +346,11 @@ int pm_batch_prepare(const pm_set *const *sets, int32_t k, const int64_t *text_o
                      pm_batch **out);
 void pm_batch_free(pm_batch *b);
 int64_t pm_batch_counts_total(const pm_batch *b);
-/* Workspace for every call below (any warp count the tuner may pick). */
+/* Workspace for every call below (any warp count the tuner may pick): a
+ * header, the device counters of instances whose counters do not fit a
+ * CTA's shared memory, and, in list mode, key staging for the parts of
+ * instances split across CTAs (one 8-byte key per 32 text bytes of a part,
+ * at most the instance's capacity). */
 int64_t pm_batch_workspace_bytes(const pm_batch *b);
 int32_t pm_batch_warps(const pm_batch *b);  /* warps per CTA of the current plan */
 

@@ -810,7 +810,13 @@ int scan_batch_host(const pm_set *const *sets, const uint8_t *const *texts, cons
         b = nullptr;
         rc = pm_batch_prepare(bs.data(), kb, off.data(), len.data(), occ_off.data(), 0u, &b);
         if (rc) { cleanup(); return rc; }
-        if (pm_batch_workspace_bytes(b) > ws_bytes) { cleanup(); return PM_ECUDA; }
+        if (pm_batch_workspace_bytes(b) > ws_bytes) {  // key staging of split instances
+            cudaFree(d_ws);
+            d_ws = nullptr;
+            ws_bytes = pm_batch_workspace_bytes(b);
+            e = cudaMalloc(&d_ws, size_t(ws_bytes));
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
         e = cudaMalloc(&d_occ, size_t(std::max<int64_t>(occ_off[size_t(kb)], 1)) * 8);
         if (e != cudaSuccess) return cuda_fail(e);
         rc = pm_batch_scan_device(b, static_cast<const uint8_t *>(d_text), static_cast<int64_t *>(d_counts),

@@ -360,6 +360,19 @@ struct BatchDesc {                 // one instance, in processing order
     int smem_entries, eb, m, nwords, nterms, d;
     int ids_off, hist_off;         // byte offsets in the CTA's table region; -1 = global
     uint32_t mid_base, lut, pad, pre;  // pre: DevAc::pre of the set
+    // A large instance is split into parts, one queue item each: the part
+    // scans warp tiles [t_lo, t_hi) of the instance. Parts add their counts
+    // into the instance's device counters (ccount_off), publish their output
+    // totals at workspace word pstat_off + part, and the last part to finish
+    // (word done_off counts them) writes the instance's counts and total.
+    // In list mode a part writes its keys, while it walks, to staging words
+    // [spill_off, spill_off + spill_cap) after the counters, and copies them
+    // into place once the parts before it have published their totals; a
+    // part whose keys do not fit walks its tiles again to write them.
+    long long t_lo, t_hi;
+    long long pstat_off, done_off;
+    long long spill_off, spill_cap;
+    int part, nparts;
 };
 
 struct BatchShape {                // launch shape and shared-memory split
@@ -376,9 +389,18 @@ struct BatchInst {
 
 int batch_shape(int warps, BatchShape &out);
 bool batch_supports(const pm_set *s);   // AC, ACGT-like alphabet, m <= 65, device tables
-// Descriptors of k instances in the order given (out may be NULL); returns
-// the number of global counter words the workspace needs.
+// Descriptors of k instances in the order given, one per instance (out may
+// be NULL); returns the number of global counter words the workspace needs.
 int64_t batch_fill(const BatchInst *inst, int k, const BatchShape &sh, BatchDesc *out);
+// Queue items of k instances: the instances ordered by estimated cost (text
+// bytes, weighted up for tables read through L2), costliest first, and each
+// instance costing more than about a quarter of a CTA's share of the batch
+// split into parts of whole warp tiles (at least two rounds of the CTA's
+// warps each). Returns the global counter words the workspace needs; in list
+// mode *spill_words receives the key staging words of the parts, which
+// follow the counters and need no clearing.
+int64_t batch_items(const BatchInst *inst, int k, const BatchShape &sh, bool list, std::vector<BatchDesc> &out,
+                    int64_t *spill_words);
 inline int64_t batch_ws_bytes(int64_t ccount_words) { return kWsHeader + 8 * ccount_words; }
 int batch_prepare_launch(const BatchShape &sh);  // host-side set-up, before any capture
 int batch_launch_raw(const BatchDesc *d_desc, int k, const uint8_t *text, int64_t *counts,

@@ -15,6 +15,7 @@
 // (ac_device.cuh); the launch is a plain kernel plus memsets, so it can be
 // captured in a CUDA graph and replayed.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -47,6 +48,7 @@ struct BatchArgs {
     long long *n_occ;
     dev::WsHeader *ws;
     unsigned long long *ccount;
+    unsigned long long *spill;     // key staging of split instances' parts
     int list;
     int region_bytes;              // per-CTA shared memory for table, ids and counters
 };
@@ -131,7 +133,7 @@ __device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSm
     E *pl = reinterpret_cast<E *>(S.pool) + lane;
     const uint32_t cap = kBatchPool;
     const int m = D.m;
-    const long long nsub = (n + kWarpTile - 1) / kWarpTile;
+    const bool split = D.nparts > 1;
     auto count_terminal = [&](uint32_t c) {
         if (s_hist) atomicAdd(&s_hist[c], 1u);
         else atomicAdd(&g_hist[c], 1ull);
@@ -141,192 +143,276 @@ __device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSm
         const uint32_t g = code & ~kGrp;
         return __ldg(D.grp_off + g + 1) - __ldg(D.grp_off + g);
     };
+    // where `write` puts the keys: the instance's output, or a part's staging
+    unsigned long long *odst = a.occ + D.occ_off;
+    unsigned long long ocap = (unsigned long long)D.occ_cap;
 
-    long long t = warp;
-    bool inflight = false;
-    if (t < nsub) {
-        if (lane == 0) bstage_issue(text, n, t, S.buf, S.bar);
-        inflight = true;
-    }
-    unsigned long long running = 0;
-    const unsigned long long obase = (unsigned long long)D.occ_off;
-    const unsigned long long ocap = (unsigned long long)D.occ_cap;
-    const long long rounds = (nsub + W - 1) / W;
-    for (long long rd = 0; rd < rounds; ++rd, t += W) {
-        const bool active = t < nsub && !failed;
-        uint32_t nh = 0, cnt = 0;
-        bool ovf = false;
-        uint32_t hw[HW];
+    // One pass over the item's warp tiles [t_lo, t_hi): warps take tiles in
+    // rounds of W; `count` bumps the per-terminal counters, `write` writes
+    // the keys from output offset base0 on. Returns the item's outputs.
+    auto pass = [&](bool count, bool write, unsigned long long base0) -> unsigned long long {
+        long long t = D.t_lo + warp;
+        bool inflight = false;
+        if (t < D.t_hi) {
+            if (lane == 0) bstage_issue(text, n, t, S.buf, S.bar);
+            inflight = true;
+        }
+        unsigned long long running = base0;
+        const long long rounds = (D.t_hi - D.t_lo + W - 1) / W;
+        for (long long rd = 0; rd < rounds; ++rd, t += W) {
+            const bool active = t < D.t_hi && !failed;
+            uint32_t nh = 0, cnt = 0;
+            bool ovf = false;
+            uint32_t hw[HW];
 #pragma unroll
-        for (int j = 0; j < HW; ++j) hw[j] = 0u;
-        long long g0 = 0;
-        if (active) {
-            const bool got = __all_sync(kFull, dev::mbar_wait_bounded(S.bar, phase));
-            if (!got) {
-                if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutTma);
-                failed = true;  // the copy stays in flight: waited for below
-            } else {
-                inflight = false;
-                phase ^= 1u;
-                const long long tile0 = t * kWarpTile;
-                const int got_bytes = bstage_bytes(text, n, t);
-                if (got_bytes < kBatchBuf) {
-                    for (int b = got_bytes + lane; b < kBatchBuf; b += 32) {
-                        const long long g = tile0 + b;
-                        S.buf[b] = g < n ? text[g] : uint8_t(D.pad);
-                    }
-                    __syncwarp();
-                }
-                uint4 tv[NV];
-                {
-                    const uint4 *bv = reinterpret_cast<const uint4 *>(S.buf + lane * kChunk);
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) tv[v] = bv[v];
-                }
-                dev::fence_proxy_async_smem();
-                __syncwarp();
-                if (t + W < nsub) {
-                    if (lane == 0) bstage_issue(text, n, t + W, S.buf, S.bar);
-                    inflight = true;
-                }
-                g0 = tile0 + (long long)lane * kChunk;
-                const int steps = kChunk + m - 1;
-                uint32_t kslot = 0;
-                auto rec = [&](int step, uint32_t idx, uint32_t e) {
-                    const uint32_t h = e & 1u;
-                    pl[kslot * 32] = E(idx - D.mid_base);
-                    kslot = min(kslot + h, cap);
-                    hw[step >> 5] |= h << (step & 31);
-                };
-                walk_dna<NV, PRE>(tv, steps, D.lut, tab, rec);
-#pragma unroll
-                for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
-                ovf = nh > cap;
-                if (!ovf) {
-                    for (uint32_t k = 0; k < nh; ++k) {
-                        const uint32_t c = ids.terminal(pl[k * 32]);
-                        const uint32_t code = ids.code(c);
-                        count_terminal(c);
-                        cnt += mult_of(code);
-                        pl[k * 32] = E(code);
-                    }
+            for (int j = 0; j < HW; ++j) hw[j] = 0u;
+            long long g0 = 0;
+            if (active) {
+                const bool got = __all_sync(kFull, dev::mbar_wait_bounded(S.bar, phase));
+                if (!got) {
+                    if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutTma);
+                    failed = true;  // the copy stays in flight: waited for below
                 } else {
-                    walk_slow<PRE>(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
-                              [&](int, uint32_t idx) {
-                                  const uint32_t c = ids.terminal(idx - D.mid_base);
-                                  count_terminal(c);
-                                  cnt += mult_of(ids.code(c));
-                              });
+                    inflight = false;
+                    phase ^= 1u;
+                    const long long tile0 = t * kWarpTile;
+                    const int got_bytes = bstage_bytes(text, n, t);
+                    if (got_bytes < kBatchBuf) {
+                        for (int b = got_bytes + lane; b < kBatchBuf; b += 32) {
+                            const long long g = tile0 + b;
+                            S.buf[b] = g < n ? text[g] : uint8_t(D.pad);
+                        }
+                        __syncwarp();
+                    }
+                    uint4 tv[NV];
+                    {
+                        const uint4 *bv = reinterpret_cast<const uint4 *>(S.buf + lane * kChunk);
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) tv[v] = bv[v];
+                    }
+                    dev::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (t + W < D.t_hi) {
+                        if (lane == 0) bstage_issue(text, n, t + W, S.buf, S.bar);
+                        inflight = true;
+                    }
+                    g0 = tile0 + (long long)lane * kChunk;
+                    const int steps = kChunk + m - 1;
+                    uint32_t kslot = 0;
+                    auto rec = [&](int step, uint32_t idx, uint32_t e) {
+                        const uint32_t h = e & 1u;
+                        pl[kslot * 32] = E(idx - D.mid_base);
+                        kslot = min(kslot + h, cap);
+                        hw[step >> 5] |= h << (step & 31);
+                    };
+                    walk_dna<NV, PRE>(tv, steps, D.lut, tab, rec);
+#pragma unroll
+                    for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
+                    ovf = nh > cap;
+                    if (!ovf) {
+                        for (uint32_t k = 0; k < nh; ++k) {
+                            const uint32_t c = ids.terminal(pl[k * 32]);
+                            const uint32_t code = ids.code(c);
+                            if (count) count_terminal(c);
+                            cnt += mult_of(code);
+                            pl[k * 32] = E(code);
+                        }
+                    } else {
+                        walk_slow<PRE>(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
+                                       [&](int, uint32_t idx) {
+                                           const uint32_t c = ids.terminal(idx - D.mid_base);
+                                           if (count) count_terminal(c);
+                                           cnt += mult_of(ids.code(c));
+                                       });
+                    }
                 }
             }
-        }
-        // ---- offsets of this round: prefix over the warps' totals ----------
-        const uint32_t incl = dev::warp_incl_scan(cnt, lane);
-        const uint32_t wtot = __shfl_sync(kFull, incl, 31);
-        if (lane == 0) S.s_tot[warp] = wtot;
-        __syncthreads();
-        unsigned long long before = 0, all = 0;
-        for (int w = 0; w < W; ++w) {
-            const unsigned long long v = S.s_tot[w];
-            if (w < warp) before += v;
-            all += v;
-        }
-        const unsigned long long base = running + before;
-        running += all;
-        if (a.list && active && !failed && wtot > 0) {
-            const uint32_t excl = incl - cnt;
-            auto put = [&](unsigned long long oi, long long pos, uint32_t r) {
-                if (oi < ocap) a.occ[obase + oi] = ((unsigned long long)pos << 32) | r;
-            };
-            if (!__any_sync(kFull, ovf)) {
-                StepBits<HW> it;
-#pragma unroll
-                for (int j = 0; j < HW; ++j) it.w[j] = hw[j];
-                it.base = 0;
-                uint32_t k = 0, my = excl;
-                bool have = false, single = true;
-                uint32_t rs = 0, glo = 0, ghi = 0;
-                long long pos = 0;
-                for (uint32_t w0 = 0; w0 < wtot; w0 += kBatchStage) {
-                    const uint32_t wend = min(w0 + (uint32_t)kBatchStage, wtot);
-                    const uint32_t lim = min(wend, incl);
-                    while (my < lim) {
-                        if (!have) {
-                            const int st = it.next();
-                            if (st < 0) dev::set_status(a.ws, dev::kErrInternal);
-                            pos = g0 + st - (m - 1);
-                            const uint32_t code = pl[k * 32];
-                            ++k;
-                            single = !(code & kGrp);
-                            if (single) {
-                                rs = code;
-                            } else {
-                                const uint32_t g = code & ~kGrp;
-                                glo = __ldg(D.grp_off + g);
-                                ghi = __ldg(D.grp_off + g + 1);
-                            }
-                            have = true;
-                        }
-                        const uint32_t r = single ? rs : __ldg(D.grp_ids + glo);
-                        S.stage[my - w0] = ((unsigned long long)pos << 32) | r;
-                        ++my;
-                        if (single || ++glo >= ghi) have = false;
-                    }
-                    __syncwarp();
-                    for (uint32_t q = w0 + lane; q < wend; q += 32) {
-                        const unsigned long long oi = base + q;
-                        if (oi < ocap) a.occ[obase + oi] = S.stage[q - w0];
-                    }
-                    __syncwarp();
-                }
-            } else {
-                unsigned long long oi = base + excl;
-                auto put_code = [&](long long pos, uint32_t code) {
-                    if (code & kGrp) {
-                        const uint32_t g = code & ~kGrp;
-                        const uint32_t hi = __ldg(D.grp_off + g + 1);
-                        for (uint32_t j = __ldg(D.grp_off + g); j < hi; ++j) put(oi++, pos, __ldg(D.grp_ids + j));
-                    } else {
-                        put(oi++, pos, code);
-                    }
+            // ---- offsets of this round: prefix over the warps' totals ----------
+            const uint32_t incl = dev::warp_incl_scan(cnt, lane);
+            const uint32_t wtot = __shfl_sync(kFull, incl, 31);
+            if (lane == 0) S.s_tot[warp] = wtot;
+            __syncthreads();
+            unsigned long long before = 0, all = 0;
+            for (int w = 0; w < W; ++w) {
+                const unsigned long long v = S.s_tot[w];
+                if (w < warp) before += v;
+                all += v;
+            }
+            const unsigned long long base = running + before;
+            running += all;
+            if (write && active && !failed && wtot > 0) {
+                const uint32_t excl = incl - cnt;
+                auto put = [&](unsigned long long oi, long long pos, uint32_t r) {
+                    if (oi < ocap) odst[oi] = ((unsigned long long)pos << 32) | r;
                 };
-                if (!ovf) {
+                if (!__any_sync(kFull, ovf)) {
                     StepBits<HW> it;
 #pragma unroll
                     for (int j = 0; j < HW; ++j) it.w[j] = hw[j];
                     it.base = 0;
-                    for (uint32_t k = 0; k < nh; ++k) {
-                        const int st = it.next();
-                        if (st < 0) dev::set_status(a.ws, dev::kErrInternal);
-                        put_code(g0 + st - (m - 1), pl[k * 32]);
+                    uint32_t k = 0, my = excl;
+                    bool have = false, single = true;
+                    uint32_t rs = 0, glo = 0, ghi = 0;
+                    long long pos = 0;
+                    for (uint32_t w0 = 0; w0 < wtot; w0 += kBatchStage) {
+                        const uint32_t wend = min(w0 + (uint32_t)kBatchStage, wtot);
+                        const uint32_t lim = min(wend, incl);
+                        while (my < lim) {
+                            if (!have) {
+                                const int st = it.next();
+                                if (st < 0) dev::set_status(a.ws, dev::kErrInternal);
+                                pos = g0 + st - (m - 1);
+                                const uint32_t code = pl[k * 32];
+                                ++k;
+                                single = !(code & kGrp);
+                                if (single) {
+                                    rs = code;
+                                } else {
+                                    const uint32_t g = code & ~kGrp;
+                                    glo = __ldg(D.grp_off + g);
+                                    ghi = __ldg(D.grp_off + g + 1);
+                                }
+                                have = true;
+                            }
+                            const uint32_t r = single ? rs : __ldg(D.grp_ids + glo);
+                            S.stage[my - w0] = ((unsigned long long)pos << 32) | r;
+                            ++my;
+                            if (single || ++glo >= ghi) have = false;
+                        }
+                        __syncwarp();
+                        for (uint32_t q = w0 + lane; q < wend; q += 32) {
+                            const unsigned long long oi = base + q;
+                            if (oi < ocap) odst[oi] = S.stage[q - w0];
+                        }
+                        __syncwarp();
                     }
                 } else {
-                    walk_slow<PRE>(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
-                              [&](int step, uint32_t idx) {
-                                  put_code(g0 + step - (m - 1), ids.code(ids.terminal(idx - D.mid_base)));
-                              });
+                    unsigned long long oi = base + excl;
+                    auto put_code = [&](long long pos, uint32_t code) {
+                        if (code & kGrp) {
+                            const uint32_t g = code & ~kGrp;
+                            const uint32_t hi = __ldg(D.grp_off + g + 1);
+                            for (uint32_t j = __ldg(D.grp_off + g); j < hi; ++j) put(oi++, pos, __ldg(D.grp_ids + j));
+                        } else {
+                            put(oi++, pos, code);
+                        }
+                    };
+                    if (!ovf) {
+                        StepBits<HW> it;
+#pragma unroll
+                        for (int j = 0; j < HW; ++j) it.w[j] = hw[j];
+                        it.base = 0;
+                        for (uint32_t k = 0; k < nh; ++k) {
+                            const int st = it.next();
+                            if (st < 0) dev::set_status(a.ws, dev::kErrInternal);
+                            put_code(g0 + st - (m - 1), pl[k * 32]);
+                        }
+                    } else {
+                        walk_slow<PRE>(text, n, g0, kChunk + m - 1, true, D.lut, 2, nullptr, tab,
+                                       [&](int step, uint32_t idx) {
+                                           put_code(g0 + step - (m - 1), ids.code(ids.terminal(idx - D.mid_base)));
+                                       });
+                    }
                 }
             }
+            __syncthreads();  // s_tot is rewritten next round
         }
-        __syncthreads();  // s_tot is rewritten next round
-    }
-    if (inflight) {  // only after a failure: let the last copy land before reuse
-        (void)dev::mbar_wait_bounded(S.bar, phase);
-        phase ^= 1u;
-    }
+        if (inflight) {  // only after a failure: let the last copy land before reuse
+            (void)dev::mbar_wait_bounded(S.bar, phase);
+            phase ^= 1u;
+        }
+        return running - base0;
+    };
 
-    // ---- results of the instance -----------------------------------------
-    if (threadIdx.x == 0) a.n_occ[D.out_slot] = (long long)running;
     long long *cnt_out = a.counts + D.count_off;
     const E *cg = reinterpret_cast<const E *>(D.canon);
-    for (int c = threadIdx.x; c < D.nterms; c += blockDim.x) {
-        const unsigned long long v = s_hist ? (unsigned long long)s_hist[c] : g_hist[c];
-        const uint32_t code = cg[c];
-        if (code & kGrp) {
-            const uint32_t g = code & ~kGrp;
-            for (uint32_t j = D.grp_off[g]; j < D.grp_off[g + 1]; ++j) cnt_out[D.grp_ids[j]] = (long long)v;
-        } else {
-            cnt_out[code] = (long long)v;
+    // counts[r] of the instance from per-terminal counters (shared or device)
+    auto write_counts = [&](bool from_device) {
+        for (int c = threadIdx.x; c < D.nterms; c += blockDim.x) {
+            const unsigned long long v = from_device ? dev::ld_acquire(&g_hist[c]) : (unsigned long long)s_hist[c];
+            const uint32_t code = cg[c];
+            if (code & kGrp) {
+                const uint32_t g = code & ~kGrp;
+                for (uint32_t j = D.grp_off[g]; j < D.grp_off[g + 1]; ++j) cnt_out[D.grp_ids[j]] = (long long)v;
+            } else {
+                cnt_out[code] = (long long)v;
+            }
+        }
+    };
+
+    if (!split) {
+        const unsigned long long total = pass(true, a.list != 0, 0ull);
+        if (threadIdx.x == 0) a.n_occ[D.out_slot] = (long long)total;
+        write_counts(s_hist == nullptr);
+        __syncthreads();
+        return;
+    }
+
+    // ---- a part of a split instance ----------------------------------------
+    __shared__ unsigned long long s_base;
+    __shared__ int s_last;
+    unsigned long long *pstat = a.ccount + D.pstat_off;  // (1 << 63) | part total
+    const bool staged = a.list && D.spill_cap > 0;
+    if (staged) {
+        odst = a.spill + D.spill_off;
+        ocap = (unsigned long long)D.spill_cap;
+    }
+    const unsigned long long total = pass(true, staged, 0ull);
+    if (threadIdx.x == 0) {
+        dev::st_relaxed(&pstat[D.part], (1ull << 63) | total);
+        unsigned long long base = 0;
+        if (a.list) {
+            // the parts before this one were taken earlier by running CTAs,
+            // and publish their totals without waiting for anything
+            const long long t0c = clock64();
+            for (int q = 0; q < D.part; ++q) {
+                unsigned long long v = dev::ld_relaxed(&pstat[q]);
+                while (!(v >> 63)) {
+                    if (clock64() - t0c > dev::kSpinLimit) {
+                        dev::set_status(a.ws, dev::kErrTimeoutWait);
+                        break;
+                    }
+                    __nanosleep(128);
+                    v = dev::ld_relaxed(&pstat[q]);
+                }
+                base += v & ~(1ull << 63);
+            }
+        }
+        s_base = base;
+    }
+    __syncthreads();
+    if (a.list) {
+        odst = a.occ + D.occ_off;
+        ocap = (unsigned long long)D.occ_cap;
+        const unsigned long long b0 = s_base;
+        if (staged && total <= (unsigned long long)D.spill_cap) {
+            // this CTA's own stores, ordered by the barrier above
+            const unsigned long long *sp = a.spill + D.spill_off;
+            const unsigned long long nkeep = b0 < ocap ? min(total, ocap - b0) : 0ull;
+            for (unsigned long long i = threadIdx.x; i < nkeep; i += blockDim.x) odst[b0 + i] = sp[i];
+        } else if (b0 < ocap) {
+            (void)pass(false, true, b0);
+        }
+    }
+    // counters into the instance's device counters; the last part writes
+    // the instance's counts and its total
+    if (s_hist)
+        for (int c = threadIdx.x; c < D.nterms; c += blockDim.x)
+            if (s_hist[c]) atomicAdd(&g_hist[c], (unsigned long long)s_hist[c]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int *done = reinterpret_cast<unsigned int *>(a.ccount + D.done_off);
+        s_last = atomicAdd(done, 1u) == unsigned(D.nparts - 1);
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        write_counts(true);
+        if (threadIdx.x == 0) {
+            unsigned long long all = 0;
+            for (int q = 0; q < D.nparts; ++q) all += dev::ld_acquire(&pstat[q]) & ~(1ull << 63);
+            a.n_occ[D.out_slot] = (long long)all;
         }
     }
     __syncthreads();
@@ -382,6 +468,7 @@ __global__ void __launch_bounds__(512, 1) ac_batch_kernel(const BatchArgs a)
 // host side
 // ---------------------------------------------------------------------------
 constexpr int kBatchWarpChoices[] = {8, 12, 16};   // autotuner candidates
+constexpr long long kSpillBytes = 32;               // text bytes per staged key of a part
 constexpr int kBatchMaxWarps = 16;
 
 struct InstLayout {
@@ -440,6 +527,45 @@ bool batch_supports(const pm_set *s)
     return s && !s->host_only && s->algo == PM_ALGO_AC && s->ac.dna && s->ac.m <= kBatchMaxM;
 }
 
+// The descriptor of one instance (or of its part p of P, tiles [t_lo, t_hi)).
+static void fill_desc(const BatchInst &I, const InstLayout &L, long long coff, BatchDesc &D)
+{
+    const AcTables &t = I.set->ac;
+    const DevAc &dv = I.set->dac;
+    std::memset(&D, 0, sizeof(D));
+    D.text_off = I.text_off;
+    D.n = I.text_len;
+    D.count_off = I.count_off;
+    D.occ_off = I.occ_off;
+    D.occ_cap = I.occ_cap;
+    D.ccount_off = coff;
+    D.out_slot = I.out_slot;
+    D.table = dv.table;
+    D.mask = dv.flag_mask;
+    D.rank = dv.flag_rank;
+    D.canon = dv.canon;
+    D.grp_off = dv.grp_off;
+    D.grp_ids = dv.grp_ids;
+    D.eb = t.entry_bytes;
+    D.smem_entries = L.smem_entries;
+    D.ids_off = L.ids_off;
+    D.hist_off = L.hist_off;
+    D.m = t.m;
+    D.nwords = int(t.flag_mask.size());
+    D.nterms = int(t.canon.size());
+    D.d = int(t.d);
+    D.mid_base = uint32_t(t.d0_row << t.lw);
+    D.lut = t.lut;
+    D.pre = uint32_t(dv.pre);
+    D.pad = 0;
+    for (uint32_t x = 0; x < 256; ++x)  // a byte outside the alphabet
+        if (t.cls[x] == 0xFF) { D.pad = x; break; }
+    D.t_lo = 0;
+    D.t_hi = (I.text_len + kWarpTile - 1) / kWarpTile;
+    D.part = 0;
+    D.nparts = 1;
+}
+
 int64_t batch_fill(const BatchInst *inst, int k, const BatchShape &sh, BatchDesc *out)
 {
     int64_t ccount = 0;
@@ -450,38 +576,76 @@ int64_t batch_fill(const BatchInst *inst, int k, const BatchShape &sh, BatchDesc
         const int64_t nt = int64_t(t.canon.size());
         const int64_t coff = ccount;
         if (L.hist_off < 0) ccount += nt;
-        if (!out) continue;
-        const DevAc &dv = I.set->dac;
-        BatchDesc &D = out[q];
-        std::memset(&D, 0, sizeof(D));
-        D.text_off = I.text_off;
-        D.n = I.text_len;
-        D.count_off = I.count_off;
-        D.occ_off = I.occ_off;
-        D.occ_cap = I.occ_cap;
-        D.ccount_off = coff;
-        D.out_slot = I.out_slot;
-        D.table = dv.table;
-        D.mask = dv.flag_mask;
-        D.rank = dv.flag_rank;
-        D.canon = dv.canon;
-        D.grp_off = dv.grp_off;
-        D.grp_ids = dv.grp_ids;
-        D.eb = t.entry_bytes;
-        D.smem_entries = L.smem_entries;
-        D.ids_off = L.ids_off;
-        D.hist_off = L.hist_off;
-        D.m = t.m;
-        D.nwords = int(t.flag_mask.size());
-        D.nterms = int(nt);
-        D.d = int(t.d);
-        D.mid_base = uint32_t(t.d0_row << t.lw);
-        D.lut = t.lut;
-        D.pre = uint32_t(dv.pre);
-        D.pad = 0;
-        for (uint32_t x = 0; x < 256; ++x)  // a byte outside the alphabet
-            if (t.cls[x] == 0xFF) { D.pad = x; break; }
+        if (out) fill_desc(I, L, coff, out[q]);
     }
+    return ccount;
+}
+
+int64_t batch_items(const BatchInst *inst, int k, const BatchShape &sh, bool list, std::vector<BatchDesc> &out,
+                    int64_t *spill_words)
+{
+    out.clear();
+    if (spill_words) *spill_words = 0;
+    if (k <= 0) return 0;
+    std::vector<InstLayout> lay(static_cast<size_t>(k));
+    std::vector<double> cost(static_cast<size_t>(k));
+    double total = 0.0;
+    for (int q = 0; q < k; ++q) {
+        const AcTables &t = inst[q].set->ac;
+        lay[size_t(q)] = layout_of(t, sh.region_bytes);
+        // a table read partly through L2 costs several times more per byte;
+        // every instance also pays for loading its tables
+        const long long entries = (long long)t.n_rows << t.lw;
+        const double w = lay[size_t(q)].smem_entries >= entries ? 1.0 : 4.0;
+        cost[size_t(q)] = double(inst[q].text_len) * w + 4.0 * double(lay[size_t(q)].smem_entries * t.entry_bytes);
+        total += cost[size_t(q)];
+    }
+    std::vector<int> order(static_cast<size_t>(k));
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[size_t(x)] > cost[size_t(y)]; });
+    // about four items per CTA: an instance above that share is split
+    const double share = total / (4.0 * double(std::max(sh.sm_count, 1)));
+    int64_t ccount = 0, spill = 0;
+    for (const int q : order) {
+        const BatchInst &I = inst[q];
+        const InstLayout &L = lay[size_t(q)];
+        const int64_t nt = int64_t(I.set->ac.canon.size());
+        const long long ntiles = (I.text_len + kWarpTile - 1) / kWarpTile;
+        long long parts = 1;
+        if (cost[size_t(q)] > share && share > 0.0) {
+            parts = (long long)std::ceil(cost[size_t(q)] / share);
+            parts = std::min(parts, ntiles / (2LL * sh.warps));  // at least two rounds of tiles each
+            parts = std::max(parts, 1LL);
+        }
+        int64_t coff = ccount;
+        if (L.hist_off < 0 || parts > 1) ccount += nt;  // parts add into device counters
+        int64_t pstat = 0, done = 0;
+        if (parts > 1) {
+            pstat = ccount;
+            ccount += parts;
+            done = ccount;
+            ccount += 1;
+        }
+        for (long long p = 0; p < parts; ++p) {
+            BatchDesc D;
+            fill_desc(I, L, coff, D);
+            D.t_lo = ntiles * p / parts;
+            D.t_hi = ntiles * (p + 1) / parts;
+            D.part = int(p);
+            D.nparts = int(parts);
+            D.pstat_off = pstat;
+            D.done_off = done;
+            if (parts > 1 && list) {
+                // one key per kSpillBytes text bytes, at most the instance's capacity
+                const long long bytes = std::min(D.t_hi * kWarpTile, (long long)I.text_len) - D.t_lo * kWarpTile;
+                D.spill_off = spill;
+                D.spill_cap = std::min<long long>((bytes + kSpillBytes - 1) / kSpillBytes, I.occ_cap);
+                spill += D.spill_cap;
+            }
+            out.push_back(D);
+        }
+    }
+    if (spill_words) *spill_words = spill;
     return ccount;
 }
 
@@ -523,6 +687,7 @@ int batch_launch_raw(const BatchDesc *d_desc, int k, const uint8_t *text, int64_
     a.n_occ = reinterpret_cast<long long *>(n_occ);
     a.ws = reinterpret_cast<dev::WsHeader *>(ws);
     a.ccount = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + kWsHeader);
+    a.spill = a.ccount + ccount_total;
     a.list = list ? 1 : 0;
     a.region_bytes = sh.region_bytes;
     const int grid = std::min(sh.sm_count, k);
@@ -538,7 +703,9 @@ int batch_launch_raw(const BatchDesc *d_desc, int k, const uint8_t *text, int64_
 struct pm_batch {
     int32_t k = 0;
     std::vector<int64_t> occ_off, count_off;
-    std::vector<pm::BatchInst> inst;  // processing order (largest text first)
+    std::vector<pm::BatchInst> inst;  // as given
+    int32_t n_items = 0;              // queue items (instances, or parts of large ones)
+    int64_t desc_cap = 0;             // descriptors the device array holds
     pm::BatchDesc *d_desc = nullptr;
     int64_t ccount_total = 0;
     int64_t ws_bytes = 0;             // enough for every candidate shape
@@ -556,12 +723,18 @@ static int apply_plan(pm_batch *b, int warps)
 {
     int rc = batch_shape(warps, b->shape);
     if (rc) return rc;
-    b->ccount_total = batch_fill(b->inst.data(), b->k, b->shape, nullptr);
-    if (b->k == 0) return PM_OK;
-    std::vector<BatchDesc> h(size_t(b->k));
-    batch_fill(b->inst.data(), b->k, b->shape, h.data());
+    std::vector<BatchDesc> h;
+    b->ccount_total = batch_items(b->inst.data(), b->k, b->shape, !(b->flags & PM_COUNTS_ONLY), h, nullptr);
+    b->n_items = int32_t(h.size());
+    if (h.empty()) return PM_OK;
     cudaError_t e = cudaSuccess;
-    if (!b->d_desc) e = cudaMalloc(&b->d_desc, h.size() * sizeof(BatchDesc));
+    if (b->desc_cap < int64_t(h.size())) {
+        if (b->d_desc) cudaFree(b->d_desc);
+        b->d_desc = nullptr;
+        b->desc_cap = 0;
+        e = cudaMalloc(&b->d_desc, h.size() * sizeof(BatchDesc));
+        if (e == cudaSuccess) b->desc_cap = int64_t(h.size());
+    }
     if (e == cudaSuccess) e = cudaMemcpy(b->d_desc, h.data(), h.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         set_cuda_error(int(e));
@@ -581,7 +754,7 @@ struct BatchBufs {
 
 static int batch_enqueue(const pm_batch *b, const BatchBufs &o, cudaStream_t st)
 {
-    return batch_launch_raw(b->d_desc, b->k, o.text, o.counts, o.occ, o.n_occ, o.ws, b->ccount_total,
+    return batch_launch_raw(b->d_desc, b->n_items, o.text, o.counts, o.occ, o.n_occ, o.ws, b->ccount_total,
                             b->shape, !(b->flags & PM_COUNTS_ONLY), st);
 }
 
@@ -628,22 +801,23 @@ int pm_batch_prepare(const pm_set *const *sets, int32_t k, const int64_t *text_o
         for (int32_t j = 0; j < k; ++j)
             b->count_off[size_t(j) + 1] = b->count_off[size_t(j)] + sets[j]->ac.d;
         b->d_total = b->count_off[size_t(k)];
-        std::vector<int32_t> order(static_cast<size_t>(k));
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int32_t x, int32_t y) { return text_len[x] > text_len[y]; });
         b->inst.resize(size_t(k));
-        for (int32_t q = 0; q < k; ++q) {
-            const int32_t j = order[size_t(q)];
-            b->inst[size_t(q)] = BatchInst{sets[j], text_off[j], text_len[j], b->count_off[size_t(j)],
+        for (int32_t j = 0; j < k; ++j)
+            b->inst[size_t(j)] = BatchInst{sets[j], text_off[j], text_len[j], b->count_off[size_t(j)],
                                            occ_off[j], occ_off[j + 1] - occ_off[j], j};
+        // the workspace must hold the counters and part words of every
+        // warp count the tuner may pick
+        int rc = PM_OK;
+        b->ws_bytes = 0;
+        for (int w : kBatchWarpChoices) {
+            BatchShape sh;
+            rc = batch_shape(w, sh);
+            if (rc) { delete b; return rc; }
+            std::vector<BatchDesc> tmp;
+            int64_t spill = 0;
+            const int64_t cw = batch_items(b->inst.data(), k, sh, !(flags & PM_COUNTS_ONLY), tmp, &spill);
+            b->ws_bytes = std::max<int64_t>(b->ws_bytes, batch_ws_bytes(cw) + 8 * spill);
         }
-        // the largest warp count leaves the smallest region, hence the most
-        // counters in the workspace: size the workspace for it
-        BatchShape widest;
-        int rc = batch_shape(kBatchMaxWarps, widest);
-        if (rc) { delete b; return rc; }
-        b->ws_bytes = batch_ws_bytes(batch_fill(b->inst.data(), k, widest, nullptr));
         rc = apply_plan(b, 12);
         if (rc) { pm_batch_free(b); return rc; }
     } catch (const std::bad_alloc &) {

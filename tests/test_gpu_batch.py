@@ -221,3 +221,55 @@ def test_pm_scan_batch_host_call_against_oracle(base, d_base, flags):
             assert np.array_equal(occ, want_occ), f"instance {j}: occurrences"
     for s in sets:
         s.close()
+
+
+def test_batch_splits_large_instances(d_base, base):
+    """Large instances among many small ones are split into parts taken by
+    different CTAs (each part counts, then writes after the parts before
+    it): results per instance equal the oracle's in list mode, counts-only
+    mode and with short capacities, including an instance that is one long
+    run of a letter (every lane's pool overflows in every part)."""
+    big = 4 << 20
+    a_run = np.full(big, ord("A"), np.uint8)
+    text = np.concatenate([base, a_run])
+    d_text = torch.from_numpy(text).cuda()
+    a_off = base.size
+    Ps, off, ln = [], [], []
+    for j in range(3):  # three large EST slices
+        o = (j * 2_500_000) & ~15
+        P = synth.batch_patterns(base[:BASE_N], o, big, 300 + 200 * j, 8 + 8 * j, 970 + j)
+        Ps.append(P), off.append(o), ln.append(min(big, BASE_N - o))
+    Ps.append(np.concatenate([np.full((2, 8), ord("A"), np.uint8), synth.random_patterns(20, 8, 9)]))
+    off.append(a_off), ln.append(big)
+    for j in range(60):  # many small ones
+        o = 7_000_000 + 4096 * j
+        P = synth.batch_patterns(base[:BASE_N], o, 4096, 50, 8 + (j % 5), 990 + j)
+        Ps.append(P), off.append(o), ln.append(1000 + 37 * j)
+    sets = [pm.PatternSet.ac(P) for P in Ps]
+    want = [oracle.dictionary(text[o:o + n], P, threads=THREADS) for P, o, n in zip(Ps, off, ln)]
+    off, ln = np.array(off, np.int64), np.array(ln, np.int64)
+    b = pm.Batch.exact(sets, d_text, off, ln)
+    for w in (8, 16):
+        b.set_warps(w)
+        b.scan()
+        assert b.status() == pm.PM_OK
+        _check(b.results(), want, f"split instances, {w} warps")
+    b.capture()
+    for rep in range(2):
+        b.occ.fill_(-1)
+        b.counts.fill_(-1)
+        b.replay()
+        assert b.status() == pm.PM_OK
+        _check(b.results(), want, f"split instances, graph replay {rep}")
+    c = pm.Batch(sets, d_text, off, ln, None)
+    c.scan()
+    assert c.status() == pm.PM_OK
+    for j, ((_, cnt, tot), (wo, wc)) in enumerate(zip(c.results(), want)):
+        assert tot == wo.size and np.array_equal(cnt, wc), f"counts-only instance {j}"
+    tot = np.array([w[0].size for w in want])
+    caps = tot // 3
+    s = pm.Batch(sets, d_text, off, ln, caps)
+    s.scan()
+    assert s.status() == pm.PM_OK
+    for j, (o, cnt, t) in enumerate(s.results()):
+        assert t == tot[j] and np.array_equal(o, want[j][0][: caps[j]]), f"short capacity instance {j}"
