@@ -87,7 +87,12 @@ typedef struct pm_params {
                                  shared memory, 2 16-bit in shared memory,
                                  3 64-bit in device memory */
     int32_t ids_place;        /* AC terminal-id structure: 0 auto, 1 shared
-                                 memory, 2 device memory (through L1/L2) */
+                                 memory, 2 device memory (through L1/L2),
+                                 3 late: the rank structure in shared memory,
+                                 and in list mode terminal ids are mapped to
+                                 pattern codes and counted by the expand
+                                 kernel (frees shared memory for the table
+                                 and warps; not for PFAC sets) */
     int32_t stride;           /* AC characters per table lookup: 0 or 1 one; 2 two
                                  (a 16-entry row per state and character pair,
                                  for ACGT sets of at most 4096 rows and m <= 33;

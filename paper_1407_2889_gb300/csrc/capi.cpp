@@ -111,7 +111,7 @@ void free_dev(void *&p)
 
 void release_device(pm_set *s)
 {
-    void *ptrs[] = {s->dac.table, s->dac.flag_mask, s->dac.flag_rank, s->dac.canon,
+    void *ptrs[] = {s->dac.table, s->dac.flag_mask, s->dac.flag_rank, s->dac.canon, s->dac.tmul,
                     s->dac.grp_off, s->dac.grp_ids, s->dac.cls,
                     s->dwm.shift, s->dwm.hoff, s->dwm.hids, s->dwm.hpfx, s->dwm.pats,
                     s->dwm.shift2, s->dwm.dir, s->dwm.ccode, s->dwm.cr,
@@ -166,6 +166,19 @@ int upload_ac(pm_set *s)
             rc = upload(&d.flag_rank, t.flag_rank.data(), t.flag_rank.size() * 4, tot);
             if (!rc) rc = upload(&d.canon, t.canon.data(), t.canon.size() * 4, tot);
         }
+    }
+    if (!rc) {
+        // late ids: min(multiplicity - 1, 3) of each terminal, 2 bits
+        std::vector<uint32_t> bits((t.canon.size() + 15) / 16 + 1, 0u);
+        for (size_t c = 0; c < t.canon.size(); ++c) {
+            uint32_t v = 0;
+            if (t.canon[c] & 0x80000000u) {
+                const uint32_t g = t.canon[c] & 0x7FFFFFFFu;
+                v = std::min<uint32_t>(t.grp_off[g + 1] - t.grp_off[g] - 1u, 3u);
+            }
+            bits[c >> 4] |= v << ((c & 15) * 2);
+        }
+        rc = upload(reinterpret_cast<void **>(&d.tmul), bits.data(), bits.size() * 4, tot);
     }
     if (!rc)
         rc = upload(reinterpret_cast<void **>(&d.grp_off), t.grp_off.data(), t.grp_off.size() * 4, tot);
@@ -379,7 +392,7 @@ static bool params_ok(const pm_params *p)
     return p->placement >= 0 && p->placement <= PM_PLACE_GLOBAL && p->smem_table_bytes >= 0 &&
            p->warps_per_cta >= 0 && p->warps_per_cta <= 32 && p->ctas_per_sm >= 0 &&
            p->ctas_per_sm <= 8 && p->wm_prefix_len >= 0 && p->wm_prefix_len <= 3 &&
-           p->counters >= 0 && p->counters <= 3 && p->ids_place >= 0 && p->ids_place <= 2 &&
+           p->counters >= 0 && p->counters <= 3 && p->ids_place >= 0 && p->ids_place <= 3 &&
            p->stride >= 0 && p->stride <= 2;
 }
 
@@ -647,7 +660,7 @@ int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t
     for (int place : {PM_PLACE_AUTO, PM_PLACE_HYBRID})
         for (int w : {0, 16, 12, 8})
             for (int c : {0, 1, 2, 3})
-                for (int idp : {0, 1, 2}) {
+                for (int idp : {0, 1, 2, 3}) {
                     pm_params p = s->params;
                     p.stride = 1;
                     p.placement = place;
@@ -664,8 +677,14 @@ int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t
         DevAc plan = saved;
         if (ac_plan(t, p, dp, plan) != PM_OK) continue;
         bool dup = false;
+        // a late-ids plan's list mode does not count in the scan kernel, so
+        // plans differing only in counters are one candidate there; the
+        // first one tried (automatic counters: the best that fit for counts
+        // mode) is kept
+        const bool late_list = list && plan.ids_smem == 2;
         for (const Tried &x : tried)
-            dup = dup || (x.plan.warps == plan.warps && x.plan.hist_smem == plan.hist_smem &&
+            dup = dup || (x.plan.warps == plan.warps &&
+                          (x.plan.hist_smem == plan.hist_smem || (late_list && x.plan.ids_smem == 2)) &&
                           x.plan.ids_smem == plan.ids_smem && x.plan.smem_entries == plan.smem_entries &&
                           x.plan.variant == plan.variant && x.plan.ctas_per_sm == plan.ctas_per_sm);
         if (dup) continue;

@@ -308,6 +308,7 @@ int build_pfac(const uint8_t *P, int64_t d, int32_t m, AcTables &t)
 {
     const int rc = build_ac(P, d, m, t);
     if (rc) return rc;
+    t.goto_only = true;
     const int64_t W = int64_t(1) << t.lw;
     for (int64_t row = 0; row < t.n_rows; ++row) {
         for (int64_t c = 0; c < W; ++c) {

@@ -38,6 +38,7 @@ struct AcTables {
     int64_t d0_row = 0;      // first row holding match entries
     int64_t n_distinct = 0;  // distinct patterns (= terminal states)
     bool has_dups = false;
+    bool goto_only = false;  // PFAC: every non-goto entry dead
     int32_t entry_bytes = 2;
     std::vector<uint32_t> table;   // n_rows << lw encoded entries
     std::vector<uint32_t> mid;     // (n_rows - d0_row) << lw
@@ -185,14 +186,20 @@ struct DevAc {
     uint32_t *flag_mask = nullptr;
     void *flag_rank = nullptr;      // u16 or u32 per mask word (entry_bytes)
     void *canon = nullptr;          // u16 or u32 per terminal (entry_bytes)
+    uint32_t *tmul = nullptr;       // 2 bits per terminal: min(multiplicity - 1, 3)
     int64_t smem_entries = 0;       // table entries copied to shared memory
     int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0;
     int32_t hist_smem = 0;          // per-terminal counters in shared memory
-    int32_t ids_smem = 0;           // rank structure and canon in shared memory
+    // 1: rank structure and canon in shared memory; 2 (late ids): rank
+    // structure and 2-bit multiplicities there, canon in device memory, and in list
+    // mode the slots carry terminal ids that the expand kernel maps to
+    // pattern codes and counts (hist_smem then applies to counts mode only)
+    int32_t ids_smem = 0;
     int32_t nv = 0, hv = 0;         // register text vectors (chunk + halo)
     int32_t variant = 0;            // kernel instance id
     int32_t pre = 0;                // ACGT table stored on the device as (next_row << 2) | match
     int64_t smem_bytes = 0;
+    int64_t smem_bytes_list = 0;    // list mode (smaller with late ids: no counters)
     int32_t placement = 0;
     int64_t max_warps = 0;          // warps in the largest grid a launch uses
 };
@@ -296,11 +303,20 @@ struct ListParts {
 int64_t list_workspace_bytes(int64_t nsub, bool list, int64_t nterms, int slot_entry_bytes);
 void list_workspace_parts(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes, ListParts &out);
 // slots of 4-byte entries hold (offset << 16) | 16-bit code (group flag
-// 0x8000), 8-byte entries (offset << 32) | 32-bit code (group flag 2^31)
+// 0x8000), 8-byte entries (offset << 32) | 32-bit code (group flag 2^31).
+// With `late` (late ids) the low half is a terminal id instead: the expand
+// kernel maps it through canon (entry-sized: u16 for 4-byte slots), counts
+// it into the workspace's per-terminal counters, and its last CTA writes
+// counts[r] (d entries) from them.
+struct ExpandLate {
+    const void *canon = nullptr;
+    int64_t nterms = 0;
+    int64_t *counts = nullptr;
+};
 int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes, const uint32_t *grp_off,
                   const uint32_t *grp_ids, int64_t n_grp_off, int64_t n_grp_ids, uint64_t *d_occ,
                   int64_t occ_cap, int64_t *d_n_occ, const unsigned long long *occ_base,
-                  unsigned long long pos_base, void *stream);
+                  unsigned long long pos_base, void *stream, const ExpandLate *late = nullptr);
 // two characters per lookup (scan_ac2.cu): plan (PM_ETOOBIG if the set is
 // not eligible or the tables do not fit) and scan on the AC workspace
 int ac2_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevAc2 &dev);

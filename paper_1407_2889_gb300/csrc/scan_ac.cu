@@ -58,6 +58,7 @@ struct AcArgs {
     const uint32_t *mask_g;       // match-entry bitmap words
     const void *rank_g;           // E: set bits before each word
     const void *canon_g;          // E: pattern id or group flag per terminal
+    const uint32_t *tmul_g;       // late ids: 2 bits per terminal, min(multiplicity - 1, 3)
     int nwords, nterms;
     const uint32_t *grp_off;
     const uint32_t *grp_ids;
@@ -68,6 +69,7 @@ struct AcArgs {
     long long nsub;               // warp tiles (2560 text bytes each)
     int pool_cap;
     int list, hist_smem, ids_smem, d;
+    int late;                     // list mode with late ids: slots carry terminal ids, no counting here
     long long *counts;
     long long *n_occ;
     dev::WsHeader *ws;
@@ -121,6 +123,12 @@ __host__ __device__ inline long long ac_ids_bytes(int nwords, int nterms, int eb
     return r16((long long)nwords * 4) + r16((long long)(nwords + 1) * eb) + r16((long long)nterms * eb);
 }
 
+// late ids: match bitmap, ranks and the terminals' 2-bit multiplicities
+__host__ __device__ inline long long ac_ids_late_bytes(int nwords, int nterms, int eb)
+{
+    return r16((long long)nwords * 4) + r16((long long)(nwords + 1) * eb) + r16((long long)(nterms + 15) / 16 * 4);
+}
+
 __device__ __forceinline__ int stage_bytes(const AcArgs &a, long long t, int buf)
 {
     if (!a.aligned) return 0;
@@ -137,7 +145,7 @@ __device__ __forceinline__ void stage_issue(const AcArgs &a, long long t, uint8_
     if (bytes > 0) dev::tma_load_1d(buf, a.text + t * kWarpTile, uint32_t(bytes), bar);
 }
 
-template <typename E, int NV, int HV, bool DNA, bool HYB, bool PRE>
+template <typename E, int NV, int HV, bool DNA, bool HYB, bool PRE, bool LATE>
 __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -152,13 +160,20 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
     E *s_tab = reinterpret_cast<E *>(p);
     p += r16((long long)a.smem_entries * sizeof(E));
     Ids<E> ids;
-    if (a.ids_smem) {
+    uint32_t *s_tmul = nullptr;  // late ids: the terminals' multiplicities
+    if (LATE || a.ids_smem) {
         ids.mask = reinterpret_cast<const uint32_t *>(p);
         p += r16((long long)a.nwords * 4);
         ids.rank = reinterpret_cast<const E *>(p);
         p += r16((long long)(a.nwords + 1) * sizeof(E));
-        ids.canon = reinterpret_cast<const E *>(p);
-        p += r16((long long)a.nterms * sizeof(E));
+        if (!LATE) {
+            ids.canon = reinterpret_cast<const E *>(p);
+            p += r16((long long)a.nterms * sizeof(E));
+        } else {
+            ids.canon = reinterpret_cast<const E *>(a.canon_g);
+            s_tmul = reinterpret_cast<uint32_t *>(p);
+            p += r16((long long)(a.nterms + 15) / 16 * 4);
+        }
     } else {
         ids.mask = a.mask_g;
         ids.rank = reinterpret_cast<const E *>(a.rank_g);
@@ -182,15 +197,19 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
         const int nvec = int(((long long)a.smem_entries * sizeof(E) + 15) / 16);
         for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
     }
-    if (a.ids_smem) {
+    if (LATE || a.ids_smem) {
         uint32_t *mk = const_cast<uint32_t *>(ids.mask);
         for (int i = threadIdx.x; i < a.nwords; i += blockDim.x) mk[i] = a.mask_g[i];
         E *rk = const_cast<E *>(ids.rank);
         const E *rg = reinterpret_cast<const E *>(a.rank_g);
         for (int i = threadIdx.x; i <= a.nwords; i += blockDim.x) rk[i] = rg[i];
-        E *cn = const_cast<E *>(ids.canon);
-        const E *cg = reinterpret_cast<const E *>(a.canon_g);
-        for (int i = threadIdx.x; i < a.nterms; i += blockDim.x) cn[i] = cg[i];
+        if (!LATE) {
+            E *cn = const_cast<E *>(ids.canon);
+            const E *cg = reinterpret_cast<const E *>(a.canon_g);
+            for (int i = threadIdx.x; i < a.nterms; i += blockDim.x) cn[i] = cg[i];
+        } else {
+            for (int i = threadIdx.x; i < (a.nterms + 15) / 16; i += blockDim.x) s_tmul[i] = a.tmul_g[i];
+        }
     }
     if (s_hist)
         for (int i = threadIdx.x; i < hist_words; i += blockDim.x) s_hist[i] = 0u;
@@ -235,8 +254,22 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
         const uint32_t g = code & ~kGrp;
         return __ldg(a.grp_off + g + 1) - __ldg(a.grp_off + g);
     };
+    // what a terminal's hit contributes: its outputs, and the slot value (its
+    // pattern code; with late ids the terminal id itself, whose multiplicity
+    // comes from the 2-bit table, and through canon in device memory only
+    // for groups of four or more equal patterns)
+    auto resolve = [&](uint32_t c, uint32_t &mult) -> uint32_t {
+        if (LATE) {
+            const uint32_t v = (s_tmul[c >> 4] >> ((c & 15u) << 1)) & 3u;
+            mult = v < 3u ? v + 1u : mult_of(uint32_t(__ldg(ids.canon + c)));
+            return c;
+        }
+        const uint32_t code = ids.code(c);
+        mult = mult_of(code);
+        return code;
+    };
 
-    // slot entries: (start offset in the tile, pattern code)
+    // slot entries: (start offset in the tile, pattern code or terminal id)
     typedef typename std::conditional<sizeof(E) == 2, uint32_t, unsigned long long>::type SE;
     constexpr int kOffShift = sizeof(E) == 2 ? 16 : 32;
     const long long G = (long long)gridDim.x * (blockDim.x >> 5);
@@ -320,10 +353,11 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (k0 + j < nh) {
-                        const uint32_t code = ids.code(c4[j]);
-                        count_terminal(c4[j]);
-                        cnt += mult_of(code);
-                        pl[(k0 + j) * 32] = E(code);
+                        uint32_t mult;
+                        const uint32_t val = resolve(c4[j], mult);
+                        if (!LATE || !a.late) count_terminal(c4[j]);
+                        cnt += mult;
+                        pl[(k0 + j) * 32] = E(val);
                     }
                 }
             }
@@ -331,8 +365,10 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
             walk_slow<PRE>(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
                       [&](int, uint32_t idx) {
                           const uint32_t c = ids.terminal(idx - a.mid_base);
-                          count_terminal(c);
-                          cnt += mult_of(ids.code(c));
+                          uint32_t mult;
+                          (void)resolve(c, mult);
+                          if (!LATE || !a.late) count_terminal(c);
+                          cnt += mult;
                       });
         }
 
@@ -367,8 +403,9 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
             uint32_t k = 0;
             walk_slow<PRE>(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
                       [&](int step, uint32_t idx) {
-                          const uint32_t code = ids.code(ids.terminal(idx - a.mid_base));
-                          if (k < nh) dst[k] = ((SE)(off0 + uint32_t(step)) << kOffShift) | (SE)code;
+                          uint32_t mult;
+                          const uint32_t val = resolve(ids.terminal(idx - a.mid_base), mult);
+                          if (k < nh) dst[k] = ((SE)(off0 + uint32_t(step)) << kOffShift) | (SE)val;
                           ++k;
                       });
         }
@@ -400,6 +437,7 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
     }
     __threadfence();
     __syncthreads();
+    if (LATE && a.late) return;  // the expand kernel counts and writes counts[r]
     __shared__ int s_last;
     if (threadIdx.x == 0) s_last = atomicAdd(&a.ws->done_ctas, 1u) == gridDim.x - 1;
     __syncthreads();
@@ -430,18 +468,33 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
 // and key stores are both coalesced. A row that names a group of equal
 // patterns takes a warp prefix over the entries' multiplicities instead. The
 // CTA that owns the last tile writes the total.
+// With late ids the entries carry terminal ids: each is mapped to its
+// pattern code through canon and counted per terminal (in shared memory when
+// canon and the counters fit there), the counters go to the workspace when
+// the CTA is done, and the last CTA to finish writes counts[r].
 // ---------------------------------------------------------------------------
 constexpr int kExpandThreads = 512;
 
-template <typename SE, int kOffShift, uint32_t kGrp>
+struct ExpandLateArgs {
+    const void *canon;            // u16 (4-byte slots) or u32 per terminal
+    long long nterms;
+    int smem;                     // canon and counters in shared memory: 1 32-bit, 2 16-bit counters
+    unsigned long long *ccount;   // per-terminal counters (workspace)
+    long long *counts;
+    dev::WsHeader *ws;
+};
+
+template <typename SE, int kOffShift, uint32_t kGrp, bool LATE>
 __global__ void __launch_bounds__(kExpandThreads)
 expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_ent,
               const uint32_t *__restrict__ tile_out, const unsigned long long *__restrict__ seg_sum,
               long long nseg, long long seg_tiles, long long nsub,
               const uint32_t *__restrict__ grp_off, const uint32_t *__restrict__ grp_ids,
               unsigned long long *__restrict__ occ, long long occ_cap, long long *n_occ,
-              const unsigned long long *occ_base, unsigned long long pos_base, long long ngo, long long ngi)
+              const unsigned long long *occ_base, unsigned long long pos_base, long long ngo, long long ngi,
+              const ExpandLateArgs late)
 {
+    typedef typename std::conditional<sizeof(SE) == 4, uint16_t, uint32_t>::type CE;
     extern __shared__ __align__(16) unsigned char esm[];
     unsigned long long *s_off = reinterpret_cast<unsigned long long *>(esm);  // seg_tiles + 1
     uint32_t *s_ent = reinterpret_cast<uint32_t *>(s_off + seg_tiles + 1);
@@ -450,8 +503,8 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
     constexpr int NW = kExpandThreads / 32;
     const long long seg = blockIdx.x;
     const long long t0 = seg * seg_tiles;
-    const long long nt = min(seg_tiles, nsub - t0);
-    if (nt <= 0) return;
+    const long long nt = max(0LL, min(seg_tiles, nsub - t0));
+    if (nt == 0 && !LATE) return;
 
     // base of the segment: sum of the earlier segments
     unsigned long long part = 0;
@@ -491,7 +544,7 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
         s_off[q] = run;
         run += o;
     }
-    if (tid == kExpandThreads - 1 && t0 + nt == nsub) *n_occ = (long long)run;  // the last tile's CTA
+    if (tid == kExpandThreads - 1 && nt > 0 && t0 + nt == nsub) *n_occ = (long long)run;  // the last tile's CTA
     // small group tables move to shared memory: their loads sit on a row's
     // critical path (ngo = 0: they stay in device memory)
     uint32_t *s_grp = s_ent + seg_tiles;
@@ -501,6 +554,18 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
         for (long long i = tid; i < ngi; i += kExpandThreads) s_grp[ngo + i] = grp_ids[i];
         go = s_grp;
         gid = s_grp + ngo;
+    }
+    // late ids: canon and per-terminal counters
+    const CE *canon = static_cast<const CE *>(late.canon);
+    uint32_t *s_cnt = nullptr;
+    if (LATE && late.smem) {
+        unsigned char *q = reinterpret_cast<unsigned char *>(s_grp + ngo + ngi);
+        CE *sc = reinterpret_cast<CE *>(q);
+        s_cnt = reinterpret_cast<uint32_t *>(q + r16(late.nterms * (long long)sizeof(CE)));
+        const long long words = late.smem == 2 ? (late.nterms + 1) / 2 : late.nterms;
+        for (long long i = tid; i < late.nterms; i += kExpandThreads) sc[i] = canon[i];
+        for (long long i = tid; i < words; i += kExpandThreads) s_cnt[i] = 0u;
+        canon = sc;
     }
     __syncthreads();
 
@@ -558,7 +623,24 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
             if (row >= ent) break;
             const uint32_t cnt = min(ent - row, 32u);
             const bool valid = uint32_t(lane) < cnt;   // the valid lanes are 0 .. cnt-1
-            const uint32_t code = uint32_t(v[u] & kMask);
+            uint32_t code = uint32_t(v[u] & kMask);
+            if (LATE && valid) {  // a terminal id: count it, take its pattern code
+                if (!s_cnt) {
+                    atomicAdd(&late.ccount[code], 1ull);
+                } else if (late.smem == 1) {
+                    atomicAdd(&s_cnt[code], 1u);
+                } else {
+                    // 16-bit halves: the add that takes a half to 0x8000 moves
+                    // 0x8000 to the workspace counter, so a half never wraps
+                    const uint32_t sh = (code & 1u) << 4;
+                    const uint32_t old = atomicAdd(&s_cnt[code >> 1], 1u << sh);
+                    if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
+                        atomicSub(&s_cnt[code >> 1], 0x8000u << sh);
+                        atomicAdd(&late.ccount[code], 0x8000ull);
+                    }
+                }
+                code = uint32_t(canon[code]);
+            }
             const unsigned long long key_hi = (unsigned long long)(tile0 + uint32_t(v[u] >> kOffShift)) << 32;
             const bool grp = valid && (code & kGrp);
             if (!__any_sync(kFull, grp)) {
@@ -600,6 +682,33 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
         if (qn != q && qn < nt) enter(qn);
         q = qn;
         g0 = gn;
+    }
+    if (!LATE) return;
+
+    // ---- late ids: counters -> workspace; the last CTA writes counts[r] ----
+    __syncthreads();
+    if (s_cnt)
+        for (long long c = tid; c < late.nterms; c += kExpandThreads) {
+            const uint32_t v = late.smem == 2 ? (s_cnt[c >> 1] >> ((c & 1) << 4)) & 0xFFFFu : s_cnt[c];
+            if (v) atomicAdd(&late.ccount[c], (unsigned long long)v);
+        }
+    __threadfence();
+    __syncthreads();
+    __shared__ int s_last;
+    if (tid == 0) s_last = atomicAdd(&late.ws->done_expand, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const CE *cg = static_cast<const CE *>(late.canon);
+    for (long long c = tid; c < late.nterms; c += kExpandThreads) {
+        const unsigned long long n = dev::ld_acquire(&late.ccount[c]);
+        const uint32_t code = cg[c];
+        if (code & kGrp) {
+            const uint32_t g = code & ~kGrp;
+            for (uint32_t j = grp_off[g]; j < grp_off[g + 1]; ++j) late.counts[grp_ids[j]] = (long long)n;
+        } else {
+            late.counts[code] = (long long)n;
+        }
     }
 }
 
@@ -828,27 +937,44 @@ struct Variant {
 
 // variant ids: dna u16 smem (0-2), dna u16 hybrid (3-5), dna u16 smem with
 // index entries (6-8), dna u16 hybrid with index entries (9-11), dna u32
-// hybrid with index entries (12-14), general u32 hybrid (15-17); within
-// each group HV = 1, 2, 4.
+// hybrid with index entries (12-14), general u32 hybrid (15-17), then the
+// late-ids forms of the five ACGT groups (18-32); within each group HV = 1,
+// 2, 4.
 const Variant kVariants[] = {
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, false>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, false>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, false>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, true, false>, 2, 1, true, true},
-    {ac_scan_kernel<uint16_t, 7, 2, true, true, false>, 2, 2, true, true},
-    {ac_scan_kernel<uint16_t, 9, 4, true, true, false>, 2, 4, true, true},
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, true>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, true>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, true>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, true, true>, 2, 1, true, true},
-    {ac_scan_kernel<uint16_t, 7, 2, true, true, true>, 2, 2, true, true},
-    {ac_scan_kernel<uint16_t, 9, 4, true, true, true>, 2, 4, true, true},
-    {ac_scan_kernel<uint32_t, 6, 1, true, true, true>, 4, 1, true, true},
-    {ac_scan_kernel<uint32_t, 7, 2, true, true, true>, 4, 2, true, true},
-    {ac_scan_kernel<uint32_t, 9, 4, true, true, true>, 4, 4, true, true},
-    {ac_scan_kernel<uint32_t, 6, 1, false, true, false>, 4, 1, false, true},
-    {ac_scan_kernel<uint32_t, 7, 2, false, true, false>, 4, 2, false, true},
-    {ac_scan_kernel<uint32_t, 9, 4, false, true, false>, 4, 4, false, true},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, false>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, false>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, false>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, false, false>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, false, false>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, false, false>, 2, 4, true, true},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, false>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, false>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, false>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, true, false>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, true, false>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, true, false>, 2, 4, true, true},
+    {ac_scan_kernel<uint32_t, 6, 1, true, true, true, false>, 4, 1, true, true},
+    {ac_scan_kernel<uint32_t, 7, 2, true, true, true, false>, 4, 2, true, true},
+    {ac_scan_kernel<uint32_t, 9, 4, true, true, true, false>, 4, 4, true, true},
+    {ac_scan_kernel<uint32_t, 6, 1, false, true, false, false>, 4, 1, false, true},
+    {ac_scan_kernel<uint32_t, 7, 2, false, true, false, false>, 4, 2, false, true},
+    {ac_scan_kernel<uint32_t, 9, 4, false, true, false, false>, 4, 4, false, true},
+
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, true>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, true>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, true>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, false, true>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, false, true>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, false, true>, 2, 4, true, true},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, true>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, true>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, true>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, true, true>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, true, true>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, true, true>, 2, 4, true, true},
+    {ac_scan_kernel<uint32_t, 6, 1, true, true, true, true>, 4, 1, true, true},
+    {ac_scan_kernel<uint32_t, 7, 2, true, true, true, true>, 4, 2, true, true},
+    {ac_scan_kernel<uint32_t, 9, 4, true, true, true, true>, 4, 4, true, true},
 };
 
 int hv_for_m(int m)
@@ -875,8 +1001,9 @@ long long ac_smem_bytes(const AcTables &t, int eb, const Layout &L, int hv, int 
 {
     const int nwords = int(t.flag_mask.size());
     const int nterms = int(t.canon.size());
-    return r16(L.smem_entries * eb) + (L.ids ? ac_ids_bytes(nwords, nterms, eb) : 0) +
-           ac_hist_bytes(L.hist, nterms) + (t.dna ? 0 : 256) +
+    const long long ids = L.ids == 1 ? ac_ids_bytes(nwords, nterms, eb)
+                        : L.ids == 2 ? ac_ids_late_bytes(nwords, nterms, eb) : 0;
+    return r16(L.smem_entries * eb) + ids + ac_hist_bytes(L.hist, nterms) + (t.dna ? 0 : 256) +
            (long long)L.warps * ac_warp_bytes(hv, pool_cap, eb);
 }
 
@@ -897,11 +1024,16 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     dev.nv = 5 + hv;
     dev.ctas_per_sm = opt.ctas_per_sm > 0 ? opt.ctas_per_sm : 1;
     // pm_params.counters: 0 auto, 1 32-bit shared, 2 16-bit shared, 3 global;
-    // pm_params.ids_place: 0 auto, 1 shared, 2 global
+    // pm_params.ids_place: 0 auto, 1 shared, 2 global, 3 late (Layout::ids
+    // 1, 0 and 2)
     auto hist_ok = [&](int h) {
         return opt.counters == 0 || (opt.counters == 3 ? h == 0 : h == opt.counters);
     };
-    auto ids_ok = [&](int i) { return opt.ids_place == 0 || (opt.ids_place == 1) == (i == 1); };
+    auto ids_ok = [&](int i) {
+        if (i == 2 && (t.goto_only || !t.dna)) return false;
+        if (opt.ids_place == 0) return true;
+        return i == (opt.ids_place == 1 ? 1 : opt.ids_place == 2 ? 0 : 2);
+    };
     auto fits = [&](const Layout &L) {
         const long long need = ac_smem_bytes(t, eb, L, hv, pool_cap);
         return need <= budget &&
@@ -913,17 +1045,31 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     if ((place == PM_PLACE_AUTO || place == PM_PLACE_SMEM) &&
         (opt.smem_table_bytes <= 0 || entries * eb <= opt.smem_table_bytes)) {
         // whole table in shared memory; prefer the id structure and the
-        // counters there too (32-bit, else 16-bit), then the most warps (at
-        // least 12 if possible); pm_params can pin either choice
-        const int ids_hist[6][2] = {{1, 1}, {1, 2}, {0, 1}, {0, 2}, {1, 0}, {0, 0}};
+        // counters there too (32-bit, else 16-bit), then late ids (whose
+        // list mode needs neither canon nor counters there; counts mode
+        // adds the counters that still fit), then the most warps (at least
+        // 12 if possible); pm_params can pin either choice
+        const int ids_hist[7][2] = {{1, 1}, {1, 2}, {2, -1}, {0, 1}, {0, 2}, {1, 0}, {0, 0}};
         for (int minw : {12, 4}) {
-            for (int o = 0; o < 6 && !chosen; ++o) {
-                if (!ids_ok(ids_hist[o][0]) || !hist_ok(ids_hist[o][1])) continue;
+            for (int o = 0; o < 7 && !chosen; ++o) {
+                const int ids = ids_hist[o][0], hist = ids_hist[o][1];
+                if (!ids_ok(ids) || (hist >= 0 && !hist_ok(hist))) continue;
                 const int hi = forced_warps ? forced_warps : 16;
                 const int lo = forced_warps ? forced_warps : minw;
-                for (int w = hi; w >= lo; --w) {
-                    Layout L{entries, w, ids_hist[o][1], ids_hist[o][0]};
-                    if (fits(L)) { best = L; chosen = true; break; }
+                for (int w = hi; w >= lo && !chosen; --w) {
+                    Layout L{entries, w, hist < 0 ? 0 : hist, ids};
+                    if (!fits(L)) continue;
+                    if (hist < 0) {  // counts-mode counters on top of the list layout
+                        bool any = false;
+                        for (int h : {1, 2, 0}) {
+                            Layout C = L;
+                            C.hist = h;
+                            if (hist_ok(h) && fits(C)) { L = C; any = true; break; }
+                        }
+                        if (!any) continue;
+                    }
+                    best = L;
+                    chosen = true;
                 }
             }
             if (chosen) break;
@@ -936,7 +1082,8 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
         const int w = forced_warps ? forced_warps : 16;
         // counters / ids only when pinned by pm_params (the table prefix
         // gets the room otherwise)
-        Layout L{0, w, opt.counters == 1 ? 1 : opt.counters == 2 ? 2 : 0, opt.ids_place == 1 ? 1 : 0};
+        Layout L{0, w, opt.counters == 1 ? 1 : opt.counters == 2 ? 2 : 0,
+                 opt.ids_place == 1 ? 1 : (opt.ids_place == 3 && ids_ok(2)) ? 2 : 0};
         const long long fixed = ac_smem_bytes(t, eb, L, hv, pool_cap);
         if (fixed > budget) return PM_ETOOBIG;
         long long room = budget - fixed;
@@ -963,8 +1110,12 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     if (!t.dna) group = 5;
     else if (eb == 4) group = 4;
     else group = (hyb ? 1 : 0) + (dev.pre ? 2 : 0);
+    if (best.ids == 2) group += 6;   // late ids (ACGT groups only)
     dev.variant = group * 3 + hv_slot(hv);
     dev.smem_bytes = ac_smem_bytes(t, eb, best, hv, pool_cap);
+    Layout LL = best;
+    if (best.ids == 2) LL.hist = 0;
+    dev.smem_bytes_list = ac_smem_bytes(t, eb, LL, hv, pool_cap);
     dev.max_warps = (long long)dp.sm_count * dev.ctas_per_sm * dev.warps;
     return PM_OK;
 }
@@ -1007,7 +1158,9 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
         if (e == cudaSuccess) e = cudaMemsetAsync(d_ws, 0, size_t(L.zeroed), st);
     } else {
         // keep the status word and the per-terminal counters
-        e = cudaMemsetAsync(static_cast<char *>(d_ws) + offsetof(dev::WsHeader, done_ctas), 0, 4, st);
+        static_assert(offsetof(dev::WsHeader, done_expand) == offsetof(dev::WsHeader, done_ctas) + 4,
+                      "done counters side by side");
+        e = cudaMemsetAsync(static_cast<char *>(d_ws) + offsetof(dev::WsHeader, done_ctas), 0, 8, st);
         if (e == cudaSuccess && L.zeroed > L.seg_sum)
             e = cudaMemsetAsync(static_cast<char *>(d_ws) + L.seg_sum, 0, size_t(L.zeroed - L.seg_sum), st);
     }
@@ -1020,7 +1173,10 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     }
 
     const AcKernel fn = pfac ? pfac_kernel_for(t, dv) : kVariants[dv.variant].fn;
-    rc = kernel_smem_attr(reinterpret_cast<const void *>(fn), dv.smem_bytes);
+    // late ids: list mode drops the counters from shared memory
+    const bool late = list && !pfac && dv.ids_smem == 2;
+    const long long smem = late ? dv.smem_bytes_list : dv.smem_bytes;
+    rc = kernel_smem_attr(reinterpret_cast<const void *>(fn), smem);
     if (rc) return rc;
     AcArgs a;
     a.text = d_text;
@@ -1032,6 +1188,7 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     a.mask_g = dv.flag_mask;
     a.rank_g = dv.flag_rank;
     a.canon_g = dv.canon;
+    a.tmul_g = dv.tmul;
     a.nwords = int(t.flag_mask.size());
     a.nterms = int(nterms);
     a.grp_off = dv.grp_off;
@@ -1049,8 +1206,9 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     a.nsub = nsub;
     a.pool_cap = dv.pool_cap;
     a.list = list ? 1 : 0;
-    a.hist_smem = dv.hist_smem;
+    a.hist_smem = late ? 0 : dv.hist_smem;
     a.ids_smem = dv.ids_smem;
+    a.late = late ? 1 : 0;
     a.d = int(t.d);
     a.counts = reinterpret_cast<long long *>(d_counts);
     a.n_occ = reinterpret_cast<long long *>(d_n_occ);
@@ -1065,19 +1223,26 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
 
     const int threads = dv.warps * 32;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, size_t(dv.smem_bytes));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, size_t(smem));
     if (e != cudaSuccess || per_sm < 1) { set_cuda_error(int(e)); return PM_ECUDA; }
     long long grid = (long long)dp.sm_count * std::min(per_sm, dv.ctas_per_sm);
     const long long want = (nsub + dv.warps - 1) / dv.warps;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
-    fn<<<dim3(unsigned(grid)), dim3(unsigned(threads)), size_t(dv.smem_bytes), st>>>(a);
+    fn<<<dim3(unsigned(grid)), dim3(unsigned(threads)), size_t(smem), st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     if (!list) return PM_OK;
 
+    ExpandLate xl;
+    if (late) {
+        xl.canon = dv.canon;
+        xl.nterms = nterms;
+        xl.counts = d_counts;
+    }
     return expand_launch(d_ws, nsub, nterms, se, dv.grp_off, dv.grp_ids, (int64_t)t.grp_off.size(),
-                         (int64_t)t.grp_ids.size(), d_occ, occ_cap, d_n_occ, occ_base, pos_base, st);
+                         (int64_t)t.grp_ids.size(), d_occ, occ_cap, d_n_occ, occ_base, pos_base, st,
+                         late ? &xl : nullptr);
 }
 
 }  // namespace
@@ -1107,7 +1272,7 @@ void list_workspace_parts(void *d_ws, int64_t nsub, int64_t nterms, int slot_ent
 int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes, const uint32_t *grp_off,
                   const uint32_t *grp_ids, int64_t n_grp_off, int64_t n_grp_ids, uint64_t *d_occ,
                   int64_t occ_cap, int64_t *d_n_occ, const unsigned long long *occ_base,
-                  unsigned long long pos_base, void *stream)
+                  unsigned long long pos_base, void *stream, const ExpandLate *late)
 {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     ListParts P;
@@ -1115,33 +1280,53 @@ int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes
     const long long seg_tiles = P.seg_tiles;
     const long long nseg = (nsub + seg_tiles - 1) / seg_tiles;
     // shared memory of the expand kernel: 12 bytes per tile of a segment
-    // (above 48 KB only for texts of more than about 3 GB)
+    // (above 48 KB only for texts of more than about 3 GB), then, while two
+    // CTAs still fit an SM: with late ids canon and 32-bit (else 16-bit) per-terminal
+    // counters, and the group tables (offsets and ids)
     unsigned long long *occ = reinterpret_cast<unsigned long long *>(d_occ);
     const long long cap = d_occ ? occ_cap : 0;
-    // group tables (offsets and ids) join it when they take at most 16 KB
-    const bool grp_smem = n_grp_off > 0 && (n_grp_off + n_grp_ids) * 4 <= (16 << 10);
-    const long long ngo = grp_smem ? n_grp_off : 0, ngi = grp_smem ? n_grp_ids : 0;
-    const size_t esmem = size_t((seg_tiles + 1) * 8 + seg_tiles * 4 + (ngo + ngi) * 4);
-    cudaError_t e = cudaSuccess;
+    DeviceProps dp;
+    int rc = device_props(dp);
+    if (rc) return rc;
+    const long long per_cta = std::min<long long>((long long)dp.smem_per_sm / 2 - 2048, dp.smem_optin - 1024);
+    long long esmem = (seg_tiles + 1) * 8 + seg_tiles * 4;
     const bool se4 = slot_entry_bytes == 4;
-    if (esmem > (size_t(48) << 10)) {
-        e = se4 ? cudaFuncSetAttribute(expand_kernel<uint32_t, 16, 0x8000u>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem))
-                : cudaFuncSetAttribute(expand_kernel<unsigned long long, 32, 0x80000000u>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem));
-        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    ExpandLateArgs la{};
+    const bool is_late = late && late->canon;
+    if (is_late) {
+        la.canon = late->canon;
+        la.nterms = late->nterms;
+        la.ccount = reinterpret_cast<unsigned long long *>(static_cast<char *>(d_ws) + kWsHeader);
+        la.counts = reinterpret_cast<long long *>(late->counts);
+        la.ws = static_cast<dev::WsHeader *>(d_ws);
+        const long long cb = r16(late->nterms * (se4 ? 2 : 4));
+        const long long x32 = cb + r16(late->nterms * 4), x16 = cb + r16((late->nterms + 1) / 2 * 4);
+        la.smem = esmem + x32 <= per_cta ? 1 : esmem + x16 <= per_cta ? 2 : 0;
+        esmem += la.smem == 1 ? x32 : la.smem == 2 ? x16 : 0;
     }
+    const long long grp_bytes = (n_grp_off + n_grp_ids) * 4;
+    const bool grp_smem = n_grp_off > 0 && (grp_bytes <= (16 << 10) || esmem + grp_bytes <= per_cta);
+    const long long ngo = grp_smem ? n_grp_off : 0, ngi = grp_smem ? n_grp_ids : 0;
+    esmem += (ngo + ngi) * 4;
     long long *n_occ = reinterpret_cast<long long *>(d_n_occ);
-    if (se4)
-        expand_kernel<uint32_t, 16, 0x8000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
-            static_cast<const uint32_t *>(P.slots), P.tile_ent, P.tile_out, P.seg_sum, nseg, seg_tiles, nsub,
-            grp_off, grp_ids, occ, cap, n_occ, occ_base, pos_base, ngo, ngi);
-    else
-        expand_kernel<unsigned long long, 32, 0x80000000u><<<unsigned(nseg), kExpandThreads, esmem, st>>>(
-            static_cast<const unsigned long long *>(P.slots), P.tile_ent, P.tile_out, P.seg_sum, nseg,
-            seg_tiles, nsub, grp_off, grp_ids, occ, cap, n_occ, occ_base, pos_base, ngo, ngi);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+    auto go = [&](auto kern, const auto *slots) -> cudaError_t {
+        if (esmem > (48 << 10)) {
+            const cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(esmem));
+            if (ea != cudaSuccess) return ea;
+        }
+        kern<<<unsigned(nseg), kExpandThreads, size_t(esmem), st>>>(slots, P.tile_ent, P.tile_out, P.seg_sum, nseg,
+                                                                   seg_tiles, nsub, grp_off, grp_ids, occ, cap, n_occ,
+                                                                   occ_base, pos_base, ngo, ngi, la);
+        return cudaGetLastError();
+    };
+    const uint32_t *s4 = static_cast<const uint32_t *>(P.slots);
+    const unsigned long long *s8 = static_cast<const unsigned long long *>(P.slots);
+    cudaError_t e;
+    if (se4) e = is_late ? go(expand_kernel<uint32_t, 16, 0x8000u, true>, s4)
+                         : go(expand_kernel<uint32_t, 16, 0x8000u, false>, s4);
+    else e = is_late ? go(expand_kernel<unsigned long long, 32, 0x80000000u, true>, s8)
+                     : go(expand_kernel<unsigned long long, 32, 0x80000000u, false>, s8);
+    if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); return PM_ECUDA; }
     return PM_OK;
 }
 

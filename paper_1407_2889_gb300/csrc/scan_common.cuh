@@ -24,8 +24,10 @@ constexpr uint32_t kErrInternal = 3;        // a consistency check failed
 struct WsHeader {           // lives at the start of the workspace
     uint32_t status;        // 0 = ok, else kErr*
     uint32_t done_ctas;     // CTAs that finished (the last one finalises counts)
+    uint32_t done_expand;   // expand CTAs that finished (late ids: the last one finalises counts)
+    uint32_t pad0;
     unsigned long long queue;  // batched scan: next instance to take
-    unsigned long long pad1[30];
+    unsigned long long pad1[29];
 };
 static_assert(sizeof(WsHeader) <= kWsHeader, "workspace header too large");
 

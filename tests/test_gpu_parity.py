@@ -192,6 +192,8 @@ def test_unaligned_device_text():
     {"warps_per_cta": 8},
     {"warps_per_cta": 12},
     {"ctas_per_sm": 2, "warps_per_cta": 4},
+    {"ids_place": 3, "placement": pm.PM_PLACE_HYBRID, "smem_table_bytes": 4096},
+    {"ids_place": 3, "warps_per_cta": 8, "counters": 2},
 ])
 def test_placements_and_launch_shapes_agree(kw):
     T = synth.est_text(1 << 21, 6)
@@ -203,11 +205,13 @@ def test_placements_and_launch_shapes_agree(kw):
 
 
 @pytest.mark.parametrize("counters", [1, 2, 3])
-@pytest.mark.parametrize("ids_place", [1, 2])
+@pytest.mark.parametrize("ids_place", [1, 2, 3])
 def test_counter_and_id_placements_agree(counters, ids_place):
     """Per-terminal counters (32-bit / 16-bit shared, device memory) and the
-    terminal-id structure (shared / device) give identical results; the
-    16-bit counters overflow into the device counter many times here."""
+    terminal-id structure (shared / device / late: codes and counts taken in
+    the expand kernel in list mode) give identical results; the 16-bit
+    counters overflow into the device counter many times here, and the run
+    of one letter puts a group of two equal patterns on every position."""
     T = synth.est_text(4 << 20, 21)
     P = synth.mixed_patterns(T, 3000, 8, 21)
     P = np.concatenate([P, P[:7]])
@@ -220,6 +224,11 @@ def test_counter_and_id_placements_agree(counters, ids_place):
     s = _ac(np.full((2, 8), ord("A"), np.uint8), counters=counters, ids_place=ids_place)
     occ, cnt = s.scan(A, counts_only=True)
     assert cnt.tolist() == [n - 7, n - 7]
+    k = 1 << 20
+    occ, cnt = s.scan(A[:k])
+    assert cnt.tolist() == [k - 7, k - 7]
+    pos = np.repeat(np.arange(k - 7, dtype=np.uint64), 2)
+    assert np.array_equal(occ, (pos << np.uint64(32)) | np.tile(np.array([0, 1], np.uint64), k - 7))
     s.close()
 
 
@@ -403,7 +412,7 @@ def test_scan_to_host_in_pieces(est_text_full):
     _, P = synth.est_case(1000, 8, text=est_text_full)
     want_occ, want_cnt = oracle.dictionary(T, P, threads=THREADS)
     pinned = torch.from_numpy(T).pin_memory()
-    for make in (_ac, pm.PatternSet.pfac):
+    for make in (_ac, pm.PatternSet.pfac, lambda P: _ac(P, ids_place=3)):
         s = make(P)
         counts = torch.zeros(P.shape[0], dtype=torch.int64).pin_memory()
         occ = torch.zeros(want_occ.size + 7, dtype=torch.int64).pin_memory()
@@ -500,3 +509,33 @@ def test_stride2_est_and_tuner(est_text_full):
             assert params["stride"] in (1, 2) and s.info()["stride"] == params["stride"]
             _same(s.scan(d_T), want, "after tuning")
         s.close()
+
+
+def test_late_ids_large_set_and_hot_terminal():
+    """Late ids (the expand kernel maps terminal ids to codes and counts
+    them) on a set whose canon and 32-bit counters do not fit the expand
+    CTA's shared memory, so it counts in 16-bit halves: a 300 KB run of one
+    letter inside one output segment takes one terminal (a group of three
+    equal patterns) past 0x8000 many times. List mode, counts-only mode and
+    a short capacity all equal the oracle."""
+    T = synth.est_text(64 << 20, 31).copy()
+    T[5_000_000:5_300_000] = ord("A")
+    P = synth.random_patterns(24000, 8, 31)
+    P = np.concatenate([P, np.full((3, 8), ord("A"), np.uint8)])
+    want = oracle.dictionary(T, P, threads=THREADS)
+    s = _ac(P, ids_place=3)
+    _same(s.scan(T), want, "late ids, 16-bit expand counters")
+    _same(s.scan(T, counts_only=True), (np.zeros(0, np.uint64), want[1]), "late ids counts only")
+    d = torch.from_numpy(T).cuda()
+    cap = want[0].size // 2
+    counts = torch.zeros(P.shape[0], dtype=torch.int64, device="cuda")
+    occ = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    nocc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws = torch.zeros(s.workspace_bytes(T.size), dtype=torch.uint8, device="cuda")
+    pm.pm_scan_device(s.h, d, T.size, 0, counts, occ, cap, nocc, ws, ws.numel(), None)
+    torch.cuda.synchronize()
+    assert pm.pm_scan_status(ws, None) == pm.PM_OK
+    assert int(nocc.item()) == want[0].size
+    assert np.array_equal(occ.cpu().numpy().view(np.uint64), want[0][:cap])
+    assert np.array_equal(counts.cpu().numpy(), want[1])
+    s.close()
