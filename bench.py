@@ -54,9 +54,22 @@ def measured_peaks() -> tuple[float, str]:
     return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel_name: str, workload: str):
+PLAN_KEYS = ("placement", "warps_per_cta", "counters", "ids_place", "stride")
+
+
+def plan_key(plan) -> dict:
+    """The launch-plan fields that decide which kernels run (0 = automatic;
+    stride 0 and 1 are both one character per lookup)."""
+    plan = plan or {}
+    key = {k: int(plan.get(k, 0)) for k in PLAN_KEYS}
+    key["stride"] = 2 if key["stride"] == 2 else 1
+    return key
+
+
+def recorded_traffic(kernel_name: str, workload: str, plan=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source and the same workload; else None."""
+    the current kernel source, the same workload and the same launch plan;
+    else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -64,6 +77,8 @@ def recorded_traffic(kernel_name: str, workload: str):
         rec = json.load(f)
     e = rec.get(kernel_name)
     if not e or e.get("kernel_hash") != kernel_hash() or e.get("workload") != workload:
+        return None
+    if plan_key(e.get("plan")) != plan_key(plan):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -181,6 +196,9 @@ def parse():
     ap.add_argument("--only-serve", action="store_true",
                     help="run only the serving measurement and print it")
     ap.add_argument("--no-tune", action="store_true", help="keep the planner's default launch plan")
+    ap.add_argument("--plan", default="",
+                    help="pin the AC launch plan instead of tuning: JSON of pm_params fields, "
+                         'e.g. \'{"ids_place": 3}\'')
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end pm_scan_to_host timing (ncu launch lists of the timed steps)")
     ap.add_argument("--mode", default="list", choices=["list", "counts"],
@@ -282,11 +300,12 @@ def main():
         T = T[: args.text_mib << 20]
     n = T.size
     d = P.shape[0]
-    s = pm.PatternSet.ac(P) if args.algo == "ac" else pm.PatternSet.wm(P, args.wm_b)
+    pinned_plan = json.loads(args.plan) if args.plan else None
+    s = pm.PatternSet.ac(P, pinned_plan) if args.algo == "ac" else pm.PatternSet.wm(P, args.wm_b)
     stream = torch.cuda.Stream()
     d_text = torch.from_numpy(T).cuda()
-    tuned = None
-    if not args.no_tune and args.algo == "ac":  # the autotuner picks the launch plan (not timed)
+    tuned = {"pinned": pinned_plan} if pinned_plan else None
+    if not args.no_tune and not pinned_plan and args.algo == "ac":  # the autotuner picks the launch plan (not timed)
         params, tms = s.tune(d_text, counts_only=args.mode == "counts", reps=3)
         tuned = {"ms_per_scan": tms,
                  **{k: params[k] for k in ("placement", "warps_per_cta", "counters", "ids_place", "stride")}}
@@ -347,7 +366,8 @@ def main():
     achieved = alg_bytes / avg_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
-                "traffic": recorded_traffic(f"{args.algo}_scan_kernel", f"est1gib_d{d}_m{args.m}_{args.mode}_n{n}"),
+                "traffic": recorded_traffic(f"{args.algo}_scan_kernel", f"est1gib_d{d}_m{args.m}_{args.mode}_n{n}",
+                                            pinned_plan or tuned),
                 "algorithmic_bytes_per_launch": alg_bytes,
                 "kernel": (f"{args.algo}_scan_kernel" + (" + expand_kernel (list mode)" if args.mode == "list" else ""))}
 
@@ -792,17 +812,26 @@ def serving_run(args, pinned, pm, torch, synth):
     # saturation: the same kind of requests, all queued at once (closed
     # loop), so batches form while others run; sustained capacity
     ks = min(k, 3000)
-    sat = pm.Server(budget_bytes=8 << 30, max_batch=256, max_inflight=3)
-    for t in [sat.submit(q, pinned[j * big:(j + 1) * big]) for j, q in enumerate(sets)]:
-        sat.wait(t)
-    sat.reset_stats()
-    t0 = time.perf_counter()
-    tk = [sat.submit(sets[which[j]], pinned[offs[j]:offs[j] + lens[j]]) for j in range(ks)]
-    for t in tk:
-        sat.wait(t)
-    sat_wall = time.perf_counter() - t0
-    ss = sat.stats()
-    sat.close()
+
+    def saturate(counts_only):
+        # a page-locked result pool that holds a whole batch's keys
+        sat = pm.Server(budget_bytes=8 << 30, max_batch=256, max_inflight=3, host_pool_bytes=6 << 30)
+        for t in [sat.submit(q, pinned[j * big:(j + 1) * big]) for j, q in enumerate(sets)]:
+            sat.wait(t)
+        sat.reset_stats()
+        t0 = time.perf_counter()
+        tk = [sat.submit(sets[which[j]], pinned[offs[j]:offs[j] + lens[j]], counts_only=counts_only)
+              for j in range(ks)]
+        keys = 0
+        for t in tk:
+            keys += int(sat.wait(t)[0].size)
+        wall_ = time.perf_counter() - t0
+        st_ = sat.stats()
+        sat.close()
+        return st_, wall_, keys
+
+    ss, sat_wall, sat_keys = saturate(False)
+    sat_co, sat_co_wall, _ = saturate(True)
     same = True
     for j, (occ, cnt) in results.items():
         so, sc = sets[which[j]].scan(T[offs[j]:offs[j] + lens[j]])
@@ -819,7 +848,12 @@ def serving_run(args, pinned, pm, torch, synth):
         "saturated": {"requests": ks, "gbs": ss["gbs"], "wall_s": sat_wall, "mean_batch": ss["mean_batch"],
                       "batches": ss["batches"], "p50_ms": ss["p50_us"] / 1e3, "p99_ms": ss["p99_us"] / 1e3,
                       "peak_inflight": ss["peak_inflight"], "dispatch_busy_s": ss["dispatch_busy_s"],
-                      "complete_busy_s": ss["complete_busy_s"]},
+                      "complete_busy_s": ss["complete_busy_s"],
+                      "text_bytes": int(lens[:ks].sum()), "key_bytes": 8 * sat_keys,
+                      "key_gbs": 8 * sat_keys / sat_wall / 1e9},
+        "saturated_counts_only": {"requests": ks, "gbs": sat_co["gbs"], "wall_s": sat_co_wall,
+                                  "mean_batch": sat_co["mean_batch"], "batches": sat_co["batches"],
+                                  "p50_ms": sat_co["p50_us"] / 1e3, "p99_ms": sat_co["p99_us"] / 1e3},
         "workload": "Poisson 2000 req/s; text log-uniform 1 KiB-16 MiB slices of the pinned EST text (H2D and D2H "
                     "inside the latency); 64 sets d log-uniform 100-1e5, m in {8,16,24,32}; list mode; "
                     "after a warm-up of one 16 MiB request per set",

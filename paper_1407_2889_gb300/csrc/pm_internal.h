@@ -418,6 +418,12 @@ int64_t batch_fill(const BatchInst *inst, int k, const BatchShape &sh, BatchDesc
 int64_t batch_items(const BatchInst *inst, int k, const BatchShape &sh, bool list, std::vector<BatchDesc> &out,
                     int64_t *spill_words);
 inline int64_t batch_ws_bytes(int64_t ccount_words) { return kWsHeader + 8 * ccount_words; }
+// An upper bound on the workspace words (counters, part words and key
+// staging) one instance adds to any batch_items plan of the shape,
+// whatever the rest of the batch (list: the instance's keys are listed).
+int64_t batch_words_bound(const BatchInst &I, const BatchShape &sh, bool list);
+// Queue items of a batch of k instances fit at most this many descriptors.
+inline int64_t batch_items_bound(int64_t k, const BatchShape &sh) { return 2 * k + 4 * int64_t(sh.sm_count) + 16; }
 int batch_prepare_launch(const BatchShape &sh);  // host-side set-up, before any capture
 int batch_launch_raw(const BatchDesc *d_desc, int k, const uint8_t *text, int64_t *counts,
                      uint64_t *occ, int64_t *n_occ, void *ws, int64_t ccount_total,

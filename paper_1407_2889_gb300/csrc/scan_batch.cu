@@ -649,6 +649,20 @@ int64_t batch_items(const BatchInst *inst, int k, const BatchShape &sh, bool lis
     return ccount;
 }
 
+int64_t batch_words_bound(const BatchInst &I, const BatchShape &sh, bool list)
+{
+    const AcTables &t = I.set->ac;
+    const InstLayout L = layout_of(t, sh.region_bytes);
+    const long long ntiles = (I.text_len + kWarpTile - 1) / kWarpTile;
+    const long long parts = std::max(1LL, ntiles / (2LL * std::max(sh.warps, 1)));
+    int64_t w = (L.hist_off < 0 || parts > 1) ? int64_t(t.canon.size()) : 0;
+    if (parts > 1) {
+        w += parts + 1;
+        if (list) w += std::min<int64_t>(parts * I.occ_cap, (I.text_len + kSpillBytes - 1) / kSpillBytes + parts);
+    }
+    return w;
+}
+
 static int ensure_batch_attr(long long smem_bytes)
 {
     static std::mutex mu;

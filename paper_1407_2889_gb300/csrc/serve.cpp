@@ -40,10 +40,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr int64_t kAlign = 256;
-// Requests at least this long run as their own whole-GPU scan (the plain
-// scan and expand kernels over all SMs); shorter ones share a batched
-// launch, where one CTA takes a whole request.
-constexpr int64_t kPlainMin = int64_t(256) << 10;
+// Every request shares the batched launch, where the costliest instances
+// are split across CTAs; only a request whose workspace words could exceed
+// a slot's runs as its own whole-GPU scan (the plain scan and expand
+// kernels).
 
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
@@ -201,7 +201,7 @@ struct Req {
 
 struct Slot {
     cudaStream_t st = nullptr;
-    BatchDesc *h_desc = nullptr;       // pinned, max_batch
+    BatchDesc *h_desc = nullptr;       // pinned, batch_items_bound(max_batch) queue items
     int64_t *h_nocc = nullptr;         // pinned, max_batch
     BatchDesc *d_desc = nullptr;
     int64_t *d_nocc = nullptr;
@@ -276,7 +276,10 @@ bool admit(pm_server *s, Req &r)
     r.cnt_bytes = d * 8;
     r.occ_cap = est_cap(s, r);
     r.occ_bytes = r.list ? std::max<int64_t>(r.occ_cap, 1) * 8 : 0;
-    r.plain = r.n >= kPlainMin;
+    {
+        const BatchInst I{r.set, 0, r.n, 0, 0, r.list ? r.occ_cap : 0, 0};
+        r.plain = batch_words_bound(I, s->shape, r.list) > s->p.counter_words;
+    }
     r.ws_bytes = r.plain ? pm_scan_workspace_bytes(r.set, r.n, r.list ? 0u : PM_COUNTS_ONLY) : 0;
     r.text_blk = s->arena.alloc(r.text_bytes);
     if (r.text_blk < 0) return false;
@@ -313,11 +316,13 @@ void *release(pm_server *s, Req &r)
     return ext;
 }
 
-int64_t counter_words(const pm_server *s, const Req &r)
+// Workspace words a request may add to a batch (0: it runs as a whole-GPU
+// scan with its own workspace).
+int64_t counter_words(pm_server *s, const Req &r)
 {
-    if (r.n >= kPlainMin) return 0;  // a whole-GPU scan has its own workspace
-    BatchInst I{r.set, 0, r.n, 0, 0, 0, 0};
-    return batch_fill(&I, 1, s->shape, nullptr);
+    const BatchInst I{r.set, 0, r.n, 0, 0, r.list ? est_cap(s, r) : 0, 0};
+    const int64_t w = batch_words_bound(I, s->shape, r.list);
+    return w > s->p.counter_words ? 0 : w;
 }
 
 // A whole-GPU scan of one request, its keys going to `occ`, its total to
@@ -355,21 +360,21 @@ int ensure_pws(Slot &sl, int64_t need)
 int launch_slot(pm_server *s, Slot &sl)
 {
     const int k = int(sl.reqs.size());
-    std::vector<int> order;
-    for (int j = 0; j < k; ++j)
-        if (!sl.reqs[size_t(j)]->plain) order.push_back(j);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return sl.reqs[size_t(x)]->n > sl.reqs[size_t(y)]->n; });
-    const int kb = int(order.size());
-    std::vector<BatchInst> inst(static_cast<size_t>(kb));
-    for (int q = 0; q < kb; ++q) {
-        const int j = order[size_t(q)];
+    std::vector<BatchInst> inst;
+    for (int j = 0; j < k; ++j) {
         const Req &r = *sl.reqs[size_t(j)];
+        if (r.plain) continue;
         const int64_t occ_off = r.list ? r.occ_blk / 8 : 0;
-        inst[size_t(q)] = BatchInst{r.set, r.text_blk, r.n, r.cnt_blk / 8, occ_off, r.list ? r.occ_cap : 0, j};
+        inst.push_back(BatchInst{r.set, r.text_blk, r.n, r.cnt_blk / 8, occ_off, r.list ? r.occ_cap : 0, j});
     }
-    const int64_t words = batch_fill(inst.data(), kb, s->shape, sl.h_desc);
-    if (words > sl.ws_words) return PM_EINVAL;  // admission keeps this from happening
+    // queue items: costliest first, large requests split across CTAs
+    std::vector<BatchDesc> items;
+    int64_t spill = 0;
+    const int64_t words = batch_items(inst.data(), int(inst.size()), s->shape, true, items, &spill);
+    const int kb = int(items.size());
+    if (words + spill > sl.ws_words || int64_t(kb) > batch_items_bound(s->p.max_batch, s->shape))
+        return PM_EINVAL;  // admission keeps this from happening
+    if (kb > 0) std::memcpy(sl.h_desc, items.data(), size_t(kb) * sizeof(BatchDesc));
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < k && e == cudaSuccess; ++j) {
         const Req &r = *sl.reqs[size_t(j)];
@@ -517,13 +522,21 @@ int rerun_one(pm_server *s, Slot &sl, Req &r, uint64_t *occ)
         rc = ensure_pws(sl, r.ws_bytes);
         if (rc == PM_OK) rc = launch_plain(s, r, occ, r.occ_cap, sl.d_nocc, sl.d_pws, sl.st);
     } else {
+        // split across CTAs when the parts' words fit the slot's workspace
         BatchInst I{r.set, r.text_blk, r.n, r.cnt_blk / 8, 0, r.occ_cap, 0};
-        const int64_t words = batch_fill(&I, 1, s->shape, sl.h_desc);
-        e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(BatchDesc), cudaMemcpyHostToDevice, sl.st);
+        std::vector<BatchDesc> items;
+        int64_t spill = 0;
+        int64_t words = batch_items(&I, 1, s->shape, true, items, &spill);
+        if (words + spill > sl.ws_words) {
+            items.assign(1, BatchDesc());
+            words = batch_fill(&I, 1, s->shape, items.data());
+        }
+        std::memcpy(sl.h_desc, items.data(), items.size() * sizeof(BatchDesc));
+        e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, items.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice, sl.st);
         if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
         uint8_t *base = s->arena.base();
-        rc = batch_launch_raw(sl.d_desc, 1, base, reinterpret_cast<int64_t *>(base), occ, sl.d_nocc,
-                              sl.d_ws, words, s->shape, true, sl.st);
+        rc = batch_launch_raw(sl.d_desc, int(items.size()), base, reinterpret_cast<int64_t *>(base), occ,
+                              sl.d_nocc, sl.d_ws, words, s->shape, true, sl.st);
     }
     if (rc) return rc;
     e = cudaMemcpyAsync(sl.h_nocc, sl.d_nocc, 8, cudaMemcpyDeviceToHost, sl.st);
@@ -722,11 +735,12 @@ int pm_server_create(const pm_server_params *params, pm_server **out)
         s->slots.push_back(sl);
         sl->ws_words = p.counter_words;
         e = cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_desc), size_t(p.max_batch) * sizeof(BatchDesc));
+        const size_t items = size_t(batch_items_bound(p.max_batch, s->shape));
+        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_desc), items * sizeof(BatchDesc));
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_nocc), size_t(p.max_batch) * 8);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_pstat), size_t(p.max_batch) * 4);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl->h_bstat), 4);
-        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&sl->d_desc), size_t(p.max_batch) * sizeof(BatchDesc));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&sl->d_desc), items * sizeof(BatchDesc));
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void **>(&sl->d_nocc), size_t(p.max_batch) * 8);
         if (e == cudaSuccess) e = cudaMalloc(&sl->d_ws, size_t(batch_ws_bytes(p.counter_words)));
         if (e != cudaSuccess) {

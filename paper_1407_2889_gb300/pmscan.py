@@ -318,15 +318,38 @@ def pm_set_get_info(h: int) -> dict:
     return {name: getattr(info, name) for name, _ in info._fields_}
 
 
+class _ResultOwner:
+    """Frees a pm_result once the last array viewing its buffers is gone."""
+
+    __slots__ = ("rp",)
+
+    def __init__(self, rp):
+        self.rp = rp
+
+    def __del__(self):
+        try:
+            lib().pm_result_free(self.rp)
+        except Exception:  # interpreter shutdown
+            pass
+
+
+def _view(ptr, n: int, ctype, dtype, owner) -> np.ndarray:
+    buf = (ctype * n).from_address(ctypes.addressof(ptr.contents))
+    buf._owner = owner
+    return np.frombuffer(buf, dtype=dtype)
+
+
 def _take_result(rp) -> tuple[np.ndarray, np.ndarray]:
+    """(occ, counts) arrays viewing the result's buffers, no copy: the
+    result is freed when both arrays (and every view of them) are gone."""
     r = rp.contents
     d, n_occ = r.d, r.n_occ
-    counts = np.ctypeslib.as_array(r.counts, shape=(d,)).copy() if d > 0 else np.zeros(0, np.int64)
+    owner = _ResultOwner(rp)
+    counts = _view(r.counts, d, ctypes.c_int64, np.int64, owner) if d > 0 else np.zeros(0, np.int64)
     if r.occ and n_occ > 0:
-        occ = np.ctypeslib.as_array(r.occ, shape=(n_occ,)).copy()
+        occ = _view(r.occ, n_occ, ctypes.c_uint64, np.uint64, owner)
     else:
         occ = np.zeros(0, dtype=np.uint64)
-    lib().pm_result_free(rp)
     return occ, counts
 
 

@@ -183,3 +183,24 @@ def test_results_outlive_the_server(base, sets):
     L.pm_result_free(rp)
     _same((occ, cnt), want, 0)
 
+
+
+@pytest.mark.parametrize("counter_words", [0, 30000])
+def test_large_requests_split_or_plain(base, sets, counter_words):
+    """Requests of several MiB among small ones: the batched launch splits
+    them across CTAs (parts staging their keys); with a small per-slot
+    workspace the ones whose words could not fit run as whole-GPU scans.
+    Either way every result equals the solo scan."""
+    reqs = _requests(40, 33, n_hi=1 << 16)
+    for j, (si, off, n) in enumerate([(2, 0, 8 << 20), (1, 1 << 20, 5 << 20), (4, 123, 3 << 20),
+                                      (0, 777, 2 << 20), (3, 4096, 6 << 20)]):
+        reqs.insert(3 * j, (si, off, n, j == 3))
+    solo = _solo(base, sets, reqs)
+    srv = pm.Server(budget_bytes=512 << 20, max_batch=32, max_inflight=2, counter_words=counter_words)
+    try:
+        got = _run_mixed(srv, base, sets, reqs, nthreads=2)
+        for j, (g, w) in enumerate(zip(got, solo)):
+            _same(g, w, j)
+        assert srv.stats()["completed"] == len(reqs)
+    finally:
+        srv.close()
