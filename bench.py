@@ -813,9 +813,13 @@ def serving_run(args, pinned, pm, torch, synth):
     # loop), so batches form while others run; sustained capacity
     ks = min(k, 3000)
 
+    # capacity configuration (a sweep of slots x batch size x warps on this
+    # workload): six stream slots, 16 warps per CTA, and a page-locked result
+    # pool that holds the keys of the batches in flight
+    sat_cfg = dict(budget_bytes=8 << 30, max_batch=256, max_inflight=6, warps=16, host_pool_bytes=6 << 30)
+
     def saturate(counts_only):
-        # a page-locked result pool that holds a whole batch's keys
-        sat = pm.Server(budget_bytes=8 << 30, max_batch=256, max_inflight=3, host_pool_bytes=6 << 30)
+        sat = pm.Server(**sat_cfg)
         for t in [sat.submit(q, pinned[j * big:(j + 1) * big]) for j, q in enumerate(sets)]:
             sat.wait(t)
         sat.reset_stats()
@@ -850,7 +854,8 @@ def serving_run(args, pinned, pm, torch, synth):
                       "peak_inflight": ss["peak_inflight"], "dispatch_busy_s": ss["dispatch_busy_s"],
                       "complete_busy_s": ss["complete_busy_s"],
                       "text_bytes": int(lens[:ks].sum()), "key_bytes": 8 * sat_keys,
-                      "key_gbs": 8 * sat_keys / sat_wall / 1e9},
+                      "key_gbs": 8 * sat_keys / sat_wall / 1e9,
+                      "server": {k_: v_ for k_, v_ in sat_cfg.items()}},
         "saturated_counts_only": {"requests": ks, "gbs": sat_co["gbs"], "wall_s": sat_co_wall,
                                   "mean_batch": sat_co["mean_batch"], "batches": sat_co["batches"],
                                   "p50_ms": sat_co["p50_us"] / 1e3, "p99_ms": sat_co["p99_us"] / 1e3},

@@ -197,6 +197,7 @@ struct Req {
     int status = PM_OK;
     bool done = false;
     pm_result *res = nullptr;
+    bool early = false;                // res is being filled by the batch's own copies
 };
 
 struct Slot {
@@ -412,6 +413,27 @@ int launch_slot(pm_server *s, Slot &sl)
         }
     }
     if (rc) return rc;
+    // results straight into page-locked host memory behind the kernels (the
+    // estimated capacity of keys), so a batch whose estimates hold needs no
+    // copy after it completes; without pool room the completion copies them
+    for (int j = 0; j < k && s->pool; ++j) {
+        Req &r = *sl.reqs[size_t(j)];
+        r.early = false;
+        const int64_t d = r.set->ac.d, cap = r.list ? r.occ_cap : 0;
+        void *pc = s->pool->get(d * 8);
+        void *po = r.list ? s->pool->get(std::max<int64_t>(cap, 1) * 8) : nullptr;
+        pm_result *res = (pc && (po || !r.list))
+                             ? make_result_owned(d, 0, static_cast<int64_t *>(pc), static_cast<uint64_t *>(po),
+                                                 &HostPool::release_result, s->pool)
+                             : nullptr;
+        if (!res) { HostPool::release_result(s->pool, pc, po); continue; }
+        e = cudaMemcpyAsync(res->counts, base + r.cnt_blk, size_t(r.cnt_bytes), cudaMemcpyDeviceToHost, sl.st);
+        if (e == cudaSuccess && cap > 0)
+            e = cudaMemcpyAsync(res->occ, base + r.occ_blk, size_t(cap) * 8, cudaMemcpyDeviceToHost, sl.st);
+        r.res = res;
+        if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
+        r.early = true;
+    }
     e = cudaMemcpyAsync(sl.h_nocc, sl.d_nocc, size_t(k) * 8, cudaMemcpyDeviceToHost, sl.st);
     if (e != cudaSuccess) { set_cuda_error(int(e)); return PM_ECUDA; }
     return PM_OK;
@@ -501,6 +523,9 @@ void dispatcher_main(pm_server *s)
             lk.lock();
             for (Req *r : free_slot->reqs) {
                 release(s, *r);  // nothing outside the arena before a re-run
+                if (r->res) pm_result_free(r->res);
+                r->res = nullptr;
+                r->early = false;
                 finish(s, *r, rc);
             }
             s->inflight_reqs -= int64_t(free_slot->reqs.size());
@@ -566,6 +591,9 @@ void complete_slot(pm_server *s, Slot &sl, std::unique_lock<std::mutex> &lk)
         // arena block, else a buffer of its own
         lk.lock();
         for (Req *r : over) {
+            if (r->res) pm_result_free(r->res);  // its early copy was too short
+            r->res = nullptr;
+            r->early = false;
             s->arena.free(r->occ_blk, r->occ_bytes);
             r->occ_bytes = r->n_occ * 8;
             r->occ_cap = r->n_occ;
@@ -589,6 +617,10 @@ void complete_slot(pm_server *s, Slot &sl, std::unique_lock<std::mutex> &lk)
     for (int j = 0; j < k; ++j) {
         Req &r = *sl.reqs[size_t(j)];
         if (rcs[size_t(j)] != PM_OK) continue;
+        if (r.early) {  // already in host memory
+            r.res->n_occ = r.n_occ;
+            continue;
+        }
         const int64_t d = r.set->ac.d, no = r.list ? r.n_occ : 0;
         void *pc = s->pool->get(d * 8);
         void *po = r.list ? s->pool->get(std::max<int64_t>(no, 1) * 8) : nullptr;
