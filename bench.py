@@ -495,6 +495,7 @@ def secondary(args, s, P, T, d_text, stream, launch, occ, counts, nocc, ws, pm, 
     out["ac_list_sweep"] = sweep
     out["large_sets"] = large_sets(T, d_text, stream, nocc, pm, torch, synth)
     out["wm_list_sweep"], out["pfac_list"] = other_methods(T, d_text, stream, nocc, pm, torch, synth)
+    out["two_characters"] = two_characters(T, d_text, stream, nocc, pm, torch, synth)
     out["mixed_lengths_list"] = mixed_lengths(T, d_text, stream, nocc, pm, torch, synth)
     out["small_uniform_1mib"] = small_case(stream, nocc, pm, torch, synth)
     return out
@@ -522,6 +523,48 @@ def _time_scan(pm, torch, h, d_text, n, d, stream, nocc, reps=2):
     dt = ev0.elapsed_time(ev1) / reps / 1e3
     del ws, buf
     return n / dt / 1e9, tot, dt
+
+
+def _time_counts(pm, torch, h, d_text, n, d, stream, nocc, reps=2):
+    """Counts-only GB/s of set h over n device bytes."""
+    cnt = torch.zeros(max(d, 1), dtype=torch.int64, device="cuda")
+    ws = torch.zeros(pm.pm_scan_workspace_bytes(h, n, pm.PM_COUNTS_ONLY), dtype=torch.uint8, device="cuda")
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        pm.pm_scan_device(h, d_text, n, pm.PM_COUNTS_ONLY, cnt, None, 0, nocc, ws, ws.numel(), stream)
+        ev0.record(stream)
+        for _ in range(reps):
+            pm.pm_scan_device(h, d_text, n, pm.PM_COUNTS_ONLY, cnt, None, 0, nocc, ws, ws.numel(), stream)
+        ev1.record(stream)
+    stream.synchronize()
+    assert pm.pm_scan_status(ws, stream) == pm.PM_OK
+    dt = ev0.elapsed_time(ev1) / reps / 1e3
+    return n / dt / 1e9
+
+
+def two_characters(T, d_text, stream, nocc, pm, torch, synth):
+    """One against two characters per table lookup (pm_params.stride) on
+    small ACGT sets (d, m) = (100, 8), (300, 12), (1000, 8): patterns half
+    copied from the text, half random (synth.mixed_patterns, seed 600+d),
+    full 1 GiB text, list and counts-only mode; fraction of the measured HBM
+    peak over the algorithmic bytes."""
+    n = T.size
+    peak = measured_peaks()[0]
+    out = {}
+    for d, m in ((100, 8), (300, 12), (1000, 8)):
+        P = synth.mixed_patterns(T, d, m, 600 + d)
+        row = {}
+        for stride in (1, 2):
+            q = pm.PatternSet.ac(P, {"stride": stride})
+            gbs, tot, dt = _time_scan(pm, torch, q.h, d_text, n, d, stream, nocc, reps=3)
+            cgbs = _time_counts(pm, torch, q.h, d_text, n, d, stream, nocc, reps=3)
+            row[f"stride{stride}"] = {"list_gbs": gbs, "counts_gbs": cgbs, "n_occ": tot,
+                                      "list_alg_frac": (n + 8 * tot + 8 * d) / dt / 1e9 / peak,
+                                      "counts_alg_frac": cgbs * (n + 8 * d) / n / peak}
+            q.close()
+        out[f"d{d}_m{m}"] = row
+    return out
 
 
 def mixed_lengths(T, d_text, stream, nocc, pm, torch, synth):
@@ -722,12 +765,28 @@ def batched_comparison(args, T, d_text, pm, torch, synth):
     t_plain_host = time.perf_counter() - t0
     same = bool(torch.equal(counts_p, counts_b)) and bool(torch.equal(nocc_p, b.n_occ[:k]))
     same = same and bool(torch.equal(occ_p, b.occ))
+    del ws, counts_p, occ_p
+    # the plain kernel's steady rate on these sets: every 64th instance's set
+    # scanned over the first 64 MiB of the text (launch costs amortised),
+    # weighted by the instance's length
+    sample = list(range(0, k, max(1, k // 64)))
+    span = min(64 << 20, T.size)
+    nocc1 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    t_est = 0.0
+    for j in sample:
+        gbs_j, _, _ = _time_scan(pm, torch, sets[j].h, d_text, span, int(dd[j]), stream, nocc1, reps=2)
+        t_est += float(ln[j]) / (gbs_j * 1e9)
+    plain_steady_gbs = float(ln[sample].sum()) / t_est / 1e9
     out = {
         "k": k, "text_bytes": total_bytes, "n_occ": int(n_occ.sum()),
         "batched_gbs": total_bytes / t_batch / 1e9, "batched_ms": t_batch * 1e3,
         "plain_graph_gbs": total_bytes / t_plain / 1e9, "plain_graph_ms": t_plain * 1e3,
         "plain_host_loop_ms": t_plain_host * 1e3,
         "speedup_vs_plain_graph": t_plain / t_batch, "identical_results": same,
+        "plain_steady_gbs": plain_steady_gbs,
+        "batched_vs_plain_steady": (total_bytes / t_batch / 1e9) / plain_steady_gbs,
+        "plain_steady_sample": f"{len(sample)} sets (every {max(1, k // 64)}th instance), each over the first "
+                               f"{span >> 20} MiB of the text, list mode, weighted by instance length",
         "tuned_warps": warps, "tune_best_ms": tuned_ms, "compile_s": t_compile,
         "workload": "k slices of the EST-shaped text, lengths log-uniform 1 KiB-4 MiB (seed 4000+j), "
                     "own set per instance: d log-uniform 10-10^4, m uniform 8-64, list mode",

@@ -291,8 +291,11 @@ int pm_noalloc_scan_status(void *stream);
  * the planner accepts over table placement (shared memory / hybrid prefix),
  * warps per CTA (auto, 16, 12, 8), per-terminal counters (32-bit or 16-bit
  * in shared memory, or device memory) and the terminal-id structure (shared
- * or device memory), plus the two-character scan (stride 2) when the set
- * qualifies, and keeps the fastest for the set: later scans use it.
+ * or device memory, or late: codes and counts taken by the expand kernel in
+ * list mode), plus the two-character scan (stride 2) when the set
+ * qualifies, and keeps the fastest for the set: later scans use it. In list
+ * mode, late plans that differ only in their counters count as one, and the
+ * one kept has the counters that fit best for counts-only scans.
  * Results never depend on the plan. Allocates its own scratch, synchronises
  * `stream`. *best_out / *best_ms (may be NULL) receive the chosen pm_params
  * and its time per scan. PM_EINVAL for sets other than Aho-Corasick (PFAC,

@@ -376,6 +376,7 @@ struct BatchDesc {                 // one instance, in processing order
     int smem_entries, eb, m, nwords, nterms, d;
     int ids_off, hist_off;         // byte offsets in the CTA's table region; -1 = global
     uint32_t mid_base, lut, pad, pre;  // pre: DevAc::pre of the set
+    int resident;                  // the whole table is in the CTA's shared memory
     // A large instance is split into parts, one queue item each: the part
     // scans warp tiles [t_lo, t_hi) of the instance. Parts add their counts
     // into the instance's device counters (ccount_off), publish their output

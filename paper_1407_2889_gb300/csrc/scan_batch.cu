@@ -35,7 +35,9 @@ using namespace acdev;
 constexpr int kBatchHV = 4;                   // halo vectors: m <= 65
 constexpr int kBatchNV = 5 + kBatchHV;
 constexpr int kBatchBuf = kWarpTile + 16 * kBatchHV;
-constexpr int kBatchPool = 40;
+constexpr int kBatchPool = 40;                  // hit pool slots per lane, u16 entries
+// the pool is kBatchPool + 1 u16 slots per lane; u32 instances get half as many
+constexpr int kBatchPoolBytes = (kBatchPool + 1) * 32 * 2;
 constexpr int kBatchStage = 128;              // u64 entries
 constexpr int kBatchMaxM = 16 * kBatchHV + 1;
 
@@ -57,7 +59,7 @@ __host__ __device__ constexpr long long rr16(long long x) { return (x + 15) & ~1
 
 __host__ __device__ inline long long batch_warp_bytes()
 {
-    return 16 + rr16(kBatchBuf) + rr16((long long)(kBatchPool + 1) * 32 * 4) + kBatchStage * 8;
+    return 16 + rr16(kBatchBuf) + rr16(kBatchPoolBytes) + kBatchStage * 8;
 }
 
 __device__ __forceinline__ int bstage_bytes(const uint8_t *text, long long n, long long t)
@@ -85,8 +87,9 @@ struct CtaSmem {
     unsigned long long *stage;
 };
 
-// One instance, entry type E. All threads of the CTA call it.
-template <typename E, bool PRE>
+// One instance, entry type E; HYB when the table is not wholly in shared
+// memory. All threads of the CTA call it.
+template <typename E, bool PRE, bool HYB>
 __device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSmem &S,
                              uint32_t &phase, bool &failed)
 {
@@ -129,9 +132,9 @@ __device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSm
         for (int i = threadIdx.x; i < D.nterms; i += blockDim.x) s_hist[i] = 0u;
     __syncthreads();
 
-    const TableRef<E, true> tab{s_tab, reinterpret_cast<const E *>(D.table), uint32_t(D.smem_entries)};
+    const TableRef<E, HYB> tab{s_tab, reinterpret_cast<const E *>(D.table), uint32_t(D.smem_entries)};
     E *pl = reinterpret_cast<E *>(S.pool) + lane;
-    const uint32_t cap = kBatchPool;
+    const uint32_t cap = kBatchPoolBytes / (32 * sizeof(E)) - 1;  // the last slot absorbs overflow
     const int m = D.m;
     const bool split = D.nparts > 1;
     auto count_terminal = [&](uint32_t c) {
@@ -432,7 +435,7 @@ __global__ void __launch_bounds__(512, 1) ac_batch_kernel(const BatchArgs a)
     S.bar = reinterpret_cast<uint64_t *>(p);
     S.buf = p + 16;
     S.pool = S.buf + rr16(kBatchBuf);
-    S.stage = reinterpret_cast<unsigned long long *>(S.pool + rr16((long long)(kBatchPool + 1) * 32 * 4));
+    S.stage = reinterpret_cast<unsigned long long *>(S.pool + rr16(kBatchPoolBytes));
     S.s_tot = s_tot;
     (void)W;
     if (lane == 0) dev::mbar_init(S.bar, 1);
@@ -452,12 +455,19 @@ __global__ void __launch_bounds__(512, 1) ac_batch_kernel(const BatchArgs a)
         __syncthreads();
         if (j < 0) break;
         const BatchDesc D = a.desc[j];
+        // u16 tables wholly in shared memory skip the bounds check of every
+        // lookup; u32 tables are always partly in device memory
         if (D.eb == 2) {
-            if (D.pre) run_instance<uint16_t, true>(a, D, S, phase, failed);
-            else run_instance<uint16_t, false>(a, D, S, phase, failed);
+            if (D.resident) {
+                if (D.pre) run_instance<uint16_t, true, false>(a, D, S, phase, failed);
+                else run_instance<uint16_t, false, false>(a, D, S, phase, failed);
+            } else {
+                if (D.pre) run_instance<uint16_t, true, true>(a, D, S, phase, failed);
+                else run_instance<uint16_t, false, true>(a, D, S, phase, failed);
+            }
         } else {
-            if (D.pre) run_instance<uint32_t, true>(a, D, S, phase, failed);
-            else run_instance<uint32_t, false>(a, D, S, phase, failed);
+            if (D.pre) run_instance<uint32_t, true, true>(a, D, S, phase, failed);
+            else run_instance<uint32_t, false, true>(a, D, S, phase, failed);
         }
     }
 }
@@ -548,6 +558,7 @@ static void fill_desc(const BatchInst &I, const InstLayout &L, long long coff, B
     D.grp_ids = dv.grp_ids;
     D.eb = t.entry_bytes;
     D.smem_entries = L.smem_entries;
+    D.resident = L.smem_entries >= ((long long)t.n_rows << t.lw) ? 1 : 0;
     D.ids_off = L.ids_off;
     D.hist_off = L.hist_off;
     D.m = t.m;

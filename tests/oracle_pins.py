@@ -46,7 +46,9 @@ def _all_routes(T, P, lib, B=None):
     out = [("brute",) + oracle.brute(T, P, lib=lib),
            ("dict1",) + oracle.dictionary(T, P, threads=1, lib=lib),
            ("dict3",) + oracle.dictionary(T, P, threads=3, lib=lib),
-           ("ac",) + oracle.ac_search(T, P, lib=lib)]
+           ("ac",) + oracle.ac_search(T, P, lib=lib),
+           ("dfa1",) + oracle.ac_dfa_scan(T, P, threads=1, lib=lib),
+           ("dfa3",) + oracle.ac_dfa_scan(T, P, threads=3, lib=lib)]
     for b in ([B] if B else sorted({1, min(2, m), min(3, m)})):
         out.append((f"wm{b}",) + oracle.wm_search(T, P, b, min(2, m), lib=lib))
     return out

@@ -33,6 +33,9 @@ MUTANTS = [
      "if (a->out_tail[a->nstates - 1] < 0) a->out_head[a->nstates - 1] = i;\n        else a->out_next[a->out_tail[a->nstates - 1]] = i;\n        a->out_tail[a->nstates - 1] = i;"),
     ("wm_block_b_plus_one", "int64_t h = orc_wm_h(p + (q - B), B);", "int64_t h = orc_wm_h(p + (q - B - 1 >= 0 ? q - B - 1 : 0), B);"),
     ("wm_shift_init_too_big", "w->shift[h] = m - B + 1;", "w->shift[h] = m - B + 2;"),
+    ("dfa_piece_without_overlap", "int64_t end = jb->i1 + m - 1;", "int64_t end = jb->i1;"),
+    ("dfa_goto_without_supply", "? dfa[(int64_t)a->supply[q] * ncls + c] : t;", "? 0 : t;"),
+    ("dfa_start_off_by_one", "jb->buf[jb->len++] = ORC_OCC(e - m + 1, r);", "jb->buf[jb->len++] = ORC_OCC(e - m, r);"),
     ("wm_overshift", "i += w->shift[h];", "i += w->shift[h] + 1;"),
     ("wm_prefix_wrong_window", "int64_t hp = orc_wm_h(T + (i - m + 1), Bp);", "int64_t hp = orc_wm_h(T + (i - m + 2 <= i ? i - m + 2 : i), Bp);"),
     ("wm_hash_bitshift_3", "for (int32_t k = 0; k < len; k++) h = (h << 2) + s[k];", "for (int32_t k = 0; k < len; k++) h = (h << 3) + s[k];"),

@@ -86,6 +86,29 @@ def test_noalloc_on_a_set_tuned_to_two_characters_per_lookup():
     s.close()
 
 
+@pytest.mark.parametrize("flags", [0, pm.PM_COUNTS_ONLY])
+def test_noalloc_on_a_late_ids_plan(flags):
+    """A plan with late terminal ids (the expand kernel maps ids to codes and
+    counts them, with its own finished-CTA counter in the array's header):
+    two calls in a row equal the regular scan."""
+    T = synth.est_text(8 << 20, 41)
+    P = synth.mixed_patterns(T, 2000, 8, 41)
+    P = np.concatenate([P, P[:9], P[:3]])  # groups of two and three
+    d = P.shape[0]
+    s = pm.PatternSet.ac(P, {"ids_place": 3})
+    d_text = torch.from_numpy(T).cuda()
+    cap = T.size // 4
+    want = _regular(s, d_text, T.size, flags, d, cap)
+    assert want[2] > 0
+    for call in range(2):
+        got = _noalloc(s, d_text, T.size, flags, d, cap)
+        assert got[2] == want[2], f"call {call}: total"
+        assert np.array_equal(got[1], want[1]), f"call {call}: counts"
+        if not flags & pm.PM_COUNTS_ONLY:
+            assert np.array_equal(got[0], want[0]), f"call {call}: occurrences"
+    s.close()
+
+
 def test_noalloc_rejects_a_scan_larger_than_its_scratch():
     P = synth.random_patterns(100, 8, 5)
     s = pm.PatternSet.ac(P)
