@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
             inflight = true;
         }
 
-        // ---- walk: branch-free recording of match steps --------------------
+        // ---- walk: a step that enters a terminal stores its table index ----
         const long long g0 = tile0 + (long long)lane * kChunk;
         int steps = kChunk + m - 1;
         if (!DNA) {
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
         // pool slot `cap` absorbs the stores of an overflowing lane
         auto rec = [&](int step, uint32_t idx, uint32_t e) {
             const uint32_t h = e & 1u;
-            pl[kslot * 32] = E(idx);  // the match-row base is subtracted when resolving
+            if (h) pl[kslot * 32] = E(idx);  // the match-row base is subtracted when resolving
             kslot = min(kslot + h, cap);
             hw[step >> 5] += h << (step & 31);
         };

@@ -204,7 +204,7 @@ __device__ void run_instance(const BatchArgs &a, const BatchDesc &D, const CtaSm
                     uint32_t kslot = 0;
                     auto rec = [&](int step, uint32_t idx, uint32_t e) {
                         const uint32_t h = e & 1u;
-                        pl[kslot * 32] = E(idx - D.mid_base);
+                        if (h) pl[kslot * 32] = E(idx - D.mid_base);
                         kslot = min(kslot + h, cap);
                         hw[step >> 5] |= h << (step & 31);
                     };
