@@ -658,7 +658,7 @@ int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t
     cand.push_back(s->params);
     cand.back().stride = 1;
     for (int place : {PM_PLACE_AUTO, PM_PLACE_HYBRID})
-        for (int w : {0, 16, 12, 8})
+        for (int w : {0, 24, 20, 16, 12, 8})
             for (int c : {0, 1, 2, 3})
                 for (int idp : {0, 1, 2, 3}) {
                     pm_params p = s->params;
@@ -682,11 +682,18 @@ int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t
         // first one tried (automatic counters: the best that fit for counts
         // mode) is kept
         const bool late_list = list && plan.ids_smem == 2;
-        for (const Tried &x : tried)
-            dup = dup || (x.plan.warps == plan.warps &&
-                          (x.plan.hist_smem == plan.hist_smem || (late_list && x.plan.ids_smem == 2)) &&
+        for (const Tried &x : tried) {
+            if (late_list && x.plan.ids_smem == 2) {  // only the list-mode launch matters
+                dup = dup || (x.plan.warps_list == plan.warps_list && x.plan.variant_list == plan.variant_list &&
+                              x.plan.smem_entries == plan.smem_entries);
+                continue;
+            }
+            dup = dup || (x.plan.warps == plan.warps && x.plan.warps_list == plan.warps_list &&
+                          x.plan.variant_list == plan.variant_list &&
+                          x.plan.hist_smem == plan.hist_smem &&
                           x.plan.ids_smem == plan.ids_smem && x.plan.smem_entries == plan.smem_entries &&
                           x.plan.variant == plan.variant && x.plan.ctas_per_sm == plan.ctas_per_sm);
+        }
         if (dup) continue;
         auto run = [&]() {
             return ac_launch(t, plan, d_text, n, list, static_cast<int64_t *>(counts),

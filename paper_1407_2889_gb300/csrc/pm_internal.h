@@ -199,7 +199,10 @@ struct DevAc {
     int32_t variant = 0;            // kernel instance id
     int32_t pre = 0;                // ACGT table stored on the device as (next_row << 2) | match
     int64_t smem_bytes = 0;
-    int64_t smem_bytes_list = 0;    // list mode (smaller with late ids: no counters)
+    // list mode; with late ids its layout has no counters, so it may run more
+    // warps than counts mode (warps, variant and smem_bytes above)
+    int32_t warps_list = 0, variant_list = 0;
+    int64_t smem_bytes_list = 0;
     int32_t placement = 0;
     int64_t max_warps = 0;          // warps in the largest grid a launch uses
 };

@@ -145,8 +145,10 @@ __device__ __forceinline__ void stage_issue(const AcArgs &a, long long t, uint8_
     if (bytes > 0) dev::tma_load_1d(buf, a.text + t * kWarpTile, uint32_t(bytes), bar);
 }
 
-template <typename E, int NV, int HV, bool DNA, bool HYB, bool PRE, bool LATE>
-__global__ void __launch_bounds__(512, 1) ac_scan_kernel(const AcArgs a)
+// MAXT: the launch bound, 512 threads (up to 128 registers) or 768 (up to
+// 85, for whole-table plans of more than 16 warps)
+template <typename E, int NV, int HV, bool DNA, bool HYB, bool PRE, bool LATE, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int BUF = kWarpTile + 16 * HV;
@@ -941,40 +943,59 @@ struct Variant {
 // late-ids forms of the five ACGT groups (18-32); within each group HV = 1,
 // 2, 4.
 const Variant kVariants[] = {
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, false>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, false>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, false>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, true, false, false>, 2, 1, true, true},
-    {ac_scan_kernel<uint16_t, 7, 2, true, true, false, false>, 2, 2, true, true},
-    {ac_scan_kernel<uint16_t, 9, 4, true, true, false, false>, 2, 4, true, true},
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, false>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, false>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, false>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, true, true, false>, 2, 1, true, true},
-    {ac_scan_kernel<uint16_t, 7, 2, true, true, true, false>, 2, 2, true, true},
-    {ac_scan_kernel<uint16_t, 9, 4, true, true, true, false>, 2, 4, true, true},
-    {ac_scan_kernel<uint32_t, 6, 1, true, true, true, false>, 4, 1, true, true},
-    {ac_scan_kernel<uint32_t, 7, 2, true, true, true, false>, 4, 2, true, true},
-    {ac_scan_kernel<uint32_t, 9, 4, true, true, true, false>, 4, 4, true, true},
-    {ac_scan_kernel<uint32_t, 6, 1, false, true, false, false>, 4, 1, false, true},
-    {ac_scan_kernel<uint32_t, 7, 2, false, true, false, false>, 4, 2, false, true},
-    {ac_scan_kernel<uint32_t, 9, 4, false, true, false, false>, 4, 4, false, true},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, false, 512>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, false, 512>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, false, 512>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, false, false, 512>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, false, false, 512>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, false, false, 512>, 2, 4, true, true},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, false, 512>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, false, 512>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, false, 512>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, true, false, 512>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, true, false, 512>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, true, false, 512>, 2, 4, true, true},
+    {ac_scan_kernel<uint32_t, 6, 1, true, true, true, false, 512>, 4, 1, true, true},
+    {ac_scan_kernel<uint32_t, 7, 2, true, true, true, false, 512>, 4, 2, true, true},
+    {ac_scan_kernel<uint32_t, 9, 4, true, true, true, false, 512>, 4, 4, true, true},
+    {ac_scan_kernel<uint32_t, 6, 1, false, true, false, false, 512>, 4, 1, false, true},
+    {ac_scan_kernel<uint32_t, 7, 2, false, true, false, false, 512>, 4, 2, false, true},
+    {ac_scan_kernel<uint32_t, 9, 4, false, true, false, false, 512>, 4, 4, false, true},
 
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, true>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, true>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, true>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, true, false, true>, 2, 1, true, true},
-    {ac_scan_kernel<uint16_t, 7, 2, true, true, false, true>, 2, 2, true, true},
-    {ac_scan_kernel<uint16_t, 9, 4, true, true, false, true>, 2, 4, true, true},
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, true>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, true>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, true>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, true, true, true>, 2, 1, true, true},
-    {ac_scan_kernel<uint16_t, 7, 2, true, true, true, true>, 2, 2, true, true},
-    {ac_scan_kernel<uint16_t, 9, 4, true, true, true, true>, 2, 4, true, true},
-    {ac_scan_kernel<uint32_t, 6, 1, true, true, true, true>, 4, 1, true, true},
-    {ac_scan_kernel<uint32_t, 7, 2, true, true, true, true>, 4, 2, true, true},
-    {ac_scan_kernel<uint32_t, 9, 4, true, true, true, true>, 4, 4, true, true},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, true, 512>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, true, 512>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, true, 512>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, false, true, 512>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, false, true, 512>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, false, true, 512>, 2, 4, true, true},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, true, 512>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, true, 512>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, true, 512>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, true, true, true, 512>, 2, 1, true, true},
+    {ac_scan_kernel<uint16_t, 7, 2, true, true, true, true, 512>, 2, 2, true, true},
+    {ac_scan_kernel<uint16_t, 9, 4, true, true, true, true, 512>, 2, 4, true, true},
+    {ac_scan_kernel<uint32_t, 6, 1, true, true, true, true, 512>, 4, 1, true, true},
+    {ac_scan_kernel<uint32_t, 7, 2, true, true, true, true, 512>, 4, 2, true, true},
+    {ac_scan_kernel<uint32_t, 9, 4, true, true, true, true, 512>, 4, 4, true, true},
+};
+
+// More than 16 warps per CTA: u16 ACGT tables wholly in shared memory, the
+// groups 0 and 2 above, then their late-ids forms (6 and 8); HV = 1, 2, 4.
+constexpr int kWideWarps = 24;
+constexpr int kWideBase = 100;
+const Variant kWideVariants[] = {
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, false, 768>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, false, 768>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, false, 768>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, false, 768>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, false, 768>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, false, 768>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, true, 768>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, true, 768>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, true, 768>, 2, 4, true, false},
+    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, true, 768>, 2, 1, true, false},
+    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, true, 768>, 2, 2, true, false},
+    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, true, 768>, 2, 4, true, false},
 };
 
 int hv_for_m(int m)
@@ -1018,7 +1039,11 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     const long long budget = (long long)dp.smem_optin - 1024;
     const int pool_cap = 40;
     const int place = opt.placement;
-    const int forced_warps = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, 16) : 0;
+    // more than 16 warps: the 768-thread kernels of u16 ACGT tables wholly in
+    // shared memory (one CTA per SM)
+    const bool wide_ok = t.dna && eb == 2 && !t.goto_only && (opt.ctas_per_sm <= 1);
+    const int max_w = wide_ok ? kWideWarps : 16;
+    const int forced_warps = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, max_w) : 0;
     dev.pool_cap = pool_cap;
     dev.hv = hv;
     dev.nv = 5 + hv;
@@ -1041,6 +1066,7 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     };
 
     Layout best{0, 0, 0, 0};
+    Layout list_layout{0, 0, 0, 0};
     bool chosen = false;
     if ((place == PM_PLACE_AUTO || place == PM_PLACE_SMEM) &&
         (opt.smem_table_bytes <= 0 || entries * eb <= opt.smem_table_bytes)) {
@@ -1054,21 +1080,27 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
             for (int o = 0; o < 7 && !chosen; ++o) {
                 const int ids = ids_hist[o][0], hist = ids_hist[o][1];
                 if (!ids_ok(ids) || (hist >= 0 && !hist_ok(hist))) continue;
-                const int hi = forced_warps ? forced_warps : 16;
+                const int hi = forced_warps ? forced_warps : max_w;
                 const int lo = forced_warps ? forced_warps : minw;
                 for (int w = hi; w >= lo && !chosen; --w) {
                     Layout L{entries, w, hist < 0 ? 0 : hist, ids};
                     if (!fits(L)) continue;
-                    if (hist < 0) {  // counts-mode counters on top of the list layout
+                    Layout C = L;
+                    if (hist < 0) {
+                        // counts mode: the most warps (down to lo) that still
+                        // hold shared counters, else the list layout with
+                        // device counters
                         bool any = false;
-                        for (int h : {1, 2, 0}) {
-                            Layout C = L;
-                            C.hist = h;
-                            if (hist_ok(h) && fits(C)) { L = C; any = true; break; }
-                        }
+                        for (int wc = w; wc >= lo && !any; --wc)
+                            for (int h : {1, 2}) {
+                                Layout D{entries, wc, h, ids};
+                                if (hist_ok(h) && fits(D)) { C = D; any = true; break; }
+                            }
+                        if (!any && hist_ok(0)) { C.hist = 0; any = true; }
                         if (!any) continue;
                     }
-                    best = L;
+                    best = C;
+                    list_layout = L;
                     chosen = true;
                 }
             }
@@ -1079,7 +1111,7 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     }
     if (!chosen) {
         // hybrid / global: breadth-first prefix of rows in shared memory
-        const int w = forced_warps ? forced_warps : 16;
+        const int w = forced_warps ? std::min(forced_warps, 16) : 16;
         // counters / ids only when pinned by pm_params (the table prefix
         // gets the room otherwise)
         Layout L{0, w, opt.counters == 1 ? 1 : opt.counters == 2 ? 2 : 0,
@@ -1096,6 +1128,8 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
         if (se > entries) se = entries;
         L.smem_entries = se;
         best = L;
+        list_layout = L;
+        list_layout.hist = L.ids == 2 ? 0 : L.hist;
         dev.placement = place == PM_PLACE_GLOBAL ? PM_PLACE_GLOBAL : PM_PLACE_HYBRID;
     }
     dev.warps = best.warps;
@@ -1111,12 +1145,19 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     else if (eb == 4) group = 4;
     else group = (hyb ? 1 : 0) + (dev.pre ? 2 : 0);
     if (best.ids == 2) group += 6;   // late ids (ACGT groups only)
-    dev.variant = group * 3 + hv_slot(hv);
+    // variant ids >= kWideBase index kWideVariants (groups 0, 2, 6, 8)
+    auto variant_for = [&](int warps) {
+        if (warps <= 16) return group * 3 + hv_slot(hv);
+        const int wg = (group >= 6 ? 2 : 0) + ((group % 6) == 2 ? 1 : 0);
+        return kWideBase + wg * 3 + hv_slot(hv);
+    };
+    dev.variant = variant_for(best.warps);
     dev.smem_bytes = ac_smem_bytes(t, eb, best, hv, pool_cap);
-    Layout LL = best;
-    if (best.ids == 2) LL.hist = 0;
-    dev.smem_bytes_list = ac_smem_bytes(t, eb, LL, hv, pool_cap);
-    dev.max_warps = (long long)dp.sm_count * dev.ctas_per_sm * dev.warps;
+    if (list_layout.warps == 0) list_layout = best;
+    dev.warps_list = list_layout.warps;
+    dev.variant_list = variant_for(list_layout.warps);
+    dev.smem_bytes_list = ac_smem_bytes(t, eb, list_layout, hv, pool_cap);
+    dev.max_warps = (long long)dp.sm_count * dev.ctas_per_sm * std::max(dev.warps, dev.warps_list);
     return PM_OK;
 }
 
@@ -1172,10 +1213,13 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
         return PM_OK;
     }
 
-    const AcKernel fn = pfac ? pfac_kernel_for(t, dv) : kVariants[dv.variant].fn;
-    // late ids: list mode drops the counters from shared memory
+    // list mode has its own layout (with late ids: no counters, maybe more warps)
     const bool late = list && !pfac && dv.ids_smem == 2;
-    const long long smem = late ? dv.smem_bytes_list : dv.smem_bytes;
+    const int var = list ? dv.variant_list : dv.variant;
+    const int warps = list ? dv.warps_list : dv.warps;
+    const AcKernel fn = pfac ? pfac_kernel_for(t, dv)
+                             : var >= kWideBase ? kWideVariants[var - kWideBase].fn : kVariants[var].fn;
+    const long long smem = list ? dv.smem_bytes_list : dv.smem_bytes;
     rc = kernel_smem_attr(reinterpret_cast<const void *>(fn), smem);
     if (rc) return rc;
     AcArgs a;
@@ -1221,12 +1265,12 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     a.seg_tiles = seg_tiles;
     a.slots = w + L.slots;
 
-    const int threads = dv.warps * 32;
+    const int threads = warps * 32;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, size_t(smem));
     if (e != cudaSuccess || per_sm < 1) { set_cuda_error(int(e)); return PM_ECUDA; }
     long long grid = (long long)dp.sm_count * std::min(per_sm, dv.ctas_per_sm);
-    const long long want = (nsub + dv.warps - 1) / dv.warps;
+    const long long want = (nsub + warps - 1) / warps;
     if (want < grid) grid = want;
     if (grid < 1) grid = 1;
     fn<<<dim3(unsigned(grid)), dim3(unsigned(threads)), size_t(smem), st>>>(a);

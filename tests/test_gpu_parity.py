@@ -541,3 +541,33 @@ def test_late_ids_large_set_and_hot_terminal():
     assert np.array_equal(occ.cpu().numpy().view(np.uint64), want[0][:cap])
     assert np.array_equal(counts.cpu().numpy(), want[1])
     s.close()
+
+
+@pytest.mark.parametrize("kw", [{"warps_per_cta": 24}, {"warps_per_cta": 20}, {"warps_per_cta": 17},
+                                {"warps_per_cta": 24, "ids_place": 3}, {"warps_per_cta": 22, "ids_place": 3},
+                                {"ids_place": 3}, {"warps_per_cta": 24, "counters": 2}])
+def test_more_than_16_warps(kw):
+    """Plans of more than 16 warps per CTA (the 768-thread kernels of u16
+    ACGT tables wholly in shared memory), with late ids too, whose counts
+    mode may use fewer warps than list mode: list, counts-only and a short
+    capacity equal the oracle; a run of one letter fills every pool."""
+    T = synth.est_text(6 << 20, 43).copy()
+    T[1_000_000:1_040_000] = ord("A")
+    P = synth.mixed_patterns(T, 1500, 9, 43)
+    P = np.concatenate([P, P[:11], np.full((2, 9), ord("A"), np.uint8)])
+    want = oracle.dictionary(T, P, threads=THREADS)
+    s = _ac(P, **kw)
+    assert s.info()["placement"] == pm.PM_PLACE_SMEM
+    _same(s.scan(T), want, f"{kw}")
+    _same(s.scan(T, counts_only=True), (np.zeros(0, np.uint64), want[1]), f"{kw} counts")
+    d = torch.from_numpy(T).cuda()
+    cap = want[0].size // 3
+    counts = torch.zeros(P.shape[0], dtype=torch.int64, device="cuda")
+    occ = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    nocc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws = torch.zeros(s.workspace_bytes(T.size), dtype=torch.uint8, device="cuda")
+    pm.pm_scan_device(s.h, d, T.size, 0, counts, occ, cap, nocc, ws, ws.numel(), None)
+    assert pm.pm_scan_status(ws, None) == pm.PM_OK
+    assert int(nocc.item()) == want[0].size
+    assert np.array_equal(occ.cpu().numpy().view(np.uint64), want[0][:cap])
+    s.close()
