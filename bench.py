@@ -881,20 +881,27 @@ def serving_run(args, pinned, pm, torch, synth):
     # pool that holds the keys of the batches in flight
     sat_cfg = dict(budget_bytes=8 << 30, max_batch=256, max_inflight=6, warps=16, host_pool_bytes=6 << 30)
 
-    def saturate(counts_only):
+    def saturate(counts_only, reps=5):
+        # one warmed-up server, the 3000 requests queued at once `reps`
+        # times; the run with the median rate is reported, with the spread
         sat = pm.Server(**sat_cfg)
         for t in [sat.submit(q, pinned[j * big:(j + 1) * big]) for j, q in enumerate(sets)]:
             sat.wait(t)
-        sat.reset_stats()
-        t0 = time.perf_counter()
-        tk = [sat.submit(sets[which[j]], pinned[offs[j]:offs[j] + lens[j]], counts_only=counts_only)
-              for j in range(ks)]
-        keys = 0
-        for t in tk:
-            keys += int(sat.wait(t)[0].size)
-        wall_ = time.perf_counter() - t0
-        st_ = sat.stats()
+        runs = []
+        for _ in range(reps):
+            sat.reset_stats()
+            t0 = time.perf_counter()
+            tk = [sat.submit(sets[which[j]], pinned[offs[j]:offs[j] + lens[j]], counts_only=counts_only)
+                  for j in range(ks)]
+            keys = 0
+            for t in tk:
+                keys += int(sat.wait(t)[0].size)
+            runs.append((sat.stats(), time.perf_counter() - t0, keys))
         sat.close()
+        runs.sort(key=lambda r: r[0]["gbs"])
+        st_, wall_, keys = runs[len(runs) // 2]
+        st_ = dict(st_)
+        st_["gbs_runs"] = [round(r[0]["gbs"], 2) for r in runs]
         return st_, wall_, keys
 
     ss, sat_wall, sat_keys = saturate(False)
@@ -917,9 +924,10 @@ def serving_run(args, pinned, pm, torch, synth):
                       "peak_inflight": ss["peak_inflight"], "dispatch_busy_s": ss["dispatch_busy_s"],
                       "complete_busy_s": ss["complete_busy_s"],
                       "text_bytes": int(lens[:ks].sum()), "key_bytes": 8 * sat_keys,
-                      "key_gbs": 8 * sat_keys / sat_wall / 1e9,
+                      "key_gbs": 8 * sat_keys / sat_wall / 1e9, "gbs_runs": ss["gbs_runs"],
                       "server": {k_: v_ for k_, v_ in sat_cfg.items()}},
         "saturated_counts_only": {"requests": ks, "gbs": sat_co["gbs"], "wall_s": sat_co_wall,
+                                  "gbs_runs": sat_co["gbs_runs"],
                                   "mean_batch": sat_co["mean_batch"], "batches": sat_co["batches"],
                                   "p50_ms": sat_co["p50_us"] / 1e3, "p99_ms": sat_co["p99_us"] / 1e3},
         "workload": "Poisson 2000 req/s; text log-uniform 1 KiB-16 MiB slices of the pinned EST text (H2D and D2H "
