@@ -34,7 +34,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "text GB/s scanned on 1 GB300 (AC & WM), batched vs plain; % of HBM roofline"
-KERNEL_SOURCES = ["paper_1407_2889_gb300/csrc/scan_ac.cu", "paper_1407_2889_gb300/csrc/ac_device.cuh",
+KERNEL_SOURCES = ["paper_1407_2889_gb300/csrc/scan_ac.cu", "paper_1407_2889_gb300/csrc/scan_ac_wide.cu",
+                  "paper_1407_2889_gb300/csrc/ac_scan_kernel.cuh", "paper_1407_2889_gb300/csrc/ac_device.cuh",
                   "paper_1407_2889_gb300/csrc/scan_common.cuh"]
 
 

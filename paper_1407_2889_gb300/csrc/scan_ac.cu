@@ -19,20 +19,24 @@
 // entries all lead to the root.
 //
 // The walk records, without branches, a bit per step that entered a
-// terminal state and the table index of that transition (pool, shared
-// memory). Afterwards each match is resolved to its terminal's canonical id
-// (the rank of its table entry among match entries, from a bitmap with
-// prefix counts) and to the pattern code, and per-terminal counters are
-// bumped; the last CTA turns them into counts[r].
+// terminal state, and the table index of such a step in the lane's hit pool
+// (shared memory). Afterwards each match is resolved to its terminal's
+// canonical id (the rank of its table entry among match entries, from a
+// bitmap with prefix counts) and to the pattern code, and per-terminal
+// counters are bumped; the last CTA turns them into counts[r]. With late ids
+// the scan keeps the terminal id and the expand kernel does the rest.
 //
-// List mode writes the output in three launches, so that no warp ever waits
+// List mode writes the output in two launches, so that no warp ever waits
 // for another: the scan writes each warp tile's matches, in text order, to
 // that tile's own slot of kWarpTile entries (at most one distinct pattern
-// string starts at a position) with the tile's totals; a one-CTA kernel turns
-// the totals into each tile's offset in the output; an expand kernel with
-// many resident warps copies the slots to the sorted (i, r) keys, one key per
+// string starts at a position) with the tile's totals and its segment's
+// sum; an expand kernel with many resident warps turns the totals into
+// offsets and copies the slots to the sorted (i, r) keys, one key per
 // pattern of a group of equal patterns (the paper's coalesced writes,
 // GPU-CW).
+//
+// The kernel itself is in ac_scan_kernel.cuh: this file instantiates it with
+// a 512-thread launch bound, scan_ac_wide.cu with 768 threads.
 #include <cstddef>
 #include <cstdio>
 #include <mutex>
@@ -40,7 +44,7 @@
 #include <utility>
 #include <vector>
 
-#include "ac_device.cuh"
+#include "ac_scan_kernel.cuh"
 
 namespace pm {
 namespace {
@@ -48,38 +52,6 @@ namespace {
 using dev::kFull;
 using namespace acdev;
 
-struct AcArgs {
-    const uint8_t *text;
-    long long n;
-    int aligned;
-    const void *table_g;
-    int smem_entries;
-    uint32_t mid_base;            // first table index of the match rows
-    const uint32_t *mask_g;       // match-entry bitmap words
-    const void *rank_g;           // E: set bits before each word
-    const void *canon_g;          // E: pattern id or group flag per terminal
-    const uint32_t *tmul_g;       // late ids: 2 bits per terminal, min(multiplicity - 1, 3)
-    int nwords, nterms;
-    const uint32_t *grp_off;
-    const uint32_t *grp_ids;
-    const uint8_t *cls_g;
-    int m, lw;
-    uint32_t lut;
-    uint32_t pad;
-    long long nsub;               // warp tiles (2560 text bytes each)
-    int pool_cap;
-    int list, hist_smem, ids_smem, d;
-    int late;                     // list mode with late ids: slots carry terminal ids, no counting here
-    long long *counts;
-    long long *n_occ;
-    dev::WsHeader *ws;
-    unsigned long long *ccount;   // per-terminal totals
-    uint32_t *tile_ent;           // list: entries (one per matching position) per warp tile
-    uint32_t *tile_out;           // list: outputs (keys, groups expanded) per warp tile
-    unsigned long long *seg_sum;  // list: outputs per segment of seg_tiles warp tiles
-    long long seg_tiles;
-    void *slots;                  // list: kWarpTile entries per warp tile
-};
 
 // Workspace carve-up shared by the launchers and the workspace size:
 //   [header][per-terminal counters][list: segment sums u64] -- zeroed by every scan
@@ -98,13 +70,6 @@ inline long long ac_segments(long long nsub, int sm_count)
     return b < 1 ? 1 : b;
 }
 
-__host__ __device__ constexpr long long r16(long long x) { return (x + 15) & ~15LL; }
-
-__host__ __device__ inline long long ac_warp_bytes(int hv, int pool_cap, int eb)
-{
-    // barrier | text buffer | pool (pool_cap + 1 slots per lane)
-    return 16 + r16(kWarpTile + 16 * hv) + r16((long long)(pool_cap + 1) * 32 * eb);
-}
 
 AcWsLayout ac_ws_layout(long long nsub, bool list, long long nterms, int slot_entry_bytes, int sm_count)
 {
@@ -129,336 +94,6 @@ __host__ __device__ inline long long ac_ids_late_bytes(int nwords, int nterms, i
     return r16((long long)nwords * 4) + r16((long long)(nwords + 1) * eb) + r16((long long)(nterms + 15) / 16 * 4);
 }
 
-__device__ __forceinline__ int stage_bytes(const AcArgs &a, long long t, int buf)
-{
-    if (!a.aligned) return 0;
-    const long long avail = (a.n & ~15LL) - t * kWarpTile;
-    if (avail <= 0) return 0;
-    return avail >= buf ? buf : int(avail);
-}
-
-__device__ __forceinline__ void stage_issue(const AcArgs &a, long long t, uint8_t *buf,
-                                            uint64_t *bar, int bufsz)
-{
-    const int bytes = stage_bytes(a, t, bufsz);
-    dev::mbar_arrive_expect_tx(bar, uint32_t(bytes));
-    if (bytes > 0) dev::tma_load_1d(buf, a.text + t * kWarpTile, uint32_t(bytes), bar);
-}
-
-// MAXT: the launch bound, 512 threads (up to 128 registers) or 768 (up to
-// 85, for whole-table plans of more than 16 warps)
-template <typename E, int NV, int HV, bool DNA, bool HYB, bool PRE, bool LATE, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int BUF = kWarpTile + 16 * HV;
-    constexpr int HW = (16 * NV + 31) / 32;
-    constexpr uint32_t kGrp = sizeof(E) == 2 ? 0x8000u : 0x80000000u;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-
-    // ---- shared memory carve-up (mirrors ac_smem_bytes on the host) -------
-    unsigned char *p = smem;
-    E *s_tab = reinterpret_cast<E *>(p);
-    p += r16((long long)a.smem_entries * sizeof(E));
-    Ids<E> ids;
-    uint32_t *s_tmul = nullptr;  // late ids: the terminals' multiplicities
-    if (LATE || a.ids_smem) {
-        ids.mask = reinterpret_cast<const uint32_t *>(p);
-        p += r16((long long)a.nwords * 4);
-        ids.rank = reinterpret_cast<const E *>(p);
-        p += r16((long long)(a.nwords + 1) * sizeof(E));
-        if (!LATE) {
-            ids.canon = reinterpret_cast<const E *>(p);
-            p += r16((long long)a.nterms * sizeof(E));
-        } else {
-            ids.canon = reinterpret_cast<const E *>(a.canon_g);
-            s_tmul = reinterpret_cast<uint32_t *>(p);
-            p += r16((long long)(a.nterms + 15) / 16 * 4);
-        }
-    } else {
-        ids.mask = a.mask_g;
-        ids.rank = reinterpret_cast<const E *>(a.rank_g);
-        ids.canon = reinterpret_cast<const E *>(a.canon_g);
-    }
-    // per-terminal counters: 32-bit (hist_smem 1) or two 16-bit halves per
-    // word (hist_smem 2) in shared memory, else 64-bit in the workspace
-    uint32_t *s_hist = a.hist_smem ? reinterpret_cast<uint32_t *>(p) : nullptr;
-    const long long hist_words = a.hist_smem == 2 ? (a.nterms + 1) / 2 : a.nterms;
-    p += a.hist_smem ? r16(hist_words * 4) : 0;
-    uint8_t *s_cls = p;
-    p += DNA ? 0 : 256;
-    p += warp * ac_warp_bytes(HV, a.pool_cap, sizeof(E));
-    uint64_t *bar = reinterpret_cast<uint64_t *>(p);
-    uint8_t *buf = p + 16;
-    E *pool = reinterpret_cast<E *>(buf + r16(BUF));
-
-    {   // table prefix -> shared memory (16-byte vectors; the global copy is padded)
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.table_g);
-        uint4 *dst = reinterpret_cast<uint4 *>(s_tab);
-        const int nvec = int(((long long)a.smem_entries * sizeof(E) + 15) / 16);
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
-    }
-    if (LATE || a.ids_smem) {
-        uint32_t *mk = const_cast<uint32_t *>(ids.mask);
-        for (int i = threadIdx.x; i < a.nwords; i += blockDim.x) mk[i] = a.mask_g[i];
-        E *rk = const_cast<E *>(ids.rank);
-        const E *rg = reinterpret_cast<const E *>(a.rank_g);
-        for (int i = threadIdx.x; i <= a.nwords; i += blockDim.x) rk[i] = rg[i];
-        if (!LATE) {
-            E *cn = const_cast<E *>(ids.canon);
-            const E *cg = reinterpret_cast<const E *>(a.canon_g);
-            for (int i = threadIdx.x; i < a.nterms; i += blockDim.x) cn[i] = cg[i];
-        } else {
-            for (int i = threadIdx.x; i < (a.nterms + 15) / 16; i += blockDim.x) s_tmul[i] = a.tmul_g[i];
-        }
-    }
-    if (s_hist)
-        for (int i = threadIdx.x; i < hist_words; i += blockDim.x) s_hist[i] = 0u;
-    if (!DNA)
-        for (int i = threadIdx.x; i < 256; i += blockDim.x) s_cls[i] = a.cls_g[i];
-    if (lane == 0) dev::mbar_init(bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    dev::fence_proxy_async_smem();
-    __syncthreads();
-
-    const TableRef<E, HYB> tab{s_tab, reinterpret_cast<const E *>(a.table_g),
-                               uint32_t(a.smem_entries)};
-    E *pl = pool + lane;  // this lane's pool column (stride 32 entries)
-    const uint32_t cap = uint32_t(a.pool_cap);
-    const int m = a.m;
-
-    auto count_terminal = [&](uint32_t c) {
-        if (a.hist_smem == 1) {
-            atomicAdd(&s_hist[c], 1u);
-        } else if (a.hist_smem == 2) {
-            // the add that takes a half to 0x8000 moves 0x8000 to the global
-            // counter, so a half never wraps (it would take 0x8000 more adds
-            // between that add and the move)
-            const uint32_t sh = (c & 1u) << 4;
-            const uint32_t old = atomicAdd(&s_hist[c >> 1], 1u << sh);
-            if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
-                atomicSub(&s_hist[c >> 1], 0x8000u << sh);
-                atomicAdd(&a.ccount[c], 0x8000ull);
-            }
-        } else {
-            atomicAdd(&a.ccount[c], 1ull);
-        }
-    };
-    // offset of a recorded table index among the match rows' entries (in
-    // 16-bit arithmetic for u16 tables, whose match rows span < 65536 entries)
-    auto match_off = [&](E v) -> uint32_t {
-        return sizeof(E) == 2 ? uint32_t(uint16_t(v - E(a.mid_base))) : uint32_t(v) - a.mid_base;
-    };
-    // multiplicity of a pattern code (1, or the size of its group)
-    auto mult_of = [&](uint32_t code) -> uint32_t {
-        if (!(code & kGrp)) return 1u;
-        const uint32_t g = code & ~kGrp;
-        return __ldg(a.grp_off + g + 1) - __ldg(a.grp_off + g);
-    };
-    // what a terminal's hit contributes: its outputs, and the slot value (its
-    // pattern code; with late ids the terminal id itself, whose multiplicity
-    // comes from the 2-bit table, and through canon in device memory only
-    // for groups of four or more equal patterns)
-    auto resolve = [&](uint32_t c, uint32_t &mult) -> uint32_t {
-        if (LATE) {
-            const uint32_t v = (s_tmul[c >> 4] >> ((c & 15u) << 1)) & 3u;
-            mult = v < 3u ? v + 1u : mult_of(uint32_t(__ldg(ids.canon + c)));
-            return c;
-        }
-        const uint32_t code = ids.code(c);
-        mult = mult_of(code);
-        return code;
-    };
-
-    // slot entries: (start offset in the tile, pattern code or terminal id)
-    typedef typename std::conditional<sizeof(E) == 2, uint32_t, unsigned long long>::type SE;
-    constexpr int kOffShift = sizeof(E) == 2 ? 16 : 32;
-    const long long G = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long gwarp = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    SE *slots = reinterpret_cast<SE *>(a.slots);
-
-    uint32_t phase = 0;
-    bool inflight = false;
-    bool failed = false;
-    unsigned long long my_total = 0;
-
-    if (gwarp < a.nsub) {
-        if (lane == 0) stage_issue(a, gwarp, buf, bar, BUF);
-        inflight = true;
-    }
-
-    for (long long st = gwarp; st < a.nsub && !failed; st += G) {
-        const bool got = __all_sync(kFull, dev::mbar_wait_bounded(bar, phase));
-        if (!got) {
-            if (lane == 0) dev::set_status(a.ws, dev::kErrTimeoutTma);
-            failed = true;  // the copy stays in flight: waited for below
-            break;
-        }
-        inflight = false;
-        phase ^= 1u;
-        const long long tile0 = st * kWarpTile;
-        const int got_bytes = stage_bytes(a, st, BUF);
-        if (got_bytes < BUF) {  // tail of the text, or an unaligned text
-            for (int b = got_bytes + lane; b < BUF; b += 32) {
-                const long long g = tile0 + b;
-                buf[b] = g < a.n ? a.text[g] : uint8_t(a.pad);
-            }
-            __syncwarp();
-        }
-        uint4 tv[NV];
-        {
-            const uint4 *bv = reinterpret_cast<const uint4 *>(buf + lane * kChunk);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) tv[v] = bv[v];
-        }
-        dev::fence_proxy_async_smem();
-        __syncwarp();
-        if (st + G < a.nsub) {
-            if (lane == 0) stage_issue(a, st + G, buf, bar, BUF);
-            inflight = true;
-        }
-
-        // ---- walk: a step that enters a terminal stores its table index ----
-        const long long g0 = tile0 + (long long)lane * kChunk;
-        int steps = kChunk + m - 1;
-        if (!DNA) {
-            const long long left = a.n - g0;
-            steps = left <= 0 ? 0 : (left < steps ? int(left) : steps);
-        }
-        uint32_t hw[HW];
-#pragma unroll
-        for (int j = 0; j < HW; ++j) hw[j] = 0u;
-        uint32_t kslot = 0;
-        // pool slot `cap` absorbs the stores of an overflowing lane
-        auto rec = [&](int step, uint32_t idx, uint32_t e) {
-            const uint32_t h = e & 1u;
-            if (h) pl[kslot * 32] = E(idx);  // the match-row base is subtracted when resolving
-            kslot = min(kslot + h, cap);
-            hw[step >> 5] += h << (step & 31);
-        };
-        if (DNA) walk_dna<NV, PRE>(tv, steps, a.lut, tab, rec);
-        else walk_gen<NV>(tv, steps, a.lw, s_cls, tab, rec);
-        uint32_t nh = 0;  // exact even when the pool overflowed
-#pragma unroll
-        for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
-        const bool ovf = nh > cap;
-
-        // ---- resolve: match entry -> terminal -> pattern code ---------------
-        uint32_t cnt = 0;
-        if (!ovf) {
-            for (uint32_t k0 = 0; k0 < nh; k0 += 4) {
-                uint32_t c4[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    c4[j] = ids.terminal(k0 + j < nh ? match_off(pl[(k0 + j) * 32]) : 0u);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (k0 + j < nh) {
-                        uint32_t mult;
-                        const uint32_t val = resolve(c4[j], mult);
-                        if (!LATE || !a.late) count_terminal(c4[j]);
-                        cnt += mult;
-                        pl[(k0 + j) * 32] = E(val);
-                    }
-                }
-            }
-        } else {
-            walk_slow<PRE>(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
-                      [&](int, uint32_t idx) {
-                          const uint32_t c = ids.terminal(idx - a.mid_base);
-                          uint32_t mult;
-                          (void)resolve(c, mult);
-                          if (!LATE || !a.late) count_terminal(c);
-                          cnt += mult;
-                      });
-        }
-
-        if (!a.list) {
-            my_total += cnt;
-            continue;
-        }
-
-        // ---- this tile's matches -> its slot, in text order -----------------
-        const uint32_t e_incl = dev::warp_incl_scan(nh, lane);
-        const uint32_t e_excl = e_incl - nh;
-        uint32_t o_tot = cnt;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) o_tot += __shfl_xor_sync(kFull, o_tot, o);
-        SE *dst = slots + st * kWarpTile + e_excl;
-        // start offset (in the tile) of a match whose last byte is `step`
-        const uint32_t off0 = uint32_t(lane * kChunk - (m - 1));
-        if (!ovf) {
-            // the lane's match steps in order, word by word of its step mask
-            uint32_t k = 0;
-#pragma unroll
-            for (int j = 0; j < HW; ++j) {
-                uint32_t wj = hw[j];
-                while (wj) {
-                    const uint32_t b = uint32_t(__ffs(int(wj))) - 1u;
-                    wj &= wj - 1u;
-                    dst[k] = ((SE)(off0 + uint32_t(j * 32) + b) << kOffShift) | (SE)pl[k * 32];
-                    ++k;
-                }
-            }
-        } else {
-            uint32_t k = 0;
-            walk_slow<PRE>(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
-                      [&](int step, uint32_t idx) {
-                          uint32_t mult;
-                          const uint32_t val = resolve(ids.terminal(idx - a.mid_base), mult);
-                          if (k < nh) dst[k] = ((SE)(off0 + uint32_t(step)) << kOffShift) | (SE)val;
-                          ++k;
-                      });
-        }
-        if (lane == 31) {
-            a.tile_ent[st] = e_incl;
-            a.tile_out[st] = o_tot;
-            if (o_tot) atomicAdd(&a.seg_sum[st / a.seg_tiles], (unsigned long long)o_tot);
-        }
-    }
-
-    // a copy still in flight after an error exit: wait for it (bounded) so
-    // it is not still writing this CTA's shared memory when the CTA exits
-    if (inflight) (void)dev::mbar_wait_bounded(bar, phase);
-
-    if (!a.list) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) my_total += __shfl_down_sync(kFull, my_total, o);
-        if (lane == 0 && my_total)
-            atomicAdd(reinterpret_cast<unsigned long long *>(a.n_occ), my_total);
-    }
-
-    // ---- per-terminal counters -> global; the last CTA writes counts[r] ----
-    __syncthreads();
-    if (s_hist) {
-        for (int c = threadIdx.x; c < a.nterms; c += blockDim.x) {
-            const uint32_t v = a.hist_smem == 2 ? (s_hist[c >> 1] >> ((c & 1) << 4)) & 0xFFFFu : s_hist[c];
-            if (v) atomicAdd(&a.ccount[c], (unsigned long long)v);
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    if (LATE && a.late) return;  // the expand kernel counts and writes counts[r]
-    __shared__ int s_last;
-    if (threadIdx.x == 0) s_last = atomicAdd(&a.ws->done_ctas, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (s_last) {
-        __threadfence();
-        const E *cg = reinterpret_cast<const E *>(a.canon_g);
-        for (int c = threadIdx.x; c < a.nterms; c += blockDim.x) {
-            const unsigned long long v = dev::ld_acquire(&a.ccount[c]);
-            const uint32_t code = cg[c];
-            if (code & kGrp) {
-                const uint32_t g = code & ~kGrp;
-                for (uint32_t j = a.grp_off[g]; j < a.grp_off[g + 1]; ++j)
-                    a.counts[a.grp_ids[j]] = (long long)v;
-            } else {
-                a.counts[code] = (long long)v;
-            }
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // List mode, step 2: slots -> sorted keys ((i << 32) | r). CTA b owns the
@@ -929,13 +564,6 @@ __global__ void __launch_bounds__(512, 1) pfac_scan_kernel(const AcArgs a)
     }
 }
 
-typedef void (*AcKernel)(const AcArgs);
-
-struct Variant {
-    AcKernel fn;
-    int eb, hv;
-    bool dna, hyb;
-};
 
 // variant ids: dna u16 smem (0-2), dna u16 hybrid (3-5), dna u16 smem with
 // index entries (6-8), dna u16 hybrid with index entries (9-11), dna u32
@@ -979,24 +607,9 @@ const Variant kVariants[] = {
     {ac_scan_kernel<uint32_t, 9, 4, true, true, true, true, 512>, 4, 4, true, true},
 };
 
-// More than 16 warps per CTA: u16 ACGT tables wholly in shared memory, the
-// groups 0 and 2 above, then their late-ids forms (6 and 8); HV = 1, 2, 4.
-constexpr int kWideWarps = 24;
-constexpr int kWideBase = 100;
-const Variant kWideVariants[] = {
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, false, 768>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, false, 768>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, false, 768>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, false, 768>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, false, 768>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, false, 768>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, false, true, 768>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, false, true, 768>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, false, true, 768>, 2, 4, true, false},
-    {ac_scan_kernel<uint16_t, 6, 1, true, false, true, true, 768>, 2, 1, true, false},
-    {ac_scan_kernel<uint16_t, 7, 2, true, false, true, true, 768>, 2, 2, true, false},
-    {ac_scan_kernel<uint16_t, 9, 4, true, false, true, true, 768>, 2, 4, true, false},
-};
+constexpr int kWideWarps = 24;   // warps per CTA of the 768-thread instances
+constexpr int kWideBase = 100;   // variant ids from here index kWideVariants
+
 
 int hv_for_m(int m)
 {
@@ -1039,9 +652,8 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     const long long budget = (long long)dp.smem_optin - 1024;
     const int pool_cap = 40;
     const int place = opt.placement;
-    // more than 16 warps: the 768-thread kernels of u16 ACGT tables wholly in
-    // shared memory (one CTA per SM)
-    const bool wide_ok = t.dna && eb == 2 && !t.goto_only && (opt.ctas_per_sm <= 1);
+    // more than 16 warps: the 768-thread kernels of ACGT tables (one CTA per SM)
+    const bool wide_ok = t.dna && !t.goto_only && (opt.ctas_per_sm <= 1);
     const int max_w = wide_ok ? kWideWarps : 16;
     const int forced_warps = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, max_w) : 0;
     dev.pool_cap = pool_cap;
@@ -1111,7 +723,7 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     }
     if (!chosen) {
         // hybrid / global: breadth-first prefix of rows in shared memory
-        const int w = forced_warps ? std::min(forced_warps, 16) : 16;
+        const int w = forced_warps ? forced_warps : 16;
         // counters / ids only when pinned by pm_params (the table prefix
         // gets the room otherwise)
         Layout L{0, w, opt.counters == 1 ? 1 : opt.counters == 2 ? 2 : 0,
@@ -1145,10 +757,11 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     else if (eb == 4) group = 4;
     else group = (hyb ? 1 : 0) + (dev.pre ? 2 : 0);
     if (best.ids == 2) group += 6;   // late ids (ACGT groups only)
-    // variant ids >= kWideBase index kWideVariants (groups 0, 2, 6, 8)
+    // variant ids >= kWideBase index kWideVariants: ACGT groups 0-4 and
+    // their late-ids forms 6-10 are wide groups 0-9
     auto variant_for = [&](int warps) {
         if (warps <= 16) return group * 3 + hv_slot(hv);
-        const int wg = (group >= 6 ? 2 : 0) + ((group % 6) == 2 ? 1 : 0);
+        const int wg = group >= 6 ? group - 1 : group;
         return kWideBase + wg * 3 + hv_slot(hv);
     };
     dev.variant = variant_for(best.warps);

@@ -571,3 +571,25 @@ def test_more_than_16_warps(kw):
     assert int(nocc.item()) == want[0].size
     assert np.array_equal(occ.cpu().numpy().view(np.uint64), want[0][:cap])
     s.close()
+
+
+@pytest.mark.parametrize("kw", [
+    {"placement": pm.PM_PLACE_HYBRID, "smem_table_bytes": 16384, "warps_per_cta": 24},
+    {"placement": pm.PM_PLACE_HYBRID, "smem_table_bytes": 8192, "warps_per_cta": 20, "ids_place": 3},
+    {"placement": pm.PM_PLACE_HYBRID, "warps_per_cta": 18, "counters": 2},
+])
+@pytest.mark.parametrize("m", [9, 20])
+def test_more_than_16_warps_hybrid(kw, m):
+    """The 768-thread kernels with the table partly in device memory: u16
+    tables (m = 9) and u32 tables (m = 20: more than 32,768 rows), list and
+    counts-only, against the oracle."""
+    T = synth.est_text(4 << 20, 47)
+    P = synth.mixed_patterns(T, 3000, m, 47)
+    P = np.concatenate([P, P[:5]])
+    want = oracle.dictionary(T, P, threads=THREADS)
+    s = _ac(P, **kw)
+    inf = s.info()
+    assert inf["placement"] == pm.PM_PLACE_HYBRID and inf["entry_bytes"] == (2 if m == 9 else 4)
+    _same(s.scan(T), want, f"{kw} m={m}")
+    _same(s.scan(T, counts_only=True), (np.zeros(0, np.uint64), want[1]), f"{kw} m={m} counts")
+    s.close()
