@@ -59,7 +59,7 @@ struct Ac2Args {
 
 __host__ __device__ constexpr long long r16a(long long x) { return (x + 15) & ~15LL; }
 
-constexpr int kAc2MaxWarps = 20;  // one CTA per SM
+constexpr int kAc2MaxWarps = 24;  // one CTA per SM (a 768-thread launch bound, up to 85 registers)
 
 // prmt.b32 in its generic mode: a selector nibble with bit 3 set fills its
 // result byte with the sign (bit 7) of the selected byte (the __byte_perm
