@@ -603,8 +603,10 @@ def other_methods(T, d_text, stream, nocc, pm, torch, synth):
         for mm in synth.EST_M:
             _, Pq = synth.est_case(dd, mm, text=T)
             q = pm.PatternSet.wm(Pq, 3)
+            params, _ = q.tune(d_text, reps=1)   # warps per CTA
             gbs, tot, _ = _time_scan(pm, torch, q.h, d_text, n, dd, stream, nocc, reps=1)
-            wm[f"d{dd}_m{mm}"] = {"gbs": gbs, "n_occ": tot, "exact_code_tables": q.info()["dna_mode"]}
+            wm[f"d{dd}_m{mm}"] = {"gbs": gbs, "n_occ": tot, "exact_code_tables": q.info()["dna_mode"],
+                                  "warps_per_cta": params["warps_per_cta"]}
             q.close()
             torch.cuda.empty_cache()
     pf = {}

@@ -301,8 +301,9 @@ int pm_noalloc_scan_status(void *stream);
  * one kept has the counters that fit best for counts-only scans.
  * Results never depend on the plan. Allocates its own scratch, synchronises
  * `stream`. *best_out / *best_ms (may be NULL) receive the chosen pm_params
- * and its time per scan. PM_EINVAL for sets other than Aho-Corasick (PFAC,
- * Wu-Manber, mixed lengths) and for host-only sets.
+ * and its time per scan. Wu-Manber sets tune warps per CTA only (auto, 24,
+ * 20, 16, 12, 8; more than 16 for exact-code tables of ACGT sets).
+ * PM_EINVAL for PFAC and mixed-length sets and for host-only sets.
  */
 int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t reps,
             void *stream, pm_params *best_out, float *best_ms);

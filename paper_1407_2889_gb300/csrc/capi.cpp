@@ -611,10 +611,93 @@ int64_t pm_noalloc_scratch_bytes(void) { return ac_noalloc_limit_bytes(); }
 
 int pm_noalloc_scan_status(void *stream) { return ac_noalloc_status(stream); }
 
+// Wu-Manber sets: warps per CTA (more than 16 only for exact-code tables, in
+// the 768-thread kernels), timed on the caller's text like the AC tuner.
+static int tune_wm(pm_set *s, const uint8_t *d_text, int64_t n, bool list, int32_t reps, cudaStream_t st,
+                   pm_params *best_out, float *best_ms)
+{
+    DeviceProps dp;
+    int rc = device_props(dp);
+    if (rc) return rc;
+    const WmTables &t = s->wm;
+    void *ws = nullptr, *counts = nullptr, *nocc = nullptr, *occ = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int64_t n_occ = 0;
+    auto cleanup = [&]() {
+        for (void *p : {ws, counts, nocc, occ})
+            if (p) cudaFree(p);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = cudaMalloc(&ws, size_t(wm_workspace_bytes(t, n, list)));
+    if (e == cudaSuccess) e = cudaMalloc(&counts, size_t(t.d) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&nocc, 8);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess && list) {
+        rc = wm_launch(t, s->dwm, d_text, n, false, static_cast<int64_t *>(counts), nullptr, 0,
+                       static_cast<int64_t *>(nocc), ws, st);
+        if (!rc) e = cudaMemcpyAsync(&n_occ, nocc, 8, cudaMemcpyDeviceToHost, st);
+        if (!rc && e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (!rc && e == cudaSuccess) e = cudaMalloc(&occ, size_t(std::max<int64_t>(n_occ, 1)) * 8);
+    }
+    if (e != cudaSuccess || rc) {
+        if (e != cudaSuccess) set_cuda_error(int(e));
+        cudaGetLastError();
+        cleanup();
+        return rc ? rc : (e == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA);
+    }
+    const DevWm saved = s->dwm;
+    DevWm best = saved;
+    pm_params best_p = s->params;
+    float best_t = -1.0f;
+    std::vector<std::pair<int, int>> tried;   // (warps, hist_smem)
+    for (int w : {0, 24, 20, 16, 12, 8}) {
+        pm_params p = s->params;
+        p.warps_per_cta = w;
+        DevWm plan = saved;
+        if (wm_plan(t, p, dp, plan) != PM_OK) continue;
+        bool dup = false;
+        for (const auto &x : tried) dup = dup || (x.first == plan.warps && x.second == plan.hist_smem);
+        if (dup) continue;
+        tried.push_back({plan.warps, plan.hist_smem});
+        auto run = [&]() {
+            return wm_launch(t, plan, d_text, n, list, static_cast<int64_t *>(counts), static_cast<uint64_t *>(occ),
+                             n_occ, static_cast<int64_t *>(nocc), ws, st);
+        };
+        rc = run();
+        if (!rc) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && !rc && e == cudaSuccess; ++r) rc = run();
+        if (!rc && e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (!rc && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { set_cuda_error(int(e)); rc = PM_ECUDA; }
+        if (!rc && pm_scan_status(ws, st) != PM_OK) rc = PM_ETIMEOUT;
+        if (rc) break;
+        ms /= float(reps);
+        if (best_t < 0.0f || ms < best_t) { best_t = ms; best = plan; best_p = p; }
+    }
+    cleanup();
+    if (rc) return rc;
+    if (best_t < 0.0f) return PM_ETOOBIG;
+    s->dwm = best;
+    s->params = best_p;
+    if (best_out) *best_out = best_p;
+    if (best_ms) *best_ms = best_t;
+    return PM_OK;
+}
+
 int pm_tune(pm_set *s, const uint8_t *d_text, int64_t n, uint32_t flags, int32_t reps,
             void *stream, pm_params *best_out, float *best_ms)
 {
-    if (!s || s->host_only || s->algo != PM_ALGO_AC || !d_text || n <= 0) return PM_EINVAL;
+    if (!s || s->host_only || !d_text || n <= 0) return PM_EINVAL;
+    if (s->algo == PM_ALGO_WM) {
+        if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
+        return tune_wm(s, d_text, n, !(flags & PM_COUNTS_ONLY), reps < 1 ? 1 : reps,
+                       static_cast<cudaStream_t>(stream), best_out, best_ms);
+    }
+    if (s->algo != PM_ALGO_AC) return PM_EINVAL;
     if (n >= (int64_t(1) << 32)) return PM_ETOOBIG;
     if (reps < 1) reps = 1;
     const bool list = !(flags & PM_COUNTS_ONLY);

@@ -332,8 +332,10 @@ __device__ __forceinline__ void wm_walk_dna(const WmArgs &a, const uint8_t *s_sh
     }
 }
 
-template <bool SHIFT_SMEM, bool DNA, int NV, bool WIDE, bool VAR>
-__global__ void __launch_bounds__(512, 1) wm_scan_kernel(const WmArgs a)
+// MAXT: launch bound, 512 threads, or 768 for exact-code plans of more than
+// 16 warps (up to 85 registers)
+template <bool SHIFT_SMEM, bool DNA, int NV, bool WIDE, bool VAR, int MAXT = 512>
+__global__ void __launch_bounds__(MAXT, 1) wm_scan_kernel(const WmArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -561,7 +563,8 @@ int wm_plan(const WmTables &t, const pm_params &opt, const DeviceProps &dp, DevW
     const int hbits = 5 * t.B;
     dev.pool_cap = 40;
     dev.ctas_per_sm = opt.ctas_per_sm > 0 ? opt.ctas_per_sm : 1;
-    const int forced = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, 16) : 0;
+    // more than 16 warps only in the 768-thread exact-code kernels (ACGT sets)
+    const int forced = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, t.dna ? 24 : 16) : 0;
     const bool shift_smem = hbits <= 15;
     const int choices[3] = {16, 12, 8};
     for (int pass = 0; pass < 2; ++pass) {
@@ -622,10 +625,14 @@ int wm_launch(const WmTables &t, const DevWm &dv, const uint8_t *d_text, int64_t
     const int nv = wm_nv(t.m);
     const bool wide = t.m > 16;
     K fn;
+    const bool big = dv.warps > 16;   // exact-code kernels with a 768-thread bound
     if (t.var && dv.dna) {
-        fn = wm_scan_kernel<false, true, 1, false, true>;
+        fn = big ? wm_scan_kernel<false, true, 1, false, true, 768> : wm_scan_kernel<false, true, 1, false, true>;
     } else if (t.var) {
         fn = dv.shift_smem ? wm_scan_kernel<true, false, 1, false, true> : wm_scan_kernel<false, false, 1, false, true>;
+    } else if (dv.dna && big) {
+        fn = nv == 6 ? (wide ? wm_scan_kernel<false, true, 6, true, false, 768> : wm_scan_kernel<false, true, 6, false, false, 768>)
+                     : wm_scan_kernel<false, true, 7, true, false, 768>;
     } else if (dv.dna) {
         fn = nv == 6 ? (wide ? wm_scan_kernel<false, true, 6, true, false> : wm_scan_kernel<false, true, 6, false, false>)
                      : wm_scan_kernel<false, true, 7, true, false>;

@@ -578,7 +578,7 @@ class PatternSet:
         return pm_scan(self.h, T, flags, stream)
 
     def tune(self, d_text, counts_only: bool = False, reps: int = 3, stream=None):
-        """Autotune the launch plan on a device text (AC sets); (params, ms)."""
+        """Autotune the launch plan on a device text (AC and WM sets); (params, ms)."""
         return pm_tune(self.h, d_text, int(d_text.numel()), PM_COUNTS_ONLY if counts_only else 0,
                        reps, stream)
 

@@ -243,9 +243,14 @@ def test_autotuner_keeps_results():
     _same(s.scan(T, counts_only=True), (np.zeros(0, np.uint64), want[1]), "tuned counts")
     s.close()
     w = _wm(P, 3)
-    with pytest.raises(pm.PmError):
-        w.tune(torch.from_numpy(T[:4096]).cuda())
+    params, ms = w.tune(torch.from_numpy(T).cuda(), reps=1)
+    assert ms > 0 and params["warps_per_cta"] in (0, 8, 12, 16, 20, 24)
+    _same(w.scan(T), want, f"WM tuned {params}")
     w.close()
+    pf = pm.PatternSet.pfac(P)
+    with pytest.raises(pm.PmError):
+        pf.tune(torch.from_numpy(T[:4096]).cuda())
+    pf.close()
 
 
 def test_device_api_capacity_and_status():
@@ -593,3 +598,24 @@ def test_more_than_16_warps_hybrid(kw, m):
     _same(s.scan(T), want, f"{kw} m={m}")
     _same(s.scan(T, counts_only=True), (np.zeros(0, np.uint64), want[1]), f"{kw} m={m} counts")
     s.close()
+
+
+@pytest.mark.parametrize("w", [17, 20, 24])
+@pytest.mark.parametrize("m", [8, 20])
+def test_wm_more_than_16_warps(w, m):
+    """Wu-Manber exact-code plans of more than 16 warps per CTA (the
+    768-thread kernels), fixed and mixed lengths, list and counts-only,
+    against the oracle."""
+    T = synth.est_text(4 << 20, 53)
+    P = synth.mixed_patterns(T, 1200, m, 53)
+    P = np.concatenate([P, P[:7]])
+    want = oracle.dictionary(T, P, threads=THREADS)
+    s = _wm(P, 3, warps_per_cta=w)
+    assert s.info()["dna_mode"] == 1
+    _same(s.scan(T), want, f"WM m={m} warps={w}")
+    _same(s.scan(T, counts_only=True), (np.zeros(0, np.uint64), want[1]), f"WM m={m} warps={w} counts")
+    s.close()
+    Pv = synth.mixed_length_patterns(T, 600, 8, 16, 53)
+    sv = pm.PatternSet.wmv(Pv, 3, {"warps_per_cta": w})
+    _same(sv.scan(T), oracle.dictionary_var(T, Pv, threads=THREADS), f"WM mixed lengths warps={w}")
+    sv.close()
