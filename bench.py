@@ -721,6 +721,7 @@ def batched_comparison(args, T, d_text, pm, torch, synth):
         b = pm.Batch.exact(sets, d_text, off, ln, stream=stream)
         tuned_ms = b.tune(reps=2, stream=stream)
         warps = b.warps
+        placement = b.placement
         b.capture()
         b.replay(stream)
     stream.synchronize()
@@ -795,10 +796,11 @@ def batched_comparison(args, T, d_text, pm, torch, synth):
         "plain_steady_sample": f"{len(sample)} sets (every {max(1, k // 64)}th instance), each over the first "
                                f"{span >> 20} MiB of the text, list mode, weighted by instance length",
         "tuned_warps": warps, "tune_best_ms": tuned_ms, "compile_s": t_compile,
-        "plan": {"warps_per_cta": warps, "chunk_bytes_per_lane": 80,
+        "plan": {"warps_per_cta": warps, "chunk_bytes_per_lane": 80, "placement_policy": placement,
                  "placement": "per instance: whole table in the CTA's shared memory when it fits, else its "
-                              "breadth-first prefix (ids and counters in shared memory while each takes at "
-                              "most a quarter of the region)",
+                              "breadth-first prefix, with ids and counters in shared memory while each takes "
+                              "at most a quarter of the region (policy 0) or in device memory (policy 1); "
+                              "the tuner picks warps x policy",
                  "split": "instances above a quarter of a CTA's share split into parts of whole warp tiles"},
         "workload": "k slices of the EST-shaped text, lengths log-uniform 1 KiB-4 MiB (seed 4000+j), "
                     "own set per instance: d log-uniform 10-10^4, m uniform 8-64, list mode",

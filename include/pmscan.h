@@ -381,16 +381,25 @@ int pm_batch_scan_device(const pm_batch *b, const uint8_t *d_text, int64_t *d_co
 
 /*
  * Autotuner: times `reps` batched scans (after one warm-up) for each
- * candidate warps-per-CTA (8, 12, 16; each fixes how shared memory is split
- * between per-warp buffers and the instance's table prefix, ids and
- * counters), keeps the fastest and returns its time per scan in *best_ms
- * (may be NULL). Synchronises `stream`; results of every candidate are
- * identical, and the buffers hold the last candidate's. Drops a captured graph.
+ * candidate plan, warps per CTA (8, 12, 16; each fixes how shared memory is
+ * split between per-warp buffers and the instance region) x table placement
+ * (see pm_batch_set_placement), keeps the fastest and returns its time per
+ * scan in *best_ms (may be NULL). Synchronises `stream`; results of every
+ * candidate are identical, and the buffers hold the last candidate's. Drops
+ * a captured graph.
  */
 int pm_batch_tune(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_t *d_occ,
                   int64_t *d_n_occ, void *d_workspace, int64_t workspace_bytes, int32_t reps,
                   void *stream, float *best_ms);
 int pm_batch_set_warps(pm_batch *b, int32_t warps);  /* 1..16; drops a captured graph */
+/* Table placement of instances whose tables do not all fit the CTA's shared
+ * memory: 0 (default) keeps their terminal ids and counters there while each
+ * takes at most a quarter of the region and gives the table's breadth-first
+ * prefix the rest; 1 keeps ids and counters in device memory and gives the
+ * prefix the whole region. PM_EINVAL for other values; drops a captured
+ * graph. Results never depend on it. */
+int pm_batch_set_placement(pm_batch *b, int32_t placement);
+int32_t pm_batch_placement(const pm_batch *b);  /* the current plan's placement, or -1 */
 
 /*
  * CUDA graph of one batched scan on these buffers (the workspace memset and

@@ -397,6 +397,10 @@ struct BatchDesc {                 // one instance, in processing order
 
 struct BatchShape {                // launch shape and shared-memory split
     int warps = 12;
+    // where an instance whose tables do not all fit puts its ids and
+    // counters: 0 shared memory while each takes at most a quarter of the
+    // region, 1 device memory (the table prefix gets the whole region)
+    int policy = 0;
     int region_bytes = 0;          // per-CTA table / ids / counters region
     long long smem_bytes = 0;
     int sm_count = 0;

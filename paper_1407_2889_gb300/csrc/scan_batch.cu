@@ -489,7 +489,7 @@ struct InstLayout {
 // otherwise counters and ids stay in shared memory only while each takes at
 // most a quarter of the region, and the table gets the rest (its
 // breadth-first prefix: the rows a walk visits most).
-static InstLayout layout_of(const AcTables &t, int region)
+static InstLayout layout_of(const AcTables &t, int region, int policy)
 {
     const int eb = t.entry_bytes;
     const long long entries = (long long)t.n_rows << t.lw;
@@ -506,8 +506,8 @@ static InstLayout layout_of(const AcTables &t, int region)
     }
     long long off = region;
     L.hist_off = L.ids_off = -1;
-    if (hb <= region / 4) { off -= hb; L.hist_off = int(off); }
-    if (ib <= region / 4) { off -= ib; L.ids_off = int(off); }
+    if (policy == 0 && hb <= region / 4) { off -= hb; L.hist_off = int(off); }
+    if (policy == 0 && ib <= region / 4) { off -= ib; L.ids_off = int(off); }
     long long se = off / eb;
     se &= ~((long long)(16 / eb) - 1);
     L.smem_entries = int(std::min(entries, se));
@@ -583,7 +583,7 @@ int64_t batch_fill(const BatchInst *inst, int k, const BatchShape &sh, BatchDesc
     for (int q = 0; q < k; ++q) {
         const BatchInst &I = inst[q];
         const AcTables &t = I.set->ac;
-        const InstLayout L = layout_of(t, sh.region_bytes);
+        const InstLayout L = layout_of(t, sh.region_bytes, sh.policy);
         const int64_t nt = int64_t(t.canon.size());
         const int64_t coff = ccount;
         if (L.hist_off < 0) ccount += nt;
@@ -603,7 +603,7 @@ int64_t batch_items(const BatchInst *inst, int k, const BatchShape &sh, bool lis
     double total = 0.0;
     for (int q = 0; q < k; ++q) {
         const AcTables &t = inst[q].set->ac;
-        lay[size_t(q)] = layout_of(t, sh.region_bytes);
+        lay[size_t(q)] = layout_of(t, sh.region_bytes, sh.policy);
         // a table read partly through L2 costs several times more per byte;
         // every instance also pays for loading its tables
         const long long entries = (long long)t.n_rows << t.lw;
@@ -663,7 +663,7 @@ int64_t batch_items(const BatchInst *inst, int k, const BatchShape &sh, bool lis
 int64_t batch_words_bound(const BatchInst &I, const BatchShape &sh, bool list)
 {
     const AcTables &t = I.set->ac;
-    const InstLayout L = layout_of(t, sh.region_bytes);
+    const InstLayout L = layout_of(t, sh.region_bytes, sh.policy);
     const long long ntiles = (I.text_len + kWarpTile - 1) / kWarpTile;
     const long long parts = std::max(1LL, ntiles / (2LL * std::max(sh.warps, 1)));
     int64_t w = (L.hist_off < 0 || parts > 1) ? int64_t(t.canon.size()) : 0;
@@ -744,10 +744,11 @@ namespace pm {
 
 // Lay the batch out for `warps` warps per CTA and upload the descriptors
 // (into the existing device array once there is one).
-static int apply_plan(pm_batch *b, int warps)
+static int apply_plan(pm_batch *b, int warps, int policy)
 {
     int rc = batch_shape(warps, b->shape);
     if (rc) return rc;
+    b->shape.policy = policy;
     std::vector<BatchDesc> h;
     b->ccount_total = batch_items(b->inst.data(), b->k, b->shape, !(b->flags & PM_COUNTS_ONLY), h, nullptr);
     b->n_items = int32_t(h.size());
@@ -834,16 +835,18 @@ int pm_batch_prepare(const pm_set *const *sets, int32_t k, const int64_t *text_o
         // warp count the tuner may pick
         int rc = PM_OK;
         b->ws_bytes = 0;
-        for (int w : kBatchWarpChoices) {
-            BatchShape sh;
-            rc = batch_shape(w, sh);
-            if (rc) { delete b; return rc; }
-            std::vector<BatchDesc> tmp;
-            int64_t spill = 0;
-            const int64_t cw = batch_items(b->inst.data(), k, sh, !(flags & PM_COUNTS_ONLY), tmp, &spill);
-            b->ws_bytes = std::max<int64_t>(b->ws_bytes, batch_ws_bytes(cw) + 8 * spill);
-        }
-        rc = apply_plan(b, 12);
+        for (int w : kBatchWarpChoices)
+            for (int policy : {0, 1}) {
+                BatchShape sh;
+                rc = batch_shape(w, sh);
+                if (rc) { delete b; return rc; }
+                sh.policy = policy;
+                std::vector<BatchDesc> tmp;
+                int64_t spill = 0;
+                const int64_t cw = batch_items(b->inst.data(), k, sh, !(flags & PM_COUNTS_ONLY), tmp, &spill);
+                b->ws_bytes = std::max<int64_t>(b->ws_bytes, batch_ws_bytes(cw) + 8 * spill);
+            }
+        rc = apply_plan(b, 12, 0);
         if (rc) { pm_batch_free(b); return rc; }
     } catch (const std::bad_alloc &) {
         pm_batch_free(b);
@@ -871,7 +874,16 @@ int pm_batch_set_warps(pm_batch *b, int32_t warps)
 {
     if (!b || warps < 1 || warps > kBatchMaxWarps) return PM_EINVAL;
     drop_graph(b);
-    return apply_plan(b, warps);
+    return apply_plan(b, warps, b->shape.policy);
+}
+
+int32_t pm_batch_placement(const pm_batch *b) { return b ? b->shape.policy : -1; }
+
+int pm_batch_set_placement(pm_batch *b, int32_t placement)
+{
+    if (!b || placement < 0 || placement > 1) return PM_EINVAL;
+    drop_graph(b);
+    return apply_plan(b, b->shape.warps, placement);
 }
 
 int pm_batch_scan_device(const pm_batch *b, const uint8_t *d_text, int64_t *d_counts,
@@ -904,10 +916,11 @@ int pm_batch_tune(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_
         if (e0) cudaEventDestroy(e0);
         return PM_ECUDA;
     }
-    int best_w = b->shape.warps;
+    int best_w = b->shape.warps, best_p = b->shape.policy;
     float best = -1.0f;
-    for (int w : kBatchWarpChoices) {
-        rc = apply_plan(b, w);
+    for (int w : kBatchWarpChoices)
+    for (int policy : {0, 1}) {
+        rc = apply_plan(b, w, policy);
         if (!rc) rc = batch_prepare_launch(b->shape);
         if (!rc) rc = batch_enqueue(b, o, st);  // warm-up
         if (!rc) {
@@ -919,7 +932,7 @@ int pm_batch_tune(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_
             if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
             if (e != cudaSuccess) { set_cuda_error(int(e)); rc = PM_ECUDA; }
             if (!rc && pm_scan_status(d_workspace, stream) != PM_OK) rc = PM_ETIMEOUT;
-            if (!rc && (best < 0.0f || ms < best)) { best = ms; best_w = w; }
+            if (!rc && (best < 0.0f || ms < best)) { best = ms; best_w = w; best_p = policy; }
         }
         if (rc) break;
     }
@@ -927,7 +940,7 @@ int pm_batch_tune(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_
     cudaEventDestroy(e1);
     if (rc) return rc;
     if (best_ms) *best_ms = best / float(reps);
-    return apply_plan(b, best_w);
+    return apply_plan(b, best_w, best_p);
 }
 
 int pm_batch_capture(pm_batch *b, const uint8_t *d_text, int64_t *d_counts, uint64_t *d_occ,

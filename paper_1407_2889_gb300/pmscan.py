@@ -31,7 +31,7 @@ EXPORTED = [
     "pm_scan_device_noalloc", "pm_noalloc_scratch_bytes", "pm_noalloc_scan_status", "pm_scan_status",
     "pm_scan_batch", "pm_batch_prepare", "pm_batch_free", "pm_batch_counts_total",
     "pm_batch_workspace_bytes", "pm_batch_warps", "pm_batch_scan_device", "pm_batch_tune",
-    "pm_batch_set_warps", "pm_batch_capture", "pm_batch_replay",
+    "pm_batch_set_warps", "pm_batch_set_placement", "pm_batch_placement", "pm_batch_capture", "pm_batch_replay",
     "pm_tune", "pm_server_create", "pm_server_submit", "pm_server_wait", "pm_server_get_stats",
     "pm_server_reset_stats", "pm_server_destroy",
     "pm_selfcheck_host_walk", "pm_strerror", "pm_last_cuda_error", "pm_version",
@@ -161,6 +161,10 @@ def lib():
         L.pm_batch_tune.argtypes = [vp, vp, vp, vp, vp, vp, i64, i32, vp, ctypes.POINTER(ctypes.c_float)]
         L.pm_batch_set_warps.restype = ctypes.c_int
         L.pm_batch_set_warps.argtypes = [vp, i32]
+        L.pm_batch_set_placement.restype = ctypes.c_int
+        L.pm_batch_set_placement.argtypes = [vp, i32]
+        L.pm_batch_placement.restype = i32
+        L.pm_batch_placement.argtypes = [vp]
         L.pm_batch_capture.restype = ctypes.c_int
         L.pm_batch_capture.argtypes = [vp, vp, vp, vp, vp, vp, i64]
         L.pm_batch_replay.restype = ctypes.c_int
@@ -513,6 +517,14 @@ def pm_batch_set_warps(b: int, warps: int) -> None:
     _check(lib().pm_batch_set_warps(b, int(warps)), "pm_batch_set_warps")
 
 
+def pm_batch_set_placement(b: int, placement: int) -> None:
+    _check(lib().pm_batch_set_placement(b, int(placement)), "pm_batch_set_placement")
+
+
+def pm_batch_placement(b: int) -> int:
+    return int(lib().pm_batch_placement(b))
+
+
 def pm_batch_capture(b: int, d_text, d_counts, d_occ, d_n_occ, d_workspace,
                      workspace_bytes: int) -> None:
     _check(lib().pm_batch_capture(b, _dev_ptr(d_text), _dev_ptr(d_counts), _dev_ptr(d_occ),
@@ -661,6 +673,13 @@ class Batch:
     @property
     def warps(self) -> int:
         return pm_batch_warps(self.b)
+
+    def set_placement(self, placement: int) -> None:
+        pm_batch_set_placement(self.b, placement)
+
+    @property
+    def placement(self) -> int:
+        return pm_batch_placement(self.b)
 
     def capture(self) -> None:
         pm_batch_capture(self.b, *self._bufs())

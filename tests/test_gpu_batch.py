@@ -109,12 +109,17 @@ def test_batch_every_warp_count_and_graph_replay(d_base, mixed):
     sets, Ps, off, ln, want = mixed
     b = pm.Batch.exact(sets, d_base, off, ln)
     for w in (8, 12, 16, 4):
-        b.set_warps(w)
-        b.scan()
-        assert b.status() == pm.PM_OK
-        _check(b.results(), want, f"{w} warps per CTA")
+        for placement in (0, 1):
+            b.set_warps(w)
+            b.set_placement(placement)
+            assert b.placement == placement
+            b.scan()
+            assert b.status() == pm.PM_OK
+            _check(b.results(), want, f"{w} warps per CTA, placement {placement}")
+    with pytest.raises(pm.PmError):
+        b.set_placement(2)
     ms = b.tune(reps=2)
-    assert ms > 0 and b.warps in (8, 12, 16)
+    assert ms > 0 and b.warps in (8, 12, 16) and b.placement in (0, 1)
     b.capture()
     for rep in range(2):
         b.occ.fill_(-1)
