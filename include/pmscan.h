@@ -78,10 +78,11 @@ extern "C" {
 typedef struct pm_params {
     int32_t placement;        /* PM_PLACE_* */
     int32_t smem_table_bytes; /* cap on the shared-memory part of the table */
-    int32_t warps_per_cta;    /* 1..32 (0 automatic); Aho-Corasick plans use at
-                                 most 24 (u16 ACGT tables wholly in shared
-                                 memory, 768-thread kernels) or 16 (others),
-                                 Wu-Manber and mixed lengths at most 16 */
+    int32_t warps_per_cta;    /* 1..32 (0 automatic); clamped to the kernel's
+                                 launch bound: at most 24 (768-thread kernels)
+                                 for Aho-Corasick, PFAC and Wu-Manber over
+                                 ACGT-like alphabets, for mixed lengths and
+                                 for the stride-2 scan, else 16 */
     int32_t ctas_per_sm;      /* persistent CTAs per SM */
     int32_t wm_prefix_len;    /* Wu-Manber B' (default 2, clamped to m) */
     int32_t host_only;        /* 1: build host tables only (no device upload);

@@ -24,6 +24,7 @@ struct AcArgs {
     const void *rank_g;           // E: set bits before each word
     const void *canon_g;          // E: pattern id or group flag per terminal
     const uint32_t *tmul_g;       // late ids: 2 bits per terminal, min(multiplicity - 1, 3)
+    const uint32_t *emul_g;       // late ids: 2 bits per match entry, the same for the terminal it enters
     int nwords, nterms;
     const uint32_t *grp_off;
     const uint32_t *grp_ids;
@@ -34,7 +35,7 @@ struct AcArgs {
     long long nsub;               // warp tiles (2560 text bytes each)
     int pool_cap;
     int list, hist_smem, ids_smem, d;
-    int late;                     // list mode with late ids: slots carry terminal ids, no counting here
+    int late;                     // list mode with late ids: slots carry match-entry offsets, no counting here
     long long *counts;
     long long *n_occ;
     dev::WsHeader *ws;
@@ -108,8 +109,18 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
     E *s_tab = reinterpret_cast<E *>(p);
     p += r16((long long)a.smem_entries * sizeof(E));
     Ids<E> ids;
-    uint32_t *s_tmul = nullptr;  // late ids: the terminals' multiplicities
-    if (LATE || a.ids_smem) {
+    uint32_t *s_tmul = nullptr;  // late ids, counts mode: the terminals' multiplicities
+    uint32_t *s_emul = nullptr;  // late ids, list mode: the match entries' multiplicities
+    const bool late_list = LATE && a.late;
+    if (late_list) {
+        // only the multiplicities; the id structure stays in device memory
+        // for groups of four or more equal patterns
+        ids.mask = a.mask_g;
+        ids.rank = reinterpret_cast<const E *>(a.rank_g);
+        ids.canon = reinterpret_cast<const E *>(a.canon_g);
+        s_emul = reinterpret_cast<uint32_t *>(p);
+        p += r16((long long)a.nwords * 8);
+    } else if (LATE || a.ids_smem) {
         ids.mask = reinterpret_cast<const uint32_t *>(p);
         p += r16((long long)a.nwords * 4);
         ids.rank = reinterpret_cast<const E *>(p);
@@ -145,7 +156,9 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
         const int nvec = int(((long long)a.smem_entries * sizeof(E) + 15) / 16);
         for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
     }
-    if (LATE || a.ids_smem) {
+    if (late_list) {
+        for (int i = threadIdx.x; i < 2 * a.nwords; i += blockDim.x) s_emul[i] = a.emul_g[i];
+    } else if (LATE || a.ids_smem) {
         uint32_t *mk = const_cast<uint32_t *>(ids.mask);
         for (int i = threadIdx.x; i < a.nwords; i += blockDim.x) mk[i] = a.mask_g[i];
         E *rk = const_cast<E *>(ids.rank);
@@ -215,6 +228,13 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
         const uint32_t code = ids.code(c);
         mult = mult_of(code);
         return code;
+    };
+    // late ids in list mode: the outputs of a match entry (offset o among
+    // the match rows' entries) from its 2-bit multiplicity; the id structure
+    // in device memory names the group of four or more
+    auto entry_mult = [&](uint32_t o) -> uint32_t {
+        const uint32_t v = (s_emul[o >> 4] >> ((o & 15u) << 1)) & 3u;
+        return v < 3u ? v + 1u : mult_of(uint32_t(ids.canon[ids.terminal(o)]));
     };
 
     // slot entries: (start offset in the tile, pattern code or terminal id)
@@ -291,8 +311,10 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
         const bool ovf = nh > cap;
 
         // ---- resolve: match entry -> terminal -> pattern code ---------------
+        // (late ids in list mode: no resolve; the compaction below adds up the
+        // multiplicities)
         uint32_t cnt = 0;
-        if (!ovf) {
+        if (!late_list && !ovf) {
             for (uint32_t k0 = 0; k0 < nh; k0 += 4) {
                 uint32_t c4[4];
 #pragma unroll
@@ -303,19 +325,19 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
                     if (k0 + j < nh) {
                         uint32_t mult;
                         const uint32_t val = resolve(c4[j], mult);
-                        if (!LATE || !a.late) count_terminal(c4[j]);
+                        count_terminal(c4[j]);
                         cnt += mult;
                         pl[(k0 + j) * 32] = E(val);
                     }
                 }
             }
-        } else {
+        } else if (!late_list) {
             walk_slow<PRE>(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
                       [&](int, uint32_t idx) {
                           const uint32_t c = ids.terminal(idx - a.mid_base);
                           uint32_t mult;
                           (void)resolve(c, mult);
-                          if (!LATE || !a.late) count_terminal(c);
+                          count_terminal(c);
                           cnt += mult;
                       });
         }
@@ -328,13 +350,35 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
         // ---- this tile's matches -> its slot, in text order -----------------
         const uint32_t e_incl = dev::warp_incl_scan(nh, lane);
         const uint32_t e_excl = e_incl - nh;
-        uint32_t o_tot = cnt;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) o_tot += __shfl_xor_sync(kFull, o_tot, o);
         SE *dst = slots + st * kWarpTile + e_excl;
         // start offset (in the tile) of a match whose last byte is `step`
         const uint32_t off0 = uint32_t(lane * kChunk - (m - 1));
-        if (!ovf) {
+        if (late_list && !ovf) {
+            // slot values: match-entry offsets (the expand kernel takes the
+            // terminal ids, codes and counts from them)
+            uint32_t k = 0;
+#pragma unroll
+            for (int j = 0; j < HW; ++j) {
+                uint32_t wj = hw[j];
+                while (wj) {
+                    const uint32_t b = uint32_t(__ffs(int(wj))) - 1u;
+                    wj &= wj - 1u;
+                    const uint32_t o = match_off(pl[k * 32]);
+                    cnt += entry_mult(o);
+                    dst[k] = ((SE)(off0 + uint32_t(j * 32) + b) << kOffShift) | (SE)o;
+                    ++k;
+                }
+            }
+        } else if (late_list) {
+            uint32_t k = 0;
+            walk_slow<PRE>(a.text, a.n, g0, kChunk + m - 1, DNA, a.lut, a.lw, s_cls, tab,
+                      [&](int step, uint32_t idx) {
+                          const uint32_t o = idx - a.mid_base;
+                          cnt += entry_mult(o);
+                          if (k < nh) dst[k] = ((SE)(off0 + uint32_t(step)) << kOffShift) | (SE)o;
+                          ++k;
+                      });
+        } else if (!ovf) {
             // the lane's match steps in order, word by word of its step mask
             uint32_t k = 0;
 #pragma unroll
@@ -357,6 +401,9 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
                           ++k;
                       });
         }
+        uint32_t o_tot = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) o_tot += __shfl_xor_sync(kFull, o_tot, o);
         if (lane == 31) {
             a.tile_ent[st] = e_incl;
             a.tile_out[st] = o_tot;

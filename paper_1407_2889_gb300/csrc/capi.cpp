@@ -111,7 +111,7 @@ void free_dev(void *&p)
 
 void release_device(pm_set *s)
 {
-    void *ptrs[] = {s->dac.table, s->dac.flag_mask, s->dac.flag_rank, s->dac.canon, s->dac.tmul,
+    void *ptrs[] = {s->dac.table, s->dac.flag_mask, s->dac.flag_rank, s->dac.canon, s->dac.tmul, s->dac.emul,
                     s->dac.grp_off, s->dac.grp_ids, s->dac.cls,
                     s->dwm.shift, s->dwm.hoff, s->dwm.hids, s->dwm.hpfx, s->dwm.pats,
                     s->dwm.shift2, s->dwm.dir, s->dwm.ccode, s->dwm.cr,
@@ -168,17 +168,25 @@ int upload_ac(pm_set *s)
         }
     }
     if (!rc) {
-        // late ids: min(multiplicity - 1, 3) of each terminal, 2 bits
+        // late ids: min(multiplicity - 1, 3) of each terminal, 2 bits (counts
+        // mode), and the same per match entry (list mode)
+        auto mult2 = [&](size_t c) -> uint32_t {
+            if (!(t.canon[c] & 0x80000000u)) return 0u;
+            const uint32_t g = t.canon[c] & 0x7FFFFFFFu;
+            return std::min<uint32_t>(t.grp_off[g + 1] - t.grp_off[g] - 1u, 3u);
+        };
         std::vector<uint32_t> bits((t.canon.size() + 15) / 16 + 1, 0u);
-        for (size_t c = 0; c < t.canon.size(); ++c) {
-            uint32_t v = 0;
-            if (t.canon[c] & 0x80000000u) {
-                const uint32_t g = t.canon[c] & 0x7FFFFFFFu;
-                v = std::min<uint32_t>(t.grp_off[g + 1] - t.grp_off[g] - 1u, 3u);
-            }
-            bits[c >> 4] |= v << ((c & 15) * 2);
-        }
+        for (size_t c = 0; c < t.canon.size(); ++c) bits[c >> 4] |= mult2(c) << ((c & 15) * 2);
         rc = upload(reinterpret_cast<void **>(&d.tmul), bits.data(), bits.size() * 4, tot);
+        const size_t nw = t.flag_mask.size();
+        std::vector<uint32_t> ebits(2 * nw + 1, 0u);
+        for (size_t k = 0; k < nw * 32; ++k) {
+            const uint32_t mw = t.flag_mask[k >> 5], b = uint32_t(k & 31);
+            if (!((mw >> b) & 1u)) continue;
+            const size_t c = t.flag_rank[k >> 5] + uint32_t(__builtin_popcount(mw & ((1u << b) - 1u)));
+            ebits[k >> 4] |= mult2(c) << ((k & 15) * 2);
+        }
+        if (!rc) rc = upload(reinterpret_cast<void **>(&d.emul), ebits.data(), ebits.size() * 4, tot);
     }
     if (!rc)
         rc = upload(reinterpret_cast<void **>(&d.grp_off), t.grp_off.data(), t.grp_off.size() * 4, tot);

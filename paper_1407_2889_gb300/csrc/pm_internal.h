@@ -187,6 +187,7 @@ struct DevAc {
     void *flag_rank = nullptr;      // u16 or u32 per mask word (entry_bytes)
     void *canon = nullptr;          // u16 or u32 per terminal (entry_bytes)
     uint32_t *tmul = nullptr;       // 2 bits per terminal: min(multiplicity - 1, 3)
+    uint32_t *emul = nullptr;       // 2 bits per match entry: the same for the terminal it enters
     int64_t smem_entries = 0;       // table entries copied to shared memory
     int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0;
     int32_t hist_smem = 0;          // per-terminal counters in shared memory
@@ -313,7 +314,9 @@ void list_workspace_parts(void *d_ws, int64_t nsub, int64_t nterms, int slot_ent
 // counts[r] (d entries) from them.
 struct ExpandLate {
     const void *canon = nullptr;
-    int64_t nterms = 0;
+    const uint32_t *mask = nullptr;  // match-entry bitmap and its ranks (type of canon)
+    const void *rank = nullptr;
+    int64_t nterms = 0, nwords = 0;
     int64_t *counts = nullptr;
 };
 int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes, const uint32_t *grp_off,

@@ -88,11 +88,15 @@ __host__ __device__ inline long long ac_ids_bytes(int nwords, int nterms, int eb
     return r16((long long)nwords * 4) + r16((long long)(nwords + 1) * eb) + r16((long long)nterms * eb);
 }
 
-// late ids: match bitmap, ranks and the terminals' 2-bit multiplicities
+// late ids, counts mode: match bitmap, ranks and the terminals' 2-bit
+// multiplicities
 __host__ __device__ inline long long ac_ids_late_bytes(int nwords, int nterms, int eb)
 {
     return r16((long long)nwords * 4) + r16((long long)(nwords + 1) * eb) + r16((long long)(nterms + 15) / 16 * 4);
 }
+
+// late ids, list mode: the match entries' 2-bit multiplicities
+__host__ __device__ inline long long ac_emul_bytes(int nwords) { return r16((long long)nwords * 8); }
 
 
 // ---------------------------------------------------------------------------
@@ -105,23 +109,30 @@ __host__ __device__ inline long long ac_ids_late_bytes(int nwords, int nterms, i
 // and key stores are both coalesced. A row that names a group of equal
 // patterns takes a warp prefix over the entries' multiplicities instead. The
 // CTA that owns the last tile writes the total.
-// With late ids the entries carry terminal ids: each is mapped to its
-// pattern code through canon and counted per terminal (in shared memory when
-// canon and the counters fit there), the counters go to the workspace when
-// the CTA is done, and the last CTA to finish writes counts[r].
+// With late ids the entries carry match-entry offsets: each is mapped to
+// its terminal id (rank of the entry in the match bitmap) and through canon
+// to its pattern code and counted per terminal (in shared memory when the id
+// structure and the counters fit there), the counters go to the workspace
+// when the CTA is done, and the last CTA to finish writes counts[r].
+// CM, the counter mode: 0 no late ids; late ids with canon and 32-bit (1) or
+// 16-bit (2) counters in shared memory, or both in device memory (3). GS:
+// the group tables are in shared memory. Both are template parameters so
+// that every table load is a plain shared or global load.
 // ---------------------------------------------------------------------------
 constexpr int kExpandThreads = 512;
 
 struct ExpandLateArgs {
     const void *canon;            // u16 (4-byte slots) or u32 per terminal
-    long long nterms;
-    int smem;                     // canon and counters in shared memory: 1 32-bit, 2 16-bit counters
+    const uint32_t *mask;         // match-entry bitmap
+    const void *rank;             // set bits before each bitmap word (type of canon)
+    long long nterms, nwords;
+    int smem;                     // canon and counters in shared memory: 1 32-bit, 2 16-bit counters; 0 neither
     unsigned long long *ccount;   // per-terminal counters (workspace)
     long long *counts;
     dev::WsHeader *ws;
 };
 
-template <typename SE, int kOffShift, uint32_t kGrp, bool LATE>
+template <typename SE, int kOffShift, uint32_t kGrp, int CM, bool GS>
 __global__ void __launch_bounds__(kExpandThreads)
 expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_ent,
               const uint32_t *__restrict__ tile_out, const unsigned long long *__restrict__ seg_sum,
@@ -132,6 +143,7 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
               const ExpandLateArgs late)
 {
     typedef typename std::conditional<sizeof(SE) == 4, uint16_t, uint32_t>::type CE;
+    constexpr bool LATE = CM != 0;
     extern __shared__ __align__(16) unsigned char esm[];
     unsigned long long *s_off = reinterpret_cast<unsigned long long *>(esm);  // seg_tiles + 1
     uint32_t *s_ent = reinterpret_cast<uint32_t *>(s_off + seg_tiles + 1);
@@ -182,28 +194,40 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
         run += o;
     }
     if (tid == kExpandThreads - 1 && nt > 0 && t0 + nt == nsub) *n_occ = (long long)run;  // the last tile's CTA
-    // small group tables move to shared memory: their loads sit on a row's
-    // critical path (ngo = 0: they stay in device memory)
+    // small group tables move to shared memory (GS): their loads sit on a
+    // row's critical path
     uint32_t *s_grp = s_ent + seg_tiles;
-    const uint32_t *go = grp_off, *gid = grp_ids;
-    if (ngo > 0) {
+    if (GS) {
         for (long long i = tid; i < ngo; i += kExpandThreads) s_grp[i] = grp_off[i];
         for (long long i = tid; i < ngi; i += kExpandThreads) s_grp[ngo + i] = grp_ids[i];
-        go = s_grp;
-        gid = s_grp + ngo;
     }
-    // late ids: canon and per-terminal counters
-    const CE *canon = static_cast<const CE *>(late.canon);
-    uint32_t *s_cnt = nullptr;
-    if (LATE && late.smem) {
-        unsigned char *q = reinterpret_cast<unsigned char *>(s_grp + ngo + ngi);
-        CE *sc = reinterpret_cast<CE *>(q);
-        s_cnt = reinterpret_cast<uint32_t *>(q + r16(late.nterms * (long long)sizeof(CE)));
-        const long long words = late.smem == 2 ? (late.nterms + 1) / 2 : late.nterms;
-        for (long long i = tid; i < late.nterms; i += kExpandThreads) sc[i] = canon[i];
+    const uint32_t *s_go = s_grp, *s_gid = s_grp + ngo;
+    auto grp_first = [&](uint32_t g) -> uint32_t { return GS ? s_go[g] : __ldg(grp_off + g); };
+    auto grp_id = [&](uint32_t j) -> uint32_t { return GS ? s_gid[j] : __ldg(grp_ids + j); };
+    // late ids: canon, match bitmap, ranks and per-terminal counters (in
+    // shared memory for CM 1, 2)
+    const CE *canon_g = static_cast<const CE *>(late.canon);
+    const CE *rank_g = static_cast<const CE *>(late.rank);
+    unsigned char *lq = reinterpret_cast<unsigned char *>(s_grp + (GS ? ngo + ngi : 0));
+    CE *s_canon = reinterpret_cast<CE *>(lq);
+    uint32_t *s_mask = reinterpret_cast<uint32_t *>(lq + r16(late.nterms * (long long)sizeof(CE)));
+    CE *s_rank = reinterpret_cast<CE *>(reinterpret_cast<unsigned char *>(s_mask) + r16(late.nwords * 4));
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(s_rank) +
+                                                   r16((late.nwords + 1) * (long long)sizeof(CE)));
+    if (CM == 1 || CM == 2) {
+        const long long words = CM == 2 ? (late.nterms + 1) / 2 : late.nterms;
+        for (long long i = tid; i < late.nterms; i += kExpandThreads) s_canon[i] = canon_g[i];
+        for (long long i = tid; i < late.nwords; i += kExpandThreads) s_mask[i] = late.mask[i];
+        for (long long i = tid; i <= late.nwords; i += kExpandThreads) s_rank[i] = rank_g[i];
         for (long long i = tid; i < words; i += kExpandThreads) s_cnt[i] = 0u;
-        canon = sc;
     }
+    // terminal id of match-entry offset o: its rank among the bitmap's set bits
+    auto terminal_of = [&](uint32_t o) -> uint32_t {
+        const uint32_t w = o >> 5;
+        const uint32_t mw = CM == 3 ? __ldg(late.mask + w) : s_mask[w];
+        const uint32_t rw = uint32_t(CM == 3 ? __ldg(rank_g + w) : s_rank[w]);
+        return rw + __popc(mw & ((1u << (o & 31u)) - 1u));
+    };
     __syncthreads();
 
     const unsigned long long cap = (unsigned long long)occ_cap;
@@ -261,22 +285,26 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
             const uint32_t cnt = min(ent - row, 32u);
             const bool valid = uint32_t(lane) < cnt;   // the valid lanes are 0 .. cnt-1
             uint32_t code = uint32_t(v[u] & kMask);
-            if (LATE && valid) {  // a terminal id: count it, take its pattern code
-                if (!s_cnt) {
+            if (LATE && valid) {  // a match entry: count its terminal, take its pattern code
+                code = terminal_of(code);
+                if (CM == 3) {
                     atomicAdd(&late.ccount[code], 1ull);
-                } else if (late.smem == 1) {
-                    atomicAdd(&s_cnt[code], 1u);
+                    code = uint32_t(__ldg(canon_g + code));
                 } else {
-                    // 16-bit halves: the add that takes a half to 0x8000 moves
-                    // 0x8000 to the workspace counter, so a half never wraps
-                    const uint32_t sh = (code & 1u) << 4;
-                    const uint32_t old = atomicAdd(&s_cnt[code >> 1], 1u << sh);
-                    if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
-                        atomicSub(&s_cnt[code >> 1], 0x8000u << sh);
-                        atomicAdd(&late.ccount[code], 0x8000ull);
+                    if (CM == 1) {
+                        atomicAdd(&s_cnt[code], 1u);
+                    } else {
+                        // 16-bit halves: the add that takes a half to 0x8000 moves
+                        // 0x8000 to the workspace counter, so a half never wraps
+                        const uint32_t sh = (code & 1u) << 4;
+                        const uint32_t old = atomicAdd(&s_cnt[code >> 1], 1u << sh);
+                        if (((old >> sh) & 0xFFFFu) == 0x7FFFu) {
+                            atomicSub(&s_cnt[code >> 1], 0x8000u << sh);
+                            atomicAdd(&late.ccount[code], 0x8000ull);
+                        }
                     }
+                    code = uint32_t(s_canon[code]);
                 }
-                code = uint32_t(canon[code]);
             }
             const unsigned long long key_hi = (unsigned long long)(tile0 + uint32_t(v[u] >> kOffShift)) << 32;
             const bool grp = valid && (code & kGrp);
@@ -292,8 +320,8 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
             uint32_t lo = code, mult = valid ? 1u : 0u;
             if (grp) {
                 const uint32_t g = code & ~kGrp;
-                lo = go[g];
-                mult = go[g + 1] - lo;
+                lo = grp_first(g);
+                mult = grp_first(g + 1) - lo;
             }
             const uint32_t extra = grp ? mult - 1u : 0u;
             uint32_t excl, tot;
@@ -309,7 +337,7 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
             }
             const uint32_t o0 = pos + excl;
             for (uint32_t k = 0; k < mult; ++k) {
-                const uint32_t id = grp ? gid[lo + k] : code;
+                const uint32_t id = grp ? grp_id(lo + k) : code;
                 if (o0 + k < room) out[o0 + k] = key_hi | id;
             }
             pos += tot;
@@ -324,9 +352,9 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
 
     // ---- late ids: counters -> workspace; the last CTA writes counts[r] ----
     __syncthreads();
-    if (s_cnt)
+    if (CM == 1 || CM == 2)
         for (long long c = tid; c < late.nterms; c += kExpandThreads) {
-            const uint32_t v = late.smem == 2 ? (s_cnt[c >> 1] >> ((c & 1) << 4)) & 0xFFFFu : s_cnt[c];
+            const uint32_t v = CM == 2 ? (s_cnt[c >> 1] >> ((c & 1) << 4)) & 0xFFFFu : s_cnt[c];
             if (v) atomicAdd(&late.ccount[c], (unsigned long long)v);
         }
     __threadfence();
@@ -360,7 +388,7 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
 // the tile's slot, so the expand kernel of the DFA scan finishes the list.
 // ---------------------------------------------------------------------------
 template <typename E, bool DNA, bool HYB>
-__global__ void __launch_bounds__(512, 1) pfac_scan_kernel(const AcArgs a)
+__global__ void __launch_bounds__(768, 1) pfac_scan_kernel(const AcArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr uint32_t kGrp = sizeof(E) == 2 ? 0x8000u : 0x80000000u;
@@ -624,6 +652,7 @@ int hv_slot(int hv) { return hv == 1 ? 0 : hv == 2 ? 1 : 2; }
 struct Layout {
     long long smem_entries;
     int warps, hist, ids;
+    int lst;  // the list-mode layout of late ids (multiplicities per match entry only)
 };
 
 long long ac_hist_bytes(int hist, long long nterms)
@@ -636,7 +665,8 @@ long long ac_smem_bytes(const AcTables &t, int eb, const Layout &L, int hv, int 
     const int nwords = int(t.flag_mask.size());
     const int nterms = int(t.canon.size());
     const long long ids = L.ids == 1 ? ac_ids_bytes(nwords, nterms, eb)
-                        : L.ids == 2 ? ac_ids_late_bytes(nwords, nterms, eb) : 0;
+                        : L.ids == 2 ? (L.lst ? ac_emul_bytes(nwords) : ac_ids_late_bytes(nwords, nterms, eb))
+                                     : 0;
     return r16(L.smem_entries * eb) + ids + ac_hist_bytes(L.hist, nterms) + (t.dna ? 0 : 256) +
            (long long)L.warps * ac_warp_bytes(hv, pool_cap, eb);
 }
@@ -652,8 +682,9 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
     const long long budget = (long long)dp.smem_optin - 1024;
     const int pool_cap = 40;
     const int place = opt.placement;
-    // more than 16 warps: the 768-thread kernels of ACGT tables (one CTA per SM)
-    const bool wide_ok = t.dna && !t.goto_only && (opt.ctas_per_sm <= 1);
+    // more than 16 warps: the 768-thread kernels of ACGT tables (one CTA per
+    // SM); the PFAC kernel is one of them
+    const bool wide_ok = t.dna && (opt.ctas_per_sm <= 1);
     const int max_w = wide_ok ? kWideWarps : 16;
     const int forced_warps = opt.warps_per_cta > 0 ? std::min(opt.warps_per_cta, max_w) : 0;
     dev.pool_cap = pool_cap;
@@ -684,31 +715,36 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
         (opt.smem_table_bytes <= 0 || entries * eb <= opt.smem_table_bytes)) {
         // whole table in shared memory; prefer the id structure and the
         // counters there too (32-bit, else 16-bit), then late ids (whose
-        // list mode needs neither canon nor counters there; counts mode
-        // adds the counters that still fit), then the most warps (at least
-        // 12 if possible); pm_params can pin either choice
+        // list mode keeps only the multiplicities there; counts mode adds
+        // the counters that still fit), then the most warps (at least 12 if
+        // possible; PFAC, whose walks hide latency only by having more of
+        // them in flight, the most warps first); pm_params can pin either
+        // choice
         const int ids_hist[7][2] = {{1, 1}, {1, 2}, {2, -1}, {0, 1}, {0, 2}, {1, 0}, {0, 0}};
-        for (int minw : {12, 4}) {
+        for (int minw : {t.goto_only ? max_w : 12, 12, 4}) {
             for (int o = 0; o < 7 && !chosen; ++o) {
                 const int ids = ids_hist[o][0], hist = ids_hist[o][1];
                 if (!ids_ok(ids) || (hist >= 0 && !hist_ok(hist))) continue;
                 const int hi = forced_warps ? forced_warps : max_w;
                 const int lo = forced_warps ? forced_warps : minw;
                 for (int w = hi; w >= lo && !chosen; --w) {
-                    Layout L{entries, w, hist < 0 ? 0 : hist, ids};
+                    Layout L{entries, w, hist < 0 ? 0 : hist, ids, hist < 0 ? 1 : 0};
                     if (!fits(L)) continue;
                     Layout C = L;
                     if (hist < 0) {
-                        // counts mode: the most warps (down to lo) that still
-                        // hold shared counters, else the list layout with
-                        // device counters
+                        // counts mode (id structure in shared memory): the
+                        // most warps (down to lo) that still hold shared
+                        // counters, else device counters
                         bool any = false;
                         for (int wc = w; wc >= lo && !any; --wc)
                             for (int h : {1, 2}) {
-                                Layout D{entries, wc, h, ids};
+                                Layout D{entries, wc, h, ids, 0};
                                 if (hist_ok(h) && fits(D)) { C = D; any = true; break; }
                             }
-                        if (!any && hist_ok(0)) { C.hist = 0; any = true; }
+                        for (int wc = w; wc >= lo && !any && hist_ok(0); --wc) {
+                            Layout D{entries, wc, 0, ids, 0};
+                            if (fits(D)) { C = D; any = true; }
+                        }
                         if (!any) continue;
                     }
                     best = C;
@@ -722,13 +758,17 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
         if (chosen) dev.placement = PM_PLACE_SMEM;
     }
     if (!chosen) {
-        // hybrid / global: breadth-first prefix of rows in shared memory
-        const int w = forced_warps ? forced_warps : 16;
+        // hybrid / global: breadth-first prefix of rows in shared memory;
+        // 16 warps, or 24 for PFAC, whose walks hide latency only by
+        // having more of them in flight
+        const int w = forced_warps ? forced_warps : (t.goto_only && wide_ok) ? kWideWarps : 16;
         // counters / ids only when pinned by pm_params (the table prefix
         // gets the room otherwise)
         Layout L{0, w, opt.counters == 1 ? 1 : opt.counters == 2 ? 2 : 0,
-                 opt.ids_place == 1 ? 1 : (opt.ids_place == 3 && ids_ok(2)) ? 2 : 0};
-        const long long fixed = ac_smem_bytes(t, eb, L, hv, pool_cap);
+                 opt.ids_place == 1 ? 1 : (opt.ids_place == 3 && ids_ok(2)) ? 2 : 0, 0};
+        Layout LL = L;  // list mode: late ids keep no counters and only the multiplicities
+        if (L.ids == 2) { LL.hist = 0; LL.lst = 1; }
+        const long long fixed = std::max(ac_smem_bytes(t, eb, L, hv, pool_cap), ac_smem_bytes(t, eb, LL, hv, pool_cap));
         if (fixed > budget) return PM_ETOOBIG;
         long long room = budget - fixed;
         if (dev.ctas_per_sm > 1)
@@ -739,9 +779,9 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
         se &= ~((long long)(16 / eb) - 1);   // whole 16-byte vectors
         if (se > entries) se = entries;
         L.smem_entries = se;
+        LL.smem_entries = se;
         best = L;
-        list_layout = L;
-        list_layout.hist = L.ids == 2 ? 0 : L.hist;
+        list_layout = LL;
         dev.placement = place == PM_PLACE_GLOBAL ? PM_PLACE_GLOBAL : PM_PLACE_HYBRID;
     }
     dev.warps = best.warps;
@@ -846,6 +886,7 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     a.rank_g = dv.flag_rank;
     a.canon_g = dv.canon;
     a.tmul_g = dv.tmul;
+    a.emul_g = dv.emul;
     a.nwords = int(t.flag_mask.size());
     a.nterms = int(nterms);
     a.grp_off = dv.grp_off;
@@ -894,7 +935,10 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     ExpandLate xl;
     if (late) {
         xl.canon = dv.canon;
+        xl.mask = dv.flag_mask;
+        xl.rank = dv.flag_rank;
         xl.nterms = nterms;
+        xl.nwords = (int64_t)t.flag_mask.size();
         xl.counts = d_counts;
     }
     return expand_launch(d_ws, nsub, nterms, se, dv.grp_off, dv.grp_ids, (int64_t)t.grp_off.size(),
@@ -938,8 +982,9 @@ int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes
     const long long nseg = (nsub + seg_tiles - 1) / seg_tiles;
     // shared memory of the expand kernel: 12 bytes per tile of a segment
     // (above 48 KB only for texts of more than about 3 GB), then, while two
-    // CTAs still fit an SM: with late ids canon and 32-bit (else 16-bit) per-terminal
-    // counters, and the group tables (offsets and ids)
+    // CTAs still fit an SM: with late ids canon, the match bitmap and its
+    // ranks and 32-bit (else 16-bit) per-terminal counters, and the group
+    // tables (offsets and ids)
     unsigned long long *occ = reinterpret_cast<unsigned long long *>(d_occ);
     const long long cap = d_occ ? occ_cap : 0;
     DeviceProps dp;
@@ -952,11 +997,15 @@ int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes
     const bool is_late = late && late->canon;
     if (is_late) {
         la.canon = late->canon;
+        la.mask = late->mask;
+        la.rank = late->rank;
         la.nterms = late->nterms;
+        la.nwords = late->nwords;
         la.ccount = reinterpret_cast<unsigned long long *>(static_cast<char *>(d_ws) + kWsHeader);
         la.counts = reinterpret_cast<long long *>(late->counts);
         la.ws = static_cast<dev::WsHeader *>(d_ws);
-        const long long cb = r16(late->nterms * (se4 ? 2 : 4));
+        const int ceb = se4 ? 2 : 4;
+        const long long cb = r16(late->nterms * ceb) + r16(late->nwords * 4) + r16((late->nwords + 1) * ceb);
         const long long x32 = cb + r16(late->nterms * 4), x16 = cb + r16((late->nterms + 1) / 2 * 4);
         la.smem = esmem + x32 <= per_cta ? 1 : esmem + x16 <= per_cta ? 2 : 0;
         esmem += la.smem == 1 ? x32 : la.smem == 2 ? x16 : 0;
@@ -976,13 +1025,25 @@ int expand_launch(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes
                                                                    occ_base, pos_base, ngo, ngi, la);
         return cudaGetLastError();
     };
-    const uint32_t *s4 = static_cast<const uint32_t *>(P.slots);
-    const unsigned long long *s8 = static_cast<const unsigned long long *>(P.slots);
-    cudaError_t e;
-    if (se4) e = is_late ? go(expand_kernel<uint32_t, 16, 0x8000u, true>, s4)
-                         : go(expand_kernel<uint32_t, 16, 0x8000u, false>, s4);
-    else e = is_late ? go(expand_kernel<unsigned long long, 32, 0x80000000u, true>, s8)
-                     : go(expand_kernel<unsigned long long, 32, 0x80000000u, false>, s8);
+    const int cm = !is_late ? 0 : la.smem == 1 ? 1 : la.smem == 2 ? 2 : 3;
+    // one instance per slot width, counter mode and group-table placement
+    auto pick = [&](auto se_tag) -> cudaError_t {
+        typedef decltype(se_tag) SE;
+        constexpr int sh = sizeof(SE) == 4 ? 16 : 32;
+        constexpr uint32_t grp = sizeof(SE) == 4 ? 0x8000u : 0x80000000u;
+        const SE *sl = static_cast<const SE *>(P.slots);
+        switch (cm * 2 + (grp_smem ? 1 : 0)) {
+            case 0: return go(expand_kernel<SE, sh, grp, 0, false>, sl);
+            case 1: return go(expand_kernel<SE, sh, grp, 0, true>, sl);
+            case 2: return go(expand_kernel<SE, sh, grp, 1, false>, sl);
+            case 3: return go(expand_kernel<SE, sh, grp, 1, true>, sl);
+            case 4: return go(expand_kernel<SE, sh, grp, 2, false>, sl);
+            case 5: return go(expand_kernel<SE, sh, grp, 2, true>, sl);
+            case 6: return go(expand_kernel<SE, sh, grp, 3, false>, sl);
+            default: return go(expand_kernel<SE, sh, grp, 3, true>, sl);
+        }
+    };
+    const cudaError_t e = se4 ? pick(uint32_t(0)) : pick(0ull);
     if (e != cudaSuccess) { set_cuda_error(int(e)); cudaGetLastError(); return PM_ECUDA; }
     return PM_OK;
 }

@@ -93,9 +93,12 @@ def test_pfac_est_sets_and_every_position_matching(est_text_full):
     T = est_text_full[: 32 << 20]
     for d, m in ((1000, 8), (8000, 8), (20000, 16), (8000, 32)):
         _, P = synth.est_case(d, m, text=est_text_full)
-        s = pm.PatternSet.pfac(P)
-        _same(s.scan(T), oracle.dictionary(T, P, threads=THREADS), f"PFAC d={d} m={m}")
-        s.close()
+        want = oracle.dictionary(T, P, threads=THREADS)
+        # the default ACGT plans run 24 warps per CTA; 12 and 20 are pinned
+        for kw in ({},) + (({"warps_per_cta": 12}, {"warps_per_cta": 20}) if d == 8000 else ()):
+            s = pm.PatternSet.pfac(P, kw or None)
+            _same(s.scan(T), want, f"PFAC d={d} m={m} {kw}")
+            s.close()
     A = np.full(300000, ord("A"), np.uint8)
     s = pm.PatternSet.pfac(np.full((3, 8), ord("A"), np.uint8))
     _same(s.scan(A), oracle.dictionary(A, np.full((3, 8), ord("A"), np.uint8)), "PFAC all hits")
@@ -548,6 +551,25 @@ def test_late_ids_large_set_and_hot_terminal():
     s.close()
 
 
+def test_late_ids_large_groups_and_device_id_structure():
+    """Late ids in list mode on a u32 table (more than 32,767 patterns) with
+    groups of four to six equal patterns, whose multiplicity the scan takes
+    from the id structure in device memory; the id structure and counters
+    do not fit the expand CTA's shared memory either, so it looks terminals
+    up in device memory too. List and counts-only against the oracle."""
+    T = synth.est_text(16 << 20, 53).copy()
+    T[2_000_000:2_100_000] = ord("C")
+    P = synth.random_patterns(60000, 8, 53)
+    P = np.concatenate([P, np.full((6, 8), ord("C"), np.uint8), P[:4], P[:4], P[:4]])
+    want = oracle.dictionary(T, P, threads=THREADS)
+    for kw in ({"ids_place": 3}, {"ids_place": 3, "warps_per_cta": 8}):
+        s = _ac(P, **kw)
+        assert s.info()["entry_bytes"] == 4
+        _same(s.scan(T), want, f"{kw}")
+        _same(s.scan(T, counts_only=True), (np.zeros(0, np.uint64), want[1]), f"{kw} counts")
+        s.close()
+
+
 @pytest.mark.parametrize("kw", [{"warps_per_cta": 24}, {"warps_per_cta": 20}, {"warps_per_cta": 17},
                                 {"warps_per_cta": 24, "ids_place": 3}, {"warps_per_cta": 22, "ids_place": 3},
                                 {"ids_place": 3}, {"warps_per_cta": 24, "counters": 2}])
@@ -555,11 +577,12 @@ def test_more_than_16_warps(kw):
     """Plans of more than 16 warps per CTA (the 768-thread kernels of u16
     ACGT tables wholly in shared memory), with late ids too, whose counts
     mode may use fewer warps than list mode: list, counts-only and a short
-    capacity equal the oracle; a run of one letter fills every pool."""
+    capacity equal the oracle; a run of one letter fills every pool, and
+    its pattern is a group of five equal ones."""
     T = synth.est_text(6 << 20, 43).copy()
     T[1_000_000:1_040_000] = ord("A")
     P = synth.mixed_patterns(T, 1500, 9, 43)
-    P = np.concatenate([P, P[:11], np.full((2, 9), ord("A"), np.uint8)])
+    P = np.concatenate([P, P[:11], np.full((5, 9), ord("A"), np.uint8)])
     want = oracle.dictionary(T, P, threads=THREADS)
     s = _ac(P, **kw)
     assert s.info()["placement"] == pm.PM_PLACE_SMEM
