@@ -114,9 +114,11 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
     const bool late_list = LATE && a.late;
     if (late_list) {
         // only the multiplicities; the id structure stays in device memory
-        // for groups of four or more equal patterns
-        ids.mask = a.mask_g;
-        ids.rank = reinterpret_cast<const E *>(a.rank_g);
+        // for groups of four or more equal patterns (ids keeps the places
+        // of its counts-mode layout, unread here, so that its loads stay
+        // shared-memory loads there)
+        ids.mask = reinterpret_cast<const uint32_t *>(p);
+        ids.rank = reinterpret_cast<const E *>(p);
         ids.canon = reinterpret_cast<const E *>(a.canon_g);
         s_emul = reinterpret_cast<uint32_t *>(p);
         p += r16((long long)a.nwords * 8);
@@ -234,7 +236,11 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
     // in device memory names the group of four or more
     auto entry_mult = [&](uint32_t o) -> uint32_t {
         const uint32_t v = (s_emul[o >> 4] >> ((o & 15u) << 1)) & 3u;
-        return v < 3u ? v + 1u : mult_of(uint32_t(ids.canon[ids.terminal(o)]));
+        if (v < 3u) return v + 1u;
+        const uint32_t w = o >> 5;
+        const uint32_t c = uint32_t(__ldg(reinterpret_cast<const E *>(a.rank_g) + w)) +
+                           __popc(__ldg(a.mask_g + w) & ((1u << (o & 31u)) - 1u));
+        return mult_of(uint32_t(__ldg(reinterpret_cast<const E *>(a.canon_g) + c)));
     };
 
     // slot entries: (start offset in the tile, pattern code or terminal id)

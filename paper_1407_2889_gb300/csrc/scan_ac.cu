@@ -105,7 +105,7 @@ __host__ __device__ inline long long ac_emul_bytes(int nwords) { return r16((lon
 // segments' totals (added up by the scan), each tile's offset inside the
 // segment comes from a block scan of the tiles' totals kept in shared
 // memory, and its warps then copy one tile at a time in rows of 32 entries
-// (lane l takes entry l of a row, eight rows loaded together), so slot loads
+// (lane l takes entry l of a row, ten rows loaded together), so slot loads
 // and key stores are both coalesced. A row that names a group of equal
 // patterns takes a warp prefix over the entries' multiplicities instead. The
 // CTA that owns the last tile writes the total.
@@ -231,7 +231,7 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
     __syncthreads();
 
     const unsigned long long cap = (unsigned long long)occ_cap;
-    constexpr int R = 8;  // rows of 32 entries loaded together; lane l takes entry 32 u + l of a row
+    constexpr int R = 10;  // rows of 32 entries loaded together; lane l takes entry 32 u + l of a row
     constexpr uint32_t kMask = (uint32_t)((((SE)1) << kOffShift) - 1);
     // The warp's work items are (tile q, first entry g0) in order; the slot
     // loads of the next item are in flight while the current one is written.
