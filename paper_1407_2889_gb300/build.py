@@ -19,7 +19,8 @@ LIB = os.path.join(BUILD, "libpmscan.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["scan_ac.cu", "scan_ac_wide.cu", "scan_wm.cu", "scan_batch.cu", "scan_acv.cu", "scan_ac2.cu"]
+CU_SOURCES = ["scan_ac.cu", "scan_ac_wide.cu", "scan_ac_wide_counts.cu", "scan_wm.cu", "scan_batch.cu", "scan_acv.cu",
+              "scan_ac2.cu"]
 CPP_SOURCES = ["compile.cpp", "capi.cpp", "serve.cpp"]
 HEADERS = ["pm_internal.h", "scan_common.cuh", "ac_device.cuh", "ac_scan_kernel.cuh"]
 

@@ -1,9 +1,10 @@
 // ac_scan_kernel.cuh -- the plain Aho-Corasick scan kernel (one character
-// per lookup) and its launch arguments, shared by the two translation units
+// per lookup) and its launch arguments, shared by the three translation units
 // that instantiate it: scan_ac.cu (512-thread launch bound, up to 16 warps
-// per CTA and 128 registers) and scan_ac_wide.cu (768 threads, up to 24
-// warps and 85 registers). The work decomposition and the walk are described
-// at the top of scan_ac.cu.
+// per CTA and 128 registers), scan_ac_wide.cu (768 threads, up to 24 warps
+// and 85 registers) and scan_ac_wide_counts.cu (the 768-thread ones for
+// counts-only scans). The work decomposition and the walk are described at
+// the top of scan_ac.cu.
 #pragma once
 
 #include <cstdint>
@@ -59,9 +60,11 @@ struct Variant {
 // HV slot (HV = 1, 2, 4). Wide groups 0-4 are the ACGT groups of the
 // 512-thread table (u16 whole table, u16 hybrid, u16 whole table with index
 // entries, u16 hybrid with index entries, u32 hybrid with index entries),
-// 5-9 their late-ids forms.
+// 5-9 their late-ids forms. kWideCountsVariants (scan_ac_wide_counts.cu)
+// are the same kernels for counts-only scans, which record no step bits.
 constexpr int kWideGroups = 10;
 extern const Variant kWideVariants[kWideGroups * 3];
+extern const Variant kWideCountsVariants[kWideGroups * 3];
 
 namespace {
 
@@ -93,8 +96,10 @@ __device__ __forceinline__ void stage_issue(const AcArgs &a, long long t, uint8_
 }
 
 // MAXT: the launch bound, 512 threads (up to 128 registers) or 768 (up to
-// 85, for whole-table plans of more than 16 warps)
-template <typename E, int NV, int HV, bool DNA, bool HYB, bool PRE, bool LATE, int MAXT>
+// 85, for plans of more than 16 warps). CO: an instance for counts-only
+// scans, whose walk records no step bits (a lane's hit count is its pool
+// counter, and a full pool counts as an overflow).
+template <typename E, int NV, int HV, bool DNA, bool HYB, bool PRE, bool LATE, int MAXT, bool CO = false>
 __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -307,14 +312,18 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
             const uint32_t h = e & 1u;
             if (h) pl[kslot * 32] = E(idx);  // the match-row base is subtracted when resolving
             kslot = min(kslot + h, cap);
-            hw[step >> 5] += h << (step & 31);
+            if (!CO) hw[step >> 5] += h << (step & 31);
         };
         if (DNA) walk_dna<NV, PRE>(tv, steps, a.lut, tab, rec);
         else walk_gen<NV>(tv, steps, a.lw, s_cls, tab, rec);
-        uint32_t nh = 0;  // exact even when the pool overflowed
+        uint32_t nh = 0;  // exact even when the pool overflowed (CO: up to cap)
+        if (CO) {
+            nh = kslot;
+        } else {
 #pragma unroll
-        for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
-        const bool ovf = nh > cap;
+            for (int j = 0; j < HW; ++j) nh += __popc(hw[j]);
+        }
+        const bool ovf = CO ? kslot >= cap : nh > cap;
 
         // ---- resolve: match entry -> terminal -> pattern code ---------------
         // (late ids in list mode: no resolve; the compaction below adds up the
@@ -348,7 +357,7 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
                       });
         }
 
-        if (!a.list) {
+        if (CO || !a.list) {
             my_total += cnt;
             continue;
         }
@@ -363,6 +372,7 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
             // slot values: match-entry offsets (the expand kernel takes the
             // terminal ids, codes and counts from them)
             uint32_t k = 0;
+            bool big = false;  // a group of four or more equal patterns
 #pragma unroll
             for (int j = 0; j < HW; ++j) {
                 uint32_t wj = hw[j];
@@ -370,9 +380,17 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
                     const uint32_t b = uint32_t(__ffs(int(wj))) - 1u;
                     wj &= wj - 1u;
                     const uint32_t o = match_off(pl[k * 32]);
-                    cnt += entry_mult(o);
+                    const uint32_t v = (s_emul[o >> 4] >> ((o & 15u) << 1)) & 3u;
+                    cnt += v + 1u;
+                    big |= v == 3u;
                     dst[k] = ((SE)(off0 + uint32_t(j * 32) + b) << kOffShift) | (SE)o;
                     ++k;
+                }
+            }
+            if (big) {  // rare: those hits' true multiplicities instead of 4
+                for (uint32_t q = 0; q < nh; ++q) {
+                    const uint32_t o = match_off(pl[q * 32]);
+                    if (((s_emul[o >> 4] >> ((o & 15u) << 1)) & 3u) == 3u) cnt += entry_mult(o) - 4u;
                 }
             }
         } else if (late_list) {
@@ -421,7 +439,7 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
     // it is not still writing this CTA's shared memory when the CTA exits
     if (inflight) (void)dev::mbar_wait_bounded(bar, phase);
 
-    if (!a.list) {
+    if (CO || !a.list) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) my_total += __shfl_down_sync(kFull, my_total, o);
         if (lane == 0 && my_total)

@@ -36,7 +36,8 @@
 // GPU-CW).
 //
 // The kernel itself is in ac_scan_kernel.cuh: this file instantiates it with
-// a 512-thread launch bound, scan_ac_wide.cu with 768 threads.
+// a 512-thread launch bound, scan_ac_wide.cu and scan_ac_wide_counts.cu
+// (counts-only scans) with 768 threads.
 #include <cstddef>
 #include <cstdio>
 #include <mutex>
@@ -871,7 +872,8 @@ int ac_enqueue(const AcTables &t, const DevAc &dv, const uint8_t *d_text, int64_
     const int var = list ? dv.variant_list : dv.variant;
     const int warps = list ? dv.warps_list : dv.warps;
     const AcKernel fn = pfac ? pfac_kernel_for(t, dv)
-                             : var >= kWideBase ? kWideVariants[var - kWideBase].fn : kVariants[var].fn;
+                             : var >= kWideBase ? (list ? kWideVariants : kWideCountsVariants)[var - kWideBase].fn
+                                                : kVariants[var].fn;
     const long long smem = list ? dv.smem_bytes_list : dv.smem_bytes;
     rc = kernel_smem_attr(reinterpret_cast<const void *>(fn), smem);
     if (rc) return rc;
