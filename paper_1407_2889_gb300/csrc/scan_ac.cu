@@ -326,9 +326,11 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
             }
             const uint32_t extra = grp ? mult - 1u : 0u;
             uint32_t excl, tot;
+            bool pairs = false;  // every group in the row is a pair
             if (__all_sync(kFull, extra < 4u)) {
                 const uint32_t e0 = __ballot_sync(kFull, extra & 1u);
                 const uint32_t e1 = __ballot_sync(kFull, extra & 2u);
+                pairs = e1 == 0u;
                 excl = uint32_t(lane) + __popc(e0 & lt) + 2u * __popc(e1 & lt);
                 tot = cnt + __popc(e0) + 2u * __popc(e1);
             } else {
@@ -337,9 +339,15 @@ expand_kernel(const SE *__restrict__ slots, const uint32_t *__restrict__ tile_en
                 tot = __shfl_sync(kFull, incl, 31);
             }
             const uint32_t o0 = pos + excl;
-            for (uint32_t k = 0; k < mult; ++k) {
-                const uint32_t id = grp ? grp_id(lo + k) : code;
-                if (o0 + k < room) out[o0 + k] = key_hi | id;
+            if (pairs) {
+                // the first key of every entry, then the second of each pair
+                if (valid && o0 < room) out[o0] = key_hi | (grp ? grp_id(lo) : code);
+                if (extra && o0 + 1u < room) out[o0 + 1u] = key_hi | grp_id(lo + 1u);
+            } else {
+                for (uint32_t k = 0; k < mult; ++k) {
+                    const uint32_t id = grp ? grp_id(lo + k) : code;
+                    if (o0 + k < room) out[o0 + k] = key_hi | id;
+                }
             }
             pos += tot;
         }
