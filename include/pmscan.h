@@ -92,11 +92,13 @@ typedef struct pm_params {
                                  3 64-bit in device memory */
     int32_t ids_place;        /* AC terminal-id structure: 0 auto, 1 shared
                                  memory, 2 device memory (through L1/L2),
-                                 3 late: the rank structure in shared memory,
-                                 and in list mode terminal ids are mapped to
-                                 pattern codes and counted by the expand
-                                 kernel (frees shared memory for the table
-                                 and warps; not for PFAC sets) */
+                                 3 late: in list mode the scan keeps only a
+                                 2-bit multiplicity per match entry, and the
+                                 expand kernel maps match entries to terminal
+                                 ids and pattern codes and counts them (frees
+                                 shared memory for the table and warps);
+                                 counts mode keeps the rank structure there;
+                                 not for PFAC sets */
     int32_t stride;           /* AC characters per table lookup: 0 or 1 one; 2 two
                                  (a 16-entry row per state and character pair,
                                  for ACGT sets of at most 4096 rows and m <= 33;

@@ -223,9 +223,9 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
         return __ldg(a.grp_off + g + 1) - __ldg(a.grp_off + g);
     };
     // what a terminal's hit contributes: its outputs, and the slot value (its
-    // pattern code; with late ids the terminal id itself, whose multiplicity
-    // comes from the 2-bit table, and through canon in device memory only
-    // for groups of four or more equal patterns)
+    // pattern code; in the counts mode of late ids the terminal id itself,
+    // whose multiplicity comes from the 2-bit table, and through canon in
+    // device memory only for groups of four or more equal patterns)
     auto resolve = [&](uint32_t c, uint32_t &mult) -> uint32_t {
         if (LATE) {
             const uint32_t v = (s_tmul[c >> 4] >> ((c & 15u) << 1)) & 3u;
@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(MAXT, 1) ac_scan_kernel(const AcArgs a)
         return mult_of(uint32_t(__ldg(reinterpret_cast<const E *>(a.canon_g) + c)));
     };
 
-    // slot entries: (start offset in the tile, pattern code or terminal id)
+    // slot entries: (start offset in the tile, pattern code or, with late
+    // ids, match-entry offset)
     typedef typename std::conditional<sizeof(E) == 2, uint32_t, unsigned long long>::type SE;
     constexpr int kOffShift = sizeof(E) == 2 ? 16 : 32;
     const long long G = (long long)gridDim.x * (blockDim.x >> 5);

@@ -191,10 +191,12 @@ struct DevAc {
     int64_t smem_entries = 0;       // table entries copied to shared memory
     int32_t warps = 0, ctas_per_sm = 0, pool_cap = 0;
     int32_t hist_smem = 0;          // per-terminal counters in shared memory
-    // 1: rank structure and canon in shared memory; 2 (late ids): rank
-    // structure and 2-bit multiplicities there, canon in device memory, and in list
-    // mode the slots carry terminal ids that the expand kernel maps to
-    // pattern codes and counts (hist_smem then applies to counts mode only)
+    // 1: rank structure and canon in shared memory; 2 (late ids): in counts
+    // mode rank structure and 2-bit multiplicities per terminal there, canon
+    // in device memory; in list mode only 2-bit multiplicities per match
+    // entry there, and the slots carry match-entry offsets that the expand
+    // kernel maps to terminal ids and pattern codes and counts (hist_smem
+    // then applies to counts mode only)
     int32_t ids_smem = 0;
     int32_t nv = 0, hv = 0;         // register text vectors (chunk + halo)
     int32_t variant = 0;            // kernel instance id
@@ -308,10 +310,11 @@ int64_t list_workspace_bytes(int64_t nsub, bool list, int64_t nterms, int slot_e
 void list_workspace_parts(void *d_ws, int64_t nsub, int64_t nterms, int slot_entry_bytes, ListParts &out);
 // slots of 4-byte entries hold (offset << 16) | 16-bit code (group flag
 // 0x8000), 8-byte entries (offset << 32) | 32-bit code (group flag 2^31).
-// With `late` (late ids) the low half is a terminal id instead: the expand
-// kernel maps it through canon (entry-sized: u16 for 4-byte slots), counts
-// it into the workspace's per-terminal counters, and its last CTA writes
-// counts[r] (d entries) from them.
+// With `late` (late ids) the low half is a match-entry offset instead: the
+// expand kernel takes its rank in the match bitmap (the terminal id), maps
+// that through canon (entry-sized: u16 for 4-byte slots), counts it into the
+// workspace's per-terminal counters, and its last CTA writes counts[r] (d
+// entries) from them.
 struct ExpandLate {
     const void *canon = nullptr;
     const uint32_t *mask = nullptr;  // match-entry bitmap and its ranks (type of canon)

@@ -24,7 +24,9 @@
 // canonical id (the rank of its table entry among match entries, from a
 // bitmap with prefix counts) and to the pattern code, and per-terminal
 // counters are bumped; the last CTA turns them into counts[r]. With late ids
-// the scan keeps the terminal id and the expand kernel does the rest.
+// in list mode the scan keeps the match entry's offset and only adds up its
+// outputs (a 2-bit multiplicity per match entry); the expand kernel does the
+// rest.
 //
 // List mode writes the output in two launches, so that no warp ever waits
 // for another: the scan writes each warp tile's matches, in text order, to
