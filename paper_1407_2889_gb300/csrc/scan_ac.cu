@@ -732,10 +732,18 @@ int ac_plan(const AcTables &t, const pm_params &opt, const DeviceProps &dp, DevA
         // them in flight, the most warps first); pm_params can pin either
         // choice
         const int ids_hist[7][2] = {{1, 1}, {1, 2}, {2, -1}, {0, 1}, {0, 2}, {1, 0}, {0, 0}};
-        for (int minw : {t.goto_only ? max_w : 12, 12, 4}) {
+        // A first pass (unless the warps are pinned) wants at least 20
+        // warps with the whole id structure and 32-bit counters, else late
+        // ids: a 768-thread kernel pays for its 80-register cap only from
+        // about 20 warps on (d=8000, m=8: 17 warps with everything shared
+        // ran 562 GB/s in list mode, late ids at 24 warps 784).
+        const int first_minw = forced_warps ? 0 : t.goto_only ? max_w : 20;
+        for (int minw : {first_minw, 12, 4}) {
+            if (minw == 0) continue;
             for (int o = 0; o < 7 && !chosen; ++o) {
                 const int ids = ids_hist[o][0], hist = ids_hist[o][1];
                 if (!ids_ok(ids) || (hist >= 0 && !hist_ok(hist))) continue;
+                if (minw == first_minw && !t.goto_only && o != 0 && o != 2) continue;
                 const int hi = forced_warps ? forced_warps : max_w;
                 const int lo = forced_warps ? forced_warps : minw;
                 for (int w = hi; w >= lo && !chosen; --w) {
