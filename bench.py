@@ -69,8 +69,9 @@ def plan_key(plan) -> dict:
 
 def recorded_traffic(kernel_name: str, workload: str, plan=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source, the same workload and the same launch plan;
-    else None."""
+    the current kernel source, the same workload and the same launch plan
+    (or one the record lists as resolving to the same kernels and launch
+    shapes for this workload); else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -79,7 +80,8 @@ def recorded_traffic(kernel_name: str, workload: str, plan=None):
     e = rec.get(kernel_name)
     if not e or e.get("kernel_hash") != kernel_hash() or e.get("workload") != workload:
         return None
-    if plan_key(e.get("plan")) != plan_key(plan):
+    plans = [e.get("plan")] + list(e.get("same_plans", []))
+    if not any(plan_key(q) == plan_key(plan) for q in plans):
         return None
     return e.get("dram_bytes_per_launch")
 
