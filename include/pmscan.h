@@ -210,6 +210,33 @@ void pm_set_free(pm_set *s);
 int pm_set_get_info(const pm_set *s, pm_set_info *info);
 
 /*
+ * The launch plan the planner picks for an Aho-Corasick or PFAC set on a
+ * device of the given shape: its number of SMs, the most dynamic shared
+ * memory a block may opt in to, and the shared memory per SM (bytes). The
+ * set's own pm_params (placement, warps, counters, ids) apply as at compile
+ * time. No device is touched, so this works for host-only sets
+ * (pm_params.host_only) and without a GPU: for inspecting what the planner
+ * does and testing it. A set compiled for a device runs the plan of that
+ * device's shape (until pm_tune replaces it). PM_EINVAL for other
+ * algorithms or non-positive sizes; PM_ETOOBIG when nothing fits.
+ */
+typedef struct pm_plan_info {
+    int32_t placement;        /* PM_PLACE_SMEM, PM_PLACE_HYBRID or PM_PLACE_GLOBAL */
+    int32_t warps;            /* warps per CTA, counts-only scans */
+    int32_t warps_list;       /* warps per CTA, list mode */
+    int32_t ids_place;        /* terminal-id structure: 1 shared memory,
+                                 2 device memory, 3 late (pm_params.ids_place) */
+    int32_t counters;         /* counts-only scans' per-terminal counters:
+                                 1 32-bit shared, 2 16-bit shared, 3 device */
+    int32_t ctas_per_sm;
+    int64_t smem_rows;        /* table rows held in shared memory */
+    int64_t smem_bytes;       /* dynamic shared memory per CTA, counts only */
+    int64_t smem_bytes_list;  /* the same, list mode */
+} pm_plan_info;
+int pm_plan_for_device(const pm_set *s, int32_t sm_count, int32_t smem_optin, int32_t smem_per_sm,
+                       pm_plan_info *out);
+
+/*
  * Scan T (n bytes) for every occurrence of the set (Section 1 definition).
  * flags: PM_HOST_TEXT or PM_DEVICE_TEXT, optionally | PM_COUNTS_ONLY.
  * Synchronous: returns when *out (host arrays, library-owned) is complete.

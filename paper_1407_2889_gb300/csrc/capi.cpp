@@ -500,6 +500,31 @@ void pm_set_free(pm_set *s)
     delete s;
 }
 
+int pm_plan_for_device(const pm_set *s, int32_t sm_count, int32_t smem_optin, int32_t smem_per_sm,
+                       pm_plan_info *out)
+{
+    if (!s || !out || sm_count <= 0 || smem_optin <= 0 || smem_per_sm <= 0) return PM_EINVAL;
+    if (s->algo != PM_ALGO_AC && s->algo != PM_ALGO_PFAC) return PM_EINVAL;
+    DeviceProps dp;
+    dp.sm_count = sm_count;
+    dp.smem_optin = smem_optin;
+    dp.smem_per_sm = smem_per_sm;
+    DevAc d;
+    const int rc = ac_plan(s->ac, s->params, dp, d);
+    if (rc) return rc;
+    std::memset(out, 0, sizeof(*out));
+    out->placement = d.placement;
+    out->warps = d.warps;
+    out->warps_list = d.warps_list;
+    out->ids_place = d.ids_smem == 1 ? 1 : d.ids_smem == 2 ? 3 : 2;
+    out->counters = d.hist_smem == 1 ? 1 : d.hist_smem == 2 ? 2 : 3;
+    out->ctas_per_sm = d.ctas_per_sm;
+    out->smem_rows = d.smem_entries >> s->ac.lw;
+    out->smem_bytes = d.smem_bytes;
+    out->smem_bytes_list = d.smem_bytes_list;
+    return PM_OK;
+}
+
 int pm_set_get_info(const pm_set *s, pm_set_info *info)
 {
     if (!s || !info) return PM_EINVAL;

@@ -26,7 +26,8 @@ PM_PLACE_AUTO, PM_PLACE_SMEM, PM_PLACE_HYBRID, PM_PLACE_GLOBAL = range(4)
 PM_ALGO_AC, PM_ALGO_WM, PM_ALGO_PFAC, PM_ALGO_ACV, PM_ALGO_WMV = 1, 2, 3, 4, 5
 
 EXPORTED = [
-    "pm_ac_compile", "pm_pfac_compile", "pm_acv_compile", "pm_wm_compile", "pm_wmv_compile", "pm_set_free", "pm_set_get_info", "pm_scan",
+    "pm_ac_compile", "pm_pfac_compile", "pm_acv_compile", "pm_wm_compile", "pm_wmv_compile", "pm_set_free", "pm_set_get_info",
+    "pm_plan_for_device", "pm_scan",
     "pm_scan_to_host", "pm_result_free", "pm_scan_workspace_bytes", "pm_scan_device",
     "pm_scan_device_noalloc", "pm_noalloc_scratch_bytes", "pm_noalloc_scan_status", "pm_scan_status",
     "pm_scan_batch", "pm_batch_prepare", "pm_batch_free", "pm_batch_counts_total",
@@ -44,6 +45,12 @@ class pm_params(ctypes.Structure):
                 ("wm_prefix_len", ctypes.c_int32), ("host_only", ctypes.c_int32),
                 ("counters", ctypes.c_int32), ("ids_place", ctypes.c_int32),
                 ("stride", ctypes.c_int32)]
+
+
+class pm_plan_info(ctypes.Structure):
+    _fields_ = [("placement", ctypes.c_int32), ("warps", ctypes.c_int32), ("warps_list", ctypes.c_int32),
+                ("ids_place", ctypes.c_int32), ("counters", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("smem_rows", ctypes.c_int64), ("smem_bytes", ctypes.c_int64), ("smem_bytes_list", ctypes.c_int64)]
 
 
 class pm_set_info(ctypes.Structure):
@@ -123,6 +130,9 @@ def lib():
         L.pm_set_free.argtypes = [vp]
         L.pm_set_get_info.restype = ctypes.c_int
         L.pm_set_get_info.argtypes = [vp, ctypes.POINTER(pm_set_info)]
+        L.pm_plan_for_device.restype = ctypes.c_int
+        L.pm_plan_for_device.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(pm_plan_info)]
         L.pm_scan.restype = ctypes.c_int
         L.pm_scan.argtypes = [vp, vp, i64, u32, vp, ctypes.POINTER(ctypes.POINTER(pm_result))]
         L.pm_scan_to_host.restype = ctypes.c_int
@@ -320,6 +330,13 @@ def pm_set_get_info(h: int) -> dict:
     info = pm_set_info()
     _check(lib().pm_set_get_info(h, ctypes.byref(info)), "pm_set_get_info")
     return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def pm_plan_for_device(h: int, sm_count: int, smem_optin: int, smem_per_sm: int) -> dict:
+    out = pm_plan_info()
+    _check(lib().pm_plan_for_device(h, sm_count, smem_optin, smem_per_sm, ctypes.byref(out)),
+           "pm_plan_for_device")
+    return {name: getattr(out, name) for name, _ in out._fields_}
 
 
 class _ResultOwner:
@@ -582,6 +599,11 @@ class PatternSet:
 
     def info(self) -> dict:
         return pm_set_get_info(self.h)
+
+    def plan_for(self, sm_count: int, smem_optin: int, smem_per_sm: int) -> dict:
+        """The planner's launch plan for this AC or PFAC set on a device of the
+        given shape (no device needed; works for host-only sets)."""
+        return pm_plan_for_device(self.h, sm_count, smem_optin, smem_per_sm)
 
     def scan(self, T, counts_only: bool = False, stream=None):
         flags = PM_COUNTS_ONLY if counts_only else 0
